@@ -1,0 +1,752 @@
+/*
+ * Plain FP64 CPU oracle for the Gram-based tall-skinny SVD and the
+ * randomized low-rank SVD of Li, Kluger & Tygert, "Randomized algorithms
+ * for distributed computation of PCA and SVD" (arXiv:1612.08709).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA library, and it imports nothing from it.
+ *
+ * Everything is written as the paper states it, step by step, in double
+ * precision, with plain loops (no BLAS).  OpenMP is used only to split
+ * independent rows or columns of a product across threads; it does not
+ * change what is summed, only the order in which per-thread partial sums of
+ * a Gram matrix are added.
+ *
+ * Matrices are row-major with an explicit leading dimension ("ld", in
+ * elements).  Singular vectors are stored as columns: V[i*ldv + j] is entry
+ * i of right singular vector j.
+ *
+ * Readings of the paper this file takes (each also listed in the design
+ * notes of the repository):
+ *  - The small eigenproblems and the small SVD use one-sided (Hestenes)
+ *    cyclic Jacobi with row-cyclic pair order.  A pair (p,q) is rotated when
+ *    |x_p . x_q| > tol * sqrt(|x_p|^2 |x_q|^2), tol = nrows * 2^-53; the
+ *    iteration stops after a sweep with no rotation, or after max_sweeps.
+ *    Results are sorted by decreasing column norm, ties by original index.
+ *  - MaxEntry column scaling (an addition to the paper's method): column j
+ *    of A is divided by d_j, the smallest power of two >= max_i |A_ij|
+ *    (d_j = 1 for a zero column).  It applies to the two-pass algorithm
+ *    only, where the diagonal D is absorbed into R = T W^T S~ V~^T D
+ *    before the final small SVD; the one-pass algorithm ignores it.
+ *  - The discard rule drops every column whose explicit norm is strictly
+ *    less than (largest norm) * drop_tol; the paper's value for drop_tol is
+ *    the square root of the working precision (Remark "working").
+ *  - Sign convention: each right singular vector is flipped so that its
+ *    entry of largest magnitude (lowest index on ties) is positive; the
+ *    matching left singular vector is flipped with it.
+ *  - The low-rank SVD returns the leading k of the l triplets that the
+ *    direct SVD produces; the SVD of B = Q^T A is taken as the two-pass
+ *    tall-skinny SVD of B^T = A^T Q (n x l).
+ *
+ * Pins: see tests/test_oracle_pins.py (brute-force SVD on tiny inputs,
+ * known spectra, the paper's low-rank error values on its DCT test matrix,
+ * orthonormality invariants, closed forms for n = 1, finite differences
+ * for the gradient).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef int64_t i64;
+
+#define OR_OK 0
+#define OR_ENOCONV 1
+#define OR_RANKDEF 2
+#define OR_ENOMEM (-100)
+
+/* ------------------------------------------------------------------ */
+/* Small helpers (plain loops).                                        */
+/* ------------------------------------------------------------------ */
+
+static double *dalloc(i64 n)
+{
+    if (n <= 0) n = 1;
+    return (double *)calloc((size_t)n, sizeof(double));
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* B (n x n, ldb) = A^T A for A (m x n, lda).  Definition of the Gram matrix
+ * (Algorithm 3, first step; Algorithm 4, first and Z = Y^T Y steps). */
+void or_gram(const double *A, i64 m, i64 n, i64 lda, double *B, i64 ldb)
+{
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) B[i * ldb + j] = 0.0;
+    int nt = or_num_threads();
+    /* One partial Gram per thread over a static row partition, summed in
+     * thread order afterwards, so the result is the same on every run with
+     * the same thread count. */
+    double **parts = (double **)calloc((size_t)nt, sizeof(double *));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *P = dalloc(n * n);
+        parts[t] = P;
+#pragma omp for schedule(static)
+        for (i64 k = 0; k < m; k++) {
+            const double *a = A + k * lda;
+            for (i64 i = 0; i < n; i++) {
+                double ai = a[i];
+                double *p = P + i * n;
+                for (i64 j = i; j < n; j++) p[j] += ai * a[j];
+            }
+        }
+    }
+    for (int t = 0; t < nt; t++) {
+        if (!parts[t]) continue;
+        for (i64 i = 0; i < n; i++)
+            for (i64 j = i; j < n; j++) B[i * ldb + j] += parts[t][i * n + j];
+        free(parts[t]);
+    }
+    free(parts);
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < i; j++) B[i * ldb + j] = B[j * ldb + i];
+}
+
+/* C (m x p, ldc) = A (m x n, lda) * X (n x p, ldx). */
+void or_matmul(const double *A, i64 m, i64 n, i64 lda, const double *X,
+               i64 p, i64 ldx, double *C, i64 ldc)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < m; i++) {
+        double *c = C + i * ldc;
+        for (i64 j = 0; j < p; j++) c[j] = 0.0;
+        for (i64 k = 0; k < n; k++) {
+            double a = A[i * lda + k];
+            const double *x = X + k * ldx;
+            for (i64 j = 0; j < p; j++) c[j] += a * x[j];
+        }
+    }
+}
+
+/* C (n x p, ldc) = A^T (A is m x n, lda) * X (m x p, ldx). */
+void or_matmul_tn(const double *A, i64 m, i64 n, i64 lda, const double *X,
+                  i64 p, i64 ldx, double *C, i64 ldc)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < n; i++) {
+        double *c = C + i * ldc;
+        for (i64 j = 0; j < p; j++) c[j] = 0.0;
+        for (i64 k = 0; k < m; k++) {
+            double a = A[k * lda + i];
+            const double *x = X + k * ldx;
+            for (i64 j = 0; j < p; j++) c[j] += a * x[j];
+        }
+    }
+}
+
+/* Euclidean norm of every column (Remark "normalizing"). */
+void or_col_norms(const double *Y, i64 m, i64 n, i64 ldy, double *s)
+{
+    for (i64 j = 0; j < n; j++) {
+        double acc = 0.0;
+        for (i64 i = 0; i < m; i++) acc += Y[i * ldy + j] * Y[i * ldy + j];
+        s[j] = sqrt(acc);
+    }
+}
+
+/* d_j = smallest power of two >= max_i |A_ij|; 1 for a zero column. */
+void or_maxentry_scale(const double *A, i64 m, i64 n, i64 lda, double *d)
+{
+    for (i64 j = 0; j < n; j++) {
+        double mx = 0.0;
+        for (i64 i = 0; i < m; i++) {
+            double v = fabs(A[i * lda + j]);
+            if (v > mx) mx = v;
+        }
+        if (mx == 0.0 || !isfinite(mx)) {
+            d[j] = 1.0;
+        } else {
+            int e;
+            double f = frexp(mx, &e); /* mx = f * 2^e, f in [0.5, 1) */
+            d[j] = (f == 0.5) ? mx : ldexp(1.0, e);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One-sided (Hestenes) cyclic Jacobi.                                  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Orthogonalises the columns of X (nr x nc, ldx) in place by plane
+ * rotations, accumulating the rotations in J (nc x nc, ldj, set to I here):
+ * on return X_in * J = X_out with mutually orthogonal columns.  The
+ * columns of X_out and J are then permuted into order of decreasing norm
+ * (stable), and s[j] = |X_out column j|.  Returns the number of sweeps
+ * taken, or -1 if max_sweeps sweeps all rotated something.
+ *
+ * For a symmetric positive semi-definite X this is an eigendecomposition:
+ * X J = J diag(lambda), so J holds eigenvectors and s the eigenvalues
+ * (Algorithm 3 and 4, eigendecomposition steps).  For a general X it is a
+ * singular value decomposition X = (X_out diag(1/s)) diag(s) J^T
+ * (Algorithm 4, SVD of R).
+ */
+int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
+              double *s, int max_sweeps)
+{
+    const double tol = (double)nr * ldexp(1.0, -53);
+    for (i64 i = 0; i < nc; i++)
+        for (i64 j = 0; j < nc; j++) J[i * ldj + j] = (i == j) ? 1.0 : 0.0;
+
+    int sweeps_done = -1;
+    for (int sweep = 1; sweep <= max_sweeps; sweep++) {
+        i64 rotations = 0;
+        for (i64 p = 0; p < nc - 1; p++) {
+            for (i64 q = p + 1; q < nc; q++) {
+                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                for (i64 i = 0; i < nr; i++) {
+                    double xp = X[i * ldx + p], xq = X[i * ldx + q];
+                    alpha += xp * xp;
+                    beta += xq * xq;
+                    gamma += xp * xq;
+                }
+                if (gamma == 0.0 || !(fabs(gamma) > tol * sqrt(alpha * beta)))
+                    continue;
+                rotations++;
+                /* Rotation angle that annihilates the (p,q) inner product:
+                 * t = tan(theta) is the smaller root of t^2 + 2 zeta t - 1. */
+                double zeta = (beta - alpha) / (2.0 * gamma);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
+                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double sn = c * t;
+                for (i64 i = 0; i < nr; i++) {
+                    double xp = X[i * ldx + p], xq = X[i * ldx + q];
+                    X[i * ldx + p] = c * xp - sn * xq;
+                    X[i * ldx + q] = sn * xp + c * xq;
+                }
+                for (i64 i = 0; i < nc; i++) {
+                    double jp = J[i * ldj + p], jq = J[i * ldj + q];
+                    J[i * ldj + p] = c * jp - sn * jq;
+                    J[i * ldj + q] = sn * jp + c * jq;
+                }
+            }
+        }
+        if (rotations == 0) {
+            sweeps_done = sweep;
+            break;
+        }
+    }
+
+    /* Norms and a stable sort by decreasing norm (insertion sort on an
+     * index array keeps equal norms in original order). */
+    i64 *idx = (i64 *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(i64));
+    double *nrm = dalloc(nc);
+    or_col_norms(X, nr, nc, ldx, nrm);
+    for (i64 j = 0; j < nc; j++) idx[j] = j;
+    for (i64 a = 1; a < nc; a++) {
+        i64 key = idx[a];
+        i64 b = a - 1;
+        while (b >= 0 && nrm[idx[b]] < nrm[key]) {
+            idx[b + 1] = idx[b];
+            b--;
+        }
+        idx[b + 1] = key;
+    }
+    double *tx = dalloc(nr * nc), *tj = dalloc(nc * nc);
+    for (i64 i = 0; i < nr; i++)
+        for (i64 j = 0; j < nc; j++) tx[i * nc + j] = X[i * ldx + idx[j]];
+    for (i64 i = 0; i < nc; i++)
+        for (i64 j = 0; j < nc; j++) tj[i * nc + j] = J[i * ldj + idx[j]];
+    for (i64 i = 0; i < nr; i++)
+        for (i64 j = 0; j < nc; j++) X[i * ldx + j] = tx[i * nc + j];
+    for (i64 i = 0; i < nc; i++)
+        for (i64 j = 0; j < nc; j++) J[i * ldj + j] = tj[i * nc + j];
+    for (i64 j = 0; j < nc; j++) s[j] = nrm[idx[j]];
+    free(idx);
+    free(nrm);
+    free(tx);
+    free(tj);
+    return sweeps_done;
+}
+
+/* Flip V column j (n rows) and U column j (m rows) so that V's entry of
+ * largest magnitude (lowest index on ties) is positive. */
+static void canonical_signs(double *U, i64 m, i64 ldu, double *V, i64 n,
+                            i64 ldv, i64 r)
+{
+    for (i64 j = 0; j < r; j++) {
+        i64 best = 0;
+        double bv = -1.0;
+        for (i64 i = 0; i < n; i++) {
+            double a = fabs(V[i * ldv + j]);
+            if (a > bv) {
+                bv = a;
+                best = i;
+            }
+        }
+        if (V[best * ldv + j] < 0.0) {
+            for (i64 i = 0; i < n; i++) V[i * ldv + j] = -V[i * ldv + j];
+            if (U)
+                for (i64 i = 0; i < m; i++) U[i * ldu + j] = -U[i * ldu + j];
+        }
+    }
+}
+
+/* Number of leading entries of the decreasing sequence s kept by the
+ * discard rule: s_j is dropped when s_j < s_0 * drop_tol (or s_j == 0). */
+static i64 keep_count(const double *s, i64 n, double drop_tol)
+{
+    if (n == 0) return 0;
+    double thr = s[0] * drop_tol;
+    i64 r = 0;
+    for (i64 j = 0; j < n; j++)
+        if (s[j] > 0.0 && !(s[j] < thr)) r = j + 1;
+    return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3: Gram-based TS-SVD, single orthonormalisation.           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A (m x n, lda) -> U (m x n, ldu), S (n), V (n x n, ldv), *rank.
+ * Columns r..n-1 of U and V and entries r..n-1 of S are set to zero.
+ * Returns OR_OK, OR_RANKDEF (r < n), or OR_ENOCONV (Jacobi cap hit).
+ */
+int or_ts_svd1(const double *A, i64 m, i64 n, i64 lda, double drop_tol,
+               int max_sweeps, double *U, i64 ldu, double *S, double *V,
+               i64 ldv, i64 *rank)
+{
+    int status = OR_OK;
+    double *B = dalloc(n * n), *Vt = dalloc(n * n), *lam = dalloc(n);
+    double *Ut = dalloc(m * n), *sig = dalloc(n);
+    /* Form the Gram matrix B = A^T A. */
+    or_gram(A, m, n, lda, B, n);
+    /* Eigendecomposition B = V D V^T. */
+    if (or_jacobi(B, n, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
+    /* U~ = A V. */
+    or_matmul(A, m, n, lda, Vt, n, n, Ut, n);
+    /* Sigma = Euclidean norms of the columns of U~. */
+    or_col_norms(Ut, m, n, n, sig);
+    /* The eigenvalue order fixes the column order; the explicit norms can
+     * deviate from it only at rounding level, so the kept set is the
+     * leading columns whose norms pass the rule against the largest norm. */
+    double smax = 0.0;
+    for (i64 j = 0; j < n; j++)
+        if (sig[j] > smax) smax = sig[j];
+    i64 r = 0;
+    for (i64 j = 0; j < n; j++)
+        if (sig[j] > 0.0 && !(sig[j] < smax * drop_tol)) r = j + 1;
+    /* U = U~ Sigma^{-1}; discarded columns are zeroed. */
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++)
+            U[i * ldu + j] = (j < r) ? Ut[i * n + j] / sig[j] : 0.0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) V[i * ldv + j] = (j < r) ? Vt[i * n + j] : 0.0;
+    for (i64 j = 0; j < n; j++) S[j] = (j < r) ? sig[j] : 0.0;
+    canonical_signs(U, m, ldu, V, n, ldv, r);
+    *rank = r;
+    if (status == OR_OK && r < n) status = OR_RANKDEF;
+    free(B);
+    free(Vt);
+    free(lam);
+    free(Ut);
+    free(sig);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 4: Gram-based TS-SVD, double orthonormalisation.           */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Same interface as or_ts_svd1, plus `scale` (MaxEntry column scaling).
+ * Also returns, when `diag` is non-NULL, diag[0] = first-pass rank r,
+ * diag[1] = second-pass rank r', diag[2..] unused.
+ */
+int or_ts_svd2(const double *A, i64 m, i64 n, i64 lda, int scale,
+               double drop_tol, int max_sweeps, double *U, i64 ldu, double *S,
+               double *V, i64 ldv, i64 *rank, i64 *diag)
+{
+    int status = OR_OK;
+    double *d = dalloc(n);
+    double *As = dalloc(m * n);
+    double *B = dalloc(n * n), *Vt = dalloc(n * n), *lam = dalloc(n);
+    double *Yt = dalloc(m * n), *sigt = dalloc(n);
+
+    /* Optional MaxEntry scaling: work on A D^{-1}. */
+    if (scale)
+        or_maxentry_scale(A, m, n, lda, d);
+    else
+        for (i64 j = 0; j < n; j++) d[j] = 1.0;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) As[i * n + j] = A[i * lda + j] / d[j];
+
+    /* B = A^T A. */
+    or_gram(As, m, n, n, B, n);
+    /* B = V~ D~ V~^T. */
+    if (or_jacobi(B, n, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
+    /* Y~ = A V~. */
+    or_matmul(As, m, n, n, Vt, n, n, Yt, n);
+    /* Sigma~ = column norms of Y~. */
+    or_col_norms(Yt, m, n, n, sigt);
+    double smax = 0.0;
+    for (i64 j = 0; j < n; j++)
+        if (sigt[j] > smax) smax = sigt[j];
+    /* Discard: columns whose norm is below max * drop_tol. */
+    i64 r = 0;
+    for (i64 j = 0; j < n; j++)
+        if (sigt[j] > 0.0 && !(sigt[j] < smax * drop_tol)) r = j + 1;
+
+    /* Y = Y~ Sigma~^{-1} (m x r). */
+    double *Y = dalloc(m * r);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < r; j++) Y[i * r + j] = Yt[i * n + j] / sigt[j];
+
+    /* Z = Y^T Y; Z = W D W^T. */
+    double *Z = dalloc(r * r), *W = dalloc(r * r), *mu = dalloc(r);
+    or_gram(Y, m, r, r, Z, r);
+    if (or_jacobi(Z, r, r, r, W, r, mu, max_sweeps) < 0) status = OR_ENOCONV;
+    /* Q~ = Y W; T = column norms of Q~. */
+    double *Qt = dalloc(m * r), *T = dalloc(r);
+    or_matmul(Y, m, r, r, W, r, r, Qt, r);
+    or_col_norms(Qt, m, r, r, T);
+    double tmax = 0.0;
+    for (i64 j = 0; j < r; j++)
+        if (T[j] > tmax) tmax = T[j];
+    i64 r2 = 0;
+    for (i64 j = 0; j < r; j++)
+        if (T[j] > 0.0 && !(T[j] < tmax * drop_tol)) r2 = j + 1;
+
+    /* Q = Q~ T^{-1} (m x r2). */
+    double *Q = dalloc(m * r2);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < r2; j++) Q[i * r2 + j] = Qt[i * r + j] / T[j];
+
+    /* R = T W^T Sigma~ V~^T (r2 x n), with D folded in: R = ... V~^T D. */
+    double *R = dalloc(r2 * n);
+    for (i64 a = 0; a < r2; a++)
+        for (i64 c = 0; c < n; c++) {
+            double acc = 0.0;
+            for (i64 b = 0; b < r; b++)
+                acc += W[b * r + a] * sigt[b] * Vt[c * n + b];
+            R[a * n + c] = T[a] * acc * d[c];
+        }
+
+    /* SVD R = P Sigma V^T via one-sided Jacobi on R^T (n x r2):
+     * R^T P = X with orthogonal columns, Sigma = column norms, V = X/Sigma. */
+    double *Rt = dalloc(n * r2), *P = dalloc(r2 * r2), *sg = dalloc(r2);
+    for (i64 a = 0; a < r2; a++)
+        for (i64 c = 0; c < n; c++) Rt[c * r2 + a] = R[a * n + c];
+    if (or_jacobi(Rt, n, r2, r2, P, r2, sg, max_sweeps) < 0) status = OR_ENOCONV;
+
+    /* U = Q P (m x r2). */
+    double *Uq = dalloc(m * r2);
+    or_matmul(Q, m, r2, r2, P, r2, r2, Uq, r2);
+
+    i64 rk = 0;
+    for (i64 j = 0; j < r2; j++)
+        if (sg[j] > 0.0) rk = j + 1;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) U[i * ldu + j] = (j < rk) ? Uq[i * r2 + j] : 0.0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++)
+            V[i * ldv + j] = (j < rk) ? Rt[i * r2 + j] / sg[j] : 0.0;
+    for (i64 j = 0; j < n; j++) S[j] = (j < rk) ? sg[j] : 0.0;
+    canonical_signs(U, m, ldu, V, n, ldv, rk);
+    *rank = rk;
+    if (diag) {
+        diag[0] = r;
+        diag[1] = r2;
+    }
+    if (status == OR_OK && rk < n) status = OR_RANKDEF;
+
+    free(d); free(As); free(B); free(Vt); free(lam); free(Yt); free(sigt);
+    free(Y); free(Z); free(W); free(mu); free(Qt); free(T); free(Q); free(R);
+    free(Rt); free(P); free(sg); free(Uq);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithms 5, 6 and 8: randomized low-rank SVD (Gram flavour).       */
+/* ------------------------------------------------------------------ */
+
+/* Orthonormal basis of the range of Y (rows x cols) by the one- or
+ * two-pass TS-SVD; returns the basis width and writes it to Qout
+ * (rows x cols, leading width columns). */
+static i64 ts_basis(const double *Y, i64 rows, i64 cols, int passes,
+                    double drop_tol, int max_sweeps, double *Qout, int *st)
+{
+    double *S = dalloc(cols), *V = dalloc(cols * cols);
+    i64 r = 0;
+    int s;
+    if (passes == 1)
+        s = or_ts_svd1(Y, rows, cols, cols, drop_tol, max_sweeps, Qout, cols,
+                       S, V, cols, &r);
+    else
+        s = or_ts_svd2(Y, rows, cols, cols, 0, drop_tol, max_sweeps, Qout,
+                       cols, S, V, cols, &r, NULL);
+    if (s == OR_ENOCONV) *st = OR_ENOCONV;
+    free(S);
+    free(V);
+    return r;
+}
+
+/*
+ * Algorithm 8 = Algorithm 6 fed by Algorithm 5, with Algorithm 3 for the
+ * power steps and Algorithm 4 for the last step and for the SVD of B.
+ * A (m x n, lda); Omega (n x l, row-major, ld = l) is the starting matrix
+ * Q~_0 (i.i.d. Gaussian, supplied by the caller).  Outputs: U (m x k, ldu),
+ * S (k), V (n x k, ldv), *rank = number of nonzero triplets returned.
+ * If `ranks` is non-NULL it receives the basis widths of every step in
+ * order: [Q_1, Q~_1, ..., Q_i, Q~_i, Q, direct-SVD rank] (2*iters + 2).
+ */
+int or_lowrank_svd(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l,
+                   int iters, const double *Omega, double drop_tol,
+                   int max_sweeps, double *U, i64 ldu, double *S, double *V,
+                   i64 ldv, i64 *rank, i64 *ranks)
+{
+    int st = OR_OK;
+    i64 w = l; /* current basis width */
+    double *Qtil = dalloc(n * l), *Q = dalloc(m * l);
+    double *Y = dalloc(m * l), *Yt = dalloc(n * l), *tmp;
+    i64 ri = 0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < l; j++) Qtil[i * l + j] = Omega[i * l + j];
+
+    for (int it = 0; it < iters; it++) {
+        /* Y_j = A Q~_{j-1}. */
+        or_matmul(A, m, n, lda, Qtil, w, w, Y, w);
+        /* Y_j = Q_j R_j by Algorithm 3. */
+        tmp = dalloc(m * w);
+        i64 w1 = ts_basis(Y, m, w, 1, drop_tol, max_sweeps, tmp, &st);
+        for (i64 i = 0; i < m; i++)
+            for (i64 j = 0; j < w1; j++) Q[i * w1 + j] = tmp[i * w + j];
+        free(tmp);
+        if (ranks) ranks[ri++] = w1;
+        /* Y~_j = A^T Q_j. */
+        or_matmul_tn(A, m, n, lda, Q, w1, w1, Yt, w1);
+        /* Y~_j = Q~_j R~_j by Algorithm 3. */
+        tmp = dalloc(n * w1);
+        i64 w2 = ts_basis(Yt, n, w1, 1, drop_tol, max_sweeps, tmp, &st);
+        for (i64 i = 0; i < n; i++)
+            for (i64 j = 0; j < w2; j++) Qtil[i * w2 + j] = tmp[i * w1 + j];
+        free(tmp);
+        if (ranks) ranks[ri++] = w2;
+        w = w2;
+    }
+    /* Y = A Q~_i; Y = Q R by Algorithm 4. */
+    or_matmul(A, m, n, lda, Qtil, w, w, Y, w);
+    tmp = dalloc(m * w);
+    i64 wq = ts_basis(Y, m, w, 2, drop_tol, max_sweeps, tmp, &st);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < wq; j++) Q[i * wq + j] = tmp[i * w + j];
+    free(tmp);
+    if (ranks) ranks[ri++] = wq;
+
+    /* Algorithm 6: B = Q^T A, taken as B^T = A^T Q (n x wq); its two-pass
+     * TS-SVD B^T = U1 S V1^T gives B = V1 S U1^T, so U~ = V1, V = U1. */
+    double *Bt = dalloc(n * wq), *U1 = dalloc(n * wq), *S1 = dalloc(wq),
+           *V1 = dalloc(wq * wq);
+    or_matmul_tn(A, m, n, lda, Q, wq, wq, Bt, wq);
+    i64 rb = 0;
+    int s2 = or_ts_svd2(Bt, n, wq, wq, 0, drop_tol, max_sweeps, U1, wq, S1, V1,
+                        wq, &rb, NULL);
+    if (s2 == OR_ENOCONV) st = OR_ENOCONV;
+    if (ranks) ranks[ri++] = rb;
+    /* U = Q U~ = Q V1 (m x wq). */
+    double *Uf = dalloc(m * wq);
+    or_matmul(Q, m, wq, wq, V1, wq, wq, Uf, wq);
+
+    i64 kk = k < rb ? k : rb;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < k; j++) U[i * ldu + j] = (j < kk) ? Uf[i * wq + j] : 0.0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < k; j++) V[i * ldv + j] = (j < kk) ? U1[i * wq + j] : 0.0;
+    for (i64 j = 0; j < k; j++) S[j] = (j < kk) ? S1[j] : 0.0;
+    canonical_signs(U, m, ldu, V, n, ldv, kk);
+    *rank = kk;
+    if (st == OR_OK && kk < k) st = OR_RANKDEF;
+
+    free(Qtil); free(Q); free(Y); free(Yt); free(Bt); free(U1); free(S1);
+    free(V1); free(Uf);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* Thin-SVD adjoint.                                                    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Gradient of a loss L(U, S, V) through the thin SVD A = U diag(S) V^T of a
+ * full-column-rank A (m x n, m >= n, distinct singular values), given
+ * dU = dL/dU (m x n), dS = dL/dS (n), dV = dL/dV (n x n).  This is the
+ * standard adjoint of the thin SVD (Townsend 2016; Giles 2008), written
+ * out term by term:
+ *   F_ij = 1/(s_j^2 - s_i^2) for i != j, 0 on the diagonal,
+ *   J = U^T dU, K = V^T dV,
+ *   dA = U [ (F o (J - J^T)) S + diag(dS) + S (F o (K - K^T)) ] V^T
+ *        + (I - U U^T) dU S^{-1} V^T
+ * (the term U S^{-1} dV^T (I - V V^T) vanishes because V is square).
+ * U is recomputed as A V S^{-1}, as the forward pass would return it.
+ */
+void or_ts_svd_backward(const double *A, i64 m, i64 n, i64 lda,
+                        const double *S, const double *V, i64 ldv,
+                        const double *dU, i64 lddu, const double *dS,
+                        const double *dV, i64 lddv, double *dA, i64 ldda)
+{
+    double *U = dalloc(m * n), *J = dalloc(n * n), *K = dalloc(n * n);
+    double *M = dalloc(n * n), *Vc = dalloc(n * n), *dVc = dalloc(n * n);
+    double *dUc = dalloc(m * n);
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) {
+            Vc[i * n + j] = V[i * ldv + j];
+            dVc[i * n + j] = dV ? dV[i * lddv + j] : 0.0;
+        }
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) dUc[i * n + j] = dU ? dU[i * lddu + j] : 0.0;
+    /* U = A V S^{-1}. */
+    or_matmul(A, m, n, lda, Vc, n, n, U, n);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) U[i * n + j] /= S[j];
+    /* J = U^T dU, K = V^T dV. */
+    or_matmul_tn(U, m, n, n, dUc, n, n, J, n);
+    or_matmul_tn(Vc, n, n, n, dVc, n, n, K, n);
+    /* Inner n x n matrix M (before the -J S^{-1} projection term). */
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) {
+            double v = 0.0;
+            if (i != j) {
+                double F = 1.0 / (S[j] * S[j] - S[i] * S[i]);
+                v += F * (J[i * n + j] - J[j * n + i]) * S[j];
+                v += S[i] * F * (K[i * n + j] - K[j * n + i]);
+            } else {
+                v += dS ? dS[i] : 0.0;
+            }
+            /* (I - U U^T) dU S^{-1} V^T = dU S^{-1} V^T - U (J S^{-1}) V^T */
+            v -= J[i * n + j] / S[j];
+            M[i * n + j] = v;
+        }
+    /* dA = U (M V^T) + dU (S^{-1} V^T). */
+    double *MVt = dalloc(n * n), *SVt = dalloc(n * n);
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) {
+            double acc = 0.0;
+            for (i64 b = 0; b < n; b++) acc += M[i * n + b] * Vc[j * n + b];
+            MVt[i * n + j] = acc;
+            SVt[i * n + j] = Vc[j * n + i] / S[i];
+        }
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < m; i++) {
+        for (i64 j = 0; j < n; j++) {
+            double acc = 0.0;
+            for (i64 b = 0; b < n; b++)
+                acc += U[i * n + b] * MVt[b * n + j] + dUc[i * n + b] * SVt[b * n + j];
+            dA[i * ldda + j] = acc;
+        }
+    }
+    free(U); free(J); free(K); free(M); free(Vc); free(dVc); free(dUc);
+    free(MVt); free(SVt);
+}
+
+/* ------------------------------------------------------------------ */
+/* Error metrics (Table "heads").                                       */
+/* ------------------------------------------------------------------ */
+
+/* MaxEntry(|U^T U - I|) over the first r columns of U (m x r, ldu). */
+double or_orth_error(const double *U, i64 m, i64 r, i64 ldu)
+{
+    double *G = dalloc(r * r);
+    or_gram(U, m, r, ldu, G, r);
+    double e = 0.0;
+    for (i64 i = 0; i < r; i++)
+        for (i64 j = 0; j < r; j++) {
+            double v = fabs(G[i * r + j] - (i == j ? 1.0 : 0.0));
+            if (v > e) e = v;
+        }
+    free(G);
+    return e;
+}
+
+/* Simple splitmix64 stream for the power method's starting vector. */
+static uint64_t sm64(uint64_t *s)
+{
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/*
+ * Spectral norm of E = A - U diag(S) V^T (A m x n; U m x r; V n x r) by
+ * `iters` steps of the power method on E^T E, from a seeded start, without
+ * forming E (the paper uses 20 steps for its tables).
+ */
+double or_spectral_error(const double *A, i64 m, i64 n, i64 lda,
+                         const double *U, i64 ldu, const double *S,
+                         const double *V, i64 ldv, i64 r, int iters,
+                         uint64_t seed)
+{
+    double *x = dalloc(n), *y = dalloc(m), *t = dalloc(r);
+    uint64_t st = seed;
+    for (i64 i = 0; i < n; i++)
+        x[i] = (double)(sm64(&st) >> 11) * ldexp(1.0, -53) - 0.5;
+    double est = 0.0;
+    for (int it = 0; it < iters; it++) {
+        double nx = 0.0;
+        for (i64 i = 0; i < n; i++) nx += x[i] * x[i];
+        nx = sqrt(nx);
+        if (nx == 0.0) return 0.0;
+        for (i64 i = 0; i < n; i++) x[i] /= nx;
+        /* y = E x = A x - U (S (V^T x)) */
+        for (i64 j = 0; j < r; j++) {
+            double acc = 0.0;
+            for (i64 i = 0; i < n; i++) acc += V[i * ldv + j] * x[i];
+            t[j] = S[j] * acc;
+        }
+#pragma omp parallel for schedule(static)
+        for (i64 i = 0; i < m; i++) {
+            double acc = 0.0;
+            for (i64 j = 0; j < n; j++) acc += A[i * lda + j] * x[j];
+            for (i64 j = 0; j < r; j++) acc -= U[i * ldu + j] * t[j];
+            y[i] = acc;
+        }
+        double ny = 0.0;
+        for (i64 i = 0; i < m; i++) ny += y[i] * y[i];
+        est = sqrt(ny);
+        /* x = E^T y = A^T y - V (S (U^T y)) */
+        for (i64 j = 0; j < r; j++) {
+            double acc = 0.0;
+            for (i64 i = 0; i < m; i++) acc += U[i * ldu + j] * y[i];
+            t[j] = S[j] * acc;
+        }
+#pragma omp parallel for schedule(static)
+        for (i64 i = 0; i < n; i++) {
+            double acc = 0.0;
+            for (i64 k = 0; k < m; k++) acc += A[k * lda + i] * y[k];
+            for (i64 j = 0; j < r; j++) acc -= V[i * ldv + j] * t[j];
+            x[i] = acc;
+        }
+    }
+    free(x);
+    free(y);
+    free(t);
+    return est;
+}

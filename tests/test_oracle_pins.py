@@ -1,0 +1,369 @@
+"""Pins for the FP64 CPU oracle, against things other than the oracle itself:
+numpy/LAPACK SVD on tiny inputs (brute force), matrices with a known
+spectrum, closed forms, the values the paper prints for its own test
+matrix, invariants, and finite differences for the gradient.
+
+Each test names the passage of the paper it pins.  All run on the CPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_pins.txt")
+
+
+def paper_pins():
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, val = line.split()[:2]
+            out[name] = float(val)
+    return out
+
+
+def match_columns_up_to_sign(X, Y):
+    """max over columns of min(|x - y|, |x + y|) (entrywise max)."""
+    err = 0.0
+    for j in range(X.shape[1]):
+        e = min(np.abs(X[:, j] - Y[:, j]).max(), np.abs(X[:, j] + Y[:, j]).max())
+        err = max(err, e)
+    return err
+
+
+# --------------------------------------------------------------------------
+# Building blocks
+# --------------------------------------------------------------------------
+
+
+def test_gram_and_products_brute_force(orc):
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((37, 9))
+    X = rng.standard_normal((9, 5))
+    Y = rng.standard_normal((37, 4))
+    assert np.abs(orc.gram(A) - A.T @ A).max() < 1e-12
+    assert np.abs(orc.matmul(A, X) - A @ X).max() < 1e-12
+    assert np.abs(orc.matmul_tn(A, Y) - A.T @ Y).max() < 1e-12
+    assert np.abs(orc.col_norms(A) - np.linalg.norm(A, axis=0)).max() < 1e-13
+
+
+def test_maxentry_scale_is_power_of_two_bound(orc):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((50, 6)) * np.array([1e-6, 1.0, 3.0, 1e6, 0.0, 1.0])
+    A[0, 5] = 4.0  # exact power of two as the column max
+    A[1:, 5] = 0.5
+    d = orc.maxentry_scale(A)
+    mx = np.abs(A).max(axis=0)
+    for j in range(6):
+        if mx[j] == 0:
+            assert d[j] == 1.0
+            continue
+        m_, e = np.frexp(d[j])
+        assert m_ == 0.5, "d_j must be a power of two"
+        assert mx[j] <= d[j] < 2 * mx[j]
+    assert d[5] == 4.0
+
+
+def test_jacobi_svd_matches_lapack(orc):
+    """One-sided Jacobi as an SVD of a general small matrix (used for the
+    final small SVD of R in Algorithm 4)."""
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((30, 10))
+    Xo, J, s, sweeps = orc.jacobi(X)
+    assert sweeps > 0
+    s_ref = np.linalg.svd(X, compute_uv=False)
+    assert np.abs(s - s_ref).max() < 1e-13 * s_ref[0]
+    assert np.abs(J.T @ J - np.eye(10)).max() < 1e-14
+    assert np.abs(X @ J - Xo).max() < 1e-13
+    Uj = Xo / s
+    Ur, _, Vrt = np.linalg.svd(X, full_matrices=False)
+    assert match_columns_up_to_sign(Uj, Ur) < 1e-12
+    assert match_columns_up_to_sign(J, Vrt.T) < 1e-12
+
+
+def test_jacobi_symmetric_eig_matches_lapack(orc):
+    """One-sided Jacobi on a symmetric positive-definite matrix gives its
+    eigendecomposition (Algorithm 3/4 eigendecomposition steps)."""
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal((40, 12))
+    B = G.T @ G
+    _, J, lam, _ = orc.jacobi(B)
+    w, Q = np.linalg.eigh(B)
+    w, Q = w[::-1], Q[:, ::-1]
+    assert np.abs(lam - w).max() < 1e-12 * w[0]
+    assert match_columns_up_to_sign(J, Q) < 1e-11
+    # eigen-equation
+    assert np.abs(B @ J - J * lam).max() < 1e-11 * w[0]
+
+
+def test_jacobi_sweep_cap_reports_nonconvergence(orc):
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((20, 12))
+    _, _, _, sweeps = orc.jacobi(X, max_sweeps=1)
+    assert sweeps == -1
+
+
+# --------------------------------------------------------------------------
+# Algorithms 3 and 4: brute force on tiny inputs
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("m,n,seed", [(40, 1, 0), (50, 7, 1), (200, 20, 2), (20, 20, 3)])
+@pytest.mark.parametrize("passes,scale", [(1, False), (2, False), (2, True)])
+def test_ts_svd_brute_force(orc, m, n, seed, passes, scale):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) * rng.uniform(0.1, 10.0, size=n)
+    U, S, V, r, st = orc.ts_svd(A, passes=passes, scale=scale, drop_tol=0.0)
+    assert st == 0 and r == n
+    Ur, Sr, Vrt = np.linalg.svd(A, full_matrices=False)
+    assert np.abs(S - Sr).max() <= 1e-12 * Sr[0]
+    assert match_columns_up_to_sign(V, Vrt.T) < 1e-9 * Sr[0] / Sr[-1]
+    assert match_columns_up_to_sign(U, Ur) < 1e-9 * Sr[0] / Sr[-1]
+    assert np.abs(A @ V - U * S).max() < 1e-12 * Sr[0]
+    tolo = 1e-14 if passes == 2 else 1e-10
+    assert orc.orth_error(U) < tolo * n
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+
+
+def test_ts_svd_sign_convention(orc):
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((60, 8))
+    U, S, V, r, st = orc.ts_svd(A)
+    for j in range(r):
+        i = int(np.argmax(np.abs(V[:, j])))
+        assert V[i, j] > 0
+
+
+# --------------------------------------------------------------------------
+# Known spectra and closed forms
+# --------------------------------------------------------------------------
+
+
+def test_ts_svd_known_spectrum_small_tall(orc):
+    """A = U diag(sigma) V^T, sigma from 1 to 1e-6 (the 20000 x 50 workload
+    at a smaller m): the two-pass algorithm recovers sigma, U and V."""
+    m, n = 3000, 50
+    s = workloads.sigma_small_tall(n)
+    A, U0, s0, V0 = workloads.known_spectrum(m, n, s, seed=1)
+    U, S, V, r, st = orc.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+    assert r == n
+    assert np.abs(S - s0).max() < 1e-13
+    assert orc.orth_error(U) < 1e-13
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+    # singular vectors: accurate to eps * sigma_1 / gap
+    assert match_columns_up_to_sign(V, V0) < 1e-8
+    assert match_columns_up_to_sign(U, U0) < 1e-8
+
+
+def test_ts_svd_n_equals_one(orc):
+    rng = np.random.default_rng(7)
+    a = rng.standard_normal((100, 1))
+    for passes in (1, 2):
+        U, S, V, r, st = orc.ts_svd(a, passes=passes, drop_tol=0.0)
+        nrm = np.linalg.norm(a)
+        assert abs(S[0] - nrm) < 1e-14 * nrm
+        assert V[0, 0] == 1.0
+        assert np.abs(U[:, 0] - a[:, 0] / nrm).max() < 1e-15
+
+
+def test_ts_svd_orthonormal_input(orc):
+    Q = workloads.orthonormal(300, 16, np.random.default_rng(8))
+    U, S, V, r, st = orc.ts_svd(Q, drop_tol=0.0)
+    assert np.abs(S - 1.0).max() < 1e-14
+
+
+def test_ts_svd_diagonal_block(orc):
+    d = np.array([3.0, -7.0, 0.5, 2.0, 11.0])
+    A = np.zeros((40, 5))
+    A[:5, :5] = np.diag(d)
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    assert np.abs(S - np.sort(np.abs(d))[::-1]).max() < 1e-14
+
+
+def test_ts_svd_rank_deficient_zero_column(orc):
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((80, 6))
+    A[:, 2] = 0.0
+    U, S, V, r, st = orc.ts_svd(A)
+    assert r == 5 and st == 2
+    assert S[5] == 0.0
+    assert np.abs(U[:, 5]).max() == 0.0
+    Sr = np.linalg.svd(A, compute_uv=False)
+    assert np.abs(S[:5] - Sr[:5]).max() < 1e-13 * Sr[0]
+
+
+def test_maxentry_scaling_rescues_badly_scaled_columns(orc):
+    """With column scales spanning 1e-6..1e6, the scaled two-pass result
+    still matches LAPACK, and V, U stay orthonormal."""
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((400, 10)) * np.logspace(-6, 6, 10)
+    U, S, V, r, st = orc.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+    Sr = np.linalg.svd(A, compute_uv=False)
+    assert np.abs(S - Sr).max() < 1e-12 * Sr[0]
+    assert orc.orth_error(U) < 1e-13
+    assert np.abs(V.T @ V - np.eye(10)).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# The paper's printed values (DCT test matrix)
+# --------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("l,pin,seed", [(20, "alg8_l20_i2_spectral_err", 4),
+                                        (10, "alg8_l10_i2_spectral_err", 5)])
+def test_lowrank_paper_values(orc, l, pin, seed):
+    """Algorithm 8 with i = 2 on the paper's DCT matrix with the spectrum of
+    eq. testSl: the spectral error equals the paper's printed value
+    (sigma_7 for l = 20, sigma_4 for l = 10) regardless of m and n."""
+    pins = paper_pins()
+    m, n = 1500, 400
+    A, U0, s0, V0 = workloads.paper_dct_matrix(m, n, l)
+    Om = workloads.gaussian(n, l, seed)
+    U, S, V, r, st = orc.lowrank_svd(A, l, l, 2, Om)
+    err = orc.spectral_error(A, U[:, :r], S[:r], V[:, :r])
+    assert abs(err - pins[pin]) < 0.006 * pins[pin]
+    assert abs(err - s0[r]) < 1e-6 * s0[r]
+    # the paper prints MaxEntry(|U*U - I|) between 2.9e-16 and 3.8e-15
+    assert orc.orth_error(U[:, :r]) < 1e-13
+    assert orc.orth_error(V[:, :r]) < 1e-13
+
+
+def test_tall_skinny_single_vs_double_orthonormalisation(orc):
+    """Tables tab1234*: on the paper's DCT matrix, Algorithm 3 leaves U
+    orthonormal only to ~1e-4 while Algorithm 4 reaches ~1e-14; both have
+    spectral error equal to the first discarded sigma (the paper's 9.92e-08
+    = sigma_701 of n = 2000 corresponds to a cut at 1e-7 sigma_1)."""
+    pins = paper_pins()
+    m, n = 4000, 200
+    A, _, s0, _ = workloads.paper_dct_matrix(m, n, n)
+    U1, S1, V1, r1, _ = orc.ts_svd(A, passes=1, drop_tol=1e-7)
+    U2, S2, V2, r2, _ = orc.ts_svd(A, passes=2, scale=False, drop_tol=1e-7)
+    o1, o2 = orc.orth_error(U1[:, :r1]), orc.orth_error(U2[:, :r2])
+    assert pins["alg3_orth_min"] / 100 < o1 < 1e-2
+    assert o2 < 10 * pins["alg4_orth_max"]
+    e1 = orc.spectral_error(A, U1[:, :r1], S1[:r1], V1[:, :r1])
+    assert abs(e1 - s0[r1]) < 0.05 * s0[r1]
+    assert s0[r1] < pins["alg3_tall_spectral_err"] * 1.1
+
+
+# --------------------------------------------------------------------------
+# Low-rank: invariants and closed forms
+# --------------------------------------------------------------------------
+
+
+def test_lowrank_exact_low_rank_matrix(orc):
+    """A of exact rank 8 <= l: the randomized SVD is exact."""
+    m, n, r = 500, 300, 8
+    rng = np.random.default_rng(11)
+    U0 = workloads.orthonormal(m, r, rng)
+    V0 = workloads.orthonormal(n, r, rng)
+    s0 = np.linspace(2.0, 1.0, r)
+    A = (U0 * s0) @ V0.T
+    Om = workloads.gaussian(n, 12, 12)
+    U, S, V, rk, st = orc.lowrank_svd(A, 8, 12, 2, Om, drop_tol=1e-10)
+    assert rk == 8
+    assert np.abs(S - s0).max() < 1e-13
+    assert match_columns_up_to_sign(V, V0) < 1e-12
+
+
+def test_lowrank_eckart_young_bound(orc):
+    m, n = 600, 400
+    A, Ur, s, Vr = workloads.lowrank_plus_noise(m, n, 40, seed=13)
+    Om = workloads.gaussian(n, 20, 14)
+    U, S, V, rk, st = orc.lowrank_svd(A, 15, 20, 2, Om, drop_tol=0.0)
+    err = orc.spectral_error(A, U, S, V, iters=40)
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert err >= sv[15] * (1 - 1e-6)
+    assert err < 1.5 * sv[15]
+    # the leading singular values are accurate
+    assert np.abs(S[:5] - sv[:5]).max() < 1e-6 * sv[0]
+
+
+# --------------------------------------------------------------------------
+# Error metrics
+# --------------------------------------------------------------------------
+
+
+def test_spectral_error_and_orth_metrics(orc):
+    rng = np.random.default_rng(15)
+    A = rng.standard_normal((80, 12))
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    k = 5
+    e = orc.spectral_error(A, U[:, :k], S[:k], V[:, :k], iters=60)
+    E = A - (U[:, :k] * S[:k]) @ V[:, :k].T
+    nE = np.linalg.norm(E, 2)
+    # the power method approaches the norm from below
+    assert e <= nE * (1 + 1e-12)
+    assert e > nE * (1 - 1e-3)
+    X = rng.standard_normal((30, 4))
+    assert abs(orc.orth_error(X) - np.abs(X.T @ X - np.eye(4)).max()) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Gradient of the thin SVD
+# --------------------------------------------------------------------------
+
+
+def _loss_numpy(A, w, Bm, k):
+    U, S, Vt = np.linalg.svd(A, full_matrices=False)
+    return float(w @ S + np.sum((U[:, :k].T @ Bm) ** 2))
+
+
+def test_backward_matches_finite_differences(orc):
+    """The oracle's analytic adjoint against central differences of a
+    sign-invariant loss L = sum_j w_j sigma_j + ||U_k^T B||_F^2 evaluated
+    through LAPACK's SVD (an independent forward)."""
+    m, n, k = 120, 8, 3
+    s = workloads.sigma_distinct_gaps(n)
+    A, U0, s0, V0 = workloads.known_spectrum(m, n, s, seed=16)
+    rng = np.random.default_rng(17)
+    w = rng.standard_normal(n)
+    Bm = rng.standard_normal((m, 2))
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    dU = np.zeros((m, n))
+    dU[:, :k] = 2.0 * Bm @ (Bm.T @ U[:, :k])
+    dA = orc.ts_svd_backward(A, S, V, dU=dU, dS=w)
+    for t in range(3):
+        E = rng.standard_normal((m, n))
+        h = 1e-6
+        fd = (_loss_numpy(A + h * E, w, Bm, k) - _loss_numpy(A - h * E, w, Bm, k)) / (2 * h)
+        an = float(np.sum(dA * E))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (fd, an)
+
+
+def test_backward_singular_value_only_closed_form(orc):
+    """dL/dA for L = sum_j w_j sigma_j is U diag(w) V^T exactly."""
+    rng = np.random.default_rng(18)
+    A = rng.standard_normal((50, 6))
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    w = rng.standard_normal(6)
+    dA = orc.ts_svd_backward(A, S, V, dS=w)
+    assert np.abs(dA - (U * w) @ V.T).max() < 1e-12
+
+
+def test_backward_dv_term_finite_differences(orc):
+    """The V-adjoint term, against central differences through LAPACK."""
+    m, n = 60, 5
+    s = workloads.sigma_distinct_gaps(n)
+    A, _, _, _ = workloads.known_spectrum(m, n, s, seed=19)
+    rng = np.random.default_rng(20)
+    C = rng.standard_normal((n, n))
+
+    def loss(X):
+        # sign-invariant: sum_j (v_j^T c_j)^2
+        _, _, Vt = np.linalg.svd(X, full_matrices=False)
+        return float(np.sum(np.sum(Vt.T * C, axis=0) ** 2))
+
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    dV = 2.0 * C * np.sum(V * C, axis=0)
+    dA = orc.ts_svd_backward(A, S, V, dV=dV)
+    E = rng.standard_normal((m, n))
+    h = 1e-6
+    fd = (loss(A + h * E) - loss(A - h * E)) / (2 * h)
+    an = float(np.sum(dA * E))
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (fd, an)
