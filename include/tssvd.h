@@ -1,0 +1,159 @@
+/*
+ * tssvd.h - C ABI of the GB300 (sm_103a) library for the Gram-based
+ * tall-skinny SVD and the randomized low-rank SVD of
+ *   H. Li, Y. Kluger, M. Tygert, "Randomized algorithms for distributed
+ *   computation of principal component analysis and singular value
+ *   decomposition", arXiv:1612.08709.
+ *
+ * Conventions (all entry points):
+ *  - Every matrix pointer is a DEVICE pointer owned by the caller.  The
+ *    library never frees or retains caller memory.
+ *  - Row-major storage with an explicit leading dimension for the input A
+ *    (lda >= n elements).  Outputs are dense row-major: U is m x n
+ *    (leading dimension n), S has n entries, V is n x n with column j the
+ *    j-th right singular vector.  Singular values are in decreasing order.
+ *  - Signs: each right singular vector is flipped so that its entry of
+ *    largest magnitude (lowest index on ties) is positive; the matching
+ *    left singular vector is flipped with it.
+ *  - Work is queued on opts->stream (a cudaStream_t; NULL = the legacy
+ *    default stream).  Each call returns only after that stream has
+ *    finished the call's work, because the status code is read back from
+ *    the device; output buffers are then complete.
+ *  - Scratch memory: opts->workspace of opts->workspace_bytes bytes (query
+ *    the size with the *_workspace_size functions).  If workspace is NULL
+ *    the library uses an internal per-device buffer that it grows on demand
+ *    with cudaMalloc and keeps until process exit; calls that use the
+ *    internal buffer are serialised by a lock.
+ *  - Return value: TSSVD_OK (0); a positive status below (results are
+ *    still written); or -i when argument i (1-based) is invalid, in which
+ *    case nothing is written and nothing is queued.
+ */
+#ifndef TSSVD_H
+#define TSSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSSVD_OK 0
+#define TSSVD_ENOCONV 1  /* a Jacobi solve used max_sweeps sweeps without converging */
+#define TSSVD_RANKDEF 2  /* numerical rank r < n: S[r..], U and V columns r.. are 0 */
+#define TSSVD_ETIMEOUT 3 /* a bounded device-side wait expired; results undefined */
+#define TSSVD_ECUDA 4    /* a CUDA runtime call failed; results undefined */
+#define TSSVD_ENOMEM 5   /* workspace too small, or the internal one could not grow */
+
+/* Arithmetic of the tall products (the passes over the m rows). */
+typedef enum {
+    /* Plain FP64: every tall product in FP64 fused multiply-add. */
+    TSSVD_FP64 = 0,
+    /* Mixed: the first pass's products (Gram of A and A V~) run on the
+     * tcgen05 tensor cores with BF16x3 split operands and FP32 accumulation
+     * drained to FP64; the second orthonormalisation pass, the eigensolves
+     * and all n x n work stay FP64. */
+    TSSVD_BF16X3 = 1
+} tssvd_mode;
+
+typedef struct {
+    /* 1 = single orthonormalisation (Algorithm 3); 2 = double (Algorithm 4). */
+    int passes;
+    /* MaxEntry column scaling (2 = passes only): column j of A is divided by
+     * the smallest power of two >= max_i |A_ij| before the Gram matrix is
+     * formed, and the scaling is folded back into the small SVD. */
+    int scale;
+    /* Discard threshold: a column whose explicit norm is below
+     * drop_tol * (largest norm) is dropped (Algorithms 3 and 4, discard
+     * steps).  Default sqrt(1e-11), the square root of the paper's example
+     * working precision (Remark "working"). */
+    double drop_tol;
+    int mode;       /* tssvd_mode */
+    int max_sweeps; /* Jacobi sweep cap per eigen/SVD solve (default 30) */
+    void *stream;   /* cudaStream_t */
+    void *workspace;
+    size_t workspace_bytes;
+    /* ---- written by the call ---- */
+    int64_t out_rank; /* number of nonzero singular values returned */
+    int sweeps[4];    /* Jacobi sweeps: [0] eig of A^T A, [1] eig of Y^T Y, [2] SVD of R */
+    int ranks[2];     /* ranks kept by the first and second discard steps */
+} tssvd_opts;
+
+/* Fills *opts with the defaults: passes 2, scale 1, drop_tol sqrt(1e-11),
+ * mode TSSVD_FP64, max_sweeps 30, default stream, internal workspace. */
+void tssvd_default_opts(tssvd_opts *opts);
+
+/* Human-readable text for a status code (static storage). */
+const char *tssvd_status_string(int status);
+
+/* Bytes of workspace ts_svd / ts_svd_f32 need for an m x n problem with
+ * these options (elem_bytes = 8 for ts_svd, 4 for ts_svd_f32). */
+size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts);
+
+/*
+ * Thin SVD A = U diag(S) V^T of a tall-skinny A (m x n, m >= n >= 1).
+ * passes = 2: Algorithm 4 (Gram of A, eigendecomposition, Y~ = A V~,
+ * explicit column norms (Remark "normalizing"), discard, second Gram pass
+ * on Y, R = T W^T S~ V~^T, SVD of R, U = Q P).  passes = 1: Algorithm 3.
+ *   A   [in]  m x n, row-major, leading dimension lda >= n; not modified.
+ *   U   [out] m x n, row-major (leading dimension n).
+ *   S   [out] n.
+ *   V   [out] n x n, row-major; column j = right singular vector j.
+ *   opts[in/out] options; out_rank, sweeps and ranks are written.
+ * Errors: -1 A NULL, -2 m < n or m < 1, -3 n < 1, -4 lda < n, -5 U NULL,
+ * -6 S NULL, -7 V NULL, -8 opts NULL or invalid field.
+ */
+int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S,
+           double *V, tssvd_opts *opts);
+
+/* As ts_svd for FP32 storage: A, U, S, V are float.  The n x n
+ * eigensolves and small SVD run in FP64; tall products as opts->mode says
+ * (FP64 arithmetic on the FP32 data, or BF16x3 on the tensor cores). */
+int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S,
+               float *V, tssvd_opts *opts);
+
+/* Bytes of workspace lowrank_svd needs. */
+size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_opts *opts);
+
+/*
+ * Rank-k approximation A ~ U diag(S) V^T of a general A (m x n) by
+ * Algorithm 8: randomized subspace iteration (Algorithm 5) with `iters`
+ * power steps, each normalised by the single-pass Gram TS-SVD
+ * (Algorithm 3), the last one by the two-pass TS-SVD (Algorithm 4),
+ * followed by the direct SVD of Algorithm 6 (the SVD of B = Q^T A is the
+ * two-pass TS-SVD of B^T = A^T Q, n x l).  The leading k of the l
+ * triplets are returned.  MaxEntry scaling (opts->scale) is not used.
+ *   A     [in]  m x n row-major, leading dimension lda >= n.
+ *   k, l  1 <= k <= l <= min(m, n).
+ *   iters number of power steps i >= 0.
+ *   Omega [in]  n x l row-major: the starting matrix (i.i.d. Gaussian,
+ *               drawn by the caller).
+ *   U [out] m x k, S [out] k, V [out] n x k (row-major, dense).
+ * Errors: -1 A, -2 m, -3 n, -4 lda, -5 k, -6 l, -7 iters, -8 Omega,
+ * -9 U, -10 S, -11 V, -12 opts.
+ */
+int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
+                int iters, const double *Omega, double *U, double *S, double *V,
+                tssvd_opts *opts);
+
+/*
+ * Adjoint of the thin SVD computed by ts_svd (full column rank, distinct
+ * singular values).  Given the forward inputs A, S, V and the gradients
+ * dU (m x n), dS (n), dV (n x n) of a loss with respect to U, S, V (any of
+ * the three may be NULL, meaning zero), writes dA (m x n, leading
+ * dimension n).  U is recomputed as A V diag(S)^-1 instead of being stored.
+ * With F_ij = 1/(s_j^2 - s_i^2) (0 on the diagonal), J = U^T dU, K = V^T dV:
+ *   dA = U [ (F o (J - J^T)) S + diag(dS) + S (F o (K - K^T)) - J S^-1 ] V^T
+ *        + dU S^-1 V^T.
+ * This is the standard thin-SVD adjoint (it is not part of the paper).
+ * Errors: -1 A, -2 m, -3 n, -4 lda, -5 S, -6 V, -10 dA, -11 opts.
+ */
+int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const double *S,
+                    const double *V, const double *dU, const double *dS, const double *dV,
+                    double *dA, tssvd_opts *opts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSSVD_H */

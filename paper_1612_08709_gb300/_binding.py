@@ -1,0 +1,226 @@
+"""ctypes marshalling of torch tensors into the C ABI of libtssvd.so.
+
+Argument marshalling only: every computation happens in the library's CUDA
+kernels.  Functions keep the C names (ts_svd, lowrank_svd, ts_svd_backward)
+and raise TsSvdError on a negative (invalid argument) or hard-failure
+status; soft statuses (non-convergence, rank deficiency) are returned in the
+info dictionary.
+"""
+import ctypes
+import math
+import os
+
+import torch
+
+from . import build as _build
+
+TSSVD_OK = 0
+TSSVD_ENOCONV = 1
+TSSVD_RANKDEF = 2
+TSSVD_ETIMEOUT = 3
+TSSVD_ECUDA = 4
+TSSVD_ENOMEM = 5
+
+_MODES = {"fp64": 0, "bf16x3": 1}
+
+# Square root of the paper's example working precision 1e-11 (Remark "working").
+PAPER_DROP_TOL = math.sqrt(1e-11)
+
+
+class TsSvdError(RuntimeError):
+    pass
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("passes", ctypes.c_int),
+        ("scale", ctypes.c_int),
+        ("drop_tol", ctypes.c_double),
+        ("mode", ctypes.c_int),
+        ("max_sweeps", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("out_rank", ctypes.c_int64),
+        ("sweeps", ctypes.c_int * 4),
+        ("ranks", ctypes.c_int * 2),
+    ]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads libtssvd.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if _build._stale():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libtssvd.so is missing (%s); run build()" % path)
+    L = ctypes.CDLL(path)
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    op = ctypes.POINTER(_Opts)
+    L.tssvd_default_opts.argtypes = [op]
+    L.tssvd_default_opts.restype = None
+    L.tssvd_status_string.argtypes = [ctypes.c_int]
+    L.tssvd_status_string.restype = ctypes.c_char_p
+    L.ts_svd_workspace_size.argtypes = [i64, i64, ctypes.c_int, op]
+    L.ts_svd_workspace_size.restype = ctypes.c_size_t
+    L.lowrank_svd_workspace_size.argtypes = [i64, i64, i64, op]
+    L.lowrank_svd_workspace_size.restype = ctypes.c_size_t
+    for name in ("ts_svd", "ts_svd_f32"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i64, i64, i64, vp, vp, vp, op]
+        f.restype = ctypes.c_int
+    L.lowrank_svd.argtypes = [vp, i64, i64, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp, op]
+    L.lowrank_svd.restype = ctypes.c_int
+    L.ts_svd_backward.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
+    L.ts_svd_backward.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points the binding expects the library to export."""
+    return ["tssvd_default_opts", "tssvd_status_string", "ts_svd_workspace_size", "ts_svd",
+            "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward"]
+
+
+def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+          stream=None, workspace=None):
+    o = _Opts()
+    lib().tssvd_default_opts(ctypes.byref(o))
+    o.passes = int(passes)
+    o.scale = int(bool(scale))
+    o.drop_tol = float(drop_tol)
+    o.mode = _MODES[mode]
+    o.max_sweeps = int(max_sweeps)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(stream.cuda_stream)
+    if workspace is not None:
+        assert workspace.is_cuda and workspace.is_contiguous()
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check(rc, name):
+    if rc < 0:
+        raise TsSvdError("%s: invalid argument %d" % (name, -rc))
+    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM):
+        raise TsSvdError("%s: %s" % (name, lib().tssvd_status_string(rc).decode()))
+    return rc
+
+
+def _info(o, rc):
+    return {"status": rc, "rank": int(o.out_rank), "sweeps": list(o.sweeps)[:3],
+            "ranks": list(o.ranks)}
+
+
+def _as_matrix(A):
+    if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dim() == 2):
+        raise TsSvdError("expected a 2-D CUDA tensor")
+    if A.stride(1) != 1:
+        raise TsSvdError("A must be row-major (unit column stride)")
+    return A
+
+
+def ts_svd_workspace_size(m, n, dtype=torch.float64, **kw):
+    o = _opts(**kw) if torch.cuda.is_available() else None
+    if o is None:
+        o = _Opts()
+        lib().tssvd_default_opts(ctypes.byref(o))
+    return int(lib().ts_svd_workspace_size(m, n, 4 if dtype == torch.float32 else 8,
+                                           ctypes.byref(o)))
+
+
+def lowrank_svd_workspace_size(m, n, l, **kw):
+    o = _Opts()
+    lib().tssvd_default_opts(ctypes.byref(o))
+    return int(lib().lowrank_svd_workspace_size(m, n, l, ctypes.byref(o)))
+
+
+def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+           stream=None, workspace=None, out=None):
+    """Thin SVD of a tall-skinny CUDA tensor A (m x n, float64 or float32).
+
+    Returns (U m x n, S n, V n x n, info).  See include/tssvd.h (ts_svd).
+    """
+    A = _as_matrix(A)
+    m, n = A.shape
+    dt = A.dtype
+    if dt not in (torch.float64, torch.float32):
+        raise TsSvdError("A must be float64 or float32")
+    if out is None:
+        U = torch.empty((m, n), dtype=dt, device=A.device)
+        S = torch.empty((n,), dtype=dt, device=A.device)
+        V = torch.empty((n, n), dtype=dt, device=A.device)
+    else:
+        U, S, V = out
+    o = _opts(passes, scale, drop_tol, mode, max_sweeps, stream, workspace)
+    f = lib().ts_svd if dt == torch.float64 else lib().ts_svd_f32
+    with torch.cuda.device(A.device):
+        rc = f(_ptr(A), m, n, A.stride(0), _ptr(U), _ptr(S), _ptr(V), ctypes.byref(o))
+    _check(rc, "ts_svd")
+    return U, S, V, _info(o, rc)
+
+
+def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+                stream=None, workspace=None):
+    """Rank-k SVD by Algorithm 8.  A (m x n) and Omega (n x l) float64 CUDA
+    tensors.  Returns (U m x k, S k, V n x k, info)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    Omega = Omega.contiguous()
+    U = torch.empty((m, k), dtype=torch.float64, device=A.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A.device)
+    V = torch.empty((n, k), dtype=torch.float64, device=A.device)
+    o = _opts(2, False, drop_tol, mode, max_sweeps, stream, workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().lowrank_svd(_ptr(A), m, n, A.stride(0), int(k), int(l), int(iters),
+                               _ptr(Omega), _ptr(U), _ptr(S), _ptr(V), ctypes.byref(o))
+    _check(rc, "lowrank_svd")
+    return U, S, V, _info(o, rc)
+
+
+def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):
+    """dA of the thin SVD (see include/tssvd.h, ts_svd_backward)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    dA = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    c = [x.contiguous() if x is not None else None for x in (S, V, dU, dS, dV)]
+    o = _opts(stream=stream, workspace=workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().ts_svd_backward(_ptr(A), m, n, A.stride(0), *[_ptr(x) for x in c], _ptr(dA),
+                                   ctypes.byref(o))
+    _check(rc, "ts_svd_backward")
+    return dA
+
+
+class TSSVD(torch.autograd.Function):
+    """Differentiable thin SVD: forward by ts_svd, backward by ts_svd_backward
+    (U is recomputed from A, V and S rather than stored)."""
+
+    @staticmethod
+    def forward(ctx, A, passes=2, scale=True, drop_tol=0.0):
+        U, S, V, info = ts_svd(A, passes=passes, scale=scale, drop_tol=drop_tol)
+        ctx.save_for_backward(A, S, V)
+        return U, S, V
+
+    @staticmethod
+    def backward(ctx, gU, gS, gV):
+        A, S, V = ctx.saved_tensors
+        dA = ts_svd_backward(A, S, V, dU=gU, dS=gS, dV=gV)
+        return dA, None, None, None

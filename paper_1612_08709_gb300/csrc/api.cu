@@ -1,0 +1,582 @@
+// C ABI entry points and the host-side orchestration of each call.
+//
+// Every step of a call is a kernel queued on the caller's stream; the host
+// only validates arguments, carves the workspace and, at the end, reads the
+// device status block back (one small device-to-host copy and a stream
+// synchronisation).  Column discards never change array shapes: a dropped
+// column is carried as a zero column with a zero inverse norm, which the
+// Jacobi solves leave untouched (its inner products are exactly zero) and
+// which sorts last, so no host round trip is needed between passes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tssvd {
+
+int num_sms()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+// ---------------------------------------------------------------- workspace
+
+// Bump allocator over a device buffer.  In sizing mode (base == nullptr)
+// it only accumulates the bytes a call would take.
+struct Bump {
+    char *base;
+    size_t off;
+    size_t cap;
+    bool overflow;
+    explicit Bump(void *b, size_t c) : base((char *)b), off(0), cap(c), overflow(false) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = nullptr;
+        if (base) {
+            if (off + count * sizeof(T) > cap)
+                overflow = true;
+            else
+                p = (T *)(base + off);
+        }
+        off += count * sizeof(T);
+        return p;
+    }
+    bool sizing() const { return base == nullptr; }
+};
+
+// The internal workspace: one growable buffer per device, used when the
+// caller passes none.  Calls that use it hold the lock for their duration.
+struct InternalWs {
+    std::mutex mu;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+InternalWs g_ws[64];
+
+#define CK(...)                                \
+    do {                                       \
+        cudaError_t e_ = (__VA_ARGS__);        \
+        if (e_ != cudaSuccess) return e_;      \
+    } while (0)
+
+// ------------------------------------------------------------ TS-SVD core
+
+// Enqueues Algorithm 3 (passes == 1) or Algorithm 4 (passes == 2) on A
+// (m x n, lda, type T).  Writes U (m x n, ldu, type T), S (n) and V (n x n,
+// row-major, ldv) as doubles or T per the template parameters; all outputs
+// carry zeros past the numerical rank.  In sizing mode only the workspace
+// is counted.
+template <typename T, typename TO>
+cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
+                    int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
+                    cudaStream_t s)
+{
+    const bool sizing = ws.sizing();
+    const i64 nn = n * n;
+    int *ctr = ws.take<int>((size_t)max_sweeps + 4);
+    unsigned long long *bits = ws.take<unsigned long long>(n);
+    double *d = ws.take<double>(n), *dinv = ws.take<double>(n);
+    const int sp1 = tn_splits(m, n, n, true);
+    const int sp2 = tn_splits(n, n, n, false);
+    const int sp = sp1 > sp2 ? sp1 : sp2;
+    double *P = ws.take<double>((size_t)sp * nn);
+    const int gy = nn_grid_rows(m, n);
+    double *NP = ws.take<double>((size_t)gy * n);
+    double *B = ws.take<double>(nn), *Xw = ws.take<double>(nn), *Jw = ws.take<double>(nn);
+    double *Vt = ws.take<double>(nn), *W = ws.take<double>(nn), *M = ws.take<double>(nn);
+    double *G = ws.take<double>(nn), *R = ws.take<double>(nn), *Pm = ws.take<double>(nn);
+    double *Vo = ws.take<double>(nn), *Pp = ws.take<double>(nn), *M3 = ws.take<double>(nn);
+    double *lam = ws.take<double>(n), *sig = ws.take<double>(n), *sinv = ws.take<double>(n);
+    double *Tn = ws.take<double>(n), *tinv = ws.take<double>(n), *Tk = ws.take<double>(n);
+    double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
+    double *cs = ws.take<double>(n);
+    int *perm = ws.take<int>(n);
+    double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
+    if (sizing) return cudaSuccess;
+    if (ws.overflow) return cudaErrorMemoryAllocation;
+
+    if (passes == 1) {
+        // ---- Algorithm 3 ----
+        // B = A^T A.
+        CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
+        CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, B, n, s));
+        // B = V D V^T.
+        CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 0, s));
+        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Vt, n, lam, nullptr,
+                                  0, s));
+        // U~ = A V, Sigma = explicit column norms of U~ (Remark "normalizing").
+        CK(launch_nn<T, TO>(A, lda, Vt, n, m, n, n, U, ldu, NP, s));
+        CK(launch_norms_reduce(NP, gy, n, sig, s));
+        // Discard, U = U~ Sigma^{-1}, sign convention.
+        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+        CK(launch_scale2(Vt, n, n, n, nullptr, nullptr, Vo, n, s));
+        CK(launch_signs(Vo, n, n, n, sinv, sgn, s));
+        CK(launch_scale2(sinv, n, 1, n, nullptr, sgn, cs, n, s));
+        CK(launch_scale_cols_inplace<TO>(U, ldu, m, n, cs, s));
+        CK(launch_keepval(sig, sinv, n, sigma, s));
+        CK(launch_count_positive(sigma, n, &st->rank, s));
+        CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
+        CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
+        return cudaSuccess;
+    }
+
+    // ---- Algorithm 4 ----
+    const double *rs1 = nullptr;
+    const double *M1 = Vt;
+    if (scale) {
+        // MaxEntry column scaling D (powers of two, so exact).
+        CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+        CK(launch_colmax<T>(A, m, n, lda, bits, s));
+        CK(launch_pow2_scale(bits, n, d, dinv, s));
+        rs1 = dinv;
+    }
+    // B = (A D^-1)^T (A D^-1).
+    CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
+    CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
+    // B = V~ D~ V~^T.
+    CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 0, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Vt, n, lam, nullptr, 0,
+                              s));
+    // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
+    if (scale) {
+        CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
+        M1 = M;
+    }
+    CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
+    CK(launch_norms_reduce(NP, gy, n, sig, s));
+    // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
+    // products instead of a separate pass over Y.
+    CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+    // Z = Y^T Y = Sigma~^-1 (Y~^T Y~) Sigma~^-1.
+    CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
+    CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
+    // Z = W D W^T.
+    CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 1, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, W, n, lam, nullptr, 0,
+                              s));
+    // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
+    CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
+    CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
+    CK(launch_norms_reduce(NP, gy, n, Tn, s));
+    CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
+    CK(launch_keepval(Tn, tinv, n, Tk, s));
+    // R = T W^T Sigma~ V~^T D.
+    CK(launch_build_g(sig, sinv, Vt, n, scale ? d : nullptr, n, G, s));
+    CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
+    CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+    // R = P Sigma V^T by one-sided Jacobi on R^T (R row-major = R^T
+    // column-major): R^T P = X, Sigma = column norms, V = X Sigma^-1.
+    CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 2, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
+    CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
+    CK(launch_count_positive(sigma, n, &st->rank, s));
+    // U = Q P = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
+    CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
+    CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
+    CK(launch_nn<double, TO>(Yt, n, M3, n, m, n, n, U, ldu, NP, s));
+    CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
+    CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
+    return cudaSuccess;
+}
+
+// Status words are summarised into the ABI's status code.
+int summarise(const std::vector<DevStatus> &sts, int nsolves_per, int *rank_out)
+{
+    int code = TSSVD_OK;
+    for (const DevStatus &h : sts)
+        if (h.err) return TSSVD_ETIMEOUT;
+    for (const DevStatus &h : sts)
+        for (int i = 0; i < nsolves_per; i++)
+            if (h.sweeps[i] < 0) code = TSSVD_ENOCONV;
+    (void)rank_out;
+    return code;
+}
+
+// Resolves the workspace for a call: the caller's, or the internal one
+// (grown if needed; the returned lock is held for the call).
+int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mutex> &lk)
+{
+    if (o->workspace) {
+        if (o->workspace_bytes < need) return TSSVD_ENOMEM;
+        *base = o->workspace;
+        return TSSVD_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSSVD_ECUDA;
+    InternalWs &w = g_ws[dev];
+    lk = std::unique_lock<std::mutex>(w.mu);
+    if (w.bytes < need) {
+        if (w.ptr) {
+            cudaDeviceSynchronize();
+            cudaFree(w.ptr);
+            w.ptr = nullptr;
+            w.bytes = 0;
+        }
+        if (cudaMalloc(&w.ptr, need) != cudaSuccess) {
+            cudaGetLastError();
+            w.ptr = nullptr;
+            return TSSVD_ENOMEM;
+        }
+        w.bytes = need;
+    }
+    *base = w.ptr;
+    return TSSVD_OK;
+}
+
+int check_opts(const tssvd_opts *o)
+{
+    if (!o) return 0;
+    if (o->passes != 1 && o->passes != 2) return 0;
+    if (!(o->drop_tol >= 0.0) || o->drop_tol >= 1.0) return 0;
+    if (o->max_sweeps < 1 || o->max_sweeps > 1000) return 0;
+    if (o->mode != TSSVD_FP64) return 0;  // other modes are built separately
+    return 1;
+}
+
+template <typename T>
+int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V,
+                 tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (lda < n) return -4;
+    if (!U) return -5;
+    if (!S) return -6;
+    if (!V) return -7;
+    if (!check_opts(opts)) return -8;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(1);
+    ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
+                  opts->max_sweeps, sz, nullptr, s);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off);
+    DevStatus *st = ws.take<DevStatus>(1);
+    if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
+    cudaError_t e = ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
+                                  opts->drop_tol, opts->max_sweeps, ws, st, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TSSVD_ENOMEM : TSSVD_ECUDA;
+    }
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    std::vector<DevStatus> v(1, h);
+    int code = summarise(v, opts->passes == 2 ? 3 : 1, nullptr);
+    opts->out_rank = h.rank;
+    for (int i = 0; i < 4; i++) opts->sweeps[i] = h.sweeps[i];
+    opts->ranks[0] = h.rank1;
+    opts->ranks[1] = opts->passes == 2 ? h.rank2 : h.rank1;
+    if (code == TSSVD_OK && h.rank < n) code = TSSVD_RANKDEF;
+    return code;
+}
+
+// ------------------------------------------------------------- low rank
+
+// Number of per-sub-call status blocks used by lowrank: 2 per power step + 2.
+cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, int iters,
+                         const double *Omega, double *U, double *S, double *V, double tol,
+                         int max_sweeps, Bump &ws, DevStatus *sts, cudaStream_t s)
+{
+    const bool sizing = ws.sizing();
+    double *Qt = ws.take<double>((size_t)n * l), *Y = ws.take<double>((size_t)m * l);
+    double *Q = ws.take<double>((size_t)m * l), *Bt = ws.take<double>((size_t)n * l);
+    double *U1 = ws.take<double>((size_t)n * l), *S1 = ws.take<double>(l);
+    double *V1 = ws.take<double>((size_t)l * l), *V1s = ws.take<double>((size_t)l * l);
+    double *Uf = ws.take<double>((size_t)m * l), *sgn = ws.take<double>(l);
+    double *tS = ws.take<double>(l), *tV = ws.take<double>((size_t)l * l);
+    const int spT = tn_splits(m, n, l, false);
+    double *P = ws.take<double>((size_t)spT * n * l);
+    const int gy = nn_grid_rows(m, l);
+    double *NP = ws.take<double>((size_t)gy * l);
+    // sub-call workspaces are carved last and reused by every sub-call
+    const size_t sub_off = ws.off;
+    const i64 big = m > n ? m : n;
+    {
+        Bump probe(nullptr, 0);
+        ts_core<double, double>(nullptr, big, l, l, (double *)nullptr, l, (double *)nullptr,
+                                (double *)nullptr, l, 2, 0, tol, max_sweeps, probe, nullptr, s);
+        ws.take<char>(probe.off + 256);
+    }
+    if (sizing) return cudaSuccess;
+    if (ws.overflow) return cudaErrorMemoryAllocation;
+    auto sub = [&](const double *Ain, i64 rows, double *Uo, double *So, double *Vo, int passes,
+                   DevStatus *st) -> cudaError_t {
+        Bump w(ws.base + ((sub_off + 255) & ~(size_t)255), ws.cap - ((sub_off + 255) & ~(size_t)255));
+        return ts_core<double, double>(Ain, rows, l, l, Uo, l, So, Vo, l, passes, 0, tol,
+                                       max_sweeps, w, st, s);
+    };
+
+    CK(cudaMemcpyAsync(Qt, Omega, sizeof(double) * n * l, cudaMemcpyDeviceToDevice, s));
+    int si = 0;
+    for (int it = 0; it < iters; it++) {
+        // Y_j = A Q~_{j-1}; Y_j = Q_j R_j (Algorithm 3).
+        CK(launch_nn<double, double>(A, lda, Qt, l, m, n, l, Y, l, NP, s));
+        CK(sub(Y, m, Q, tS, tV, 1, sts + si++));
+        // Y~_j = A^T Q_j; Y~_j = Q~_j R~_j (Algorithm 3).
+        CK(launch_tn_partial<double, double>(A, lda, Q, l, m, n, l, spT, false, P, s));
+        CK(launch_tn_reduce(P, spT, n, l, nullptr, nullptr, false, Bt, l, s));
+        CK(sub(Bt, n, Qt, tS, tV, 1, sts + si++));
+    }
+    // Y = A Q~_i; Y = Q R with double orthonormalisation (Algorithm 4).
+    CK(launch_nn<double, double>(A, lda, Qt, l, m, n, l, Y, l, NP, s));
+    CK(sub(Y, m, Q, tS, tV, 2, sts + si++));
+    // Algorithm 6: B = Q^T A via B^T = A^T Q (n x l); B^T = U1 S1 V1^T, so
+    // B = V1 S1 U1^T: U~ = V1 and V = U1.
+    CK(launch_tn_partial<double, double>(A, lda, Q, l, m, n, l, spT, false, P, s));
+    CK(launch_tn_reduce(P, spT, n, l, nullptr, nullptr, false, Bt, l, s));
+    CK(sub(Bt, n, U1, S1, V1, 2, sts + si++));
+    // Sign convention on the final V = U1; U = Q U~ = Q V1 diag(sgn).
+    CK(launch_signs(U1, l, n, l, S1, sgn, s));
+    CK(launch_scale2(V1, l, l, l, nullptr, sgn, V1s, l, s));
+    CK(launch_nn<double, double>(Q, l, V1s, l, m, l, l, Uf, l, NP, s));
+    CK(launch_convert<double>(Uf, l, m, k, U, k, s));
+    CK(launch_convert<double>(U1, l, n, k, V, k, s));
+    CK(launch_convert<double>(S1, l, 1, k, S, k, s));
+    CK(launch_count_positive(S1, k, &sts[si].rank, s));
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace tssvd
+
+using namespace tssvd;
+
+extern "C" {
+
+void tssvd_default_opts(tssvd_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->passes = 2;
+    o->scale = 1;
+    o->drop_tol = sqrt(1e-11);
+    o->mode = TSSVD_FP64;
+    o->max_sweeps = 30;
+}
+
+const char *tssvd_status_string(int st)
+{
+    switch (st) {
+    case TSSVD_OK: return "ok";
+    case TSSVD_ENOCONV: return "Jacobi solve did not converge within max_sweeps";
+    case TSSVD_RANKDEF: return "numerically rank deficient; trailing outputs are zero";
+    case TSSVD_ETIMEOUT: return "device-side wait timed out";
+    case TSSVD_ECUDA: return "CUDA runtime error";
+    case TSSVD_ENOMEM: return "workspace too small or allocation failed";
+    default: return st < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts)
+{
+    if (!opts || m < 1 || n < 1) return 0;
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(1);
+    if (elem_bytes == 4)
+        ts_core<float, float>(nullptr, m, n, n, (float *)nullptr, n, (float *)nullptr,
+                              (float *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
+                              opts->max_sweeps, sz, nullptr, nullptr);
+    else
+        ts_core<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
+                                (double *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
+                                opts->max_sweeps, sz, nullptr, nullptr);
+    return sz.off;
+}
+
+int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S, double *V,
+           tssvd_opts *opts)
+{
+    return ts_svd_entry<double>(A, m, n, lda, U, S, V, opts);
+}
+
+int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S, float *V,
+               tssvd_opts *opts)
+{
+    return ts_svd_entry<float>(A, m, n, lda, U, S, V, opts);
+}
+
+size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_opts *opts)
+{
+    if (!opts || m < 1 || n < 1 || l < 1) return 0;
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(64);
+    lowrank_core(nullptr, m, n, n, l, l, 0, nullptr, nullptr, nullptr, nullptr, opts->drop_tol,
+                 opts->max_sweeps, sz, nullptr, nullptr);
+    return sz.off;
+}
+
+int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
+                int iters, const double *Omega, double *U, double *S, double *V,
+                tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (n < 1) return -3;
+    if (lda < n) return -4;
+    if (k < 1 || k > l) return -5;
+    if (l < 1 || l > m || l > n || l > 16384) return -6;
+    if (iters < 0 || iters > 30) return -7;
+    if (!Omega) return -8;
+    if (!U) return -9;
+    if (!S) return -10;
+    if (!V) return -11;
+    if (!check_opts(opts)) return -12;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const int nst = 2 * iters + 3;
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(nst);
+    lowrank_core(A, m, n, lda, k, l, iters, Omega, U, S, V, opts->drop_tol, opts->max_sweeps, sz,
+                 nullptr, s);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off);
+    DevStatus *sts = ws.take<DevStatus>(nst);
+    if (cudaMemsetAsync(sts, 0, sizeof(DevStatus) * nst, s) != cudaSuccess) return TSSVD_ECUDA;
+    cudaError_t e = lowrank_core(A, m, n, lda, k, l, iters, Omega, U, S, V, opts->drop_tol,
+                                 opts->max_sweeps, ws, sts, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TSSVD_ENOMEM : TSSVD_ECUDA;
+    }
+    std::vector<DevStatus> h(nst);
+    if (cudaMemcpyAsync(h.data(), sts, sizeof(DevStatus) * nst, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    int code = TSSVD_OK;
+    for (int i = 0; i < nst - 1; i++) {
+        if (h[i].err) return TSSVD_ETIMEOUT;
+        const int solves = (i < 2 * iters) ? 1 : 3;
+        for (int j = 0; j < solves; j++)
+            if (h[i].sweeps[j] < 0) code = TSSVD_ENOCONV;
+    }
+    const int rank = h[nst - 1].rank;
+    opts->out_rank = rank;
+    opts->ranks[0] = h[nst - 2].rank1;
+    opts->ranks[1] = h[nst - 2].rank2;
+    for (int i = 0; i < 4; i++) opts->sweeps[i] = h[nst - 2].sweeps[i];
+    if (code == TSSVD_OK && rank < k) code = TSSVD_RANKDEF;
+    return code;
+}
+
+int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const double *S,
+                    const double *V, const double *dU, const double *dS, const double *dV,
+                    double *dA, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (lda < n) return -4;
+    if (!S) return -5;
+    if (!V) return -6;
+    if (!dA) return -10;
+    if (!opts) return -11;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 nn = n * n;
+    const int spJ = tn_splits(m, n, n, false);
+    const int spK = tn_splits(n, n, n, false);
+    const int sp = spJ > spK ? spJ : spK;
+    const int gy = nn_grid_rows(m, n);
+    auto carve = [&](Bump &w, double **Ub, double **sinv, double **M0, double **J, double **K,
+                     double **Mc, double **Vtr, double **BB, double **P, double **NP) {
+        *Ub = w.take<double>((size_t)m * 2 * n);
+        *sinv = w.take<double>(n);
+        *M0 = w.take<double>(nn);
+        *J = w.take<double>(nn);
+        *K = w.take<double>(nn);
+        *Mc = w.take<double>(nn);
+        *Vtr = w.take<double>(nn);
+        *BB = w.take<double>(2 * nn);
+        *P = w.take<double>((size_t)sp * nn);
+        *NP = w.take<double>((size_t)gy * n);
+    };
+    double *Ub, *sinv, *M0, *J, *K, *Mc, *Vtr, *BB, *P, *NP;
+    Bump sz(nullptr, 0);
+    carve(sz, &Ub, &sinv, &M0, &J, &K, &Mc, &Vtr, &BB, &P, &NP);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off);
+    carve(ws, &Ub, &sinv, &M0, &J, &K, &Mc, &Vtr, &BB, &P, &NP);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    auto body = [&]() -> cudaError_t {
+        // sinv = 1/S (the discard rule with tol 0 inverts every S_j > 0)
+        CK(launch_discard(S, n, 0.0, sinv, nullptr, s));
+        CK(launch_scale2(V, n, n, n, nullptr, sinv, M0, n, s));
+        CK(launch_nn<double, double>(A, lda, M0, n, m, n, n, Ub, 2 * n, NP, s));
+        if (dU) {
+            CK(cudaMemcpy2DAsync(Ub + n, sizeof(double) * 2 * n, dU, sizeof(double) * n,
+                                 sizeof(double) * n, m, cudaMemcpyDeviceToDevice, s));
+            // J = U^T dU
+            CK(launch_tn_partial<double, double>(Ub, 2 * n, Ub + n, 2 * n, m, n, n, spJ, false, P,
+                                                 s));
+            CK(launch_tn_reduce(P, spJ, n, n, nullptr, nullptr, false, J, n, s));
+        } else {
+            CK(cudaMemset2DAsync(Ub + n, sizeof(double) * 2 * n, 0, sizeof(double) * n, m, s));
+        }
+        if (dV) {
+            // K = V^T dV
+            CK(launch_tn_partial<double, double>(V, n, dV, n, n, n, n, spK, false, P, s));
+            CK(launch_tn_reduce(P, spK, n, n, nullptr, nullptr, false, K, n, s));
+        }
+        CK(launch_adjoint_core(dU ? J : nullptr, dV ? K : nullptr, S, dS, n, Mc, s));
+        // BB = [Mc V^T ; S^-1 V^T]  (2n x n)
+        CK(launch_transpose(V, n, n, n, nullptr, Vtr, n, s));
+        CK(launch_nn<double, double>(Mc, n, Vtr, n, n, n, n, BB, n, NP, s));
+        CK(launch_transpose(V, n, n, n, sinv, BB + nn, n, s));
+        // dA = [U | dU] BB
+        CK(launch_nn<double, double>(Ub, 2 * n, BB, n, m, 2 * n, n, dA, n, NP, s));
+        return cudaSuccess;
+    };
+    cudaError_t e = body();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return TSSVD_OK;
+}
+
+}  // extern "C"

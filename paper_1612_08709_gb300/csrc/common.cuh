@@ -1,0 +1,127 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Target: GB300 (sm_103a) only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tssvd.h"
+
+namespace tssvd {
+
+typedef int64_t i64;
+
+// Device-side status block, one per call.  `err` is set by kernels whose
+// bounded waits expire (TSSVD_ETIMEOUT); the host reads the block once at
+// the end of the call.
+struct DevStatus {
+    int err;
+    int rank1;     // first discard step
+    int rank2;     // second discard step
+    int rank;      // nonzero singular values returned
+    int sweeps[4]; // Jacobi sweeps per solve (-1 = cap reached)
+    int bar[4];    // scratch for the Jacobi grid barrier: count, generation
+    int pad[4];
+};
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// ---------------------------------------------------------------- products
+// All tall products accumulate in FP64 (DFMA on the CUDA cores).
+
+// bits[j] = max_i |A_ij| as the bit pattern of a non-negative double
+// (bits must be zeroed first).  The MaxEntry of every column.
+template <typename T>
+cudaError_t launch_colmax(const T *A, i64 m, i64 n, i64 lda, unsigned long long *bits,
+                          cudaStream_t s);
+
+// d[j] = smallest power of two >= max_i |A_ij| (1 for a zero column),
+// dinv[j] = 1 / d[j].
+cudaError_t launch_pow2_scale(const unsigned long long *bits, i64 n, double *d, double *dinv,
+                              cudaStream_t s);
+
+// Split-K partials of C = A^T B: A is K x M (lda), B is K x N (ldb), both
+// row-major.  P holds `splits` slices of M x N.  With upper_only (A == B,
+// M == N) only tiles on or above the diagonal are computed.
+template <typename TA, typename TB>
+cudaError_t launch_tn_partial(const TA *A, i64 lda, const TB *B, i64 ldb, i64 K, i64 M, i64 N,
+                              int splits, bool upper_only, double *P, cudaStream_t s);
+int tn_splits(i64 K, i64 M, i64 N, bool upper_only);
+
+// C[i][j] = rs[i] * cs[j] * sum_s P[s][i][j] (rs, cs may be null); sym:
+// only i <= j is summed and mirrored.  Deterministic (fixed order over s).
+cudaError_t launch_tn_reduce(const double *P, int splits, i64 M, i64 N, const double *rs,
+                             const double *cs, bool sym, double *C, i64 ldc, cudaStream_t s);
+
+// C = A B with A m x K (lda, type TA), B K x N (ldb, FP64); C written as TC
+// when non-null (ldc).  NP[g][j] receives per-CTA-row partial sums of
+// squares of column j of the FP64 product (g < nn_grid_rows(m, N)).
+template <typename TA, typename TC>
+cudaError_t launch_nn(const TA *A, i64 lda, const double *B, i64 ldb, i64 m, i64 K, i64 N,
+                      TC *C, i64 ldc, double *NP, cudaStream_t s);
+int nn_grid_rows(i64 m, i64 N);
+
+// out[j] = sqrt(sum_g NP[g][j]) in fixed order.
+cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
+
+// -------------------------------------------------------------- Jacobi
+// One-sided (Hestenes) Jacobi with a parallel round-robin pair order, as
+// one cooperative kernel with a bounded grid barrier.  X is nr x nc
+// column-major (column j at X + j*ldx), J (nc x nc, column-major) receives
+// the accumulated rotations: X_in J = X_out with orthogonal columns.
+// ctr must point to at least max_sweeps + 4 zeroed ints of device memory.
+cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
+                          int max_sweeps, int *ctr, DevStatus *st, int which,
+                          cudaStream_t s);
+
+// Column norms of the column-major X, stable descending order, and the
+// sorted outputs.  Eigen mode: Vout (nc x nc row-major, column r = J
+// column perm[r]) and lam[r].  SVD mode additionally: Uout (nr x nc
+// row-major, column r = X column perm[r] / sigma_r, 0 when sigma_r = 0).
+cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
+                                   int nc, double *norms, int *perm, double *Jout, i64 ldjo,
+                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s);
+
+// ---------------------------------------------------------- small ops
+// Discard rule: smax = max sig; r = 1 + last j with sig_j > 0 and not
+// (sig_j < smax*tol); inv[j] = 1/sig_j for j < r (0 otherwise).  Writes r
+// to *rank_out.
+cudaError_t launch_discard(const double *sig, i64 n, double tol, double *inv, int *rank_out,
+                           cudaStream_t s);
+// out[i][j] = rs[i] * M[i][j] * cs[j] (rs/cs may be null), rows x cols.
+cudaError_t launch_scale2(const double *M, i64 ldm, i64 rows, i64 cols, const double *rs,
+                          const double *cs, double *out, i64 ldo, cudaStream_t s);
+// G[b][c] = (keep[b] != 0 ? sig[b] : 0) * Vt[c][b] * d[c]  (n x n), keep = inv.
+cudaError_t launch_build_g(const double *sig, const double *keep, const double *Vt, i64 ldv,
+                           const double *d, i64 n, double *G, cudaStream_t s);
+// Sign canonicalisation of the columns of V (rows x cols row-major):
+// sgn[j] = +-1 so that the entry of largest magnitude (lowest index on
+// ties) becomes positive; sgn[j] = 0 when sig[j] == 0.  V is flipped in place.
+cudaError_t launch_signs(double *V, i64 ldv, i64 rows, i64 cols, const double *sig,
+                         double *sgn, cudaStream_t s);
+// rank = number of sig[j] > 0 -> *rank_out.
+cudaError_t launch_count_positive(const double *sig, i64 n, int *rank_out, cudaStream_t s);
+// out[j] = keep[j] != 0 ? val[j] : 0 (val null: 1).
+cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
+                           cudaStream_t s);
+// dst[j][i] = src[i][j] * rs[j] (rs may be null); src rows x cols.
+cudaError_t launch_transpose(const double *src, i64 lds, i64 rows, i64 cols, const double *rs,
+                             double *dst, i64 ldd, cudaStream_t s);
+// n x n core of the thin-SVD adjoint (J, K, dS may be null).
+cudaError_t launch_adjoint_core(const double *J, const double *K, const double *sv,
+                                const double *dS, i64 n, double *M, cudaStream_t s);
+// Conversions to the output type.
+template <typename T>
+cudaError_t launch_convert(const double *src, i64 lds, i64 rows, i64 cols, T *dst, i64 ldd,
+                           cudaStream_t s);
+// U[i][j] *= cs[j] in place (rows x cols, row-major).
+template <typename T>
+cudaError_t launch_scale_cols_inplace(T *U, i64 ldu, i64 rows, i64 cols, const double *cs,
+                                      cudaStream_t s);
+// Copy a row-major matrix of type TS into a double matrix.
+template <typename TS>
+cudaError_t launch_to_double(const TS *src, i64 lds, i64 rows, i64 cols, double *dst, i64 ldd,
+                             cudaStream_t s);
+
+}  // namespace tssvd

@@ -1,0 +1,327 @@
+// One-sided (Hestenes) Jacobi for the n x n eigenproblems and the small
+// SVD of Algorithm 4, in FP64 on the GPU.
+//
+// The paper leaves the small eigensolver open (Algorithms 3 and 4 only ask
+// for "the eigendecomposition" and "the singular value decomposition").
+// Hestenes' method orthogonalises the columns of X by plane rotations
+// J: X J has orthogonal columns.  For a symmetric positive semi-definite X
+// (a Gram matrix) the columns of J are its eigenvectors and the column
+// norms its eigenvalues; for a general X it is an SVD.
+//
+// Parallel order: the round-robin ("circle") schedule pairs all columns in
+// n-1 rounds of n/2 disjoint pairs, so every round's rotations are
+// independent.  One CTA handles one pair at a time (dot products reduced
+// in a fixed order, then the two-column update of X and J); rounds are
+// separated by a grid-wide barrier.  The kernel is launched cooperatively
+// so all CTAs are co-resident, and every wait in the barrier is bounded
+// (about two seconds of %globaltimer); on expiry the kernel sets the error
+// word of the status block and all CTAs return.
+#include "common.cuh"
+
+namespace tssvd {
+
+namespace {
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+// Grid barrier with a bounded wait.  Returns false when the call must be
+// abandoned (this CTA or another timed out).
+__device__ bool grid_barrier(int *count, int *gen, int *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const int my_gen = ld_volatile(gen);
+        __threadfence();
+        const int arrived = atomicAdd(count, 1) + 1;
+        if (arrived == (int)gridDim.x) {
+            atomicExch(count, 0);
+            __threadfence();
+            atomicAdd(gen, 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_volatile(gen) == my_gen) {
+                if (ld_volatile(err) != 0) break;
+                if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicCAS(err, 0, TSSVD_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_volatile(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct JacobiArgs {
+    double *X;
+    i64 ldx;
+    double *J;
+    i64 ldj;
+    int nr, nc, npad;
+    int max_sweeps;
+    double tol;
+    int *rot;  // [max_sweeps] rotation counts
+    DevStatus *st;
+    int which;
+};
+
+template <int NT>
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*red)[NT / 32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = a;
+        red[1][warp] = b;
+        red[2][warp] = c;
+    }
+    __syncthreads();
+    // every thread sums the warp partials in the same fixed order
+    a = 0.0;
+    b = 0.0;
+    c = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) {
+        a += red[0][w];
+        b += red[1][w];
+        c += red[2][w];
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
+{
+    __shared__ double red[3][NT / 32];
+    const int npairs = p.npad / 2;
+    const int rounds = p.npad - 1;
+    const double tol = p.tol;
+    int local_rot = 0;
+    int done = -1;
+    int *bar_count = &p.st->bar[0];
+    int *bar_gen = &p.st->bar[1];
+    for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
+        for (int t = 0; t < rounds; t++) {
+            for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+                const int a = pr, b = p.npad - 1 - pr;
+                int P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
+                int Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
+                if (P > Q) {
+                    int tmp = P;
+                    P = Q;
+                    Q = tmp;
+                }
+                if (Q >= p.nc) continue;  // the padding column of an odd nc
+                double *xp = p.X + (i64)P * p.ldx;
+                double *xq = p.X + (i64)Q * p.ldx;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = threadIdx.x; i < p.nr; i += NT) {
+                    const double u = __ldcg(xp + i), v = __ldcg(xq + i);
+                    al = fma(u, u, al);
+                    be = fma(v, v, be);
+                    ga = fma(u, v, ga);
+                }
+                block_sum3<NT>(al, be, ga, red);
+                __syncthreads();  // red is reused by the next pair
+                if (ga == 0.0 || !(fabs(ga) > tol * sqrt(al * be))) continue;
+                // tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0,
+                // which annihilates the (P,Q) inner product.
+                const double zeta = (be - al) / (2.0 * ga);
+                double tt;
+                if (fabs(zeta) > 1e150)
+                    tt = 0.5 / zeta;
+                else
+                    tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + tt * tt);
+                const double s = c * tt;
+                if (threadIdx.x == 0) local_rot++;
+                for (int i = threadIdx.x; i < p.nr; i += NT) {
+                    const double u = __ldcg(xp + i), v = __ldcg(xq + i);
+                    __stcg(xp + i, c * u - s * v);
+                    __stcg(xq + i, s * u + c * v);
+                }
+                double *jp = p.J + (i64)P * p.ldj;
+                double *jq = p.J + (i64)Q * p.ldj;
+                for (int i = threadIdx.x; i < p.nc; i += NT) {
+                    const double u = __ldcg(jp + i), v = __ldcg(jq + i);
+                    __stcg(jp + i, c * u - s * v);
+                    __stcg(jq + i, s * u + c * v);
+                }
+            }
+            if (t == rounds - 1 && threadIdx.x == 0 && local_rot != 0) {
+                atomicAdd(p.rot + sweep, local_rot);
+                local_rot = 0;
+            }
+            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+        }
+        if (ld_volatile(p.rot + sweep) == 0) {
+            done = sweep + 1;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.st->sweeps[p.which] = done;
+}
+
+__global__ void init_identity_kernel(double *J, i64 ldj, int nc)
+{
+    const i64 total = (i64)nc * nc;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (i64)gridDim.x * blockDim.x) {
+        const i64 c = e / nc, r = e % nc;
+        J[c * ldj + r] = (r == c) ? 1.0 : 0.0;
+    }
+}
+
+// One warp per column: norm of column j of the column-major X.
+__global__ void colnorm_cm_kernel(const double *X, i64 ldx, int nr, int nc, double *norms)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nc) return;
+    const double *x = X + (i64)warp * ldx;
+    double s = 0.0;
+    for (int i = lane; i < nr; i += 32) s = fma(x[i], x[i], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (lane == 0) norms[warp] = sqrt(s);
+}
+
+// perm[rank] = j with rank = #{i : n_i > n_j or (n_i == n_j and i < j)}:
+// a stable sort into decreasing order.
+__global__ void rank_sort_kernel(const double *norms, int nc, int *perm)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
+        // NaN sorts last (norms are otherwise >= 0), so the order is total
+        // and perm is a permutation.
+        const double v = isnan(norms[j]) ? -1.0 : norms[j];
+        int r = 0;
+        for (int i = 0; i < nc; i++) {
+            const double w = isnan(norms[i]) ? -1.0 : norms[i];
+            r += (w > v) || (w == v && i < j);
+        }
+        perm[r] = j;
+    }
+}
+
+__global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
+                                   int nc, const double *norms, const int *perm, double *Jout,
+                                   i64 ldjo, double *lam, double *Xout, i64 ldxo)
+{
+    const i64 tj = (i64)nc * nc;
+    const i64 tx = Xout ? (i64)nr * nc : 0;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tj + tx;
+         e += (i64)gridDim.x * blockDim.x) {
+        if (e < tj) {
+            const i64 i = e / nc, r = e % nc;  // row i, output column r
+            int src = perm[r];
+            if (src < 0 || src >= nc) src = (int)r;
+            Jout[i * ldjo + r] = J[(i64)src * ldj + i];
+            if (i == 0 && lam) lam[r] = norms[src];
+        } else {
+            const i64 f = e - tj;
+            const i64 i = f / nc, r = f % nc;
+            int src = perm[r];
+            if (src < 0 || src >= nc) src = (int)r;
+            const double s = norms[src];
+            Xout[i * ldxo + r] = (s > 0.0) ? X[(i64)src * ldx + i] / s : 0.0;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc, int max_sweeps,
+                          int *ctr, DevStatus *st, int which, cudaStream_t s)
+{
+    cudaError_t e;
+    {
+        i64 total = (i64)nc * nc;
+        i64 blocks = (total + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        if (blocks < 1) blocks = 1;
+        init_identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(J, ldj, nc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(int) * (size_t)(max_sweeps + 4), s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(&st->bar[0], 0, sizeof(int) * 4, s)) != cudaSuccess) return e;
+    if (nc < 2) {
+        // nothing to rotate: a single column is already "orthogonal"
+        return cudaMemsetAsync(&st->sweeps[which], 0, sizeof(int), s);
+    }
+
+    JacobiArgs a;
+    a.X = X;
+    a.ldx = ldx;
+    a.J = J;
+    a.ldj = ldj;
+    a.nr = nr;
+    a.nc = nc;
+    a.npad = nc + (nc & 1);
+    a.max_sweeps = max_sweeps;
+    a.tol = (double)nr * 0x1p-53;
+    a.rot = ctr;
+    a.st = st;
+    a.which = which;
+
+    constexpr int NT = 128;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<NT>, NT, 0)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int npairs = a.npad / 2;
+    int blocks = num_sms() * per_sm;
+    if (blocks > npairs) blocks = npairs;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
+                                       args, 0, s);
+}
+
+cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
+                                   int nc, double *norms, int *perm, double *Jout, i64 ldjo,
+                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s)
+{
+    cudaError_t e;
+    {
+        const int warps_per_block = 8;
+        const int blocks = (nc + warps_per_block - 1) / warps_per_block;
+        colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(X, ldx, nr, nc, norms);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    rank_sort_kernel<<<(nc + 255) / 256, 256, 0, s>>>(norms, nc, perm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        i64 total = (i64)nc * nc + (Xout ? (i64)nr * nc : 0);
+        i64 blocks = (total + 255) / 256;
+        if (blocks > (i64)num_sms() * 8) blocks = (i64)num_sms() * 8;
+        if (blocks < 1) blocks = 1;
+        permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, J, ldj, nr, nc, norms, perm,
+                                                            Jout, ldjo, lam, Xout, ldxo);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tssvd
