@@ -69,7 +69,7 @@ typedef struct {
      * working precision (Remark "working"). */
     double drop_tol;
     int mode;       /* tssvd_mode */
-    int max_sweeps; /* Jacobi sweep cap per eigen/SVD solve (default 30) */
+    int max_sweeps; /* Jacobi sweep cap per eigen/SVD solve (default 50) */
     void *stream;   /* cudaStream_t */
     void *workspace;
     size_t workspace_bytes;
@@ -80,7 +80,7 @@ typedef struct {
 } tssvd_opts;
 
 /* Fills *opts with the defaults: passes 2, scale 1, drop_tol sqrt(1e-11),
- * mode TSSVD_FP64, max_sweeps 30, default stream, internal workspace. */
+ * mode TSSVD_FP64, max_sweeps 50, default stream, internal workspace. */
 void tssvd_default_opts(tssvd_opts *opts);
 
 /* Human-readable text for a status code (static storage). */

@@ -29,6 +29,8 @@ def lib():
         L.or_maxentry_scale.argtypes = [_dp, _i64, _i64, _i64, _dp]
         L.or_jacobi.argtypes = [_dp, _i64, _i64, _i64, _dp, _i64, _dp, ctypes.c_int]
         L.or_jacobi.restype = ctypes.c_int
+        L.or_jacobi_eig.argtypes = [_dp, _i64, _i64, _dp, _i64, _dp, ctypes.c_int]
+        L.or_jacobi_eig.restype = ctypes.c_int
         L.or_ts_svd1.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_double, ctypes.c_int,
                                  _dp, _i64, _dp, _dp, _i64, _lp]
         L.or_ts_svd1.restype = ctypes.c_int
@@ -63,7 +65,7 @@ def _c(a):
 # Paper default for the discard threshold: square root of a working
 # precision of 1e-11 (Remark "working"; Algorithms 3 and 4, discard steps).
 PAPER_DROP_TOL = 1e-11 ** 0.5
-MAX_SWEEPS = 30
+MAX_SWEEPS = 50
 
 
 def num_threads():
@@ -120,6 +122,16 @@ def jacobi(X, max_sweeps=MAX_SWEEPS):
     s = np.zeros(nc)
     sw = lib().or_jacobi(_p(X), nr, nc, nc, _p(J), nc, _p(s), int(max_sweeps))
     return X, J, s, sw
+
+
+def jacobi_eig(B, max_sweeps=MAX_SWEEPS):
+    """Gram-form Jacobi eigendecomposition: returns (lam, V, B_rot, sweeps)."""
+    B = _c(B).copy()
+    n = B.shape[0]
+    V = np.zeros((n, n))
+    lam = np.zeros(n)
+    sw = lib().or_jacobi_eig(_p(B), n, n, _p(V), n, _p(lam), int(max_sweeps))
+    return lam, V, B, sw
 
 
 def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, max_sweeps=MAX_SWEEPS,

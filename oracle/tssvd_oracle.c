@@ -24,7 +24,10 @@
  *    cyclic Jacobi with row-cyclic pair order.  A pair (p,q) is rotated when
  *    |x_p . x_q| > tol * sqrt(|x_p|^2 |x_q|^2), tol = nrows * 2^-53; the
  *    iteration stops after a sweep with no rotation, or after max_sweeps.
- *    Results are sorted by decreasing column norm, ties by original index.
+ *    For the two Gram eigenproblems the method runs in Gram form (the
+ *    inner products are the entries of the Gram matrix itself, see
+ *    or_jacobi_eig); the SVD of R runs on the columns of R^T.  Results are
+ *    sorted in decreasing order, ties by original index.
  *  - MaxEntry column scaling (an addition to the paper's method): column j
  *    of A is divided by d_j, the smallest power of two >= max_i |A_ij|
  *    (d_j = 1 for a zero column).  It applies to the two-pass algorithm
@@ -286,6 +289,93 @@ int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
     return sweeps_done;
 }
 
+/*
+ * Eigendecomposition of a symmetric positive semi-definite B (n x n, ldb)
+ * by one-sided Jacobi in Gram form: B is taken as the Gram matrix of an
+ * implicit matrix X (B = X^T X), and the rotation of pair (p,q) is the one
+ * that orthogonalises columns p and q of X, computed from b_pp, b_qq, b_pq
+ * and applied as B <- J^T B J (so b_pq becomes 0, b_pp <- b_pp - t b_pq,
+ * b_qq <- b_qq + t b_pq).  Rotations accumulate in V (n x n, ldv, set to I
+ * here).  Same rotation test and stopping rule as or_jacobi with
+ * tol = n * 2^-53 (relative to sqrt(|b_pp b_qq|)).  On return lam holds the
+ * diagonal of the rotated B sorted in decreasing order (stable), V's
+ * columns are permuted to match, and B holds the rotated matrix (unsorted).
+ * Returns the number of sweeps, or -1 if the cap was reached.
+ */
+int or_jacobi_eig(double *B, i64 n, i64 ldb, double *V, i64 ldv, double *lam,
+                  int max_sweeps)
+{
+    const double tol = (double)n * ldexp(1.0, -53);
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) V[i * ldv + j] = (i == j) ? 1.0 : 0.0;
+    int sweeps_done = -1;
+    for (int sweep = 1; sweep <= max_sweeps; sweep++) {
+        i64 rotations = 0;
+        for (i64 p = 0; p < n - 1; p++) {
+            for (i64 q = p + 1; q < n; q++) {
+                double a = B[p * ldb + p], b = B[q * ldb + q], g = B[p * ldb + q];
+                if (g == 0.0 || !(fabs(g) > tol * sqrt(fabs(a * b)))) continue;
+                rotations++;
+                double zeta = (b - a) / (2.0 * g);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
+                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double sn = c * t;
+                /* B <- B J (columns p, q), then B <- J^T B (rows p, q). */
+                for (i64 k = 0; k < n; k++) {
+                    double bp = B[k * ldb + p], bq = B[k * ldb + q];
+                    B[k * ldb + p] = c * bp - sn * bq;
+                    B[k * ldb + q] = sn * bp + c * bq;
+                }
+                for (i64 k = 0; k < n; k++) {
+                    double bp = B[p * ldb + k], bq = B[q * ldb + k];
+                    B[p * ldb + k] = c * bp - sn * bq;
+                    B[q * ldb + k] = sn * bp + c * bq;
+                }
+                /* the 2 x 2 block in closed form */
+                B[p * ldb + p] = a - t * g;
+                B[q * ldb + q] = b + t * g;
+                B[p * ldb + q] = 0.0;
+                B[q * ldb + p] = 0.0;
+                for (i64 k = 0; k < n; k++) {
+                    double vp = V[k * ldv + p], vq = V[k * ldv + q];
+                    V[k * ldv + p] = c * vp - sn * vq;
+                    V[k * ldv + q] = sn * vp + c * vq;
+                }
+            }
+        }
+        if (rotations == 0) {
+            sweeps_done = sweep;
+            break;
+        }
+    }
+    /* stable sort by decreasing diagonal */
+    i64 *idx = (i64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(i64));
+    double *dg = dalloc(n), *tv = dalloc(n * n);
+    for (i64 j = 0; j < n; j++) {
+        idx[j] = j;
+        dg[j] = B[j * ldb + j];
+    }
+    for (i64 a = 1; a < n; a++) {
+        i64 key = idx[a];
+        i64 b = a - 1;
+        while (b >= 0 && dg[idx[b]] < dg[key]) {
+            idx[b + 1] = idx[b];
+            b--;
+        }
+        idx[b + 1] = key;
+    }
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) tv[i * n + j] = V[i * ldv + idx[j]];
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) V[i * ldv + j] = tv[i * n + j];
+    for (i64 j = 0; j < n; j++) lam[j] = dg[idx[j]];
+    free(idx);
+    free(dg);
+    free(tv);
+    return sweeps_done;
+}
+
 /* Flip V column j (n rows) and U column j (m rows) so that V's entry of
  * largest magnitude (lowest index on ties) is positive. */
 static void canonical_signs(double *U, i64 m, i64 ldu, double *V, i64 n,
@@ -340,7 +430,7 @@ int or_ts_svd1(const double *A, i64 m, i64 n, i64 lda, double drop_tol,
     /* Form the Gram matrix B = A^T A. */
     or_gram(A, m, n, lda, B, n);
     /* Eigendecomposition B = V D V^T. */
-    if (or_jacobi(B, n, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
+    if (or_jacobi_eig(B, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
     /* U~ = A V. */
     or_matmul(A, m, n, lda, Vt, n, n, Ut, n);
     /* Sigma = Euclidean norms of the columns of U~. */
@@ -402,7 +492,7 @@ int or_ts_svd2(const double *A, i64 m, i64 n, i64 lda, int scale,
     /* B = A^T A. */
     or_gram(As, m, n, n, B, n);
     /* B = V~ D~ V~^T. */
-    if (or_jacobi(B, n, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
+    if (or_jacobi_eig(B, n, n, Vt, n, lam, max_sweeps) < 0) status = OR_ENOCONV;
     /* Y~ = A V~. */
     or_matmul(As, m, n, n, Vt, n, n, Yt, n);
     /* Sigma~ = column norms of Y~. */
@@ -423,7 +513,7 @@ int or_ts_svd2(const double *A, i64 m, i64 n, i64 lda, int scale,
     /* Z = Y^T Y; Z = W D W^T. */
     double *Z = dalloc(r * r), *W = dalloc(r * r), *mu = dalloc(r);
     or_gram(Y, m, r, r, Z, r);
-    if (or_jacobi(Z, r, r, r, W, r, mu, max_sweeps) < 0) status = OR_ENOCONV;
+    if (or_jacobi_eig(Z, r, r, W, r, mu, max_sweeps) < 0) status = OR_ENOCONV;
     /* Q~ = Y W; T = column norms of Q~. */
     double *Qt = dalloc(m * r), *T = dalloc(r);
     or_matmul(Y, m, r, r, W, r, r, Qt, r);

@@ -93,7 +93,7 @@ def exported_symbols():
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward"]
 
 
-def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
           stream=None, workspace=None):
     o = _Opts()
     lib().tssvd_default_opts(ctypes.byref(o))
@@ -152,7 +152,7 @@ def lowrank_svd_workspace_size(m, n, l, **kw):
     return int(lib().lowrank_svd_workspace_size(m, n, l, ctypes.byref(o)))
 
 
-def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
            stream=None, workspace=None, out=None):
     """Thin SVD of a tall-skinny CUDA tensor A (m x n, float64 or float32).
 
@@ -177,7 +177,7 @@ def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sw
     return U, S, V, _info(o, rc)
 
 
-def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=30,
+def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
                 stream=None, workspace=None):
     """Rank-k SVD by Algorithm 8.  A (m x n) and Omega (n x l) float64 CUDA
     tensors.  Returns (U m x k, S k, V n x k, info)."""

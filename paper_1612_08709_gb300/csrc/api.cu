@@ -108,6 +108,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
     double *cs = ws.take<double>(n);
     int *perm = ws.take<int>(n);
+    double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
     double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
     if (sizing) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
@@ -117,11 +118,9 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         // B = A^T A.
         CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, B, n, s));
-        // B = V D V^T.
-        CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 0, s));
-        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Vt, n, lam, nullptr,
-                                  0, s));
+        // B = V D V^T (Gram-form Jacobi; B is rotated in place).
+        CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+                             s));
         // U~ = A V, Sigma = explicit column norms of U~ (Remark "normalizing").
         CK(launch_nn<T, TO>(A, lda, Vt, n, m, n, n, U, ldu, NP, s));
         CK(launch_norms_reduce(NP, gy, n, sig, s));
@@ -151,11 +150,8 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     // B = (A D^-1)^T (A D^-1).
     CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
     CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
-    // B = V~ D~ V~^T.
-    CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 0, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Vt, n, lam, nullptr, 0,
-                              s));
+    // B = V~ D~ V~^T (Gram-form Jacobi; B is rotated in place).
+    CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
@@ -170,10 +166,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
     CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
     // Z = W D W^T.
-    CK(cudaMemcpyAsync(Xw, B, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 1, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, W, n, lam, nullptr, 0,
-                              s));
+    CK(launch_jacobi_eig(B, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
     // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
     CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
@@ -383,7 +376,7 @@ void tssvd_default_opts(tssvd_opts *o)
     o->scale = 1;
     o->drop_tol = sqrt(1e-11);
     o->mode = TSSVD_FP64;
-    o->max_sweeps = 30;
+    o->max_sweeps = 50;
 }
 
 const char *tssvd_status_string(int st)

@@ -75,6 +75,16 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
                           int max_sweeps, int *ctr, DevStatus *st, int which,
                           cudaStream_t s);
 
+// Eigendecomposition of the symmetric B (n x n row-major, rotated in place)
+// by Gram-form Jacobi, same pair schedule and barrier.  V (n x n,
+// column-major) accumulates the rotations; on return lam holds the
+// eigenvalues (diagonal of the rotated B) in decreasing order and Vout
+// (row-major, ldvo) the matching eigenvectors as columns.  prm: scratch of
+// 4 * ceil(n/2) doubles; perm: n ints; ctr as for launch_jacobi.
+cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *lam, double *Vout,
+                              i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
+                              int *perm, DevStatus *st, int which, cudaStream_t s);
+
 // Column norms of the column-major X, stable descending order, and the
 // sorted outputs.  Eigen mode: Vout (nc x nc row-major, column r = J
 // column perm[r]) and lam[r].  SVD mode additionally: Uout (nr x nc

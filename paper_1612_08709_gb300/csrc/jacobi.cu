@@ -181,6 +181,167 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
     if (blockIdx.x == 0 && threadIdx.x == 0) p.st->sweeps[p.which] = done;
 }
 
+// ------------------------------------------------------------------
+// Gram-form Jacobi for the symmetric eigenproblems (Gram matrices).
+//
+// B (n x n, row-major, symmetric) is the Gram matrix of an implicit X; the
+// rotation of pair (P,Q) orthogonalises columns P and Q of X and is
+// computed from b_PP, b_QQ, b_PQ alone.  A round of the circle schedule
+// applies all n/2 rotations at once as B <- J^T B J:
+//   phase A: the CTA of each pair computes (c, s, t) from its own 2 x 2
+//            block and publishes them;            -- grid barrier --
+//   phase B: the CTA of pair (P,Q) rewrites rows P and Q of B (each
+//            2 x 2 block B[{P,Q},{K,K'}] becomes G_PQ^T B G_KK') and
+//            columns P and Q of V;                 -- grid barrier --
+// Rows P and Q of the new B depend only on rows P and Q of the old B, so
+// the update is in place and race-free.
+struct EigArgs {
+    double *B;
+    i64 ldb;
+    double *V;  // column-major n x n
+    i64 ldv;
+    double4 *prm;  // [npairs] (c, s, t, rotate)
+    int n, npad;
+    int max_sweeps;
+    double tol;
+    int *rot;
+    DevStatus *st;
+    int which;
+};
+
+__device__ __forceinline__ double4 ld4cg(const double4 *p)
+{
+    const double2 a = __ldcg((const double2 *)p), b = __ldcg((const double2 *)p + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ void st4cg(double4 *p, double4 v)
+{
+    __stcg((double2 *)p, make_double2(v.x, v.y));
+    __stcg((double2 *)p + 1, make_double2(v.z, v.w));
+}
+
+__device__ __forceinline__ void circle_pair(int pr, int t, int npad, int &P, int &Q)
+{
+    const int rounds = npad - 1;
+    const int a = pr, b = npad - 1 - pr;
+    P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
+    Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
+    if (P > Q) {
+        int tmp = P;
+        P = Q;
+        Q = tmp;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
+{
+    const int npairs = p.npad / 2;
+    const int rounds = p.npad - 1;
+    const int n = p.n;
+    int local_rot = 0;
+    int done = -1;
+    int *bar_count = &p.st->bar[0];
+    int *bar_gen = &p.st->bar[1];
+    for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
+        for (int t = 0; t < rounds; t++) {
+            // ---- phase A: rotation of each pair from its 2 x 2 block
+            if (threadIdx.x == 0) {
+                for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+                    int P, Q;
+                    circle_pair(pr, t, p.npad, P, Q);
+                    double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
+                    if (Q < n) {
+                        const double a = __ldcg(p.B + (i64)P * p.ldb + P);
+                        const double b = __ldcg(p.B + (i64)Q * p.ldb + Q);
+                        const double g = __ldcg(p.B + (i64)P * p.ldb + Q);
+                        if (g != 0.0 && fabs(g) > p.tol * sqrt(fabs(a * b))) {
+                            const double zeta = (b - a) / (2.0 * g);
+                            double tt;
+                            if (fabs(zeta) > 1e150)
+                                tt = 0.5 / zeta;
+                            else
+                                tt = (zeta >= 0.0 ? 1.0 : -1.0) /
+                                     (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                            const double c = 1.0 / sqrt(1.0 + tt * tt);
+                            r = make_double4(c, c * tt, tt, 1.0);
+                            local_rot++;
+                        }
+                    }
+                    st4cg(p.prm + pr, r);
+                }
+            }
+            if (t == rounds - 1 && threadIdx.x == 0 && local_rot != 0) {
+                atomicAdd(p.rot + sweep, local_rot);
+                local_rot = 0;
+            }
+            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+            // ---- phase B: rows P, Q of J^T B J and columns P, Q of V J
+            for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+                int P, Q;
+                circle_pair(pr, t, p.npad, P, Q);
+                const double4 me = ld4cg(p.prm + pr);
+                const bool hasQ = Q < n;
+                double *rP = p.B + (i64)P * p.ldb;
+                double *rQ = hasQ ? p.B + (i64)Q * p.ldb : nullptr;
+                const double c = me.x, s = me.y;
+                for (int k = threadIdx.x; k < npairs; k += NT) {
+                    int K, K2;
+                    circle_pair(k, t, p.npad, K, K2);
+                    const bool hasK2 = K2 < n;
+                    if (k == pr) {
+                        if (me.w != 0.0) {
+                            const double a = __ldcg(rP + P), b = __ldcg(rQ + Q);
+                            const double g = __ldcg(rP + Q);
+                            __stcg(rP + P, a - me.z * g);
+                            __stcg(rQ + Q, b + me.z * g);
+                            __stcg(rP + Q, 0.0);
+                            __stcg(rQ + P, 0.0);
+                        }
+                        continue;
+                    }
+                    const double4 o = ld4cg(p.prm + k);
+                    double x = __ldcg(rP + K), y = hasK2 ? __ldcg(rP + K2) : 0.0;
+                    double z = hasQ ? __ldcg(rQ + K) : 0.0;
+                    double w = (hasQ && hasK2) ? __ldcg(rQ + K2) : 0.0;
+                    // rows (own rotation), then columns (the other pair's)
+                    const double x1 = c * x - s * z, y1 = c * y - s * w;
+                    const double z1 = s * x + c * z, w1 = s * y + c * w;
+                    const double ck = o.x, sk = o.y;
+                    __stcg(rP + K, ck * x1 - sk * y1);
+                    if (hasK2) __stcg(rP + K2, sk * x1 + ck * y1);
+                    if (hasQ) {
+                        __stcg(rQ + K, ck * z1 - sk * w1);
+                        if (hasK2) __stcg(rQ + K2, sk * z1 + ck * w1);
+                    }
+                }
+                if (me.w != 0.0) {
+                    double *vp = p.V + (i64)P * p.ldv;
+                    double *vq = p.V + (i64)Q * p.ldv;
+                    for (int i = threadIdx.x; i < n; i += NT) {
+                        const double u = __ldcg(vp + i), v = __ldcg(vq + i);
+                        __stcg(vp + i, c * u - s * v);
+                        __stcg(vq + i, s * u + c * v);
+                    }
+                }
+            }
+            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+        }
+        if (ld_volatile(p.rot + sweep) == 0) {
+            done = sweep + 1;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.st->sweeps[p.which] = done;
+}
+
+__global__ void diag_kernel(const double *B, i64 ldb, int n, double *d)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) d[j] = B[(i64)j * ldb + j];
+}
+
 __global__ void init_identity_kernel(double *J, i64 ldj, int nc)
 {
     const i64 total = (i64)nc * nc;
@@ -298,6 +459,69 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
                                        args, 0, s);
+}
+
+cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *lam, double *Vout,
+                              i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
+                              int *perm, DevStatus *st, int which, cudaStream_t s)
+{
+    cudaError_t e;
+    {
+        i64 total = (i64)n * n;
+        i64 blocks = (total + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        if (blocks < 1) blocks = 1;
+        init_identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(V, ldv, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(int) * (size_t)(max_sweeps + 4), s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(&st->bar[0], 0, sizeof(int) * 4, s)) != cudaSuccess) return e;
+    if (n >= 2) {
+        EigArgs a;
+        a.B = B;
+        a.ldb = ldb;
+        a.V = V;
+        a.ldv = ldv;
+        a.prm = (double4 *)prm;
+        a.n = n;
+        a.npad = n + (n & 1);
+        a.max_sweeps = max_sweeps;
+        a.tol = (double)n * 0x1p-53;
+        a.rot = ctr;
+        a.st = st;
+        a.which = which;
+        constexpr int NT = 128;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_eig_kernel<NT>, NT,
+                                                                0)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+        int npairs = a.npad / 2;
+        int blocks = num_sms() * per_sm;
+        if (blocks > npairs) blocks = npairs;
+        void *args[] = {&a};
+        if ((e = cudaLaunchCooperativeKernel((const void *)jacobi_eig_kernel<NT>, dim3(blocks),
+                                             dim3(NT), args, 0, s)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = cudaMemsetAsync(&st->sweeps[which], 0, sizeof(int), s)) != cudaSuccess) return e;
+    }
+    // the rotation-parameter scratch (>= 2n doubles) now holds the diagonal
+    double *dg = prm;
+    diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(B, ldb, n, dg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    rank_sort_kernel<<<(n + 255) / 256, 256, 0, s>>>(dg, n, perm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        i64 total = (i64)n * n;
+        i64 blocks = (total + 255) / 256;
+        if (blocks > (i64)num_sms() * 8) blocks = (i64)num_sms() * 8;
+        if (blocks < 1) blocks = 1;
+        permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(nullptr, 0, V, ldv, 0, n, dg, perm,
+                                                            Vout, ldvo, lam, nullptr, 0);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,

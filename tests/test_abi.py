@@ -50,7 +50,7 @@ def test_default_opts_and_status_strings_without_gpu():
     L = pkg.lib()
     o = _Opts()
     L.tssvd_default_opts(ctypes.byref(o))
-    assert o.passes == 2 and o.scale == 1 and o.max_sweeps == 30
+    assert o.passes == 2 and o.scale == 1 and o.max_sweeps == 50
     assert abs(o.drop_tol - 1e-11 ** 0.5) < 1e-20
     assert L.tssvd_status_string(0) == b"ok"
     assert b"invalid" in L.tssvd_status_string(-3)

@@ -55,7 +55,7 @@ def compare_svd(A, got, ref, s_tol=1e-11, v_tol=1e-10, o_tol=1e-12, check_vector
     assert np.abs(A @ V[:, :r] - U[:, :r] * S[:r]).max() <= 10 * s_tol * s1
     if check_vectors:
         g = gaps(Sr[:r])
-        tolv = np.minimum(v_tol * s1 / g, 1.0)
+        tolv = np.clip(v_tol * s1 / g, 1e-13, 1.0)
         ev = col_err_up_to_sign(V[:, :r], Vr[:, :r])
         eu = col_err_up_to_sign(U[:, :r], Ur[:, :r])
         assert np.all(ev <= tolv), (ev / tolv).max()
@@ -93,7 +93,9 @@ def test_ts_svd_fp64_matches_oracle(orc, m, n, seed, passes, scale):
     ref = orc.ts_svd(A, passes=passes, scale=scale, drop_tol=0.0)
     got, info = run_gpu(A, passes=passes, scale=scale, drop_tol=0.0)
     assert info["rank"] == ref[3] and info["status"] == ref[4]
-    o_tol = 1e-12 if passes == 2 else 1e-6
+    # Algorithm 3 is orthonormal only to ~eps * kappa^2; hold the GPU to the
+    # oracle's own level there.
+    o_tol = 1e-12 if passes == 2 else max(1e-12, 100 * orth(ref[0][:, :ref[3]]))
     compare_svd(A, got, ref[:4], o_tol=o_tol, check_vectors=(passes == 2))
 
 
@@ -133,7 +135,8 @@ def test_ts_svd_rank_deficient(orc):
         got, info = run_gpu(A, passes=passes)
         assert info["rank"] == ref[3] == 22
         assert info["status"] == ref[4] == 2
-        compare_svd(A, got, ref[:4], o_tol=1e-12 if passes == 2 else 1e-6,
+        compare_svd(A, got, ref[:4],
+                    o_tol=1e-12 if passes == 2 else max(1e-12, 100 * orth(ref[0][:, :22])),
                     check_vectors=(passes == 2))
 
 
@@ -197,7 +200,7 @@ def test_lowrank_matches_oracle(orc, m, n, k, l, iters, seed):
     assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
     assert orth(U) <= 1e-12 and orth(V) <= 1e-12
     g = gaps(Sr)
-    tolv = np.minimum(1e-9 * Sr[0] / g, 1.0)
+    tolv = np.clip(1e-9 * Sr[0] / g, 1e-13, 1.0)
     assert np.all(col_err_up_to_sign(V, Vr) <= tolv)
     assert np.all(col_err_up_to_sign(U, Ur) <= tolv)
 

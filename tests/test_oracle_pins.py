@@ -101,6 +101,32 @@ def test_jacobi_symmetric_eig_matches_lapack(orc):
     assert np.abs(B @ J - J * lam).max() < 1e-11 * w[0]
 
 
+def test_jacobi_gram_form_eig_matches_lapack(orc):
+    """Gram-form Jacobi on B = G^T G (the eigendecomposition steps of
+    Algorithms 3 and 4) against LAPACK's symmetric eigensolver."""
+    rng = np.random.default_rng(41)
+    G = rng.standard_normal((60, 14)) * np.logspace(0, -3, 14)
+    B = G.T @ G
+    lam, V, Brot, sweeps = orc.jacobi_eig(B)
+    assert sweeps > 0
+    w, Q = np.linalg.eigh(B)
+    w, Q = w[::-1], Q[:, ::-1]
+    assert np.abs(lam - w).max() < 1e-14 * w[0]
+    assert np.abs(V.T @ V - np.eye(14)).max() < 1e-14
+    assert match_columns_up_to_sign(V, Q) < 1e-9
+    assert np.abs(B @ V - V * lam).max() < 1e-13 * w[0]
+
+
+def test_jacobi_gram_form_converges_on_singular_gram(orc):
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((2000, 24))
+    A[:, 5] = 0.0
+    A[:, 17] = 2.0 * A[:, 3]
+    lam, V, _, sweeps = orc.jacobi_eig(orc.gram(A))
+    assert 0 < sweeps < 20
+    assert abs(lam[-1]) < 1e-12 * lam[0] and abs(lam[-2]) < 1e-12 * lam[0]
+
+
 def test_jacobi_sweep_cap_reports_nonconvergence(orc):
     rng = np.random.default_rng(5)
     X = rng.standard_normal((20, 12))
