@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 TS-SVD / low-rank SVD library.
+
+One step = one full call of the hot path on one batch of synthetic input:
+by default the two-pass Gram TS-SVD (Algorithm 4 with MaxEntry scaling) of
+a 2,000,000 x 200 FP64 matrix A = U diag(sigma) V^T with seeded
+orthonormal factors and sigma geometric from 1 to 1e-8.
+
+Prints one JSON line (rank 0).  `value` is GFLOP/s of the algorithm's
+nominal products (8 m n^2 for two passes: Gram A^T A, A V~, Gram Y^T Y,
+Y W and Q P) with A resident in HBM; `e2e` is the same metric through the
+same C-ABI call with host buffers (copies inside the timed region).
+`--impl reference` times the FP64 CPU oracle instead (bounded samples of
+the same workload on the host cores).
+
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (weak scaling, no collective on the data path).
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TS-SVD & rank-k SVD GFLOP/s, % of GB300 roofline, vs plain FP64 at equal accuracy"
+
+WORKLOADS = {
+    # tall-skinny SVD at scale (2,000,000 x 200 and 1,000,000 x 1,000)
+    "ts_2m_x_200": dict(kind="ts", m=2_000_000, n=200, lo=1e-8, seed=2),
+    "ts_1m_x_1000": dict(kind="ts", m=1_000_000, n=1000, lo=1e-8, seed=3),
+    # the small plain case (20,000 x 50, sigma 1..1e-6)
+    "ts_20k_x_50": dict(kind="ts", m=20_000, n=50, lo=1e-6, seed=1),
+}
+
+# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the
+# recipe's unit count and maximum SM clock); the DFMA probe measured 1.20.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ts_2m_x_200", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-rows", type=int, default=200_000,
+                    help="rows of the bounded host sample the oracle is timed on")
+    return ap.parse_args()
+
+
+def nominal_flops(w):
+    m, n = w["m"], w["n"]
+    return 8.0 * m * n * n
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=5)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                mhz.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def host_sample(w, rows):
+    import numpy as np
+    import workloads
+    s = workloads.sigma_geometric(w["n"], w["lo"])
+    A, _, _, _ = workloads.known_spectrum(rows, w["n"], s, w["seed"])
+    return A
+
+
+def time_oracle(w, rows, reps=1):
+    import oracle
+    A = host_sample(w, rows)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+    dt = (time.perf_counter() - t0) / reps
+    flops = 8.0 * rows * w["n"] ** 2
+    return flops / dt / 1e9, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    rows = min(args.cpu_rows, w["m"])
+    for _ in range(max(0, min(args.warmup, 1))):
+        time_oracle(w, min(rows, 20000))
+    vals, dts = [], []
+    cores = None
+    for _ in range(args.steps):
+        v, dt, cores = time_oracle(w, rows)
+        vals.append(v)
+        dts.append(dt)
+    value = statistics.mean(vals)
+    sample = "%d x %d rows of the same recipe per step (of %d x %d)" % (rows, w["n"], w["m"],
+                                                                      w["n"])
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.mean(dts), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "passes": 2,
+                      "scale": 1, "mode": "fp64-cpu-oracle"},
+           "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# -------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1612_08709_gb300 as pkg
+    import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    m, n = w["m"], w["n"]
+    L = pkg.lib()
+
+    # input A = U diag(sigma) V^T, built on the device (torch QR of seeded
+    # Gaussians); each rank its own replica seed
+    sigma = workloads.sigma_geometric(n, w["lo"])
+    A, U0, s0, V0 = workloads.known_spectrum_torch(m, n, sigma, w["seed"] + 1000 * rank, dev)
+    del U0, V0
+    U = torch.empty((m, n), dtype=torch.float64, device=dev)
+    S = torch.empty((n,), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    wsb = pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode=args.mode)
+    ws = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+    kw = dict(passes=2, scale=True, drop_tol=0.0, mode=args.mode, workspace=ws, out=(U, S, V))
+
+    def step():
+        return pkg.ts_svd(A, **kw)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    # per-kernel CUDA events over the timed region (recorded by the library
+    # on the stream each kernel is launched on)
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
+    n0 = L.tssvd_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = L.tssvd_launch_count() - n0
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    flops = nominal_flops(w)
+    value = flops * world / (ms_max * 1e-3) / 1e9
+
+    # accuracy of the last result (outside the timed region)
+    with torch.no_grad():
+        s_t = torch.as_tensor(s0 if not torch.is_tensor(s0) else s0.cpu().numpy(), device=dev)
+        sig_err = float((S - s_t).abs().max() / s_t[0])
+        orth_u = float((U.T @ U - torch.eye(n, dtype=U.dtype, device=dev)).abs().max())
+        orth_v = float((V.T @ V - torch.eye(n, dtype=V.dtype, device=dev)).abs().max())
+        resid = float(torch.linalg.norm(A @ V - U * S) / torch.linalg.norm(A))
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        Uh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Sh = torch.empty((n,), dtype=torch.float64, pin_memory=True)
+        Vh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        Ad = torch.empty_like(A)
+        kw2 = dict(kw)
+
+        def e2e_step():
+            Ad.copy_(Ah, non_blocking=True)
+            pkg.ts_svd(Ad, **kw2)
+            Uh.copy_(U, non_blocking=True)
+            Sh.copy_(S, non_blocking=True)
+            Vh.copy_(V, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = f0.elapsed_time(f1) / args.e2e_steps
+        te = torch.tensor([ms_e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": flops * world / (float(te.item()) * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (m * n + n + n * n) * 8,
+               "ms_per_step": float(te.item())}
+        del Ah, Uh, Sh, Vh, Ad
+
+    # roofline of the dominant kernel
+    algo = {"nn_tall": 2.0 * m * n * n, "tn_gram": float(m) * n * (n + 1)}
+    dom = max(kernels.items(), key=lambda kv: kv[1][1]) if kernels else None
+    roof = None
+    if dom is not None:
+        name, (cnt, tot_ms) = dom
+        per_launch_ms = tot_ms / max(cnt, 1)
+        fl = algo.get(name)
+        achieved = (fl / (per_launch_ms * 1e-3) / 1e9) if fl else None
+        traffic = load_traffic(name, args.workload, args.mode)
+        if args.mode == "fp64":
+            roof = {"bound": "alu", "kernel": name,
+                    "achieved": (achieved / 1e3) if achieved else None,
+                    "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                    "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
+                    "traffic": traffic,
+                    "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)",
+                    "share_of_step": tot_ms / (ms * args.steps) if ms > 0 else None}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = min(args.cpu_rows, m)
+        v, dt, cores = time_oracle(w, rows)
+        cpu = {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": "%d x %d rows of the same recipe, one two-pass TS-SVD, %.1f s"
+                         % (rows, n, dt)}
+
+    out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.mode == "fp64" else "bf16x3+f64", "data": "synthetic",
+           "config": {"workload": args.workload, "m": m, "n": n, "passes": 2, "scale": 1,
+                      "mode": args.mode, "drop_tol": 0.0,
+                      "sigma": "geometric 1..%g" % w["lo"],
+                      "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 8 / 1e9),
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+           "clocks": clk,
+           "accuracy": {"sigma_err_normwise": sig_err, "orth_U": orth_u, "orth_V": orth_v,
+                        "residual_rel": resid, "rank": info["rank"],
+                        "sweeps": info["sweeps"]},
+           "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def read_profile(L):
+    """{kernel: (launches, total_ms)} from the library's event records."""
+    need = int(L.tssvd_profile_report(None, 0))
+    buf = ctypes.create_string_buffer(need + 64)
+    L.tssvd_profile_report(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        parts = line.split()
+        if len(parts) == 3:
+            out[parts[0]] = (int(parts[1]), float(parts[2]))
+    return out
+
+
+def load_traffic(kernel, workload, mode):
+    """DRAM bytes per launch from a committed ncu summary, if it matches."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get("%s|%s|%s" % (kernel, workload, mode))
+    if not e:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,20 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     const double *V, const double *dU, const double *dS, const double *dV,
                     double *dA, tssvd_opts *opts);
 
+/*
+ * Instrumentation (not part of the paper's method).
+ * tssvd_launch_count: number of kernels the library has launched in this
+ * process.  tssvd_profile_enable(1) makes every later launch record a CUDA
+ * event pair on its own stream; tssvd_profile_report synchronises the
+ * device, writes one line per kernel name "name launches total_ms" into
+ * buf (NUL-terminated, truncated to len) and clears the records; with
+ * buf == NULL it only returns the bytes the full report needs and keeps the
+ * records.  tssvd_profile_enable returns the previous setting.
+ */
+long long tssvd_launch_count(void);
+int tssvd_profile_enable(int on);
+size_t tssvd_profile_report(char *buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,12 @@ def lib():
     L.lowrank_svd.restype = ctypes.c_int
     L.ts_svd_backward.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
     L.ts_svd_backward.restype = ctypes.c_int
+    L.tssvd_launch_count.argtypes = []
+    L.tssvd_launch_count.restype = ctypes.c_longlong
+    L.tssvd_profile_enable.argtypes = [ctypes.c_int]
+    L.tssvd_profile_enable.restype = ctypes.c_int
+    L.tssvd_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    L.tssvd_profile_report.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -90,7 +96,8 @@ def lib():
 def exported_symbols():
     """Names of the C entry points the binding expects the library to export."""
     return ["tssvd_default_opts", "tssvd_status_string", "ts_svd_workspace_size", "ts_svd",
-            "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward"]
+            "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
+            "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,

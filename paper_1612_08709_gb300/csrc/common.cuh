@@ -27,6 +27,15 @@ struct DevStatus {
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
+// Wraps one kernel launch: counts it, and when profiling is on records a
+// CUDA event pair around it on its stream (see profiler.cu).
+struct ProfScope {
+    int idx;
+    cudaStream_t s;
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+};
+
 // ---------------------------------------------------------------- products
 // All tall products accumulate in FP64 (DFMA on the CUDA cores).
 

@@ -276,6 +276,7 @@ cudaError_t launch_colmax(const T *A, i64 m, i64 n, i64 lda, unsigned long long 
     if (ry > 65535) ry = 65535;
     i64 rows_per = (m + ry - 1) / ry;
     ry = (m + rows_per - 1) / rows_per;
+    ProfScope ps_("colmax", s);
     colmax_kernel<T><<<dim3(cx, (unsigned)ry), 256, 0, s>>>(A, m, n, lda, rows_per, bits);
     return cudaGetLastError();
 }
@@ -283,6 +284,7 @@ cudaError_t launch_colmax(const T *A, i64 m, i64 n, i64 lda, unsigned long long 
 cudaError_t launch_pow2_scale(const unsigned long long *bits, i64 n, double *d, double *dinv,
                               cudaStream_t s)
 {
+    ProfScope ps_("pow2", s);
     pow2_kernel<<<ceil_div_i(n, 256), 256, 0, s>>>(bits, n, d, dinv);
     return cudaGetLastError();
 }
@@ -309,6 +311,7 @@ cudaError_t launch_tn_partial(const TA *A, i64 lda, const TB_ *B, i64 ldb, i64 K
     i64 kchunk = (K + splits - 1) / splits;
     kchunk = (kchunk + KB - 1) / KB * KB;
     if (kchunk < KB) kchunk = KB;
+    ProfScope ps_((upper_only ? "tn_gram" : (K > 4 * M ? "tn_tall" : "tn_small")), s);
     tn_partial_kernel<TA, TB_><<<dim3((unsigned)tiles, (unsigned)splits), NTHR, 0, s>>>(
         A, lda, B, ldb, K, M, N, kchunk, tn, upper_only ? 1 : 0, P);
     return cudaGetLastError();
@@ -321,6 +324,7 @@ cudaError_t launch_tn_reduce(const double *P, int splits, i64 M, i64 N, const do
     i64 blocks = (total + 255) / 256;
     if (blocks > (i64)num_sms() * 16) blocks = (i64)num_sms() * 16;
     if (blocks < 1) blocks = 1;
+    ProfScope ps_("tn_reduce", s);
     tn_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, splits, M, N, rs, cs, sym ? 1 : 0, C, ldc);
     return cudaGetLastError();
 }
@@ -342,12 +346,14 @@ cudaError_t launch_nn(const TA *A, i64 lda, const double *B, i64 ldb, i64 m, i64
 {
     const int gx = ceil_div_i(N, TB);
     const int gy = nn_grid_rows(m, N);
+    ProfScope ps_((m > 4 * K ? "nn_tall" : "nn_small"), s);
     nn_kernel<TA, TC><<<dim3(gx, gy), NTHR, 0, s>>>(A, lda, B, ldb, m, K, N, C, ldc, NP);
     return cudaGetLastError();
 }
 
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s)
 {
+    ProfScope ps_("norms_reduce", s);
     norms_reduce_kernel<<<ceil_div_i(N, 256), 256, 0, s>>>(NP, g, N, out);
     return cudaGetLastError();
 }

@@ -420,6 +420,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
         i64 blocks = (total + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         if (blocks < 1) blocks = 1;
+        ProfScope ps_("init_identity", s);
         init_identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(J, ldj, nc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -457,6 +458,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     int blocks = num_sms() * per_sm;
     if (blocks > npairs) blocks = npairs;
     void *args[] = {&a};
+    ProfScope ps_("jacobi_svd", s);
     return cudaLaunchCooperativeKernel((const void *)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
                                        args, 0, s);
 }
@@ -471,6 +473,7 @@ cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *la
         i64 blocks = (total + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         if (blocks < 1) blocks = 1;
+        ProfScope ps_("init_identity", s);
         init_identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(V, ldv, n);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -501,6 +504,7 @@ cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *la
         int blocks = num_sms() * per_sm;
         if (blocks > npairs) blocks = npairs;
         void *args[] = {&a};
+        ProfScope ps_("jacobi_eig", s);
         if ((e = cudaLaunchCooperativeKernel((const void *)jacobi_eig_kernel<NT>, dim3(blocks),
                                              dim3(NT), args, 0, s)) != cudaSuccess)
             return e;
@@ -509,15 +513,22 @@ cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *la
     }
     // the rotation-parameter scratch (>= 2n doubles) now holds the diagonal
     double *dg = prm;
+    {
+    ProfScope ps_("diag", s);
     diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(B, ldb, n, dg);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+    ProfScope ps_("rank_sort", s);
     rank_sort_kernel<<<(n + 255) / 256, 256, 0, s>>>(dg, n, perm);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         i64 total = (i64)n * n;
         i64 blocks = (total + 255) / 256;
         if (blocks > (i64)num_sms() * 8) blocks = (i64)num_sms() * 8;
         if (blocks < 1) blocks = 1;
+        ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(nullptr, 0, V, ldv, 0, n, dg, perm,
                                                             Vout, ldvo, lam, nullptr, 0);
     }
@@ -532,16 +543,21 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
     {
         const int warps_per_block = 8;
         const int blocks = (nc + warps_per_block - 1) / warps_per_block;
+        ProfScope ps_("colnorm", s);
         colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(X, ldx, nr, nc, norms);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    {
+    ProfScope ps_("rank_sort", s);
     rank_sort_kernel<<<(nc + 255) / 256, 256, 0, s>>>(norms, nc, perm);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
         i64 total = (i64)nc * nc + (Xout ? (i64)nr * nc : 0);
         i64 blocks = (total + 255) / 256;
         if (blocks > (i64)num_sms() * 8) blocks = (i64)num_sms() * 8;
         if (blocks < 1) blocks = 1;
+        ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, J, ldj, nr, nc, norms, perm,
                                                             Jout, ldjo, lam, Xout, ldxo);
     }

@@ -1,0 +1,125 @@
+// Kernel launch counting and optional per-kernel CUDA-event timing.
+//
+// Every launch made by the library goes through a ProfScope: it always
+// increments the launch counter, and when profiling is enabled it records
+// a CUDA event pair around the launch on the launch's own stream.  The
+// report (tssvd_profile_report) synchronises the device, sums the elapsed
+// times per kernel name and releases the events.
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tssvd {
+
+namespace {
+
+struct Rec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+std::atomic<long long> g_launches{0};
+std::atomic<int> g_enabled{0};
+std::mutex g_mu;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t take_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+}  // namespace
+
+ProfScope::ProfScope(const char *name, cudaStream_t s) : idx(-1), s(s)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_enabled.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Rec r{name, take_event(), take_event()};
+    if (!r.a || !r.b) return;
+    if (cudaEventRecord(r.a, s) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    idx = (int)g_recs.size();
+    g_recs.push_back(r);
+}
+
+ProfScope::~ProfScope()
+{
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (idx < (int)g_recs.size()) {
+        if (cudaEventRecord(g_recs[idx].b, s) != cudaSuccess) cudaGetLastError();
+    }
+}
+
+}  // namespace tssvd
+
+using namespace tssvd;
+
+extern "C" {
+
+int tssvd_profile_enable(int on)
+{
+    int prev = g_enabled.exchange(on ? 1 : 0);
+    return prev;
+}
+
+long long tssvd_launch_count(void) { return g_launches.load(); }
+
+size_t tssvd_profile_report(char *buf, size_t len)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaDeviceSynchronize();
+    const bool consume = (buf != nullptr);
+    std::map<std::string, std::pair<long long, double>> agg;
+    for (Rec &r : g_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        auto &e = agg[r.name];
+        e.first += 1;
+        e.second += ms;
+        if (consume) {
+            g_pool.push_back(r.a);
+            g_pool.push_back(r.b);
+        }
+    }
+    if (consume) g_recs.clear();
+    std::string out;
+    char line[256];
+    for (auto &kv : agg) {
+        snprintf(line, sizeof(line), "%s %lld %.6f\n", kv.first.c_str(), kv.second.first,
+                 kv.second.second);
+        out += line;
+    }
+    if (buf && len > 0) {
+        size_t n = out.size() < len - 1 ? out.size() : len - 1;
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return out.size() + 1;
+}
+
+}  // extern "C"

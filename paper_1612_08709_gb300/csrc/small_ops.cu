@@ -216,6 +216,7 @@ __global__ void adjoint_core_kernel(const double *J, const double *K, const doub
 cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
                            cudaStream_t s)
 {
+    ProfScope ps_("keepval", s);
     keepval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(val, keep, n, out);
     return cudaGetLastError();
 }
@@ -223,6 +224,7 @@ cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double 
 cudaError_t launch_transpose(const double *src, i64 lds, i64 rows, i64 cols, const double *rs,
                              double *dst, i64 ldd, cudaStream_t s)
 {
+    ProfScope ps_("transpose", s);
     transpose_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, rows, cols, rs, dst, ldd);
     return cudaGetLastError();
 }
@@ -230,6 +232,7 @@ cudaError_t launch_transpose(const double *src, i64 lds, i64 rows, i64 cols, con
 cudaError_t launch_adjoint_core(const double *J, const double *K, const double *sv,
                                 const double *dS, i64 n, double *M, cudaStream_t s)
 {
+    ProfScope ps_("adjoint_core", s);
     adjoint_core_kernel<<<grid_for(n * n), 256, 0, s>>>(J, K, sv, dS, n, M);
     return cudaGetLastError();
 }
@@ -237,6 +240,7 @@ cudaError_t launch_adjoint_core(const double *J, const double *K, const double *
 cudaError_t launch_discard(const double *sig, i64 n, double tol, double *inv, int *rank_out,
                            cudaStream_t s)
 {
+    ProfScope ps_("discard", s);
     discard_kernel<<<1, 1024, 0, s>>>(sig, n, tol, inv, rank_out);
     return cudaGetLastError();
 }
@@ -244,6 +248,7 @@ cudaError_t launch_discard(const double *sig, i64 n, double tol, double *inv, in
 cudaError_t launch_scale2(const double *M, i64 ldm, i64 rows, i64 cols, const double *rs,
                           const double *cs, double *out, i64 ldo, cudaStream_t s)
 {
+    ProfScope ps_("scale2", s);
     scale2_kernel<<<grid_for(rows * cols), 256, 0, s>>>(M, ldm, rows, cols, rs, cs, out, ldo);
     return cudaGetLastError();
 }
@@ -251,6 +256,7 @@ cudaError_t launch_scale2(const double *M, i64 ldm, i64 rows, i64 cols, const do
 cudaError_t launch_build_g(const double *sig, const double *keep, const double *Vt, i64 ldv,
                            const double *d, i64 n, double *G, cudaStream_t s)
 {
+    ProfScope ps_("build_g", s);
     build_g_kernel<<<grid_for(n * n), 256, 0, s>>>(sig, keep, Vt, ldv, d, n, G);
     return cudaGetLastError();
 }
@@ -259,12 +265,14 @@ cudaError_t launch_signs(double *V, i64 ldv, i64 rows, i64 cols, const double *s
                          cudaStream_t s)
 {
     const i64 threads = cols * 32;
+    ProfScope ps_("signs", s);
     signs_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(V, ldv, rows, cols, sig, sgn);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_positive(const double *sig, i64 n, int *rank_out, cudaStream_t s)
 {
+    ProfScope ps_("count_positive", s);
     count_positive_kernel<<<1, 1024, 0, s>>>(sig, n, rank_out);
     return cudaGetLastError();
 }
@@ -273,6 +281,7 @@ template <typename T>
 cudaError_t launch_convert(const double *src, i64 lds, i64 rows, i64 cols, T *dst, i64 ldd,
                            cudaStream_t s)
 {
+    ProfScope ps_("convert", s);
     convert_kernel<T><<<grid_for(rows * cols), 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
     return cudaGetLastError();
 }
@@ -281,6 +290,7 @@ template <typename T>
 cudaError_t launch_scale_cols_inplace(T *U, i64 ldu, i64 rows, i64 cols, const double *cs,
                                       cudaStream_t s)
 {
+    ProfScope ps_("scale_cols", s);
     scale_cols_inplace_kernel<T><<<grid_for(rows * cols, 16), 256, 0, s>>>(U, ldu, rows, cols, cs);
     return cudaGetLastError();
 }
@@ -289,6 +299,7 @@ template <typename TS>
 cudaError_t launch_to_double(const TS *src, i64 lds, i64 rows, i64 cols, double *dst, i64 ldd,
                              cudaStream_t s)
 {
+    ProfScope ps_("to_double", s);
     to_double_kernel<TS><<<grid_for(rows * cols, 16), 256, 0, s>>>(src, lds, rows, cols, dst, ldd);
     return cudaGetLastError();
 }
