@@ -37,6 +37,9 @@ WORKLOADS = {
     # tall-skinny SVD at scale (2,000,000 x 200 and 1,000,000 x 1,000)
     "ts_2m_x_200": dict(kind="ts", m=2_000_000, n=200, lo=1e-8, seed=2),
     "ts_1m_x_1000": dict(kind="ts", m=1_000_000, n=1000, lo=1e-8, seed=3),
+    # a 200,000 x 200 case of the same recipe (inputs still larger than L2)
+    # for kernel profiling
+    "ts_200k_x_200": dict(kind="ts", m=200_000, n=200, lo=1e-8, seed=2),
     # the small plain case (20,000 x 50, sigma 1..1e-6)
     "ts_20k_x_50": dict(kind="ts", m=20_000, n=50, lo=1e-6, seed=1),
 }

@@ -153,6 +153,21 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     double *dA, tssvd_opts *opts);
 
 /*
+ * Gram matrix B = A^T A of A (m x n, row-major, lda >= n): the first step of
+ * Algorithms 3 and 4 (and the Z = Y^T Y step of Algorithm 4), in FP64 on
+ * the CUDA cores.  Split-K over the rows: each CTA accumulates a partial
+ * Gram of a row slab (the per-partition Gram matrices the paper aggregates,
+ * Section 2) into workspace, and a second kernel sums the partials in a
+ * fixed order, so the result is deterministic.  B is n x n row-major
+ * (leading dimension n), written in full (both triangles).  Uses
+ * opts->stream and opts->workspace (ts_gram_workspace_size bytes) like
+ * ts_svd; returns after the stream has finished.
+ * Errors: -1 A, -2 m, -3 n, -4 lda, -5 B, -6 opts.
+ */
+size_t ts_gram_workspace_size(int64_t m, int64_t n);
+int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd_opts *opts);
+
+/*
  * Instrumentation (not part of the paper's method).
  * tssvd_launch_count: number of kernels the library has launched in this
  * process.  tssvd_profile_enable(1) makes every later launch record a CUDA

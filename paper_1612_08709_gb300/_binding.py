@@ -83,6 +83,10 @@ def lib():
     L.lowrank_svd.restype = ctypes.c_int
     L.ts_svd_backward.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
     L.ts_svd_backward.restype = ctypes.c_int
+    L.ts_gram_workspace_size.argtypes = [i64, i64]
+    L.ts_gram_workspace_size.restype = ctypes.c_size_t
+    L.ts_gram.argtypes = [vp, i64, i64, i64, vp, op]
+    L.ts_gram.restype = ctypes.c_int
     L.tssvd_launch_count.argtypes = []
     L.tssvd_launch_count.restype = ctypes.c_longlong
     L.tssvd_profile_enable.argtypes = [ctypes.c_int]
@@ -97,7 +101,8 @@ def exported_symbols():
     """Names of the C entry points the binding expects the library to export."""
     return ["tssvd_default_opts", "tssvd_status_string", "ts_svd_workspace_size", "ts_svd",
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
-            "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report"]
+            "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
+            "ts_gram_workspace_size", "ts_gram"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -200,6 +205,18 @@ def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max
                                _ptr(Omega), _ptr(U), _ptr(S), _ptr(V), ctypes.byref(o))
     _check(rc, "lowrank_svd")
     return U, S, V, _info(o, rc)
+
+
+def ts_gram(A, stream=None, workspace=None):
+    """B = A^T A (n x n, FP64) of a float64 CUDA tensor A (m x n)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    B = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    o = _opts(stream=stream, workspace=workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().ts_gram(_ptr(A), m, n, A.stride(0), _ptr(B), ctypes.byref(o))
+    _check(rc, "ts_gram")
+    return B
 
 
 def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):

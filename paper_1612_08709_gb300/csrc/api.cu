@@ -489,6 +489,42 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     return code;
 }
 
+size_t ts_gram_workspace_size(int64_t m, int64_t n)
+{
+    if (m < 1 || n < 1) return 0;
+    Bump sz(nullptr, 0);
+    sz.take<double>((size_t)tn_splits(m, n, n, true) * n * n);
+    return sz.off;
+}
+
+int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (lda < n) return -4;
+    if (!B) return -5;
+    if (!opts) return -6;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const int sp = tn_splits(m, n, n, true);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, ts_gram_workspace_size(m, n), &base, lk);
+    if (rc) return rc;
+    Bump ws(base, ts_gram_workspace_size(m, n));
+    double *P = ws.take<double>((size_t)sp * n * n);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    cudaError_t e = launch_tn_partial<double, double>(A, lda, A, lda, m, n, n, sp, true, P, s);
+    if (e == cudaSuccess) e = launch_tn_reduce(P, sp, n, n, nullptr, nullptr, true, B, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return TSSVD_OK;
+}
+
 int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const double *S,
                     const double *V, const double *dU, const double *dS, const double *dV,
                     double *dA, tssvd_opts *opts)

@@ -235,3 +235,16 @@ def test_invalid_argument_raises():
     A = torch.zeros((3, 5), dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.TsSvdError):
         pkg.ts_svd(A)
+
+
+@gpu
+@pytest.mark.parametrize("m,n,seed", [(5003, 77, 41), (20000, 200, 42), (300, 300, 43), (100, 1, 44)])
+def test_gram_matches_oracle(orc, m, n, seed):
+    """Step a2 on its own: B = A^T A against the oracle's Gram."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    A = np.random.default_rng(seed).standard_normal((m, n))
+    B = pkg.ts_gram(torch.as_tensor(A, device="cuda")).cpu().numpy()
+    Br = orc.gram(A)
+    assert np.abs(B - Br).max() <= 1e-13 * np.abs(Br).max()
+    assert np.array_equal(B, B.T)
