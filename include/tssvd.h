@@ -168,6 +168,31 @@ size_t ts_gram_workspace_size(int64_t m, int64_t n);
 int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd_opts *opts);
 
 /*
+ * ts_gram_noalloc: B = A^T A like ts_gram, for callers that must not have
+ * the library allocate device memory (for example a host framework that
+ * owns all device memory through its own pool, or code that cannot accept
+ * the device-wide synchronisation cudaMalloc may cause).  The paper has no
+ * counterpart; it is a deployment variant of the Gram step.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *    The split-K partial sums live in a fixed 4 MiB scratch array that is
+ *    part of the library's device image; every GPU that loads the library
+ *    holds it until the process exits.
+ *  - Size limit: n <= 724 (n*n partial entries must fit the scratch); a
+ *    larger n returns -3 and prints the reason.  m is unrestricted.
+ *  - The first call on each device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one scratch array, which keeps the last call's
+ *    contents (every entry a call reads is written by the same call first).
+ *    Calls whose work overlaps on the GPU (for example on two streams at
+ *    once) race on it: serialise them.
+ *  - stream is a cudaStream_t (NULL = legacy default stream); the call
+ *    returns after the stream has finished.  B is n x n row-major.
+ * Errors: -1 A, -2 m, -3 n (or n > 724), -4 lda, -5 B; TSSVD_ECUDA.
+ */
+int ts_gram_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, double *B, void *stream);
+
+/*
  * Instrumentation (not part of the paper's method).
  * tssvd_launch_count: number of kernels the library has launched in this
  * process.  tssvd_profile_enable(1) makes every later launch record a CUDA
