@@ -52,8 +52,12 @@ typedef enum {
     /* Mixed: the first pass's products (Gram of A and A V~) run on the
      * tcgen05 tensor cores with BF16x3 split operands and FP32 accumulation
      * drained to FP64; the second orthonormalisation pass, the eigensolves
-     * and all n x n work stay FP64. */
-    TSSVD_BF16X3 = 1
+     * and all n x n work stay FP64.  Two bf16 terms per value (about 16
+     * significant bits), three term products per product.  n <= 256. */
+    TSSVD_BF16X3 = 1,
+    /* As TSSVD_BF16X3 with three bf16 terms per value (about 24 significant
+     * bits, the accuracy of FP32 inputs) and six term products. n <= 256. */
+    TSSVD_BF16X6 = 2
 } tssvd_mode;
 
 typedef struct {
@@ -161,11 +165,26 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
  * fixed order, so the result is deterministic.  B is n x n row-major
  * (leading dimension n), written in full (both triangles).  Uses
  * opts->stream and opts->workspace (ts_gram_workspace_size bytes) like
- * ts_svd; returns after the stream has finished.
+ * ts_svd; returns after the stream has finished.  opts->mode selects FP64
+ * DFMA or the BF16-split tensor-core product (n <= 256).
  * Errors: -1 A, -2 m, -3 n, -4 lda, -5 B, -6 opts.
  */
 size_t ts_gram_workspace_size(int64_t m, int64_t n);
 int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd_opts *opts);
+
+/*
+ * Tall product C = A M: A is m x k (row-major, lda), M is k x n (ldm), C is
+ * m x n (ldc), all FP64 device memory.  The product Y~ = A V~ of
+ * Algorithms 3 and 4 (and U = Q P, Y = A Q~ of Algorithm 5) as a call of its
+ * own.  opts->mode selects FP64 DFMA or the BF16-split tensor-core product
+ * (n <= 256).  Uses opts->stream and opts->workspace
+ * (ts_matmul_workspace_size bytes); returns after the stream has finished.
+ * Errors: -1 A, -2 m, -3 k, -4 lda, -5 M, -6 n, -7 ldm, -8 C, -9 ldc,
+ * -10 opts.
+ */
+size_t ts_matmul_workspace_size(int64_t m, int64_t k, int64_t n);
+int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *M, int64_t n,
+              int64_t ldm, double *C, int64_t ldc, tssvd_opts *opts);
 
 /*
  * ts_gram_noalloc: B = A^T A like ts_gram, for callers that must not have

@@ -21,7 +21,7 @@ TSSVD_ETIMEOUT = 3
 TSSVD_ECUDA = 4
 TSSVD_ENOMEM = 5
 
-_MODES = {"fp64": 0, "bf16x3": 1}
+_MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
 
 # Square root of the paper's example working precision 1e-11 (Remark "working").
 PAPER_DROP_TOL = math.sqrt(1e-11)
@@ -87,6 +87,10 @@ def lib():
     L.ts_gram_workspace_size.restype = ctypes.c_size_t
     L.ts_gram.argtypes = [vp, i64, i64, i64, vp, op]
     L.ts_gram.restype = ctypes.c_int
+    L.ts_matmul_workspace_size.argtypes = [i64, i64, i64]
+    L.ts_matmul_workspace_size.restype = ctypes.c_size_t
+    L.ts_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, op]
+    L.ts_matmul.restype = ctypes.c_int
     L.tssvd_launch_count.argtypes = []
     L.tssvd_launch_count.restype = ctypes.c_longlong
     L.tssvd_profile_enable.argtypes = [ctypes.c_int]
@@ -102,7 +106,7 @@ def exported_symbols():
     return ["tssvd_default_opts", "tssvd_status_string", "ts_svd_workspace_size", "ts_svd",
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
-            "ts_gram_workspace_size", "ts_gram"]
+            "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -207,16 +211,31 @@ def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max
     return U, S, V, _info(o, rc)
 
 
-def ts_gram(A, stream=None, workspace=None):
+def ts_gram(A, mode="fp64", stream=None, workspace=None):
     """B = A^T A (n x n, FP64) of a float64 CUDA tensor A (m x n)."""
     A = _as_matrix(A)
     m, n = A.shape
     B = torch.empty((n, n), dtype=torch.float64, device=A.device)
-    o = _opts(stream=stream, workspace=workspace)
+    o = _opts(mode=mode, stream=stream, workspace=workspace)
     with torch.cuda.device(A.device):
         rc = lib().ts_gram(_ptr(A), m, n, A.stride(0), _ptr(B), ctypes.byref(o))
     _check(rc, "ts_gram")
     return B
+
+
+def ts_matmul(A, M, mode="fp64", stream=None, workspace=None):
+    """C = A M for float64 CUDA tensors A (m x k) and M (k x n)."""
+    A = _as_matrix(A)
+    M = _as_matrix(M)
+    m, k = A.shape
+    n = M.shape[1]
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    o = _opts(mode=mode, stream=stream, workspace=workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().ts_matmul(_ptr(A), m, k, A.stride(0), _ptr(M), n, M.stride(0), _ptr(C), n,
+                             ctypes.byref(o))
+    _check(rc, "ts_matmul")
+    return C
 
 
 def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):

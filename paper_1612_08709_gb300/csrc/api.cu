@@ -83,11 +83,14 @@ InternalWs g_ws[64];
 // row-major, ldv) as doubles or T per the template parameters; all outputs
 // carry zeros past the numerical rank.  In sizing mode only the workspace
 // is counted.
+inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSSVD_BF16X3 ? 2 : 0); }
+
 template <typename T, typename TO>
 cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                     int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                    cudaStream_t s)
+                    cudaStream_t s, int mode = TSSVD_FP64)
 {
+    const int terms = (passes == 2) ? mode_terms(mode) : 0;
     const bool sizing = ws.sizing();
     const i64 nn = n * n;
     int *ctr = ws.take<int>((size_t)max_sweeps + 4);
@@ -110,6 +113,10 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     int *perm = ws.take<int>(n);
     double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
     double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
+    const int tsp = terms ? tc_gram_splits(m) : 0;
+    double *Ptc = terms ? ws.take<double>((size_t)tsp * nn) : nullptr;
+    uint8_t *Bimg = terms ? ws.take<uint8_t>(tc_split_b_bytes((int)n, (int)n, terms)) : nullptr;
+    double *G2 = terms ? ws.take<double>(nn) : nullptr;
     if (sizing) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
 
@@ -147,9 +154,16 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_pow2_scale(bits, n, d, dinv, s));
         rs1 = dinv;
     }
-    // B = (A D^-1)^T (A D^-1).
-    CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
-    CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
+    if (terms) {
+        // Mixed form of the first pass: both products on the tensor cores
+        // with BF16-split operands.  B = (A D^-1)^T (A D^-1).
+        CK(launch_tc_gram<T>(A, lda, m, (int)n, terms, tsp, Ptc, st, s));
+        CK(launch_tn_reduce(Ptc, tsp, n, n, rs1, rs1, true, B, n, s));
+    } else {
+        // B = (A D^-1)^T (A D^-1).
+        CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
+        CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
+    }
     // B = V~ D~ V~^T (Gram-form Jacobi; B is rotated in place).
     CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
@@ -157,14 +171,26 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
         M1 = M;
     }
-    CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
-    CK(launch_norms_reduce(NP, gy, n, sig, s));
-    // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
-    // products instead of a separate pass over Y.
-    CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
-    // Z = Y^T Y = Sigma~^-1 (Y~^T Y~) Sigma~^-1.
-    CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
-    CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
+    if (terms) {
+        CK(launch_tc_split_b(M1, n, (int)n, (int)n, terms, Bimg, s));
+        CK(launch_tc_nn<T>(A, lda, m, (int)n, Bimg, (int)n, terms, Yt, n, st, s));
+        // the explicit column norms of Y~ come from the diagonal of its
+        // FP64 Gram matrix, which the second pass forms anyway
+        CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
+        CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, G2, n, s));
+        CK(launch_diag_sqrt(G2, n, n, sig, s));
+        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+        CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
+    } else {
+        CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
+        CK(launch_norms_reduce(NP, gy, n, sig, s));
+        // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
+        // products instead of a separate pass over Y.
+        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+        // Z = Y^T Y = Sigma~^-1 (Y~^T Y~) Sigma~^-1.
+        CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
+        CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
+    }
     // Z = W D W^T.
     CK(launch_jacobi_eig(B, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
     // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
@@ -243,7 +269,7 @@ int check_opts(const tssvd_opts *o)
     if (o->passes != 1 && o->passes != 2) return 0;
     if (!(o->drop_tol >= 0.0) || o->drop_tol >= 1.0) return 0;
     if (o->max_sweeps < 1 || o->max_sweeps > 1000) return 0;
-    if (o->mode != TSSVD_FP64) return 0;  // other modes are built separately
+    if (o->mode != TSSVD_FP64 && o->mode != TSSVD_BF16X3 && o->mode != TSSVD_BF16X6) return 0;
     return 1;
 }
 
@@ -259,12 +285,17 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     if (!S) return -6;
     if (!V) return -7;
     if (!check_opts(opts)) return -8;
+    if (opts->mode != TSSVD_FP64 && n > 256) {
+        fprintf(stderr, "tssvd: the mixed-precision modes take n <= 256 (n = %lld)\n",
+                (long long)n);
+        return -3;
+    }
     cudaStream_t s = (cudaStream_t)opts->stream;
 
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(1);
     ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
-                  opts->max_sweeps, sz, nullptr, s);
+                  opts->max_sweeps, sz, nullptr, s, opts->mode);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
@@ -273,7 +304,7 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     DevStatus *st = ws.take<DevStatus>(1);
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
     cudaError_t e = ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
-                                  opts->drop_tol, opts->max_sweeps, ws, st, s);
+                                  opts->drop_tol, opts->max_sweeps, ws, st, s, opts->mode);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
@@ -400,11 +431,11 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
     if (elem_bytes == 4)
         ts_core<float, float>(nullptr, m, n, n, (float *)nullptr, n, (float *)nullptr,
                               (float *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
-                              opts->max_sweeps, sz, nullptr, nullptr);
+                              opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
     else
         ts_core<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
                                 (double *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
-                                opts->max_sweeps, sz, nullptr, nullptr);
+                                opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
     return sz.off;
 }
 
@@ -493,8 +524,23 @@ size_t ts_gram_workspace_size(int64_t m, int64_t n)
 {
     if (m < 1 || n < 1) return 0;
     Bump sz(nullptr, 0);
-    sz.take<double>((size_t)tn_splits(m, n, n, true) * n * n);
+    sz.take<DevStatus>(1);
+    const int sp = tn_splits(m, n, n, true);
+    const int tsp = tc_gram_splits(m);
+    sz.take<double>((size_t)(sp > tsp ? sp : tsp) * n * n);
     return sz.off;
+}
+
+// Reads the status block back; TSSVD_ETIMEOUT if a device wait expired.
+int finish_call(DevStatus *st, cudaStream_t s)
+{
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return h.err ? TSSVD_ETIMEOUT : TSSVD_OK;
 }
 
 int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd_opts *opts)
@@ -504,25 +550,83 @@ int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd
     if (n < 1 || n > 16384) return -3;
     if (lda < n) return -4;
     if (!B) return -5;
-    if (!opts) return -6;
+    if (!check_opts(opts)) return -6;
+    const int terms = mode_terms(opts->mode);
+    if (terms && n > 256) return -3;
     cudaStream_t s = (cudaStream_t)opts->stream;
-    const int sp = tn_splits(m, n, n, true);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
-    int rc = acquire_ws(opts, ts_gram_workspace_size(m, n), &base, lk);
+    const size_t need = ts_gram_workspace_size(m, n);
+    int rc = acquire_ws(opts, need, &base, lk);
     if (rc) return rc;
-    Bump ws(base, ts_gram_workspace_size(m, n));
+    Bump ws(base, need);
+    DevStatus *st = ws.take<DevStatus>(1);
+    const int sp = terms ? tc_gram_splits(m) : tn_splits(m, n, n, true);
     double *P = ws.take<double>((size_t)sp * n * n);
     if (ws.overflow) return TSSVD_ENOMEM;
-    cudaError_t e = launch_tn_partial<double, double>(A, lda, A, lda, m, n, n, sp, true, P, s);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess)
+        e = terms ? launch_tc_gram<double>(A, lda, m, (int)n, terms, sp, P, st, s)
+                  : launch_tn_partial<double, double>(A, lda, A, lda, m, n, n, sp, true, P, s);
     if (e == cudaSuccess) e = launch_tn_reduce(P, sp, n, n, nullptr, nullptr, true, B, n, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
         return TSSVD_ECUDA;
     }
-    return TSSVD_OK;
+    return finish_call(st, s);
+}
+
+size_t ts_matmul_workspace_size(int64_t m, int64_t k, int64_t n)
+{
+    if (m < 1 || k < 1 || n < 1) return 0;
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(1);
+    sz.take<uint8_t>(tc_split_b_bytes((int)k, (int)n, 3));
+    sz.take<double>((size_t)nn_grid_rows(m, n) * n);
+    return sz.off;
+}
+
+int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *M, int64_t n,
+              int64_t ldm, double *C, int64_t ldc, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (k < 1 || k > (1 << 20)) return -3;
+    if (lda < k) return -4;
+    if (!M) return -5;
+    if (n < 1 || n > 16384) return -6;
+    if (ldm < n) return -7;
+    if (!C) return -8;
+    if (ldc < n) return -9;
+    if (!check_opts(opts)) return -10;
+    const int terms = mode_terms(opts->mode);
+    if (terms && n > 256) return -6;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    const size_t need = ts_matmul_workspace_size(m, k, n);
+    int rc = acquire_ws(opts, need, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, need);
+    DevStatus *st = ws.take<DevStatus>(1);
+    uint8_t *img = ws.take<uint8_t>(tc_split_b_bytes((int)k, (int)n, 3));
+    double *NP = ws.take<double>((size_t)nn_grid_rows(m, n) * n);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (terms) {
+        if (e == cudaSuccess) e = launch_tc_split_b(M, ldm, (int)k, (int)n, terms, img, s);
+        if (e == cudaSuccess)
+            e = launch_tc_nn<double>(A, lda, m, (int)k, img, (int)n, terms, C, ldc, st, s);
+    } else if (e == cudaSuccess) {
+        e = launch_nn<double, double>(A, lda, M, ldm, m, k, n, C, ldc, NP, s);
+    }
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return finish_call(st, s);
 }
 
 int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const double *S,

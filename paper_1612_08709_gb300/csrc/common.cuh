@@ -74,6 +74,23 @@ int nn_grid_rows(i64 m, i64 N);
 // out[j] = sqrt(sum_g NP[g][j]) in fixed order.
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
 
+// ------------------------------------------------- tensor-core products
+// BF16-split products on tcgen05 (gemm_tc.cu).  S = number of bf16 terms
+// per value (2 or 3).  Both require n (resp. N) <= 256.
+int tc_gram_splits(i64 m);
+// Partials P[split][i][j] (splits x n x n) of A^T A, FP64.
+template <typename T>
+cudaError_t launch_tc_gram(const T *A, i64 lda, i64 m, int n, int S, int splits, double *P,
+                           DevStatus *st, cudaStream_t s);
+// Bytes of the split image of a K x N right-hand matrix.
+size_t tc_split_b_bytes(int K, int N, int S);
+cudaError_t launch_tc_split_b(const double *M, i64 ldm, int K, int N, int S, uint8_t *img,
+                              cudaStream_t s);
+// C (m x N, FP64, ldc) = A (m x K) * M, with M given as its split image.
+template <typename T>
+cudaError_t launch_tc_nn(const T *A, i64 lda, i64 m, int K, const uint8_t *img, int N, int S,
+                         double *C, i64 ldc, DevStatus *st, cudaStream_t s);
+
 // -------------------------------------------------------------- Jacobi
 // One-sided (Hestenes) Jacobi with a parallel round-robin pair order, as
 // one cooperative kernel with a bounded grid barrier.  X is nr x nc
@@ -121,6 +138,8 @@ cudaError_t launch_signs(double *V, i64 ldv, i64 rows, i64 cols, const double *s
                          double *sgn, cudaStream_t s);
 // rank = number of sig[j] > 0 -> *rank_out.
 cudaError_t launch_count_positive(const double *sig, i64 n, int *rank_out, cudaStream_t s);
+// out[j] = sqrt(max(G[j][j], 0)).
+cudaError_t launch_diag_sqrt(const double *G, i64 ldg, i64 n, double *out, cudaStream_t s);
 // out[j] = keep[j] != 0 ? val[j] : 0 (val null: 1).
 cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
                            cudaStream_t s);

@@ -170,6 +170,15 @@ __global__ void scale_cols_inplace_kernel(T *U, i64 ldu, i64 rows, i64 cols, con
     }
 }
 
+__global__ void diag_sqrt_kernel(const double *G, i64 ldg, i64 n, double *out)
+{
+    const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        const double v = G[j * ldg + j];
+        out[j] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+}
+
 __global__ void keepval_kernel(const double *val, const double *keep, i64 n, double *out)
 {
     const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,6 +221,13 @@ __global__ void adjoint_core_kernel(const double *J, const double *K, const doub
 }
 
 }  // namespace
+
+cudaError_t launch_diag_sqrt(const double *G, i64 ldg, i64 n, double *out, cudaStream_t s)
+{
+    ProfScope ps_("diag_sqrt", s);
+    diag_sqrt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, ldg, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
                            cudaStream_t s)

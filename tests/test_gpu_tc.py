@@ -1,0 +1,85 @@
+"""The BF16-split tensor-core products (tcgen05) against FP64 references,
+and the mixed-precision TS-SVD against the oracle.
+
+Error bounds: a value split into S bf16 terms keeps about 8S significant
+bits; the S(S+1)/2 term products drop terms of relative size 2^(-8S), and
+the FP32 accumulator rounds once per 16-deep MMA step.  A*M (K <= 256)
+takes at most 16 steps; the Gram drains its FP32 accumulator to FP64
+every 1024 rows, i.e. every 64 steps, which bounds its accumulation error
+by about 66 * 2^-24 = 4e-6 of the absolute sum.  Entry (i, j) is held to
+   tol * (|A| |M|)_ij      (relative to the sum of absolute term products)
+with tol = 1e-4 for two terms, 2e-6 (products) / 5e-6 (Gram) for three.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+gpu = pytest.mark.gpu
+TOL = {"bf16x3": 1e-4, "bf16x6": 2e-6}
+TOL_GRAM = {"bf16x3": 1e-4, "bf16x6": 5e-6}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("m,n,seed", [(64, 16, 1), (1000, 37, 2), (5003, 128, 3), (20000, 200, 4),
+                                      (3001, 256, 5), (130, 129, 6)])
+def test_tc_gram_matches_fp64(m, n, seed, mode):
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    A = np.random.default_rng(seed).standard_normal((m, n))
+    B = pkg.ts_gram(torch.as_tensor(A, device="cuda"), mode=mode).cpu().numpy()
+    ref = A.T @ A
+    scale = np.abs(A).T @ np.abs(A)
+    err = np.abs(B - ref) / scale
+    assert err.max() <= TOL_GRAM[mode], err.max()
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("m,k,n,seed", [(128, 16, 16, 1), (1000, 50, 50, 2), (777, 200, 200, 3),
+                                        (4099, 65, 256, 4), (300, 33, 7, 5)])
+def test_tc_matmul_matches_fp64(m, k, n, seed, mode):
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, k))
+    M = rng.standard_normal((k, n))
+    C = pkg.ts_matmul(torch.as_tensor(A, device="cuda"), torch.as_tensor(M, device="cuda"),
+                      mode=mode).cpu().numpy()
+    ref = A @ M
+    scale = np.abs(A) @ np.abs(M)
+    err = np.abs(C - ref) / scale
+    assert err.max() <= TOL[mode], err.max()
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("m,n,lo,seed", [(20000, 50, 1e-6, 1), (5000, 200, 1e-4, 2),
+                                         (3001, 130, 1e-3, 3)])
+def test_ts_svd_mixed_matches_oracle(orc, m, n, lo, seed, mode):
+    """Mixed form: sigma within the FP32-form bound (1e-5 sigma_1), U and V
+    orthonormal to the FP64 level (second pass in FP64).  With two bf16
+    terms (about 16 bits) and a condition number of 1e6 the first pass is
+    too rough for two passes to reach 1e-12; that case is held to 1e-11."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    A, _, s0, _ = workloads.known_spectrum(m, n, workloads.sigma_geometric(n, lo), seed)
+    ref = orc.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+    U, S, V, info = pkg.ts_svd(torch.as_tensor(A, device="cuda"), passes=2, scale=True,
+                               drop_tol=0.0, mode=mode)
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    assert info["rank"] == n
+    assert np.abs(S - ref[1]).max() <= 1e-5 * ref[1][0]
+    o_tol = 1e-11 if (mode == "bf16x3" and lo < 1e-5) else 1e-12
+    assert np.abs(U.T @ U - np.eye(n)).max() <= o_tol
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
+    # A V = U S holds to the accuracy of the first pass
+    assert np.abs(A @ V - U * S).max() <= 1e-5 * ref[1][0]
