@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ts_2m_x_200", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-rows", type=int, default=200_000,
@@ -290,24 +290,9 @@ def run_ours(args):
                "ms_per_step": float(te.item())}
         del Ah, Uh, Sh, Vh, Ad
 
-    # roofline of the dominant kernel
-    algo = {"nn_tall": 2.0 * m * n * n, "tn_gram": float(m) * n * (n + 1)}
-    dom = max(kernels.items(), key=lambda kv: kv[1][1]) if kernels else None
-    roof = None
-    if dom is not None:
-        name, (cnt, tot_ms) = dom
-        per_launch_ms = tot_ms / max(cnt, 1)
-        fl = algo.get(name)
-        achieved = (fl / (per_launch_ms * 1e-3) / 1e9) if fl else None
-        traffic = load_traffic(name, args.workload, args.mode)
-        if args.mode == "fp64":
-            roof = {"bound": "alu", "kernel": name,
-                    "achieved": (achieved / 1e3) if achieved else None,
-                    "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                    "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
-                    "traffic": traffic,
-                    "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)",
-                    "share_of_step": tot_ms / (ms * args.steps) if ms > 0 else None}
+    # roofline of the dominant kernel (largest total event time in the
+    # timed region): algorithmic flops or bytes per launch / mean duration
+    roof = roofline(kernels, m, n, ms, args, A.element_size())
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rows = min(args.cpu_rows, m)
@@ -319,7 +304,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.mode == "fp64" else "bf16x3+f64", "data": "synthetic",
+           "dtype": "f64" if args.mode == "fp64" else args.mode + "+f64", "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "passes": 2, "scale": 1,
                       "mode": args.mode, "drop_tol": 0.0,
                       "sigma": "geometric 1..%g" % w["lo"],
@@ -335,6 +320,51 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# HBM copy bandwidth measured on the GB300s (the recipe's peak file
+# when present, else the recipe's fallback figure).
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def roofline(kernels, m, n, ms, args, esize):
+    """Roofline entry of the dominant kernel.
+
+    FP64 DFMA kernels are bound by the FP64 pipe ("alu"): algorithmic flops
+    2mn^2 (tall A*M) or mn(n+1) (Gram).  The tensor-core kernels are bound
+    by HBM at these shapes: algorithmic bytes = the input read once (and
+    the FP64 output written once for A*M).
+    """
+    if not kernels:
+        return None
+    name, (cnt, tot_ms) = max(kernels.items(), key=lambda kv: kv[1][1])
+    per_launch_s = tot_ms / max(cnt, 1) * 1e-3
+    share = tot_ms / (ms * args.steps) if ms > 0 else None
+    traffic = load_traffic(name, args.workload, args.mode)
+    alu = {"nn_tall": 2.0 * m * n * n, "tn_gram": float(m) * n * (n + 1)}
+    hbm = {"tc_gram": float(esize) * m * n, "tc_nn": float(esize) * m * n + 8.0 * m * n}
+    if name in alu:
+        ach = alu[name] / per_launch_s / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)",
+                "share_of_step": share}
+    if name in hbm:
+        ach = hbm[name] / per_launch_s / 1e9
+        peak, src = hbm_peak()
+        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic, "peak_source": src,
+                "share_of_step": share}
+    return {"bound": "latency", "kernel": name, "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None, "share_of_step": share,
+            "note": "grid-barrier-bound n x n Jacobi solve; no throughput roofline applies"}
 
 
 def read_profile(L):

@@ -57,7 +57,13 @@ typedef enum {
     TSSVD_BF16X3 = 1,
     /* As TSSVD_BF16X3 with three bf16 terms per value (about 24 significant
      * bits, the accuracy of FP32 inputs) and six term products. n <= 256. */
-    TSSVD_BF16X6 = 2
+    TSSVD_BF16X6 = 2,
+    /* FP64-accurate products on the tensor cores: every tall product of
+     * both passes is emulated with seven 7-bit integer digits per value
+     * (exact in bf16), exact per-level FP32 accumulation in tensor memory
+     * and double-FP32 accumulation of the level sums, so the results carry
+     * about 48 significant bits; the n x n work stays FP64.  Any n. */
+    TSSVD_FP64_TC = 3
 } tssvd_mode;
 
 typedef struct {

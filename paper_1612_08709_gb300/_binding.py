@@ -21,7 +21,7 @@ TSSVD_ETIMEOUT = 3
 TSSVD_ECUDA = 4
 TSSVD_ENOMEM = 5
 
-_MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+_MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp64_tc": 3}
 
 # Square root of the paper's example working precision 1e-11 (Remark "working").
 PAPER_DROP_TOL = math.sqrt(1e-11)

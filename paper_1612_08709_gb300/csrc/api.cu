@@ -219,6 +219,147 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     return cudaSuccess;
 }
 
+// The FP64-accurate tensor-core form: the same steps as ts_core, with every
+// tall product on the digit-sliced tensor-core kernels.
+template <typename T, typename TO>
+cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
+                       int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
+                       cudaStream_t s)
+{
+    const bool sizing = ws.sizing();
+    const i64 nn = n * n;
+    int *ctr = ws.take<int>((size_t)max_sweeps + 4);
+    unsigned long long *bits = ws.take<unsigned long long>(n);
+    double *d = ws.take<double>(n), *dinv = ws.take<double>(n);
+    int *exA = ws.take<int>(n), *pk1 = ws.take<int>(n), *exY = ws.take<int>(n);
+    int *pk2 = ws.take<int>(n), *em = ws.take<int>(n);
+    int *er = ws.take<int>(m);
+    const int osp = oz_gram_splits(m, (int)n);
+    const int sp2 = tn_splits(n, n, n, false);
+    double *P = ws.take<double>((size_t)(osp > sp2 ? osp : sp2) * nn);
+    const int gcs = colsumsq_rows(m, n);
+    const int gys = nn_grid_rows(n, n);
+    double *NP = ws.take<double>((size_t)(gcs > gys ? gcs : gys) * n);
+    uint8_t *img = ws.take<uint8_t>(oz_image_bytes((int)n, (int)n));
+    double *B = ws.take<double>(nn), *G2 = ws.take<double>(nn), *Jw = ws.take<double>(nn);
+    double *Vt = ws.take<double>(nn), *W = ws.take<double>(nn), *M = ws.take<double>(nn);
+    double *G = ws.take<double>(nn), *R = ws.take<double>(nn), *Pm = ws.take<double>(nn);
+    double *Vo = ws.take<double>(nn), *Pp = ws.take<double>(nn), *M3 = ws.take<double>(nn);
+    double *Xw = ws.take<double>(nn);
+    double *lam = ws.take<double>(n), *sig = ws.take<double>(n), *sinv = ws.take<double>(n);
+    double *Tn = ws.take<double>(n), *tinv = ws.take<double>(n), *Tk = ws.take<double>(n);
+    double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
+    double *cs = ws.take<double>(n);
+    int *perm = ws.take<int>(n);
+    double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
+    double *Yt = ws.take<double>((size_t)m * n);
+    const bool u_is_double = sizeof(TO) == sizeof(double);
+    double *Qt = (passes == 2 && !u_is_double) ? ws.take<double>((size_t)m * n) : nullptr;
+    if (sizing) return cudaSuccess;
+    if (ws.overflow) return cudaErrorMemoryAllocation;
+
+    // MaxEntry of every column: the Gram's digit scales (and D when scaling)
+    CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+    CK(launch_colmax<T>(A, m, n, lda, bits, s));
+    CK(launch_oz_exp_from_bits(bits, (int)n, exA, s));
+    const bool sc = (passes == 2) && scale;
+    const double *rs1 = nullptr;
+    const int *pkA = nullptr;
+    if (sc) {
+        CK(launch_pow2_scale(bits, n, d, dinv, s));
+        CK(launch_neg_int(exA, (int)n, pk1, s));
+        rs1 = dinv;
+        pkA = pk1;
+    }
+    // B = (A D^-1)^T (A D^-1)
+    CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, P, st, s));
+    CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
+    // B = V~ D~ V~^T
+    CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
+    // Y~ = (A D^-1) V~ = A (D^-1 V~), with A's columns prescaled by D^-1 for
+    // the digit scales (the product is unchanged)
+    const double *M1 = Vt;
+    if (sc) {
+        CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
+        M1 = M;
+    }
+    CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
+    CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
+    CK(launch_oz_nn<T, double>(A, lda, m, (int)n, pkA, er, img, em, (int)n, Yt, n, st, s));
+
+    if (passes == 1) {
+        // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
+        CK(launch_colsumsq(Yt, n, m, n, NP, s));
+        CK(launch_norms_reduce(NP, gcs, n, sig, s));
+        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+        CK(launch_scale2(Vt, n, n, n, nullptr, nullptr, Vo, n, s));
+        CK(launch_signs(Vo, n, n, n, sinv, sgn, s));
+        CK(launch_scale2(sinv, n, 1, n, nullptr, sgn, cs, n, s));
+        CK(launch_convert<TO>(Yt, n, m, n, U, ldu, s));
+        CK(launch_scale_cols_inplace<TO>(U, ldu, m, n, cs, s));
+        CK(launch_keepval(sig, sinv, n, sigma, s));
+        CK(launch_count_positive(sigma, n, &st->rank, s));
+        CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
+        CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
+        return cudaSuccess;
+    }
+
+    // Z = Y^T Y with Y = Y~ Sigma~^-1; Sigma~ = explicit column norms of Y~
+    // (the diagonal of its Gram matrix)
+    CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+    CK(launch_colmax<double>(Yt, m, n, n, bits, s));
+    CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
+    CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, P, st, s));
+    CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
+    CK(launch_diag_sqrt(G2, n, n, sig, s));
+    CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+    CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
+    // Z = W D W^T
+    CK(launch_jacobi_eig(B, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
+    // Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W); T = explicit column norms
+    CK(launch_oz_pow2_of(sinv, (int)n, pk2, s));
+    CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
+    CK(launch_oz_rowexp<double>(Yt, n, m, (int)n, pk2, er, s));
+    CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
+    double *Qb = u_is_double ? (double *)U : Qt;
+    const i64 ldq = u_is_double ? ldu : n;
+    CK(launch_oz_nn<double, double>(Yt, n, m, (int)n, pk2, er, img, em, (int)n, Qb, ldq, st, s));
+    CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
+    CK(launch_norms_reduce(NP, gcs, n, Tn, s));
+    CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
+    CK(launch_keepval(Tn, tinv, n, Tk, s));
+    // R = T W^T Sigma~ V~^T D; R = P Sigma V^T
+    CK(launch_build_g(sig, sinv, Vt, n, sc ? d : nullptr, n, G, s));
+    CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
+    CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+    CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 2, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
+    CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
+    CK(launch_count_positive(sigma, n, &st->rank, s));
+    // U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)), prescaled like Q~
+    CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
+    CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
+    CK(launch_oz_image(M3, n, (int)n, (int)n, pk2, em, img, s));
+    CK(launch_oz_nn<double, TO>(Yt, n, m, (int)n, pk2, er, img, em, (int)n, U, ldu, st, s));
+    CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
+    CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
+    return cudaSuccess;
+}
+
+// Dispatch on the arithmetic mode.
+template <typename T, typename TO>
+cudaError_t ts_any(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
+                   int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
+                   cudaStream_t s, int mode)
+{
+    if (mode == TSSVD_FP64_TC)
+        return ts_core_oz<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps,
+                                 ws, st, s);
+    return ts_core<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps, ws, st,
+                          s, mode);
+}
+
 // Status words are summarised into the ABI's status code.
 int summarise(const std::vector<DevStatus> &sts, int nsolves_per, int *rank_out)
 {
@@ -269,7 +410,7 @@ int check_opts(const tssvd_opts *o)
     if (o->passes != 1 && o->passes != 2) return 0;
     if (!(o->drop_tol >= 0.0) || o->drop_tol >= 1.0) return 0;
     if (o->max_sweeps < 1 || o->max_sweeps > 1000) return 0;
-    if (o->mode != TSSVD_FP64 && o->mode != TSSVD_BF16X3 && o->mode != TSSVD_BF16X6) return 0;
+    if (o->mode < TSSVD_FP64 || o->mode > TSSVD_FP64_TC) return 0;
     return 1;
 }
 
@@ -285,7 +426,7 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     if (!S) return -6;
     if (!V) return -7;
     if (!check_opts(opts)) return -8;
-    if (opts->mode != TSSVD_FP64 && n > 256) {
+    if ((opts->mode == TSSVD_BF16X3 || opts->mode == TSSVD_BF16X6) && n > 256) {
         fprintf(stderr, "tssvd: the mixed-precision modes take n <= 256 (n = %lld)\n",
                 (long long)n);
         return -3;
@@ -294,8 +435,8 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
 
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(1);
-    ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
-                  opts->max_sweeps, sz, nullptr, s, opts->mode);
+    ts_any<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
+                 opts->max_sweeps, sz, nullptr, s, opts->mode);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
@@ -303,8 +444,8 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     Bump ws(base, sz.off);
     DevStatus *st = ws.take<DevStatus>(1);
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
-    cudaError_t e = ts_core<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
-                                  opts->drop_tol, opts->max_sweeps, ws, st, s, opts->mode);
+    cudaError_t e = ts_any<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
+                                 opts->drop_tol, opts->max_sweeps, ws, st, s, opts->mode);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
@@ -429,13 +570,13 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(1);
     if (elem_bytes == 4)
-        ts_core<float, float>(nullptr, m, n, n, (float *)nullptr, n, (float *)nullptr,
-                              (float *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
-                              opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
+        ts_any<float, float>(nullptr, m, n, n, (float *)nullptr, n, (float *)nullptr,
+                             (float *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
+                             opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
     else
-        ts_core<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
-                                (double *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
-                                opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
+        ts_any<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
+                               (double *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
+                               opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
     return sz.off;
 }
 
@@ -527,7 +668,12 @@ size_t ts_gram_workspace_size(int64_t m, int64_t n)
     sz.take<DevStatus>(1);
     const int sp = tn_splits(m, n, n, true);
     const int tsp = tc_gram_splits(m);
-    sz.take<double>((size_t)(sp > tsp ? sp : tsp) * n * n);
+    const int osp = oz_gram_splits(m, (int)n);
+    int mx = sp > tsp ? sp : tsp;
+    mx = mx > osp ? mx : osp;
+    sz.take<double>((size_t)mx * n * n);
+    sz.take<unsigned long long>(n);
+    sz.take<int>(n);
     return sz.off;
 }
 
@@ -561,13 +707,23 @@ int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd
     if (rc) return rc;
     Bump ws(base, need);
     DevStatus *st = ws.take<DevStatus>(1);
-    const int sp = terms ? tc_gram_splits(m) : tn_splits(m, n, n, true);
+    const bool oz = opts->mode == TSSVD_FP64_TC;
+    const int sp = oz ? oz_gram_splits(m, (int)n)
+                      : (terms ? tc_gram_splits(m) : tn_splits(m, n, n, true));
     double *P = ws.take<double>((size_t)sp * n * n);
+    unsigned long long *bits = ws.take<unsigned long long>(n);
+    int *ex = ws.take<int>(n);
     if (ws.overflow) return TSSVD_ENOMEM;
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    if (e == cudaSuccess)
+    if (oz) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s);
+        if (e == cudaSuccess) e = launch_colmax<double>(A, m, n, lda, bits, s);
+        if (e == cudaSuccess) e = launch_oz_exp_from_bits(bits, (int)n, ex, s);
+        if (e == cudaSuccess) e = launch_oz_gram<double>(A, lda, m, (int)n, ex, sp, P, st, s);
+    } else if (e == cudaSuccess) {
         e = terms ? launch_tc_gram<double>(A, lda, m, (int)n, terms, sp, P, st, s)
                   : launch_tn_partial<double, double>(A, lda, A, lda, m, n, n, sp, true, P, s);
+    }
     if (e == cudaSuccess) e = launch_tn_reduce(P, sp, n, n, nullptr, nullptr, true, B, n, s);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
@@ -582,8 +738,11 @@ size_t ts_matmul_workspace_size(int64_t m, int64_t k, int64_t n)
     if (m < 1 || k < 1 || n < 1) return 0;
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(1);
-    sz.take<uint8_t>(tc_split_b_bytes((int)k, (int)n, 3));
+    const size_t a = tc_split_b_bytes((int)k, (int)n, 3), b = oz_image_bytes((int)k, (int)n);
+    sz.take<uint8_t>(a > b ? a : b);
     sz.take<double>((size_t)nn_grid_rows(m, n) * n);
+    sz.take<int>(m);
+    sz.take<int>(n);
     return sz.off;
 }
 
@@ -610,11 +769,20 @@ int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *
     if (rc) return rc;
     Bump ws(base, need);
     DevStatus *st = ws.take<DevStatus>(1);
-    uint8_t *img = ws.take<uint8_t>(tc_split_b_bytes((int)k, (int)n, 3));
+    const size_t ib1 = tc_split_b_bytes((int)k, (int)n, 3), ib2 = oz_image_bytes((int)k, (int)n);
+    uint8_t *img = ws.take<uint8_t>(ib1 > ib2 ? ib1 : ib2);
     double *NP = ws.take<double>((size_t)nn_grid_rows(m, n) * n);
+    int *er = ws.take<int>(m);
+    int *em = ws.take<int>(n);
     if (ws.overflow) return TSSVD_ENOMEM;
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
-    if (terms) {
+    if (opts->mode == TSSVD_FP64_TC) {
+        if (e == cudaSuccess) e = launch_oz_rowexp<double>(A, lda, m, (int)k, nullptr, er, s);
+        if (e == cudaSuccess) e = launch_oz_image(M, ldm, (int)k, (int)n, nullptr, em, img, s);
+        if (e == cudaSuccess)
+            e = launch_oz_nn<double, double>(A, lda, m, (int)k, nullptr, er, img, em, (int)n, C,
+                                             ldc, st, s);
+    } else if (terms) {
         if (e == cudaSuccess) e = launch_tc_split_b(M, ldm, (int)k, (int)n, terms, img, s);
         if (e == cudaSuccess)
             e = launch_tc_nn<double>(A, lda, m, (int)k, img, (int)n, terms, C, ldc, st, s);

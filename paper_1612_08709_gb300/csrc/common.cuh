@@ -71,6 +71,11 @@ cudaError_t launch_nn(const TA *A, i64 lda, const double *B, i64 ldb, i64 m, i64
                       TC *C, i64 ldc, double *NP, cudaStream_t s);
 int nn_grid_rows(i64 m, i64 N);
 
+// Column sums of squares of X (m x n, FP64): partials NP[g][j],
+// g < colsumsq_rows(m, n); sum them with launch_norms_reduce.
+int colsumsq_rows(i64 m, i64 n);
+cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, cudaStream_t s);
+
 // out[j] = sqrt(sum_g NP[g][j]) in fixed order.
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
 
@@ -90,6 +95,32 @@ cudaError_t launch_tc_split_b(const double *M, i64 ldm, int K, int N, int S, uin
 template <typename T>
 cudaError_t launch_tc_nn(const T *A, i64 lda, i64 m, int K, const uint8_t *img, int N, int S,
                          double *C, i64 ldc, DevStatus *st, cudaStream_t s);
+
+// FP64-accurate digit-sliced products on tcgen05 (gemm_oz.cu).
+int oz_gram_tiles(int n);
+int oz_gram_splits(i64 m, int n);
+size_t oz_image_bytes(int K, int N);
+// P[split][i][j] partial Grams of X (m x n); |X[k][j]| <= 2^ex[j].
+template <typename T>
+cudaError_t launch_oz_gram(const T *X, i64 ldx, i64 m, int n, const int *ex, int splits,
+                           double *P, DevStatus *st, cudaStream_t s);
+// Digit image of diag(2^-pk) M (K x N) and its column exponents em.
+cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *pk, int *em,
+                            uint8_t *img, cudaStream_t s);
+// er[r] = exponent bounding row r of A diag(2^pk).
+template <typename T>
+cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, int *er,
+                             cudaStream_t s);
+// C = A M with A prescaled by 2^pk (see launch_oz_image), row exponents er.
+template <typename T, typename TC>
+cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
+                         const uint8_t *img, const int *em, int N, TC *C, i64 ldc, DevStatus *st,
+                         cudaStream_t s);
+cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s);
+// pk[j] = round(log2(sc[j])) (0 for sc[j] <= 0).
+cudaError_t launch_oz_pow2_of(const double *sc, int n, int *pk, cudaStream_t s);
+// out[j] = -in[j].
+cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 
 // -------------------------------------------------------------- Jacobi
 // One-sided (Hestenes) Jacobi with a parallel round-robin pair order, as

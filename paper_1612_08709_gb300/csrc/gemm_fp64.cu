@@ -247,6 +247,32 @@ __global__ void __launch_bounds__(NTHR) nn_kernel(const TA *__restrict__ A, i64 
     }
 }
 
+// Column sums of squares of X (m x n): block (cx, g) covers 32 columns and
+// a fixed row range; NP[g][j] receives its partial (deterministic).
+__global__ void __launch_bounds__(256) colsumsq_kernel(const double *__restrict__ X, i64 ldx, i64 m,
+                                                       i64 n, i64 rows_per,
+                                                       double *__restrict__ NP)
+{
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const i64 c = (i64)blockIdx.x * 32 + lane;
+    const i64 r0 = (i64)blockIdx.y * rows_per;
+    const i64 r1 = r0 + rows_per < m ? r0 + rows_per : m;
+    double acc = 0.0;
+    if (c < n)
+        for (i64 r = r0 + warp; r < r1; r += 8) {
+            const double v = X[r * ldx + c];
+            acc = fma(v, v, acc);
+        }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < n) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += red[w][lane];
+        NP[(i64)blockIdx.y * n + c] = t;
+    }
+}
+
 __global__ void norms_reduce_kernel(const double *__restrict__ NP, int g, i64 N,
                                     double *__restrict__ out)
 {
@@ -348,6 +374,27 @@ cudaError_t launch_nn(const TA *A, i64 lda, const double *B, i64 ldb, i64 m, i64
     const int gy = nn_grid_rows(m, N);
     ProfScope ps_((m > 4 * K ? "nn_tall" : "nn_small"), s);
     nn_kernel<TA, TC><<<dim3(gx, gy), NTHR, 0, s>>>(A, lda, B, ldb, m, K, N, C, ldc, NP);
+    return cudaGetLastError();
+}
+
+int colsumsq_rows(i64 m, i64 n)
+{
+    const int cx = ceil_div_i(n, 32);
+    i64 gy = ((i64)num_sms() * 8 + cx - 1) / cx;
+    const i64 max_gy = (m + 255) / 256;
+    if (gy > max_gy) gy = max_gy;
+    if (gy < 1) gy = 1;
+    if (gy > 65535) gy = 65535;
+    return (int)gy;
+}
+
+cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, cudaStream_t s)
+{
+    const int cx = ceil_div_i(n, 32);
+    const int gy = colsumsq_rows(m, n);
+    const i64 rows_per = (m + gy - 1) / gy;
+    ProfScope ps_("colsumsq", s);
+    colsumsq_kernel<<<dim3(cx, gy), 256, 0, s>>>(X, ldx, m, n, rows_per, NP);
     return cudaGetLastError();
 }
 
