@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ts_2m_x_200", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3", "bf16x6"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3", "bf16x6", "fp64_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-rows", type=int, default=200_000,
@@ -333,6 +333,16 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def bf16_peak(sustained=True):
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    try:
+        with open(p) as f:
+            return float(json.load(f)[key]), "measured (MEASURED_PEAKS.json %s)" % key
+    except (OSError, ValueError, KeyError):
+        return (1700.0 if sustained else 1900.0), "fallback"
+
+
 def roofline(kernels, m, n, ms, args, esize):
     """Roofline entry of the dominant kernel.
 
@@ -349,6 +359,9 @@ def roofline(kernels, m, n, ms, args, esize):
     traffic = load_traffic(name, args.workload, args.mode)
     alu = {"nn_tall": 2.0 * m * n * n, "tn_gram": float(m) * n * (n + 1)}
     hbm = {"tc_gram": float(esize) * m * n, "tc_nn": float(esize) * m * n + 8.0 * m * n}
+    # digit-sliced FP64-accurate products: 28 bf16 digit-pair products per
+    # FP64 product, on the tensor cores
+    tensor = {"oz_nn": 28 * 2.0 * m * n * n, "oz_gram": 28 * float(m) * n * (n + 1)}
     if name in alu:
         ach = alu[name] / per_launch_s / 1e12
         peak = FP64_PEAK_GFLOPS / 1e3
@@ -356,6 +369,13 @@ def roofline(kernels, m, n, ms, args, esize):
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)",
                 "share_of_step": share}
+    if name in tensor:
+        ach = tensor[name] / per_launch_s / 1e12
+        peak, src = bf16_peak(sustained=True)
+        return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic, "peak_source": src,
+                "share_of_step": share,
+                "note": "bf16 digit-pair products (28 per FP64-accurate product)"}
     if name in hbm:
         ach = hbm[name] / per_launch_s / 1e9
         peak, src = hbm_peak()

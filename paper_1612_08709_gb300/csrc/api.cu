@@ -253,6 +253,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     int *perm = ws.take<int>(n);
     double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
     double *Yt = ws.take<double>((size_t)m * n);
+    const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
+    uint8_t *big = ws.take<uint8_t>(gib > rib ? gib : rib);  // digit images of the tall operand
     const bool u_is_double = sizeof(TO) == sizeof(double);
     double *Qt = (passes == 2 && !u_is_double) ? ws.take<double>((size_t)m * n) : nullptr;
     if (sizing) return cudaSuccess;
@@ -272,7 +274,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         pkA = pk1;
     }
     // B = (A D^-1)^T (A D^-1)
-    CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, P, st, s));
+    CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
     // B = V~ D~ V~^T
     CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
@@ -285,7 +287,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     }
     CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
     CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
-    CK(launch_oz_nn<T, double>(A, lda, m, (int)n, pkA, er, img, em, (int)n, Yt, n, st, s));
+    CK(launch_oz_nn<T, double>(A, lda, m, (int)n, pkA, er, big, img, em, (int)n, Yt, n, st, s));
 
     if (passes == 1) {
         // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
@@ -309,7 +311,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
     CK(launch_colmax<double>(Yt, m, n, n, bits, s));
     CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
-    CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, P, st, s));
+    CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, big, P, st, s));
     CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
     CK(launch_diag_sqrt(G2, n, n, sig, s));
     CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
@@ -323,7 +325,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
     double *Qb = u_is_double ? (double *)U : Qt;
     const i64 ldq = u_is_double ? ldu : n;
-    CK(launch_oz_nn<double, double>(Yt, n, m, (int)n, pk2, er, img, em, (int)n, Qb, ldq, st, s));
+    CK(launch_oz_nn<double, double>(Yt, n, m, (int)n, pk2, er, big, img, em, (int)n, Qb, ldq, st,
+                                    s));
     CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
     CK(launch_norms_reduce(NP, gcs, n, Tn, s));
     CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
@@ -341,7 +344,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
     CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
     CK(launch_oz_image(M3, n, (int)n, (int)n, pk2, em, img, s));
-    CK(launch_oz_nn<double, TO>(Yt, n, m, (int)n, pk2, er, img, em, (int)n, U, ldu, st, s));
+    CK(launch_oz_nn<double, TO>(Yt, n, m, (int)n, pk2, er, big, img, em, (int)n, U, ldu, st, s));
     CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
     CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
     return cudaSuccess;
@@ -674,6 +677,7 @@ size_t ts_gram_workspace_size(int64_t m, int64_t n)
     sz.take<double>((size_t)mx * n * n);
     sz.take<unsigned long long>(n);
     sz.take<int>(n);
+    sz.take<uint8_t>(oz_gram_image_bytes(m, (int)n));
     return sz.off;
 }
 
@@ -713,13 +717,14 @@ int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd
     double *P = ws.take<double>((size_t)sp * n * n);
     unsigned long long *bits = ws.take<unsigned long long>(n);
     int *ex = ws.take<int>(n);
+    uint8_t *gimg = ws.take<uint8_t>(oz_gram_image_bytes(m, (int)n));
     if (ws.overflow) return TSSVD_ENOMEM;
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     if (oz) {
         if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s);
         if (e == cudaSuccess) e = launch_colmax<double>(A, m, n, lda, bits, s);
         if (e == cudaSuccess) e = launch_oz_exp_from_bits(bits, (int)n, ex, s);
-        if (e == cudaSuccess) e = launch_oz_gram<double>(A, lda, m, (int)n, ex, sp, P, st, s);
+        if (e == cudaSuccess) e = launch_oz_gram<double>(A, lda, m, (int)n, ex, sp, gimg, P, st, s);
     } else if (e == cudaSuccess) {
         e = terms ? launch_tc_gram<double>(A, lda, m, (int)n, terms, sp, P, st, s)
                   : launch_tn_partial<double, double>(A, lda, A, lda, m, n, n, sp, true, P, s);
@@ -743,6 +748,7 @@ size_t ts_matmul_workspace_size(int64_t m, int64_t k, int64_t n)
     sz.take<double>((size_t)nn_grid_rows(m, n) * n);
     sz.take<int>(m);
     sz.take<int>(n);
+    sz.take<uint8_t>(oz_row_image_bytes(m, (int)k));
     return sz.off;
 }
 
@@ -774,14 +780,15 @@ int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *
     double *NP = ws.take<double>((size_t)nn_grid_rows(m, n) * n);
     int *er = ws.take<int>(m);
     int *em = ws.take<int>(n);
+    uint8_t *aimg = ws.take<uint8_t>(oz_row_image_bytes(m, (int)k));
     if (ws.overflow) return TSSVD_ENOMEM;
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     if (opts->mode == TSSVD_FP64_TC) {
         if (e == cudaSuccess) e = launch_oz_rowexp<double>(A, lda, m, (int)k, nullptr, er, s);
         if (e == cudaSuccess) e = launch_oz_image(M, ldm, (int)k, (int)n, nullptr, em, img, s);
         if (e == cudaSuccess)
-            e = launch_oz_nn<double, double>(A, lda, m, (int)k, nullptr, er, img, em, (int)n, C,
-                                             ldc, st, s);
+            e = launch_oz_nn<double, double>(A, lda, m, (int)k, nullptr, er, aimg, img, em, (int)n,
+                                             C, ldc, st, s);
     } else if (terms) {
         if (e == cudaSuccess) e = launch_tc_split_b(M, ldm, (int)k, (int)n, terms, img, s);
         if (e == cudaSuccess)

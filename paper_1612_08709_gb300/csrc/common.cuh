@@ -20,7 +20,7 @@ struct DevStatus {
     int rank2;     // second discard step
     int rank;      // nonzero singular values returned
     int sweeps[4]; // Jacobi sweeps per solve (-1 = cap reached)
-    int bar[4];    // scratch for the Jacobi grid barrier: count, generation
+    int bar[4];    // scratch for the Jacobi grid barrier (bar[0..1]: 64-bit count)
     int pad[4];
 };
 
@@ -100,10 +100,13 @@ cudaError_t launch_tc_nn(const T *A, i64 lda, i64 m, int K, const uint8_t *img, 
 int oz_gram_tiles(int n);
 int oz_gram_splits(i64 m, int n);
 size_t oz_image_bytes(int K, int N);
-// P[split][i][j] partial Grams of X (m x n); |X[k][j]| <= 2^ex[j].
+size_t oz_gram_image_bytes(i64 m, int n);
+size_t oz_row_image_bytes(i64 m, int K);
+// P[split][i][j] partial Grams of X (m x n); |X[k][j]| <= 2^ex[j].  gimg:
+// scratch of oz_gram_image_bytes(m, n) for the digit image.
 template <typename T>
 cudaError_t launch_oz_gram(const T *X, i64 ldx, i64 m, int n, const int *ex, int splits,
-                           double *P, DevStatus *st, cudaStream_t s);
+                           uint8_t *gimg, double *P, DevStatus *st, cudaStream_t s);
 // Digit image of diag(2^-pk) M (K x N) and its column exponents em.
 cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *pk, int *em,
                             uint8_t *img, cudaStream_t s);
@@ -111,11 +114,12 @@ cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *p
 template <typename T>
 cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, int *er,
                              cudaStream_t s);
-// C = A M with A prescaled by 2^pk (see launch_oz_image), row exponents er.
+// C = A M with A prescaled by 2^pk (see launch_oz_image), row exponents er;
+// aimg: scratch of oz_row_image_bytes(m, K) for A's digit image.
 template <typename T, typename TC>
 cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
-                         const uint8_t *img, const int *em, int N, TC *C, i64 ldc, DevStatus *st,
-                         cudaStream_t s);
+                         uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
+                         DevStatus *st, cudaStream_t s);
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s);
 // pk[j] = round(log2(sc[j])) (0 for sc[j] <= 0).
 cudaError_t launch_oz_pow2_of(const double *sc, int n, int *pk, cudaStream_t s);

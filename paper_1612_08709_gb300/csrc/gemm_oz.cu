@@ -8,25 +8,29 @@
 // orthonormalisation pass) are emulated on the BF16 tensor cores:
 //
 //  * Each operand row (the index that is not summed over) has a power-of-two
-//    scale 2^e bounding its entries.  Relative to it a value is cut into
-//    seven signed base-128 digits: |v| 2^-e = sum_s d_s 2^(-7(s+1)) + tail,
-//    0 <= d_0 <= 128, 0 <= d_s <= 127, |tail| < 2^-49.  The digits are
-//    small integers, exact in bfloat16, and are extracted with integer
-//    operations on the FP64 bit pattern (no FP64 arithmetic).
+//    scale 2^e bounding its entries.  Relative to it a value is rounded to
+//    49 fractional bits and written as seven balanced base-128 digits:
+//    v 2^-e = sum_s d_s 2^(-7(s+1)) + r, |d_0| <= 129, |d_s| <= 64,
+//    |r| <= 2^-50.  The digits are small integers, exact in bfloat16, and
+//    are extracted with integer operations on the bit pattern (no FP64
+//    arithmetic).  Balanced digits and rounding keep the neglected parts
+//    free of sign bias, so their errors do not add up along a long sum.
 //  * A product sum_k a_k b_k becomes sum over digit pairs (s, t) with
-//    s + t <= 6 (28 pairs; dropped pairs weigh < 2^-49) of
+//    s + t <= 6 (28 pairs; the dropped ones weigh about 2^-49) of
 //    2^(ea+eb-14-7(s+t)) sum_k da_s db_t.  Pairs with the same level
 //    L = s + t share one FP32 accumulator in tensor memory (7 levels x 64
-//    columns).  Every term is an integer below 2^14 and a level sums at most
-//    7 * 128 of them per chunk of 128 rows, so the FP32 sums are exact
-//    (< 2^24).
-//  * After each 128-row chunk the epilogue warps combine the seven exact
-//    level sums with error-free FP32 transformations (TwoSum) into a
-//    double-FP32 value and add it to a double-FP32 running sum kept in
-//    registers (about 48 significant bits); FP64 is used only once per
-//    output element, to scale and store the result.
+//    columns).  A row adds at most 129^2 + 2*129*64 + (L-1)*64^2 < 36992
+//    to level L, so over a chunk of 256 rows every level sum stays below
+//    2^24 and is exact.
+//  * After each chunk the epilogue warps combine the seven level sums with
+//    error-free FP32 transformations (TwoSum) into a double-FP32 value and
+//    add it to an FP64 running sum per output (two FP64 additions per
+//    output and chunk, the only FP64 arithmetic of the product).
 //
-// Warp roles, stages and bounded mbarrier waits as in gemm_tc.cu.
+// Each operand is first cut into a digit image in global memory (once per
+// product), laid out exactly as the shared-memory tiles, so the product
+// kernels only stage tiles with bulk copies (TMA) and issue MMAs.  Stages
+// and bounded mbarrier waits as in gemm_tc.cu.
 #include "tc_ptx.cuh"
 
 namespace tssvd {
@@ -39,7 +43,7 @@ constexpr int kDig = 7;           // digits per value
 constexpr int kLevels = 7;        // levels s + t = 0..6
 constexpr int kNT = 64;           // output columns per CTA tile (N of the MMA)
 constexpr int kBK = 32;           // rows (Gram) or k (A*M) per stage
-constexpr int kChunkStages = 4;   // 128 rows/k per exact FP32 chunk
+constexpr int kChunkStages = 8;   // 256 rows/k per FP32 chunk (levels 0-3 exact)
 constexpr int kStages = 2;
 constexpr uint32_t kATerm = 128 * kBK * 2;  // 8 KB: one digit of the 128-row operand
 constexpr uint32_t kBTerm = kNT * kBK * 2;  // 4 KB: one digit of the 64-row operand
@@ -60,41 +64,79 @@ __device__ __forceinline__ void dsplit(double v, int &ev, unsigned long long &ma
     mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
 }
 
-// bfloat16 bit pattern of the signed integer +-d, 0 <= d <= 128.
-__device__ __forceinline__ uint32_t bf16_of_int(uint32_t d, uint32_t sign)
+// The same for a float: 24-bit significand.
+__device__ __forceinline__ void fsplit(float v, int &ev, unsigned long long &mant, uint32_t &sign)
 {
-    if (d == 0) return 0;
-    const uint32_t p = 31 - __clz(d);  // 0..7
-    return (sign << 15) | ((127 + p) << 7) | ((d << (7 - p)) & 0x7F);
+    const uint32_t b = __float_as_uint(v);
+    sign = b >> 31;
+    const int ef = (int)((b >> 23) & 0xFF);
+    if (ef == 0 || ef == 0xFF) {
+        ev = -100000;
+        mant = 0;
+        return;
+    }
+    ev = ef - 127;
+    mant = (unsigned long long)((b & 0x7FFFFFu) | (1u << 23));
 }
 
-// Seven digits of v relative to 2^e (|v| <= 2^e), for a value that is
-// prescaled by 2^p first (p added to its exponent).  out[s] = bf16 bits.
+// bfloat16 bit pattern of the integer d with |d| <= 255.
+__device__ __forceinline__ uint32_t bf16_of_int(int d)
+{
+    if (d == 0) return 0;
+    const uint32_t sign = d < 0 ? 1u : 0u;
+    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+    const uint32_t p = 31 - __clz(a);  // 0..7
+    return (sign << 15) | ((127 + p) << 7) | ((a << (7 - p)) & 0x7F);
+}
+
+// Seven balanced base-128 digits of a value |v| = mant 2^(q) (q = its
+// exponent minus the significand bits), prescaled by 2^p, relative to 2^e:
+// F = round(|v| 2^(p - e) 2^49) is recoded from the least significant end
+// into digits in [-64, 63] (the leading digit takes the carry, <= 129), so
+// the dropped digit pairs and the rounding of F carry no sign bias.
+__device__ __forceinline__ void digits_from(unsigned long long mant, int q, uint32_t vsign, int e,
+                                           int p, uint32_t (&out)[kDig])
+{
+    unsigned long long F = 0;
+    if (mant != 0) {
+        const int sh = q + p - e + 49;  // F = mant * 2^sh
+        if (sh >= 0)
+            F = sh < __clzll((long long)mant) ? (mant << sh) : 0;  // overflow only for a wrong scale
+        else if (sh > -64)
+            F = (mant + (1ull << (-sh - 1))) >> (-sh);
+    }
+    int dg[kDig];
+#pragma unroll
+    for (int s = kDig - 1; s >= 1; s--) {
+        int r = (int)(F & 127);
+        F >>= 7;
+        if (r >= 64) {
+            r -= 128;
+            F += 1;
+        }
+        dg[s] = r;
+    }
+    dg[0] = (int)(F & 0xFF);
+#pragma unroll
+    for (int s = 0; s < kDig; s++) out[s] = bf16_of_int(vsign ? -dg[s] : dg[s]);
+}
+
 __device__ __forceinline__ void digits7(double v, int e, int p, uint32_t (&out)[kDig])
 {
     int ev;
     unsigned long long mant;
     uint32_t sign;
     dsplit(v, ev, mant, sign);
-    // F = floor(|v| 2^(p-e) 2^49) = mant >> (e - ev - p + 3)
-    const int sh = e - (ev + p) + 3;
-    unsigned long long F = 0;
-    if (mant != 0) {
-        if (sh >= 64)
-            F = 0;
-        else if (sh >= 0)
-            F = mant >> sh;
-        else
-            F = mant << (-sh);  // only when |v 2^p| > 2^e: a scale error; keep bits
-    }
-    out[0] = bf16_of_int((uint32_t)(F >> 42) & 0xFF, sign);
-#pragma unroll
-    for (int s = 1; s < kDig; s++) out[s] = bf16_of_int((uint32_t)(F >> (42 - 7 * s)) & 0x7F, sign);
+    digits_from(mant, ev - 52, sign, e, p, out);
 }
 
 __device__ __forceinline__ void digits7(float v, int e, int p, uint32_t (&out)[kDig])
 {
-    digits7((double)v, e, p, out);
+    int ev;
+    unsigned long long mant;
+    uint32_t sign;
+    fsplit(v, ev, mant, sign);
+    digits_from(mant, ev - 23, sign, e, p, out);
 }
 
 // Store 8 values' digits (one 16-byte vector per digit).
@@ -129,9 +171,9 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
                  : "r"(taddr));
 }
 
-// Drain: add sum_L acc_L 2^-7L (exact level sums in TMEM) to the running
-// double-FP32 sums (hi, lo) of this thread's row, 64 columns.
-__device__ __forceinline__ void drain_levels(uint32_t tmem_row, float (&hi)[kNT], float (&lo)[kNT])
+// Drain: add sum_L acc_L 2^-7L (the level sums in TMEM) to the FP64
+// running sums of this thread's row, 64 columns.
+__device__ __forceinline__ void drain_levels(uint32_t tmem_row, double (&acc)[kNT])
 {
 #pragma unroll
     for (int g = 0; g < kNT / 8; g++) {
@@ -141,20 +183,20 @@ __device__ __forceinline__ void drain_levels(uint32_t tmem_row, float (&hi)[kNT]
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 8; c++) {
-            float s = __uint_as_float(lv[0][c]), e = 0.f;
+            // smallest level first; 2^(-7L) is the level's exact weight
+            float s = __uint_as_float(lv[kLevels - 1][c]) *
+                      __uint_as_float((uint32_t)(127 - 7 * (kLevels - 1)) << 23);
+            float e = 0.f;
 #pragma unroll
-            for (int L = 1; L < kLevels; L++) {
+            for (int L = kLevels - 2; L >= 0; L--) {
                 float t, er;
-                // 2^(-7L) exactly: the level's weight relative to level 0
                 const float w = __uint_as_float((uint32_t)(127 - 7 * L) << 23);
-                two_sum(s, __uint_as_float(lv[L][c]) * w, t, er);
+                two_sum(__uint_as_float(lv[L][c]) * w, s, t, er);
                 s = t;
                 e += er;
             }
-            float t, er;
-            two_sum(hi[g * 8 + c], s, t, er);
-            hi[g * 8 + c] = t;
-            lo[g * 8 + c] += er + e;
+            acc[g * 8 + c] += (double)s;
+            acc[g * 8 + c] += (double)e;
         }
     }
 }
@@ -200,92 +242,150 @@ __device__ __forceinline__ bool gram_tile(int t, int n, int &ti, int &tj)
     return false;
 }
 
-// ----------------------------------------------------------------- Gram
-// P[split][i][j] (n x n, FP64) for the (i, j) of the CTA's tile:
-// sum over the split's rows of X[k][i] X[k][j]; ex[c] bounds column c.
+// Threads of the digit-product kernels: warps 0-3 drain TMEM (lane
+// quarters 0-3), warp 4 stages operands with bulk copies, warp 5 issues
+// the MMAs.  Six warps keep at most two per SM sub-partition, so the
+// epilogue's 64 FP64 running sums fit in registers.
+constexpr int kOzThreads = 192;
+
+// Padded column count of a Gram digit image (whole 128-column tiles).
+__host__ __device__ __forceinline__ int gram_npad(int n) { return (n + 127) / 128 * 128; }
+
+// Gram digit image of X (m x n): per 32-row block kb and digit s, two
+// 16-row halves of npad/8 groups of 8 columns (256 bytes each, K-major
+// no-swizzle core layout).  Block (kb, s, h) starts at
+// ((kb * 7 + s) * 2 + h) * npad * 32 bytes.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1)
-    oz_gram_kernel(const T *__restrict__ X, i64 ldx, i64 m, int n, const int *__restrict__ ex,
+__global__ void oz_gram_image_kernel(const T *__restrict__ X, i64 ldx, i64 m, int n,
+                                     const int *__restrict__ ex, uint8_t *__restrict__ img)
+{
+    const int npad = gram_npad(n);
+    const i64 nkb = (m + kBK - 1) / kBK;
+    const i64 total = nkb * (kBK / 8) * npad;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (i64)gridDim.x * blockDim.x) {
+        const int c = (int)(e % npad);
+        const int q = (int)((e / npad) % (kBK / 8));
+        const i64 kb = e / ((i64)npad * (kBK / 8));
+        const int ec = c < n ? ex[c] : 0;
+        uint32_t d[8][kDig];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const i64 k = kb * kBK + 8 * q + r;
+            const T v = (c < n && k < m) ? X[k * ldx + c] : (T)0;
+            digits7(v, ec, 0, d[r]);
+        }
+        const uint32_t half = (uint32_t)npad * 32;
+        uint8_t *base = img + (size_t)kb * kDig * 2 * half + (size_t)(q >> 1) * half;
+        const uint32_t off = (uint32_t)(c >> 3) * 256 + (uint32_t)(q & 1) * 128 + (uint32_t)(c & 7) * 16;
+        store_digits8(base, 2 * half, off, d);
+    }
+}
+
+// Row-operand digit image of A diag(2^pk) (m x K): per 128-row tile and
+// 32-deep k block, 7 digits x 2 halves x 16 groups (56 KB contiguous).
+template <typename T>
+__global__ void oz_row_image_kernel(const T *__restrict__ A, i64 lda, i64 m, int K,
+                                    const int *__restrict__ pk, const int *__restrict__ er,
+                                    uint8_t *__restrict__ img)
+{
+    const int KP = (K + 15) / 16 * 16;
+    const int nkb = (KP + kBK - 1) / kBK;
+    const i64 total = (m + 127) / 128 * 128 * nkb * (kBK / 8);
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (i64)gridDim.x * blockDim.x) {
+        const int q = (int)(e % (kBK / 8));
+        const i64 row = (e / (kBK / 8)) % ((m + 127) / 128 * 128);
+        const int kb = (int)(e / ((kBK / 8) * ((m + 127) / 128 * 128)));
+        const int ei = row < m ? er[row] : 0;
+        uint32_t d[8][kDig];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = kb * kBK + 8 * q + u;
+            const bool in = row < m && k < K;
+            digits7(in ? A[row * lda + k] : (T)0, ei, (in && pk) ? pk[k] : 0, d[u]);
+        }
+        const i64 rt = row >> 7;
+        const int r = (int)(row & 127);
+        uint8_t *base = img + ((size_t)rt * nkb + kb) * kDig * kATerm + (size_t)(q >> 1) * (kATerm / 2);
+        const uint32_t off = (uint32_t)(r >> 3) * 256 + (uint32_t)(q & 1) * 128 + (uint32_t)(r & 7) * 16;
+        store_digits8(base, kATerm, off, d);
+    }
+}
+
+// ----------------------------------------------------------------- Gram
+// P[split][i][j] (n x n, FP64) for the (i, j) of the CTA's tile from the
+// Gram digit image: sum over the split's rows of X[k][i] X[k][j].
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_gram_kernel(const uint8_t *__restrict__ img, i64 m, int n, const int *__restrict__ ex,
                    i64 rows_per_split, double *__restrict__ P, DevStatus *st)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, done_bar;
     __shared__ uint32_t tmem_base_s;
-    __shared__ int exs[128 + kNT];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = &st->err;
     int ti = 0, tj = 0;
     gram_tile(blockIdx.x, n, ti, tj);
     const int i0 = ti * 128, j0 = tj * kNT;
-    const i64 r0 = (i64)blockIdx.y * rows_per_split;
-    const i64 r1 = r0 + rows_per_split < m ? r0 + rows_per_split : m;
-    const int nkb = r1 > r0 ? (int)((r1 - r0 + kBK - 1) / kBK) : 0;
+    const int npad = gram_npad(n);
+    const uint32_t half = (uint32_t)npad * 32;
+    const i64 kb0 = (i64)blockIdx.y * (rows_per_split / kBK);
+    const i64 kbm = (m + kBK - 1) / kBK;
+    i64 kb1 = kb0 + rows_per_split / kBK;
+    if (kb1 > kbm) kb1 = kbm;
+    const int nkb = kb1 > kb0 ? (int)(kb1 - kb0) : 0;
     const int nchunks = (nkb + kChunkStages - 1) / kChunkStages;
 
-    for (int c = threadIdx.x; c < 128 + kNT; c += blockDim.x) {
-        const int col = c < 128 ? i0 + c : j0 + c - 128;
-        exs[c] = col < n ? ex[col] : 0;
-    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
-            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, kEpilogue);
+        mbar_init(&acc_empty, 128);
         mbar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) tmem_alloc(&tmem_base_s, kTmemCols);
+    if (warp == 5) tmem_alloc(&tmem_base_s, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
-    if (warp < 4) {
-        const int tid = threadIdx.x;
-        for (int kb = 0; kb < nkb; kb++) {
-            const int s = kb % kStages;
-            if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, err)) break;
-            uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
-            const i64 k0 = r0 + (i64)kb * kBK;
-            // items: (operand row c of 192, 8-row chunk q of 4)
-            for (int it = tid; it < (128 + kNT) * (kBK / 8); it += kProducers) {
-                const int c = it % (128 + kNT), q = it / (128 + kNT);
-                const int col = c < 128 ? i0 + c : j0 + c - 128;
-                const int e = exs[c];
-                uint32_t d[8][kDig];
+    if (warp == 4) {
+        // ---------------- bulk-copy producer
+        if (lane == 0) {
+            int last = -1;
+            for (int kb = 0; kb < nkb; kb++) {
+                const int s = kb % kStages;
+                if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, err)) break;
+                uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
+                mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+                const uint8_t *blk = img + (size_t)(kb0 + kb) * kDig * 2 * half;
+#pragma unroll 1
+                for (int d = 0; d < kDig; d++)
 #pragma unroll
-                for (int r = 0; r < 8; r++) {
-                    const i64 k = k0 + 8 * q + r;
-                    const T v = (col < n && k < r1) ? X[k * ldx + col] : (T)0;
-                    digits7(v, e, 0, d[r]);
-                }
-                if (c < 128) {
-                    const uint32_t off = (uint32_t)(q >> 1) * (128 * 32) + (uint32_t)(c >> 3) * 256 +
-                                         (uint32_t)(q & 1) * 128 + (uint32_t)(c & 7) * 16;
-                    store_digits8(stage, kATerm, off, d);
-                } else {
-                    const int cb = c - 128;
-                    const uint32_t off = (uint32_t)(q >> 1) * (kNT * 32) + (uint32_t)(cb >> 3) * 256 +
-                                         (uint32_t)(q & 1) * 128 + (uint32_t)(cb & 7) * 16;
-                    store_digits8(stage + kDig * kATerm, kBTerm, off, d);
-                }
+                    for (int h = 0; h < 2; h++) {
+                        const uint8_t *src = blk + (size_t)(d * 2 + h) * half;
+                        bulk_g2s(stage + d * kATerm + h * (kATerm / 2), src + (size_t)(i0 / 8) * 256,
+                                 kATerm / 2, &full_bar[s]);
+                        bulk_g2s(stage + kDig * kATerm + d * kBTerm + h * (kBTerm / 2),
+                                 src + (size_t)(j0 / 8) * 256, kBTerm / 2, &full_bar[s]);
+                    }
+                last = kb;
             }
-            fence_proxy_async();
-            mbar_arrive(&full_bar[s]);
+            if (last >= 0) mbar_wait_drain(&full_bar[last % kStages], (last / kStages) & 1);
         }
-    } else if (warp < 8) {
-        const int ew = warp - 4;
-        float hi[kNT], lo[kNT];
+        __syncwarp();
+    } else if (warp < 4) {
+        // ---------------- epilogue
+        double acc[kNT];
 #pragma unroll
-        for (int j = 0; j < kNT; j++) {
-            hi[j] = 0.f;
-            lo[j] = 0.f;
-        }
-        const uint32_t trow = tmem + ((uint32_t)(ew * 32) << 16);
+        for (int j = 0; j < kNT; j++) acc[j] = 0.0;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         bool ok = true;
         for (int ch = 0; ch < nchunks; ch++) {
             if (!mbar_wait(&acc_full, ch & 1, err)) {
@@ -293,24 +393,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            drain_levels(trow, hi, lo);
+            drain_levels(trow, acc);
             tc_fence_before();
             mbar_arrive(&acc_empty);
         }
         if (ok) {
-            const int il = ew * 32 + lane;
+            const int il = warp * 32 + lane;
             const int i = i0 + il;
             if (i < n) {
                 double *Prow = P + (i64)blockIdx.y * n * n + (i64)i * n;
-                const int ei = exs[il];
+                const int ei = ex[i];
 #pragma unroll
                 for (int jj = 0; jj < kNT; jj++) {
                     const int j = j0 + jj;
-                    if (j < n) Prow[j] = ldexp((double)hi[jj] + (double)lo[jj], ei + exs[128 + jj] - 14);
+                    if (j < n) Prow[j] = ldexp(acc[jj], ei + ex[j] - 14);
                 }
             }
         }
     } else {
+        // ---------------- MMA issuer
         if (lane == 0) {
             int kb = 0;
             bool ok = true;
@@ -344,20 +445,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 5) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------- A * M
-// C[r][j] = sum_k A[r][k] M[k][j] for the CTA's tiles (128 rows x 64
-// columns, persistent over tiles with the column tile fastest).  A's
-// column k is prescaled by 2^pk[k] (exact) and its row r is bounded by
-// 2^er[r]; img holds the digits of diag(2^-pk) M per (column tile, 32-deep
-// k block), 7 x 4 KB each, with the column exponents em.
-template <typename T, typename TC>
-__global__ void __launch_bounds__(kThreads, 1)
-    oz_nn_kernel(const T *__restrict__ A, i64 lda, i64 m, int K, const int *__restrict__ pk,
-                 const int *__restrict__ er, const uint8_t *__restrict__ img,
-                 const int *__restrict__ em, int N, TC *__restrict__ C, i64 ldc, DevStatus *st)
+// C[r][j] = sum_k A[r][k] M[k][j] from the row image of A diag(2^pk) and
+// the image of diag(2^-pk) M; tiles of 128 rows x 64 columns, persistent,
+// column tile fastest.
+template <typename TC>
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_nn_kernel(const uint8_t *__restrict__ aimg, i64 m, int K, const int *__restrict__ er,
+                 const uint8_t *__restrict__ bimg, const int *__restrict__ em, int N,
+                 TC *__restrict__ C, i64 ldc, DevStatus *st)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
@@ -373,92 +472,68 @@ __global__ void __launch_bounds__(kThreads, 1)
     const i64 ntiles = (m + 127) / 128 * TN;
     const int my_tiles =
         (i64)blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-    const size_t img_tile = (size_t)nkb * kDig * kBTerm;
+    const size_t btile = (size_t)nkb * kDig * kBTerm;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
-            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_full, 1);
-        mbar_init(&acc_empty, kEpilogue);
+        mbar_init(&acc_empty, 128);
         mbar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) tmem_alloc(&tmem_base_s, kTmemCols);
+    if (warp == 5) tmem_alloc(&tmem_base_s, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
 
-    if (warp < 4) {
-        const int tid = threadIdx.x;
-        int f = 0, last_copy = -1;
-        bool ok = true;
-        for (int ti = 0; ti < my_tiles && ok; ti++) {
-            const i64 t = (i64)blockIdx.x + (i64)ti * gridDim.x;
-            const i64 rbase = (t / TN) * 128;
-            const int nt = (int)(t % TN);
-            for (int kb = 0; kb < nkb; kb++, f++) {
-                const int s = f % kStages;
-                if (!mbar_wait(&empty_bar[s], ((f / kStages) & 1) ^ 1, err)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
-                if (tid == 0) {
-                    const uint32_t bytes = kDig * kBTerm;
-                    mbar_expect_tx(&full_bar[s], bytes);
-                    bulk_g2s(stage + kDig * kATerm, img + (size_t)nt * img_tile + (size_t)kb * bytes,
-                             bytes, &full_bar[s]);
-                    last_copy = f;
-                }
-                const int k0 = kb * kBK;
-                // items: (row r of 128, 8-k chunk q of 4)
-                for (int it = tid; it < 128 * (kBK / 8); it += kProducers) {
-                    const int r = it >> 2, q = it & 3;
-                    const i64 row = rbase + r;
-                    const int e = row < m ? er[row] : 0;
-                    uint32_t d[8][kDig];
-#pragma unroll
-                    for (int u = 0; u < 8; u++) {
-                        const int k = k0 + 8 * q + u;
-                        const bool in = row < m && k < K;
-                        const T v = in ? A[row * lda + k] : (T)0;
-                        digits7(v, e, (in && pk) ? pk[k] : 0, d[u]);
+    if (warp == 4) {
+        if (lane == 0) {
+            int f = 0, last = -1;
+            bool ok = true;
+            for (int ti = 0; ti < my_tiles && ok; ti++) {
+                const i64 t = (i64)blockIdx.x + (i64)ti * gridDim.x;
+                const i64 rt = t / TN;
+                const int nt = (int)(t % TN);
+                for (int kb = 0; kb < nkb; kb++, f++) {
+                    const int s = f % kStages;
+                    if (!mbar_wait(&empty_bar[s], ((f / kStages) & 1) ^ 1, err)) {
+                        ok = false;
+                        break;
                     }
-                    const uint32_t off = (uint32_t)(q >> 1) * (128 * 32) + (uint32_t)(r >> 3) * 256 +
-                                         (uint32_t)(q & 1) * 128 + (uint32_t)(r & 7) * 16;
-                    store_digits8(stage, kATerm, off, d);
+                    uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
+                    mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+                    bulk_g2s(stage, aimg + ((size_t)rt * nkb + kb) * kDig * kATerm, kDig * kATerm,
+                             &full_bar[s]);
+                    bulk_g2s(stage + kDig * kATerm, bimg + (size_t)nt * btile + (size_t)kb * kDig * kBTerm,
+                             kDig * kBTerm, &full_bar[s]);
+                    last = f;
                 }
-                fence_proxy_async();
-                mbar_arrive(&full_bar[s]);
             }
+            if (last >= 0) mbar_wait_drain(&full_bar[last % kStages], (last / kStages) & 1);
         }
-        if (tid == 0 && last_copy >= 0)
-            mbar_wait_drain(&full_bar[last_copy % kStages], (last_copy / kStages) & 1);
-    } else if (warp < 8) {
-        const int ew = warp - 4;
-        const uint32_t trow = tmem + ((uint32_t)(ew * 32) << 16);
+        __syncwarp();
+    } else if (warp < 4) {
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         int ch_global = 0;
         bool ok = true;
         for (int ti = 0; ti < my_tiles && ok; ti++) {
             const i64 t = (i64)blockIdx.x + (i64)ti * gridDim.x;
-            const i64 row = (t / TN) * 128 + ew * 32 + lane;
+            const i64 row = (t / TN) * 128 + warp * 32 + lane;
             const int nt = (int)(t % TN);
-            float hi[kNT], lo[kNT];
+            double acc[kNT];
 #pragma unroll
-            for (int j = 0; j < kNT; j++) {
-                hi[j] = 0.f;
-                lo[j] = 0.f;
-            }
+            for (int j = 0; j < kNT; j++) acc[j] = 0.0;
             for (int ch = 0; ch < nchunks; ch++, ch_global++) {
                 if (!mbar_wait(&acc_full, ch_global & 1, err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                drain_levels(trow, hi, lo);
+                drain_levels(trow, acc);
                 tc_fence_before();
                 mbar_arrive(&acc_empty);
             }
@@ -468,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int jj = 0; jj < kNT; jj++) {
                     const int j = nt * kNT + jj;
-                    if (j < N) C[row * ldc + j] = (TC)ldexp((double)hi[jj] + (double)lo[jj], e + em[j] - 14);
+                    if (j < N) C[row * ldc + j] = (TC)ldexp(acc[jj], e + em[j] - 14);
                 }
             }
         }
@@ -511,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 5) tmem_dealloc(tmem, kTmemCols);
 }
 
 // Column exponents of diag(2^-pk) M (K x N): em[j] = smallest e with
@@ -674,20 +749,39 @@ size_t oz_image_bytes(int K, int N)
     return (size_t)TN * nkb * kDig * kBTerm;
 }
 
+size_t oz_gram_image_bytes(i64 m, int n)
+{
+    return (size_t)((m + kBK - 1) / kBK) * kDig * 2 * (size_t)gram_npad(n) * 32;
+}
+
+size_t oz_row_image_bytes(i64 m, int K)
+{
+    const int KP = (K + 15) / 16 * 16;
+    const int nkb = (KP + kBK - 1) / kBK;
+    return (size_t)((m + 127) / 128) * nkb * kDig * kATerm;
+}
+
 template <typename T>
 cudaError_t launch_oz_gram(const T *X, i64 ldx, i64 m, int n, const int *ex, int splits,
-                           double *P, DevStatus *st, cudaStream_t s)
+                           uint8_t *gimg, double *P, DevStatus *st, cudaStream_t s)
 {
-    i64 rows = (m + splits - 1) / splits;
-    rows = (rows + 127) / 128 * 128;
-    const size_t smem = (size_t)kStages * kStageBytes;
-    auto k = oz_gram_kernel<T>;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    {
+        const i64 total = (m + kBK - 1) / kBK * (kBK / 8) * gram_npad(n);
+        ProfScope ps_("oz_gram_image", s);
+        oz_gram_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(X, ldx, m, n, ex, gimg);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // whole 32-row blocks per split
+    i64 kbs = ((m + kBK - 1) / kBK + splits - 1) / splits;
+    const i64 rows = kbs * kBK;
+    const size_t smem = (size_t)kStages * kStageBytes;
+    if ((e = cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
         return e;
     ProfScope ps_("oz_gram", s);
-    k<<<dim3(oz_gram_tiles(n), splits), kThreads, smem, s>>>(X, ldx, m, n, ex, rows, P, st);
+    oz_gram_kernel<<<dim3(oz_gram_tiles(n), splits), kOzThreads, smem, s>>>(gimg, m, n, ex, rows,
+                                                                          P, st);
     return cudaGetLastError();
 }
 
@@ -719,19 +813,26 @@ cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, i
 
 template <typename T, typename TC>
 cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
-                         const uint8_t *img, const int *em, int N, TC *C, i64 ldc, DevStatus *st,
-                         cudaStream_t s)
+                         uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
+                         DevStatus *st, cudaStream_t s)
 {
-    const size_t smem = (size_t)kStages * kStageBytes;
-    auto k = oz_nn_kernel<T, TC>;
     cudaError_t e;
+    {
+        const int KP = (K + 15) / 16 * 16;
+        const i64 total = (m + 127) / 128 * 128 * ((KP + kBK - 1) / kBK) * (kBK / 8);
+        ProfScope ps_("oz_row_image", s);
+        oz_row_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(A, lda, m, K, pk, er, aimg);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem = (size_t)kStages * kStageBytes;
+    auto k = oz_nn_kernel<TC>;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
     const i64 ntiles = (m + 127) / 128 * ((N + kNT - 1) / kNT);
     const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
     ProfScope ps_("oz_nn", s);
-    k<<<grid, kThreads, smem, s>>>(A, lda, m, K, pk, er, img, em, N, C, ldc, st);
+    k<<<grid, kOzThreads, smem, s>>>(aimg, m, K, er, bimg, em, N, C, ldc, st);
     return cudaGetLastError();
 }
 
@@ -757,21 +858,24 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s)
 }
 
 template cudaError_t launch_oz_gram<double>(const double *, i64, i64, int, const int *, int,
-                                            double *, DevStatus *, cudaStream_t);
+                                            uint8_t *, double *, DevStatus *, cudaStream_t);
 template cudaError_t launch_oz_gram<float>(const float *, i64, i64, int, const int *, int,
-                                           double *, DevStatus *, cudaStream_t);
+                                           uint8_t *, double *, DevStatus *, cudaStream_t);
 template cudaError_t launch_oz_rowexp<double>(const double *, i64, i64, int, const int *, int *,
                                               cudaStream_t);
 template cudaError_t launch_oz_rowexp<float>(const float *, i64, i64, int, const int *, int *,
                                              cudaStream_t);
 template cudaError_t launch_oz_nn<double, double>(const double *, i64, i64, int, const int *,
-                                                  const int *, const uint8_t *, const int *, int,
-                                                  double *, i64, DevStatus *, cudaStream_t);
+                                                  const int *, uint8_t *, const uint8_t *,
+                                                  const int *, int, double *, i64, DevStatus *,
+                                                  cudaStream_t);
 template cudaError_t launch_oz_nn<float, double>(const float *, i64, i64, int, const int *,
-                                                 const int *, const uint8_t *, const int *, int,
-                                                 double *, i64, DevStatus *, cudaStream_t);
+                                                 const int *, uint8_t *, const uint8_t *,
+                                                 const int *, int, double *, i64, DevStatus *,
+                                                 cudaStream_t);
 template cudaError_t launch_oz_nn<double, float>(const double *, i64, i64, int, const int *,
-                                                 const int *, const uint8_t *, const int *, int,
-                                                 float *, i64, DevStatus *, cudaStream_t);
+                                                 const int *, uint8_t *, const uint8_t *,
+                                                 const int *, int, float *, i64, DevStatus *,
+                                                 cudaStream_t);
 
 }  // namespace tssvd

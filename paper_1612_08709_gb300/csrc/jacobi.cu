@@ -15,7 +15,8 @@
 // separated by a grid-wide barrier.  The kernel is launched cooperatively
 // so all CTAs are co-resident, and every wait in the barrier is bounded
 // (about two seconds of %globaltimer); on expiry the kernel sets the error
-// word of the status block and all CTAs return.
+// word of the status block and all CTAs return.  The 64-bit arrival counter
+// grows by gridDim.x per barrier and is zeroed before every launch.
 #include "common.cuh"
 
 namespace tssvd {
@@ -33,34 +34,55 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
-// Grid barrier with a bounded wait.  Returns false when the call must be
-// abandoned (this CTA or another timed out).
-__device__ bool grid_barrier(int *count, int *gen, int *err)
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid barrier with a bounded wait.  The arrival counter only grows: the
+// e-th barrier of the launch (epoch e, counted by every CTA) completes when
+// it reaches e * gridDim.x.  One release-add per CTA to arrive, acquire
+// loads to wait.  Returns false when the call must be abandoned (this CTA
+// or another timed out).
+__device__ bool grid_barrier(unsigned long long *count, int &epoch, int *err)
 {
     __shared__ int s_ok;
     __syncthreads();
+    epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const int my_gen = ld_volatile(gen);
-        __threadfence();
-        const int arrived = atomicAdd(count, 1) + 1;
-        if (arrived == (int)gridDim.x) {
-            atomicExch(count, 0);
-            __threadfence();
-            atomicAdd(gen, 1);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (ld_volatile(gen) == my_gen) {
-                if (ld_volatile(err) != 0) break;
-                if (global_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicCAS(err, 0, TSSVD_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
+        red_release_add64(count, 1ull);
+        const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+        int spins = 0;
+        unsigned long long t0 = 0;
+        while (ld_acquire64(count) < target) {
+            if (++spins < 256) continue;
+            if (t0 == 0) t0 = global_ns();
+            if (ld_volatile(err) != 0) {
+                ok = 0;
+                break;
             }
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+                atomicCAS(err, 0, TSSVD_ETIMEOUT);
+                ok = 0;
+                break;
+            }
+            spins = 200;
         }
-        __threadfence();
-        if (ld_volatile(err) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -80,15 +102,24 @@ struct JacobiArgs {
     int which;
 };
 
+// Block sums of three per-thread partials; the totals are valid in
+// thread 0 only.  A halving shuffle tree in which only the receiving lanes
+// add, then thread 0 adds the warp partials in a fixed order (FP64
+// arithmetic is scarce on this part, so no lane does redundant adds).
 template <int NT>
 __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*red)[NT / 32])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
+        const double ta = __shfl_down_sync(0xffffffffu, a, o);
+        const double tb = __shfl_down_sync(0xffffffffu, b, o);
+        const double tc = __shfl_down_sync(0xffffffffu, c, o);
+        if (lane < o) {
+            a += ta;
+            b += tb;
+            c += tc;
+        }
     }
     if (lane == 0) {
         red[0][warp] = a;
@@ -96,15 +127,16 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
         red[2][warp] = c;
     }
     __syncthreads();
-    // every thread sums the warp partials in the same fixed order
-    a = 0.0;
-    b = 0.0;
-    c = 0.0;
+    if (threadIdx.x == 0) {
+        a = red[0][0];
+        b = red[1][0];
+        c = red[2][0];
 #pragma unroll
-    for (int w = 0; w < NT / 32; w++) {
-        a += red[0][w];
-        b += red[1][w];
-        c += red[2][w];
+        for (int w = 1; w < NT / 32; w++) {
+            a += red[0][w];
+            b += red[1][w];
+            c += red[2][w];
+        }
     }
 }
 
@@ -112,13 +144,14 @@ template <int NT>
 __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
 {
     __shared__ double red[3][NT / 32];
+    __shared__ double rot_s[3];
     const int npairs = p.npad / 2;
     const int rounds = p.npad - 1;
     const double tol = p.tol;
     int local_rot = 0;
     int done = -1;
-    int *bar_count = &p.st->bar[0];
-    int *bar_gen = &p.st->bar[1];
+    unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
+    int epoch = 0;
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
         for (int t = 0; t < rounds; t++) {
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
@@ -141,18 +174,32 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                     ga = fma(u, v, ga);
                 }
                 block_sum3<NT>(al, be, ga, red);
-                __syncthreads();  // red is reused by the next pair
-                if (ga == 0.0 || !(fabs(ga) > tol * sqrt(al * be))) continue;
-                // tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0,
-                // which annihilates the (P,Q) inner product.
-                const double zeta = (be - al) / (2.0 * ga);
-                double tt;
-                if (fabs(zeta) > 1e150)
-                    tt = 0.5 / zeta;
-                else
-                    tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + tt * tt);
-                const double s = c * tt;
+                // one thread computes the rotation (FP64 division and square
+                // root are slow on this part), the block reads it from smem
+                if (threadIdx.x == 0) {
+                    double c = 1.0, sn = 0.0, rot = 0.0;
+                    if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+                        // tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0,
+                        // which annihilates the (P,Q) inner product.
+                        const double zeta = (be - al) / (2.0 * ga);
+                        double tt;
+                        if (fabs(zeta) > 1e150)
+                            tt = 0.5 / zeta;
+                        else
+                            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = c * tt;
+                        rot = 1.0;
+                    }
+                    rot_s[0] = c;
+                    rot_s[1] = sn;
+                    rot_s[2] = rot;
+                }
+                __syncthreads();  // rotation visible; red free for the next pair
+                const double c = rot_s[0], s = rot_s[1];
+                const bool do_rot = rot_s[2] != 0.0;
+                __syncthreads();  // rot_s is rewritten by the next pair
+                if (!do_rot) continue;
                 if (threadIdx.x == 0) local_rot++;
                 for (int i = threadIdx.x; i < p.nr; i += NT) {
                     const double u = __ldcg(xp + i), v = __ldcg(xq + i);
@@ -171,9 +218,9 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                 atomicAdd(p.rot + sweep, local_rot);
                 local_rot = 0;
             }
-            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
         }
-        if (ld_volatile(p.rot + sweep) == 0) {
+        if (ld_acquire(p.rot + sweep) == 0) {
             done = sweep + 1;
             break;
         }
@@ -242,8 +289,8 @@ __global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
     const int n = p.n;
     int local_rot = 0;
     int done = -1;
-    int *bar_count = &p.st->bar[0];
-    int *bar_gen = &p.st->bar[1];
+    unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
+    int epoch = 0;
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
         for (int t = 0; t < rounds; t++) {
             // ---- phase A: rotation of each pair from its 2 x 2 block
@@ -276,7 +323,7 @@ __global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
                 atomicAdd(p.rot + sweep, local_rot);
                 local_rot = 0;
             }
-            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
             // ---- phase B: rows P, Q of J^T B J and columns P, Q of V J
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
                 int P, Q;
@@ -326,9 +373,9 @@ __global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
                     }
                 }
             }
-            if (!grid_barrier(bar_count, bar_gen, &p.st->err)) return;
+            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
         }
-        if (ld_volatile(p.rot + sweep) == 0) {
+        if (ld_acquire(p.rot + sweep) == 0) {
             done = sweep + 1;
             break;
         }

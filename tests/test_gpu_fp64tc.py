@@ -73,7 +73,11 @@ def test_fp64tc_ts_svd_matches_oracle(orc, m, n, lo, seed, passes, scale):
                                drop_tol=0.0, mode="fp64_tc")
     U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
     assert info["rank"] == rr
-    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    # Algorithm 3 takes sigma from the Gram matrix, which resolves sigma_j
+    # only to about eps * sigma_1^2 / sigma_j (1e-8 at condition 1e8), for
+    # the oracle and the GPU alike
+    s_tol = 1e-11 if (passes == 2 or lo >= 1e-6) else 1e-7
+    assert np.abs(S - Sr).max() <= s_tol * Sr[0]
     if passes == 2:
         assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-12
         assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
