@@ -4,7 +4,10 @@
 One step = one full call of the hot path on one batch of synthetic input:
 by default the two-pass Gram TS-SVD (Algorithm 4 with MaxEntry scaling) of
 a 2,000,000 x 200 FP64 matrix A = U diag(sigma) V^T with seeded
-orthonormal factors and sigma geometric from 1 to 1e-8.
+orthonormal factors and sigma geometric from 1 to 1e-8, in the
+FP64-accurate tensor-core mode (digit-sliced products on tcgen05).  The
+plain FP64 (DFMA) path is timed beside it on the same input
+("fp64_path"), with both accuracies, for the comparison at equal accuracy.
 
 Prints one JSON line (rank 0).  `value` is GFLOP/s of the algorithm's
 nominal products (8 m n^2 for two passes: Gram A^T A, A V~, Gram Y^T Y,
@@ -56,7 +59,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ts_2m_x_200", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "bf16x3", "bf16x6", "fp64_tc"])
+    ap.add_argument("--mode", default="fp64_tc", choices=["fp64", "bf16x3", "bf16x6", "fp64_tc"])
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 path reported beside the headline "
+                         "(0 to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-rows", type=int, default=200_000,
@@ -254,6 +260,37 @@ def run_ours(args):
         orth_v = float((V.T @ V - torch.eye(n, dtype=V.dtype, device=dev)).abs().max())
         resid = float(torch.linalg.norm(A @ V - U * S) / torch.linalg.norm(A))
 
+    # the plain FP64 (DFMA) path on the same input, for "vs plain FP64 at
+    # equal accuracy"
+    fp64_path = None
+    if args.mode != "fp64" and args.compare_steps > 0:
+        kw64 = dict(kw)
+        kw64["mode"] = "fp64"
+        wsb64 = pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode="fp64")
+        if wsb64 > ws.numel():
+            ws = torch.empty((wsb64,), dtype=torch.uint8, device=dev)
+        kw64["workspace"] = ws
+        U64, S64, V64 = torch.empty_like(U), torch.empty_like(S), torch.empty_like(V)
+        kw64["out"] = (U64, S64, V64)
+        pkg.ts_svd(A, **kw64)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.compare_steps):
+            pkg.ts_svd(A, **kw64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = g0.elapsed_time(g1) / args.compare_steps
+        with torch.no_grad():
+            eye = torch.eye(n, dtype=U.dtype, device=dev)
+            fp64_path = {"value": flops / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64,
+                         "steps": args.compare_steps,
+                         "sigma_err_normwise": float((S64 - s_t).abs().max() / s_t[0]),
+                         "orth_U": float((U64.T @ U64 - eye).abs().max()),
+                         "speedup_of_headline": ms64 / ms_max}
+        del U64, S64, V64
+
     # end to end: pinned host buffers, copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
@@ -311,6 +348,7 @@ def run_ours(args):
                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 8 / 1e9),
                       "parallelism": "replicas" if world > 1 else "single"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+           "fp64_path": fp64_path,
            "clocks": clk,
            "accuracy": {"sigma_err_normwise": sig_err, "orth_U": orth_u, "orth_V": orth_v,
                         "residual_rel": resid, "rank": info["rank"],

@@ -162,6 +162,12 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     const double *V, const double *dU, const double *dS, const double *dV,
                     double *dA, tssvd_opts *opts);
 
+/* As ts_svd_backward for FP32 storage (the FP32 forward of ts_svd_f32);
+ * the adjoint is evaluated in FP64 and dA rounded to FP32. */
+int ts_svd_backward_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *S,
+                        const float *V, const float *dU, const float *dS, const float *dV,
+                        float *dA, tssvd_opts *opts);
+
 /*
  * Gram matrix B = A^T A of A (m x n, row-major, lda >= n): the first step of
  * Algorithms 3 and 4 (and the Z = Y^T Y step of Algorithm 4), in FP64 on

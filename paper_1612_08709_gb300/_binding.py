@@ -81,8 +81,10 @@ def lib():
         f.restype = ctypes.c_int
     L.lowrank_svd.argtypes = [vp, i64, i64, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp, op]
     L.lowrank_svd.restype = ctypes.c_int
-    L.ts_svd_backward.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
-    L.ts_svd_backward.restype = ctypes.c_int
+    for name in ("ts_svd_backward", "ts_svd_backward_f32"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
+        f.restype = ctypes.c_int
     L.ts_gram_workspace_size.argtypes = [i64, i64]
     L.ts_gram_workspace_size.restype = ctypes.c_size_t
     L.ts_gram.argtypes = [vp, i64, i64, i64, vp, op]
@@ -106,7 +108,8 @@ def exported_symbols():
     return ["tssvd_default_opts", "tssvd_status_string", "ts_svd_workspace_size", "ts_svd",
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
-            "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul"]
+            "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
+            "ts_svd_backward_f32"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -239,15 +242,20 @@ def ts_matmul(A, M, mode="fp64", stream=None, workspace=None):
 
 
 def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):
-    """dA of the thin SVD (see include/tssvd.h, ts_svd_backward)."""
+    """dA of the thin SVD (see include/tssvd.h, ts_svd_backward); FP64 or
+    FP32 storage (all tensors of A's dtype)."""
     A = _as_matrix(A)
     m, n = A.shape
-    dA = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    dt = A.dtype
+    dA = torch.empty((m, n), dtype=dt, device=A.device)
     c = [x.contiguous() if x is not None else None for x in (S, V, dU, dS, dV)]
+    for x in c:
+        if x is not None and x.dtype != dt:
+            raise TsSvdError("ts_svd_backward: all tensors must have A's dtype")
     o = _opts(stream=stream, workspace=workspace)
+    f = lib().ts_svd_backward if dt == torch.float64 else lib().ts_svd_backward_f32
     with torch.cuda.device(A.device):
-        rc = lib().ts_svd_backward(_ptr(A), m, n, A.stride(0), *[_ptr(x) for x in c], _ptr(dA),
-                                   ctypes.byref(o))
+        rc = f(_ptr(A), m, n, A.stride(0), *[_ptr(x) for x in c], _ptr(dA), ctypes.byref(o))
     _check(rc, "ts_svd_backward")
     return dA
 
@@ -257,8 +265,8 @@ class TSSVD(torch.autograd.Function):
     (U is recomputed from A, V and S rather than stored)."""
 
     @staticmethod
-    def forward(ctx, A, passes=2, scale=True, drop_tol=0.0):
-        U, S, V, info = ts_svd(A, passes=passes, scale=scale, drop_tol=drop_tol)
+    def forward(ctx, A, passes=2, scale=True, drop_tol=0.0, mode="fp64"):
+        U, S, V, info = ts_svd(A, passes=passes, scale=scale, drop_tol=drop_tol, mode=mode)
         ctx.save_for_backward(A, S, V)
         return U, S, V
 
@@ -266,4 +274,4 @@ class TSSVD(torch.autograd.Function):
     def backward(ctx, gU, gS, gV):
         A, S, V = ctx.saved_tensors
         dA = ts_svd_backward(A, S, V, dU=gU, dS=gS, dV=gV)
-        return dA, None, None, None
+        return dA, None, None, None, None

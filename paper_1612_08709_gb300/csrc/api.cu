@@ -536,6 +536,108 @@ cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, i
     return cudaSuccess;
 }
 
+// Thin-SVD adjoint for storage type T; all arithmetic in FP64.
+template <typename T>
+int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, const T *V,
+                   const T *dU, const T *dS, const T *dV, T *dA, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (lda < n) return -4;
+    if (!S) return -5;
+    if (!V) return -6;
+    if (!dA) return -10;
+    if (!opts) return -11;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 nn = n * n;
+    const int spJ = tn_splits(m, n, n, false);
+    const int spK = tn_splits(n, n, n, false);
+    const int sp = spJ > spK ? spJ : spK;
+    const int gy = nn_grid_rows(m, n);
+    const bool dbl = sizeof(T) == sizeof(double);
+    struct Bufs {
+        double *Ub, *sinv, *M0, *J, *K, *Mc, *Vtr, *BB, *P, *NP, *Sd, *Vd, *dSd, *dVd, *dAd;
+    } b;
+    auto carve = [&](Bump &w) {
+        b.Ub = w.take<double>((size_t)m * 2 * n);
+        b.sinv = w.take<double>(n);
+        b.M0 = w.take<double>(nn);
+        b.J = w.take<double>(nn);
+        b.K = w.take<double>(nn);
+        b.Mc = w.take<double>(nn);
+        b.Vtr = w.take<double>(nn);
+        b.BB = w.take<double>(2 * nn);
+        b.P = w.take<double>((size_t)sp * nn);
+        b.NP = w.take<double>((size_t)gy * n);
+        b.Sd = w.take<double>(n);
+        b.Vd = w.take<double>(nn);
+        b.dSd = w.take<double>(n);
+        b.dVd = w.take<double>(nn);
+        b.dAd = dbl ? nullptr : w.take<double>((size_t)m * n);
+    };
+    Bump sz(nullptr, 0);
+    carve(sz);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off);
+    carve(ws);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    auto body = [&]() -> cudaError_t {
+        // FP64 copies of the small operands
+        CK(launch_to_double<T>(S, n, 1, n, b.Sd, n, s));
+        CK(launch_to_double<T>(V, n, n, n, b.Vd, n, s));
+        if (dS) CK(launch_to_double<T>(dS, n, 1, n, b.dSd, n, s));
+        if (dV) CK(launch_to_double<T>(dV, n, n, n, b.dVd, n, s));
+        // sinv = 1/S (the discard rule with tol 0 inverts every S_j > 0)
+        CK(launch_discard(b.Sd, n, 0.0, b.sinv, nullptr, s));
+        // U = A V S^-1 (recomputed), the left half of [U | dU]
+        CK(launch_scale2(b.Vd, n, n, n, nullptr, b.sinv, b.M0, n, s));
+        CK(launch_nn<T, double>(A, lda, b.M0, n, m, n, n, b.Ub, 2 * n, b.NP, s));
+        if (dU) {
+            CK(launch_to_double<T>(dU, n, m, n, b.Ub + n, 2 * n, s));
+            // J = U^T dU
+            CK(launch_tn_partial<double, double>(b.Ub, 2 * n, b.Ub + n, 2 * n, m, n, n, spJ,
+                                                 false, b.P, s));
+            CK(launch_tn_reduce(b.P, spJ, n, n, nullptr, nullptr, false, b.J, n, s));
+        } else {
+            CK(cudaMemset2DAsync(b.Ub + n, sizeof(double) * 2 * n, 0, sizeof(double) * n, m, s));
+        }
+        if (dV) {
+            // K = V^T dV
+            CK(launch_tn_partial<double, double>(b.Vd, n, b.dVd, n, n, n, n, spK, false, b.P, s));
+            CK(launch_tn_reduce(b.P, spK, n, n, nullptr, nullptr, false, b.K, n, s));
+        }
+        CK(launch_adjoint_core(dU ? b.J : nullptr, dV ? b.K : nullptr, b.Sd, dS ? b.dSd : nullptr,
+                               n, b.Mc, s));
+        // BB = [Core V^T ; S^-1 V^T]  (2n x n)
+        CK(launch_transpose(b.Vd, n, n, n, nullptr, b.Vtr, n, s));
+        CK(launch_nn<double, double>(b.Mc, n, b.Vtr, n, n, n, n, b.BB, n, b.NP, s));
+        CK(launch_transpose(b.Vd, n, n, n, b.sinv, b.BB + nn, n, s));
+        // dA = [U | dU] BB
+        if (dbl) {
+            CK(launch_nn<double, T>(b.Ub, 2 * n, b.BB, n, m, 2 * n, n, dA, n, b.NP, s));
+        } else {
+            CK(launch_nn<double, double>(b.Ub, 2 * n, b.BB, n, m, 2 * n, n, b.dAd, n, b.NP, s));
+            CK(launch_convert<T>(b.dAd, n, m, n, dA, n, s));
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e = body();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return TSSVD_OK;
+}
+
 }  // namespace
 }  // namespace tssvd
 
@@ -808,83 +910,14 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     const double *V, const double *dU, const double *dS, const double *dV,
                     double *dA, tssvd_opts *opts)
 {
-    if (!A) return -1;
-    if (m < 1 || m < n) return -2;
-    if (n < 1 || n > 16384) return -3;
-    if (lda < n) return -4;
-    if (!S) return -5;
-    if (!V) return -6;
-    if (!dA) return -10;
-    if (!opts) return -11;
-    cudaStream_t s = (cudaStream_t)opts->stream;
-    const i64 nn = n * n;
-    const int spJ = tn_splits(m, n, n, false);
-    const int spK = tn_splits(n, n, n, false);
-    const int sp = spJ > spK ? spJ : spK;
-    const int gy = nn_grid_rows(m, n);
-    auto carve = [&](Bump &w, double **Ub, double **sinv, double **M0, double **J, double **K,
-                     double **Mc, double **Vtr, double **BB, double **P, double **NP) {
-        *Ub = w.take<double>((size_t)m * 2 * n);
-        *sinv = w.take<double>(n);
-        *M0 = w.take<double>(nn);
-        *J = w.take<double>(nn);
-        *K = w.take<double>(nn);
-        *Mc = w.take<double>(nn);
-        *Vtr = w.take<double>(nn);
-        *BB = w.take<double>(2 * nn);
-        *P = w.take<double>((size_t)sp * nn);
-        *NP = w.take<double>((size_t)gy * n);
-    };
-    double *Ub, *sinv, *M0, *J, *K, *Mc, *Vtr, *BB, *P, *NP;
-    Bump sz(nullptr, 0);
-    carve(sz, &Ub, &sinv, &M0, &J, &K, &Mc, &Vtr, &BB, &P, &NP);
-    void *base = nullptr;
-    std::unique_lock<std::mutex> lk;
-    int rc = acquire_ws(opts, sz.off, &base, lk);
-    if (rc) return rc;
-    Bump ws(base, sz.off);
-    carve(ws, &Ub, &sinv, &M0, &J, &K, &Mc, &Vtr, &BB, &P, &NP);
-    if (ws.overflow) return TSSVD_ENOMEM;
-    auto body = [&]() -> cudaError_t {
-        // sinv = 1/S (the discard rule with tol 0 inverts every S_j > 0)
-        CK(launch_discard(S, n, 0.0, sinv, nullptr, s));
-        CK(launch_scale2(V, n, n, n, nullptr, sinv, M0, n, s));
-        CK(launch_nn<double, double>(A, lda, M0, n, m, n, n, Ub, 2 * n, NP, s));
-        if (dU) {
-            CK(cudaMemcpy2DAsync(Ub + n, sizeof(double) * 2 * n, dU, sizeof(double) * n,
-                                 sizeof(double) * n, m, cudaMemcpyDeviceToDevice, s));
-            // J = U^T dU
-            CK(launch_tn_partial<double, double>(Ub, 2 * n, Ub + n, 2 * n, m, n, n, spJ, false, P,
-                                                 s));
-            CK(launch_tn_reduce(P, spJ, n, n, nullptr, nullptr, false, J, n, s));
-        } else {
-            CK(cudaMemset2DAsync(Ub + n, sizeof(double) * 2 * n, 0, sizeof(double) * n, m, s));
-        }
-        if (dV) {
-            // K = V^T dV
-            CK(launch_tn_partial<double, double>(V, n, dV, n, n, n, n, spK, false, P, s));
-            CK(launch_tn_reduce(P, spK, n, n, nullptr, nullptr, false, K, n, s));
-        }
-        CK(launch_adjoint_core(dU ? J : nullptr, dV ? K : nullptr, S, dS, n, Mc, s));
-        // BB = [Mc V^T ; S^-1 V^T]  (2n x n)
-        CK(launch_transpose(V, n, n, n, nullptr, Vtr, n, s));
-        CK(launch_nn<double, double>(Mc, n, Vtr, n, n, n, n, BB, n, NP, s));
-        CK(launch_transpose(V, n, n, n, sinv, BB + nn, n, s));
-        // dA = [U | dU] BB
-        CK(launch_nn<double, double>(Ub, 2 * n, BB, n, m, 2 * n, n, dA, n, NP, s));
-        return cudaSuccess;
-    };
-    cudaError_t e = body();
-    if (e != cudaSuccess) {
-        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
-        cudaGetLastError();
-        return TSSVD_ECUDA;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return TSSVD_ECUDA;
-    }
-    return TSSVD_OK;
+    return backward_entry<double>(A, m, n, lda, S, V, dU, dS, dV, dA, opts);
+}
+
+int ts_svd_backward_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *S,
+                        const float *V, const float *dU, const float *dS, const float *dV,
+                        float *dA, tssvd_opts *opts)
+{
+    return backward_entry<float>(A, m, n, lda, S, V, dU, dS, dV, dA, opts);
 }
 
 }  // extern "C"
