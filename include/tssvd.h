@@ -63,7 +63,11 @@ typedef enum {
      * (exact in bf16), exact per-level FP32 accumulation in tensor memory
      * and double-FP32 accumulation of the level sums, so the results carry
      * about 48 significant bits; the n x n work stays FP64.  Any n. */
-    TSSVD_FP64_TC = 3
+    TSSVD_FP64_TC = 3,
+    /* Batched calls only: for every (m, n) size class the library times
+     * TSSVD_FP64 and TSSVD_FP64_TC once (both FP64-accurate) and keeps the
+     * faster for that class for the rest of the process. */
+    TSSVD_AUTO = 4
 } tssvd_mode;
 
 typedef struct {
@@ -167,6 +171,38 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
 int ts_svd_backward_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *S,
                         const float *V, const float *dU, const float *dS, const float *dV,
                         float *dA, tssvd_opts *opts);
+
+/* One member of a batch for ts_svd_batched. */
+typedef struct {
+    const void *A;   /* [in]  m x n, row-major, leading dimension lda (device) */
+    int64_t m, n, lda;
+    void *U;         /* [out] m x n (leading dimension n) */
+    void *S;         /* [out] n */
+    void *V;         /* [out] n x n */
+    int64_t out_rank; /* [out] */
+    int status;      /* [out] status of this member (as ts_svd returns) */
+    int mode;        /* [out] arithmetic mode used (TSSVD_AUTO resolved) */
+} tssvd_desc;
+
+/*
+ * Many independent tall-skinny SVDs (Algorithm 3 or 4 each, as opts->passes
+ * says) of uneven sizes in one submission.  All members have the same
+ * element type (elem_bytes 8 = double, 4 = float) and the same options.
+ * The members are ordered largest first and spread over worker streams;
+ * members on one worker stream run one after another and share one slice
+ * of the workspace (ts_svd_batched_workspace_size).  The whole batch is
+ * captured once into a CUDA graph, which is cached by the batch's
+ * descriptors and options and replayed on later calls with the same ones;
+ * one graph launch on opts->stream runs the batch.  Returns after the
+ * stream has finished; each member's status, rank and resolved mode are
+ * written to its descriptor, and the call returns the first nonzero member
+ * status (TSSVD_OK if none).  opts->mode may be TSSVD_AUTO.
+ * Errors: -1 descs NULL, -2 count < 1, -3 elem_bytes, -4 opts; -(100 + i)
+ * when member i has an invalid field.
+ */
+size_t ts_svd_batched_workspace_size(const tssvd_desc *descs, int count, int elem_bytes,
+                                     const tssvd_opts *opts);
+int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opts);
 
 /*
  * Gram matrix B = A^T A of A (m x n, row-major, lda >= n): the first step of

@@ -13,6 +13,6 @@ fallback: if the library is missing, importing the binding raises.
 from ._binding import (  # noqa: F401
     TSSVD_OK, TSSVD_ENOCONV, TSSVD_RANKDEF, TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM,
     PAPER_DROP_TOL, TsSvdError, lib, library_path, ts_svd, lowrank_svd, ts_svd_backward, ts_gram,
-    ts_matmul,
+    ts_matmul, ts_svd_batched, ts_svd_batched_workspace_size,
     ts_svd_workspace_size, lowrank_svd_workspace_size, TSSVD, exported_symbols,
 )

@@ -21,7 +21,8 @@ TSSVD_ETIMEOUT = 3
 TSSVD_ECUDA = 4
 TSSVD_ENOMEM = 5
 
-_MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp64_tc": 3}
+_MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp64_tc": 3, "auto": 4}
+_MODE_NAMES = {v: k for k, v in _MODES.items()}
 
 # Square root of the paper's example working precision 1e-11 (Remark "working").
 PAPER_DROP_TOL = math.sqrt(1e-11)
@@ -44,6 +45,15 @@ class _Opts(ctypes.Structure):
         ("out_rank", ctypes.c_int64),
         ("sweeps", ctypes.c_int * 4),
         ("ranks", ctypes.c_int * 2),
+    ]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+        ("lda", ctypes.c_int64), ("U", ctypes.c_void_p), ("S", ctypes.c_void_p),
+        ("V", ctypes.c_void_p), ("out_rank", ctypes.c_int64), ("status", ctypes.c_int),
+        ("mode", ctypes.c_int),
     ]
 
 
@@ -93,6 +103,11 @@ def lib():
     L.ts_matmul_workspace_size.restype = ctypes.c_size_t
     L.ts_matmul.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, op]
     L.ts_matmul.restype = ctypes.c_int
+    L.ts_svd_batched.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_int, op]
+    L.ts_svd_batched.restype = ctypes.c_int
+    L.ts_svd_batched_workspace_size.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int,
+                                                ctypes.c_int, op]
+    L.ts_svd_batched_workspace_size.restype = ctypes.c_size_t
     L.tssvd_launch_count.argtypes = []
     L.tssvd_launch_count.restype = ctypes.c_longlong
     L.tssvd_profile_enable.argtypes = [ctypes.c_int]
@@ -109,7 +124,7 @@ def exported_symbols():
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
-            "ts_svd_backward_f32"]
+            "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -239,6 +254,59 @@ def ts_matmul(A, M, mode="fp64", stream=None, workspace=None):
                              ctypes.byref(o))
     _check(rc, "ts_matmul")
     return C
+
+
+def ts_svd_batched(As, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64",
+                   max_sweeps=50, stream=None, workspace=None, outs=None):
+    """Many TS-SVDs in one graph launch.  As: list of 2-D CUDA tensors of one
+    dtype (float64 or float32), row-major.  Returns (list of (U, S, V),
+    list of info dicts, call status).  Passing the same tensors (and `outs`)
+    again replays the cached graph."""
+    if not As:
+        raise TsSvdError("empty batch")
+    dt = As[0].dtype
+    descs = (_Desc * len(As))()
+    res = []
+    for i, A in enumerate(As):
+        A = _as_matrix(A)
+        if A.dtype != dt:
+            raise TsSvdError("all members must have the same dtype")
+        m, n = A.shape
+        if outs is None:
+            U = torch.empty((m, n), dtype=dt, device=A.device)
+            S = torch.empty((n,), dtype=dt, device=A.device)
+            V = torch.empty((n, n), dtype=dt, device=A.device)
+        else:
+            U, S, V = outs[i]
+        res.append((U, S, V))
+        descs[i].A = A.data_ptr()
+        descs[i].m, descs[i].n, descs[i].lda = m, n, A.stride(0)
+        descs[i].U, descs[i].S, descs[i].V = U.data_ptr(), S.data_ptr(), V.data_ptr()
+    o = _opts(passes, scale, drop_tol, mode, max_sweeps, stream, workspace)
+    eb = 8 if dt == torch.float64 else 4
+    with torch.cuda.device(As[0].device):
+        rc = lib().ts_svd_batched(descs, len(As), eb, ctypes.byref(o))
+    if rc < 0:
+        raise TsSvdError("ts_svd_batched: invalid argument %d" % (-rc))
+    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM):
+        raise TsSvdError("ts_svd_batched: %s" % lib().tssvd_status_string(rc).decode())
+    infos = [{"status": descs[i].status, "rank": int(descs[i].out_rank),
+              "mode": _MODE_NAMES.get(descs[i].mode, descs[i].mode)} for i in range(len(As))]
+    return res, infos, rc
+
+
+def ts_svd_batched_workspace_size(shapes, dtype=torch.float64, passes=2, scale=True,
+                                  drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50):
+    descs = (_Desc * len(shapes))()
+    for i, (m, n) in enumerate(shapes):
+        descs[i].m, descs[i].n, descs[i].lda = m, n, n
+    o = _Opts()
+    lib().tssvd_default_opts(ctypes.byref(o))
+    o.passes, o.scale, o.drop_tol = passes, int(bool(scale)), float(drop_tol)
+    o.mode, o.max_sweeps = _MODES[mode], max_sweeps
+    return int(lib().ts_svd_batched_workspace_size(descs, len(shapes),
+                                                   8 if dtype == torch.float64 else 4,
+                                                   ctypes.byref(o)))
 
 
 def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):

@@ -11,6 +11,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -407,6 +410,279 @@ int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mu
     return TSSVD_OK;
 }
 
+// ------------------------------------------------------------- batched
+
+constexpr int kWorkers = 16;  // worker streams of a batch
+
+struct WorkerStreams {
+    bool ready = false;
+    cudaStream_t w[kWorkers];
+    cudaEvent_t fork, join[kWorkers];
+    cudaStream_t own;  // blocking stream used when the caller passes NULL
+};
+WorkerStreams g_workers[64];
+
+struct BatchGraph {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;  // kernel launches per replay
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_graphs;  // small most-recent-first cache
+std::map<std::pair<int, int>, int> g_tuned;  // (log2 m, n/32) -> mode
+
+int log2_ceil(i64 v)
+{
+    int e = 0;
+    while (((i64)1 << e) < v) e++;
+    return e;
+}
+
+int ensure_workers(int dev)
+{
+    WorkerStreams &W = g_workers[dev];
+    if (W.ready) return 0;
+    for (int i = 0; i < kWorkers; i++) {
+        if (cudaStreamCreateWithFlags(&W.w[i], cudaStreamNonBlocking) != cudaSuccess) return -1;
+        if (cudaEventCreateWithFlags(&W.join[i], cudaEventDisableTiming) != cudaSuccess) return -1;
+    }
+    if (cudaEventCreateWithFlags(&W.fork, cudaEventDisableTiming) != cudaSuccess) return -1;
+    if (cudaStreamCreate(&W.own) != cudaSuccess) return -1;
+    W.ready = true;
+    return 0;
+}
+
+template <typename T>
+size_t member_ws(const tssvd_desc &d, const tssvd_opts *o, int mode)
+{
+    Bump sz(nullptr, 0);
+    ts_any<T, T>(nullptr, d.m, d.n, d.n, (T *)nullptr, d.n, (T *)nullptr, (T *)nullptr, d.n,
+                 o->passes, o->scale, o->drop_tol, o->max_sweeps, sz, nullptr, nullptr, mode);
+    return sz.off + 256;
+}
+
+// Plan of a batch: members ordered largest first, each assigned to the
+// worker with the least work so far (longest-processing-time rule).
+struct Plan {
+    std::vector<int> order, worker, modes;
+    std::vector<size_t> slice;  // bytes per worker
+    size_t status_bytes = 0, total = 0;
+};
+
+template <typename T>
+Plan make_plan(const tssvd_desc *d, int count, const tssvd_opts *o, const std::vector<int> &modes)
+{
+    Plan p;
+    p.order.resize(count);
+    for (int i = 0; i < count; i++) p.order[i] = i;
+    auto work = [&](int i) { return (double)d[i].m * (double)d[i].n * (double)d[i].n; };
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) { return work(a) > work(b); });
+    p.worker.assign(count, 0);
+    p.modes = modes;
+    std::vector<double> load(kWorkers, 0.0);
+    p.slice.assign(kWorkers, 0);
+    for (int i : p.order) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        p.worker[i] = w;
+        load[w] += work(i);
+        p.slice[w] = std::max(p.slice[w], member_ws<T>(d[i], o, modes[i]));
+    }
+    p.status_bytes = ((sizeof(DevStatus) * (size_t)count + 255) / 256) * 256;
+    p.total = p.status_bytes;
+    for (size_t b : p.slice) p.total += b;
+    return p;
+}
+
+int check_member(const tssvd_desc &d, int mode)
+{
+    if (!d.A || !d.U || !d.S || !d.V) return 1;
+    if (d.n < 1 || d.n > 16384 || d.m < d.n || d.lda < d.n) return 1;
+    if ((mode == TSSVD_BF16X3 || mode == TSSVD_BF16X6) && d.n > 256) return 1;
+    return 0;
+}
+
+template <typename T>
+int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSSVD_ECUDA;
+    std::lock_guard<std::mutex> glk(g_batch_mu);
+    if (ensure_workers(dev)) return TSSVD_ECUDA;
+    WorkerStreams &W = g_workers[dev];
+    cudaStream_t s = o->stream ? (cudaStream_t)o->stream : W.own;
+
+    // modes (resolving TSSVD_AUTO per size class)
+    std::vector<int> modes(count, o->mode);
+    if (o->mode == TSSVD_AUTO) {
+        for (int i = 0; i < count; i++) {
+            const std::pair<int, int> key(log2_ceil(d[i].m), (int)((d[i].n + 31) / 32));
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                modes[i] = it->second;
+                continue;
+            }
+            // time both FP64-accurate engines once on this member
+            const int cand[2] = {TSSVD_FP64, TSSVD_FP64_TC};
+            float best = 0.f;
+            int bestm = TSSVD_FP64;
+            size_t need = std::max(member_ws<T>(d[i], o, cand[0]), member_ws<T>(d[i], o, cand[1]));
+            void *base = nullptr;
+            std::unique_lock<std::mutex> lk;
+            tssvd_opts o2 = *o;
+            o2.workspace = nullptr;
+            if (acquire_ws(&o2, need + 256, &base, lk)) return TSSVD_ENOMEM;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int c = 0; c < 2; c++) {
+                for (int rep = 0; rep < 2; rep++) {  // the second run is timed
+                    Bump ws(base, need + 256);
+                    DevStatus *st = ws.take<DevStatus>(1);
+                    cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+                    cudaEventRecord(e0, s);
+                    cudaError_t e = ts_any<T, T>((const T *)d[i].A, d[i].m, d[i].n, d[i].lda, (T *)d[i].U,
+                                                 d[i].n, (T *)d[i].S, (T *)d[i].V, d[i].n, o->passes,
+                                                 o->scale, o->drop_tol, o->max_sweeps, ws, st, s, cand[c]);
+                    cudaEventRecord(e1, s);
+                    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return TSSVD_ECUDA;
+                    }
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (c == 0 || ms < best) {
+                    best = ms;
+                    bestm = cand[c];
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            g_tuned[key] = bestm;
+            modes[i] = bestm;
+        }
+    }
+    for (int i = 0; i < count; i++)
+        if (check_member(d[i], modes[i])) return -(100 + i);
+
+    Plan plan = make_plan<T>(d, count, o, modes);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(o, plan.total, &base, lk);
+    if (rc) return rc;
+    DevStatus *sts = (DevStatus *)base;
+    std::vector<char *> slice_base(kWorkers);
+    {
+        size_t off = plan.status_bytes;
+        for (int w = 0; w < kWorkers; w++) {
+            slice_base[w] = (char *)base + off;
+            off += plan.slice[w];
+        }
+    }
+
+    // graph cache key: members, element type, options, stream, workspace
+    std::vector<unsigned long long> key;
+    key.push_back((unsigned long long)count);
+    key.push_back((unsigned long long)sizeof(T));
+    key.push_back((unsigned long long)(uintptr_t)base);
+    key.push_back((unsigned long long)(uintptr_t)s);
+    unsigned long long tolbits;
+    std::memcpy(&tolbits, &o->drop_tol, 8);
+    key.push_back(tolbits);
+    key.push_back(((unsigned long long)o->passes << 32) | ((unsigned long long)o->scale << 16) |
+                  (unsigned long long)o->max_sweeps);
+    for (int i = 0; i < count; i++) {
+        key.push_back((unsigned long long)(uintptr_t)d[i].A);
+        key.push_back((unsigned long long)(uintptr_t)d[i].U);
+        key.push_back((unsigned long long)(uintptr_t)d[i].S);
+        key.push_back((unsigned long long)(uintptr_t)d[i].V);
+        key.push_back((unsigned long long)d[i].m);
+        key.push_back((unsigned long long)d[i].n);
+        key.push_back((unsigned long long)d[i].lda);
+        key.push_back((unsigned long long)modes[i]);
+    }
+    BatchGraph *g = nullptr;
+    for (auto &bg : g_graphs)
+        if (bg.key == key) g = &bg;
+    if (!g) {
+        const long long n0 = tssvd_launch_count();
+        const int prof = tssvd_profile_enable(0);  // no event records inside the graph
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaEventRecord(W.fork, s);
+        for (int w = 0; w < kWorkers && e == cudaSuccess; w++) e = cudaStreamWaitEvent(W.w[w], W.fork, 0);
+        std::vector<Bump> slices;
+        for (int w = 0; w < kWorkers; w++) slices.emplace_back(slice_base[w], plan.slice[w]);
+        for (int i : plan.order) {
+            if (e != cudaSuccess) break;
+            const int w = plan.worker[i];
+            cudaStream_t ws_ = W.w[w];
+            Bump b(slice_base[w], plan.slice[w]);  // members of a worker reuse its slice
+            e = cudaMemsetAsync(&sts[i], 0, sizeof(DevStatus), ws_);
+            if (e == cudaSuccess)
+                e = ts_any<T, T>((const T *)d[i].A, d[i].m, d[i].n, d[i].lda, (T *)d[i].U, d[i].n,
+                                 (T *)d[i].S, (T *)d[i].V, d[i].n, o->passes, o->scale, o->drop_tol,
+                                 o->max_sweeps, b, &sts[i], ws_, modes[i]);
+        }
+        for (int w = 0; w < kWorkers; w++) {
+            cudaError_t e2 = cudaEventRecord(W.join[w], W.w[w]);
+            if (e == cudaSuccess) e = e2;
+            e2 = cudaStreamWaitEvent(s, W.join[w], 0);
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        tssvd_profile_enable(prof);
+        if (e == cudaSuccess) e = ec;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "tssvd: batch capture failed: %s\n", cudaGetErrorString(e));
+            cudaGetLastError();
+            return TSSVD_ECUDA;
+        }
+        BatchGraph nb;
+        nb.key = key;
+        nb.exec = exec;
+        nb.kernels = tssvd_launch_count() - n0;
+        if (g_graphs.size() >= 8) {
+            cudaGraphExecDestroy(g_graphs.back().exec);
+            g_graphs.pop_back();
+        }
+        g_graphs.insert(g_graphs.begin(), nb);
+        g = &g_graphs.front();
+    } else {
+        add_launches(g->kernels);
+    }
+    std::vector<DevStatus> h(count);
+    if (cudaGraphLaunch(g->exec, s) != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), sts, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    int first = TSSVD_OK;
+    for (int i = 0; i < count; i++) {
+        int code = TSSVD_OK;
+        if (h[i].err)
+            code = TSSVD_ETIMEOUT;
+        else {
+            const int solves = o->passes == 2 ? 3 : 1;
+            for (int j = 0; j < solves; j++)
+                if (h[i].sweeps[j] < 0) code = TSSVD_ENOCONV;
+            if (code == TSSVD_OK && h[i].rank < d[i].n) code = TSSVD_RANKDEF;
+        }
+        d[i].status = code;
+        d[i].out_rank = h[i].rank;
+        d[i].mode = modes[i];
+        if (first == TSSVD_OK && code != TSSVD_OK) first = code;
+    }
+    return first;
+}
+
 int check_opts(const tssvd_opts *o)
 {
     if (!o) return 0;
@@ -764,6 +1040,34 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     for (int i = 0; i < 4; i++) opts->sweeps[i] = h[nst - 2].sweeps[i];
     if (code == TSSVD_OK && rank < k) code = TSSVD_RANKDEF;
     return code;
+}
+
+size_t ts_svd_batched_workspace_size(const tssvd_desc *descs, int count, int elem_bytes,
+                                     const tssvd_opts *opts)
+{
+    if (!descs || count < 1 || !opts || (elem_bytes != 4 && elem_bytes != 8)) return 0;
+    std::vector<int> modes(count, opts->mode == TSSVD_AUTO ? TSSVD_FP64_TC : opts->mode);
+    // TSSVD_AUTO may pick either engine: size for the larger
+    Plan p1 = elem_bytes == 8 ? make_plan<double>(descs, count, opts, modes)
+                              : make_plan<float>(descs, count, opts, modes);
+    if (opts->mode != TSSVD_AUTO) return p1.total;
+    std::vector<int> m2(count, TSSVD_FP64);
+    Plan p2 = elem_bytes == 8 ? make_plan<double>(descs, count, opts, m2)
+                              : make_plan<float>(descs, count, opts, m2);
+    return std::max(p1.total, p2.total);
+}
+
+int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opts)
+{
+    if (!descs) return -1;
+    if (count < 1) return -2;
+    if (elem_bytes != 4 && elem_bytes != 8) return -3;
+    if (!opts || opts->passes < 1 || opts->passes > 2 || !(opts->drop_tol >= 0.0) ||
+        opts->drop_tol >= 1.0 || opts->max_sweeps < 1 || opts->max_sweeps > 1000 ||
+        opts->mode < TSSVD_FP64 || opts->mode > TSSVD_AUTO)
+        return -4;
+    return elem_bytes == 8 ? batched_impl<double>(descs, count, opts)
+                           : batched_impl<float>(descs, count, opts);
 }
 
 size_t ts_gram_workspace_size(int64_t m, int64_t n)

@@ -27,6 +27,9 @@ struct DevStatus {
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
+// Adds kernel launches made by a graph replay to the launch counter.
+void add_launches(long long k);
+
 // Wraps one kernel launch: counts it, and when profiling is on records a
 // CUDA event pair around it on its stream (see profiler.cu).
 struct ProfScope {

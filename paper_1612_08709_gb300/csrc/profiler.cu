@@ -72,6 +72,8 @@ ProfScope::~ProfScope()
     }
 }
 
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
 }  // namespace tssvd
 
 using namespace tssvd;
