@@ -50,7 +50,9 @@ struct Bump {
     template <typename T>
     T *take(size_t count)
     {
-        off = (off + 255) & ~(size_t)255;
+        // 256-byte aligned absolute addresses, whatever the base
+        const size_t addr = ((size_t)base + off + 255) & ~(size_t)255;
+        off = addr - (size_t)base;
         T *p = nullptr;
         if (base) {
             if (off + count * sizeof(T) > cap)
@@ -384,7 +386,7 @@ int summarise(const std::vector<DevStatus> &sts, int nsolves_per, int *rank_out)
 int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mutex> &lk)
 {
     if (o->workspace) {
-        if (o->workspace_bytes < need) return TSSVD_ENOMEM;
+        if (o->workspace_bytes < need) return TSSVD_ENOMEM;  // (sizes queried include slack)
         *base = o->workspace;
         return TSSVD_OK;
     }
@@ -392,6 +394,7 @@ int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mu
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSSVD_ECUDA;
     InternalWs &w = g_ws[dev];
     lk = std::unique_lock<std::mutex>(w.mu);
+    need += 256;  // room to align a base that is not 256-byte aligned
     if (w.bytes < need) {
         if (w.ptr) {
             cudaDeviceSynchronize();
@@ -485,7 +488,8 @@ Plan make_plan(const tssvd_desc *d, int count, const tssvd_opts *o, const std::v
         int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
         p.worker[i] = w;
         load[w] += work(i);
-        p.slice[w] = std::max(p.slice[w], member_ws<T>(d[i], o, modes[i]));
+        const size_t need = (member_ws<T>(d[i], o, modes[i]) + 255) & ~(size_t)255;
+        p.slice[w] = std::max(p.slice[w], need);
     }
     p.status_bytes = ((sizeof(DevStatus) * (size_t)count + 255) / 256) * 256;
     p.total = p.status_bytes;
@@ -570,8 +574,9 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
     Plan plan = make_plan<T>(d, count, o, modes);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
-    int rc = acquire_ws(o, plan.total, &base, lk);
+    int rc = acquire_ws(o, plan.total + 256, &base, lk);
     if (rc) return rc;
+    base = (void *)(((size_t)base + 255) & ~(size_t)255);
     DevStatus *sts = (DevStatus *)base;
     std::vector<char *> slice_base(kWorkers);
     {
@@ -720,7 +725,7 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
     if (rc) return rc;
-    Bump ws(base, sz.off);
+    Bump ws(base, sz.off + 256);
     DevStatus *st = ws.take<DevStatus>(1);
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
     cudaError_t e = ts_any<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
@@ -858,7 +863,7 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
     if (rc) return rc;
-    Bump ws(base, sz.off);
+    Bump ws(base, sz.off + 256);
     carve(ws);
     if (ws.overflow) return TSSVD_ENOMEM;
     auto body = [&]() -> cudaError_t {
@@ -958,7 +963,7 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
         ts_any<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
                                (double *)nullptr, n, opts->passes, opts->scale, opts->drop_tol,
                                opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
-    return sz.off;
+    return sz.off + 256;
 }
 
 int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S, double *V,
@@ -980,7 +985,7 @@ size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_o
     sz.take<DevStatus>(64);
     lowrank_core(nullptr, m, n, n, l, l, 0, nullptr, nullptr, nullptr, nullptr, opts->drop_tol,
                  opts->max_sweeps, sz, nullptr, nullptr);
-    return sz.off;
+    return sz.off + 256;
 }
 
 int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
@@ -1009,7 +1014,7 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
     if (rc) return rc;
-    Bump ws(base, sz.off);
+    Bump ws(base, sz.off + 256);
     DevStatus *sts = ws.take<DevStatus>(nst);
     if (cudaMemsetAsync(sts, 0, sizeof(DevStatus) * nst, s) != cudaSuccess) return TSSVD_ECUDA;
     cudaError_t e = lowrank_core(A, m, n, lda, k, l, iters, Omega, U, S, V, opts->drop_tol,
@@ -1050,11 +1055,11 @@ size_t ts_svd_batched_workspace_size(const tssvd_desc *descs, int count, int ele
     // TSSVD_AUTO may pick either engine: size for the larger
     Plan p1 = elem_bytes == 8 ? make_plan<double>(descs, count, opts, modes)
                               : make_plan<float>(descs, count, opts, modes);
-    if (opts->mode != TSSVD_AUTO) return p1.total;
+    if (opts->mode != TSSVD_AUTO) return p1.total + 256;
     std::vector<int> m2(count, TSSVD_FP64);
     Plan p2 = elem_bytes == 8 ? make_plan<double>(descs, count, opts, m2)
                               : make_plan<float>(descs, count, opts, m2);
-    return std::max(p1.total, p2.total);
+    return std::max(p1.total, p2.total) + 256;
 }
 
 int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opts)
@@ -1084,7 +1089,7 @@ size_t ts_gram_workspace_size(int64_t m, int64_t n)
     sz.take<unsigned long long>(n);
     sz.take<int>(n);
     sz.take<uint8_t>(oz_gram_image_bytes(m, (int)n));
-    return sz.off;
+    return sz.off + 256;
 }
 
 // Reads the status block back; TSSVD_ETIMEOUT if a device wait expired.
@@ -1115,7 +1120,7 @@ int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd
     const size_t need = ts_gram_workspace_size(m, n);
     int rc = acquire_ws(opts, need, &base, lk);
     if (rc) return rc;
-    Bump ws(base, need);
+    Bump ws(base, need + 256);
     DevStatus *st = ws.take<DevStatus>(1);
     const bool oz = opts->mode == TSSVD_FP64_TC;
     const int sp = oz ? oz_gram_splits(m, (int)n)
@@ -1155,7 +1160,7 @@ size_t ts_matmul_workspace_size(int64_t m, int64_t k, int64_t n)
     sz.take<int>(m);
     sz.take<int>(n);
     sz.take<uint8_t>(oz_row_image_bytes(m, (int)k));
-    return sz.off;
+    return sz.off + 256;
 }
 
 int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *M, int64_t n,
@@ -1179,7 +1184,7 @@ int ts_matmul(const double *A, int64_t m, int64_t k, int64_t lda, const double *
     const size_t need = ts_matmul_workspace_size(m, k, n);
     int rc = acquire_ws(opts, need, &base, lk);
     if (rc) return rc;
-    Bump ws(base, need);
+    Bump ws(base, need + 256);
     DevStatus *st = ws.take<DevStatus>(1);
     const size_t ib1 = tc_split_b_bytes((int)k, (int)n, 3), ib2 = oz_image_bytes((int)k, (int)n);
     uint8_t *img = ws.take<uint8_t>(ib1 > ib2 ? ib1 : ib2);
