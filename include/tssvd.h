@@ -137,6 +137,12 @@ size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_o
  * followed by the direct SVD of Algorithm 6 (the SVD of B = Q^T A is the
  * two-pass TS-SVD of B^T = A^T Q, n x l).  The leading k of the l
  * triplets are returned.  MaxEntry scaling (opts->scale) is not used.
+ * opts->mode: TSSVD_FP64 runs every product in FP64 FMA; TSSVD_FP64_TC
+ * runs the products A X and A^T Q and the TS-SVDs with FP64-accurate
+ * digit-sliced tensor-core products (the digit images of A, 14 bytes per
+ * entry each for the row and the column image, are built once per call
+ * and reused by every power step); TSSVD_BF16X3/X6 apply to the TS-SVDs'
+ * first passes only (l <= 256), the products with A staying FP64.
  *   A     [in]  m x n row-major, leading dimension lda >= n.
  *   k, l  1 <= k <= l <= min(m, n).
  *   iters number of power steps i >= 0.

@@ -180,9 +180,8 @@ def ts_svd_workspace_size(m, n, dtype=torch.float64, **kw):
                                            ctypes.byref(o)))
 
 
-def lowrank_svd_workspace_size(m, n, l, **kw):
-    o = _Opts()
-    lib().tssvd_default_opts(ctypes.byref(o))
+def lowrank_svd_workspace_size(m, n, l, mode="fp64"):
+    o = _opts(2, False, PAPER_DROP_TOL, mode, 50, None, None)
     return int(lib().lowrank_svd_workspace_size(m, n, l, ctypes.byref(o)))
 
 

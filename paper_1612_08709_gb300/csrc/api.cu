@@ -756,55 +756,93 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
 // Number of per-sub-call status blocks used by lowrank: 2 per power step + 2.
 cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, int iters,
                          const double *Omega, double *U, double *S, double *V, double tol,
-                         int max_sweeps, Bump &ws, DevStatus *sts, cudaStream_t s)
+                         int max_sweeps, Bump &ws, DevStatus *sts, cudaStream_t s,
+                         int mode = TSSVD_FP64)
 {
     const bool sizing = ws.sizing();
+    const bool oz = mode == TSSVD_FP64_TC;
     double *Qt = ws.take<double>((size_t)n * l), *Y = ws.take<double>((size_t)m * l);
     double *Q = ws.take<double>((size_t)m * l), *Bt = ws.take<double>((size_t)n * l);
     double *U1 = ws.take<double>((size_t)n * l), *S1 = ws.take<double>(l);
     double *V1 = ws.take<double>((size_t)l * l), *V1s = ws.take<double>((size_t)l * l);
     double *Uf = ws.take<double>((size_t)m * l), *sgn = ws.take<double>(l);
     double *tS = ws.take<double>(l), *tV = ws.take<double>((size_t)l * l);
-    const int spT = tn_splits(m, n, l, false);
+    const int spT = oz ? oz_tn_splits(m, (int)n, (int)l) : tn_splits(m, n, l, false);
     double *P = ws.take<double>((size_t)spT * n * l);
     const int gy = nn_grid_rows(m, l);
     double *NP = ws.take<double>((size_t)gy * l);
+    // digit images of A (built once per call) and of the thin factors
+    unsigned long long *bits = oz ? ws.take<unsigned long long>(n > l ? n : l) : nullptr;
+    int *exA = oz ? ws.take<int>(n) : nullptr, *erA = oz ? ws.take<int>(m) : nullptr;
+    int *exQ = oz ? ws.take<int>(l) : nullptr, *em = oz ? ws.take<int>(l) : nullptr;
+    uint8_t *rimgA = oz ? ws.take<uint8_t>(oz_row_image_bytes(m, (int)n)) : nullptr;
+    uint8_t *cimgA = oz ? ws.take<uint8_t>(oz_gram_image_bytes(m, (int)n)) : nullptr;
+    uint8_t *cimgQ = oz ? ws.take<uint8_t>(oz_gram_image_bytes(m, (int)l)) : nullptr;
+    uint8_t *bimg = oz ? ws.take<uint8_t>(oz_image_bytes((int)n, (int)l)) : nullptr;
     // sub-call workspaces are carved last and reused by every sub-call
     const size_t sub_off = ws.off;
     const i64 big = m > n ? m : n;
     {
         Bump probe(nullptr, 0);
-        ts_core<double, double>(nullptr, big, l, l, (double *)nullptr, l, (double *)nullptr,
-                                (double *)nullptr, l, 2, 0, tol, max_sweeps, probe, nullptr, s);
-        ws.take<char>(probe.off + 256);
+        ts_any<double, double>(nullptr, big, l, l, (double *)nullptr, l, (double *)nullptr,
+                               (double *)nullptr, l, 2, 0, tol, max_sweeps, probe, nullptr, s, mode);
+        Bump probe1(nullptr, 0);
+        ts_any<double, double>(nullptr, big, l, l, (double *)nullptr, l, (double *)nullptr,
+                               (double *)nullptr, l, 1, 0, tol, max_sweeps, probe1, nullptr, s, mode);
+        ws.take<char>((probe.off > probe1.off ? probe.off : probe1.off) + 256);
     }
     if (sizing) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
     auto sub = [&](const double *Ain, i64 rows, double *Uo, double *So, double *Vo, int passes,
                    DevStatus *st) -> cudaError_t {
         Bump w(ws.base + ((sub_off + 255) & ~(size_t)255), ws.cap - ((sub_off + 255) & ~(size_t)255));
-        return ts_core<double, double>(Ain, rows, l, l, Uo, l, So, Vo, l, passes, 0, tol,
-                                       max_sweeps, w, st, s);
+        return ts_any<double, double>(Ain, rows, l, l, Uo, l, So, Vo, l, passes, 0, tol, max_sweeps,
+                                      w, st, s, mode);
+    };
+    // Y = A X (m x l) and C = A^T Z (n x l) on the selected engine
+    auto AX = [&](const double *X, double *Yo, DevStatus *st) -> cudaError_t {
+        if (!oz) return launch_nn<double, double>(A, lda, X, l, m, n, l, Yo, l, NP, s);
+        CK(launch_oz_image(X, l, (int)n, (int)l, nullptr, em, bimg, s));
+        return launch_oz_nn_run<double>(rimgA, m, (int)n, erA, bimg, em, (int)l, Yo, l, st, s);
+    };
+    auto AtZ = [&](const double *Z, double *Co, DevStatus *st) -> cudaError_t {
+        if (!oz) {
+            CK(launch_tn_partial<double, double>(A, lda, Z, l, m, n, l, spT, false, P, s));
+        } else {
+            CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * l, s));
+            CK(launch_colmax<double>(Z, m, l, l, bits, s));
+            CK(launch_oz_exp_from_bits(bits, (int)l, exQ, s));
+            CK(launch_oz_col_image(Z, l, m, (int)l, exQ, cimgQ, s));
+            CK(launch_oz_tn(cimgA, exA, (int)n, cimgQ, exQ, (int)l, m, spT, P, st, s));
+        }
+        return launch_tn_reduce(P, spT, n, l, nullptr, nullptr, false, Co, l, s);
     };
 
-    CK(cudaMemcpyAsync(Qt, Omega, sizeof(double) * n * l, cudaMemcpyDeviceToDevice, s));
     int si = 0;
+    if (oz) {
+        CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+        CK(launch_colmax<double>(A, m, n, lda, bits, s));
+        CK(launch_oz_exp_from_bits(bits, (int)n, exA, s));
+        CK(launch_oz_rowexp<double>(A, lda, m, (int)n, nullptr, erA, s));
+        CK(launch_oz_row_image<double>(A, lda, m, (int)n, nullptr, erA, rimgA, s));
+        CK(launch_oz_col_image(A, lda, m, (int)n, exA, cimgA, s));
+    }
+    CK(cudaMemcpyAsync(Qt, Omega, sizeof(double) * n * l, cudaMemcpyDeviceToDevice, s));
+    DevStatus *pst = sts + (2 * iters + 2);  // status of the products' waits
     for (int it = 0; it < iters; it++) {
         // Y_j = A Q~_{j-1}; Y_j = Q_j R_j (Algorithm 3).
-        CK(launch_nn<double, double>(A, lda, Qt, l, m, n, l, Y, l, NP, s));
+        CK(AX(Qt, Y, pst));
         CK(sub(Y, m, Q, tS, tV, 1, sts + si++));
         // Y~_j = A^T Q_j; Y~_j = Q~_j R~_j (Algorithm 3).
-        CK(launch_tn_partial<double, double>(A, lda, Q, l, m, n, l, spT, false, P, s));
-        CK(launch_tn_reduce(P, spT, n, l, nullptr, nullptr, false, Bt, l, s));
+        CK(AtZ(Q, Bt, pst));
         CK(sub(Bt, n, Qt, tS, tV, 1, sts + si++));
     }
     // Y = A Q~_i; Y = Q R with double orthonormalisation (Algorithm 4).
-    CK(launch_nn<double, double>(A, lda, Qt, l, m, n, l, Y, l, NP, s));
+    CK(AX(Qt, Y, pst));
     CK(sub(Y, m, Q, tS, tV, 2, sts + si++));
     // Algorithm 6: B = Q^T A via B^T = A^T Q (n x l); B^T = U1 S1 V1^T, so
     // B = V1 S1 U1^T: U~ = V1 and V = U1.
-    CK(launch_tn_partial<double, double>(A, lda, Q, l, m, n, l, spT, false, P, s));
-    CK(launch_tn_reduce(P, spT, n, l, nullptr, nullptr, false, Bt, l, s));
+    CK(AtZ(Q, Bt, pst));
     CK(sub(Bt, n, U1, S1, V1, 2, sts + si++));
     // Sign convention on the final V = U1; U = Q U~ = Q V1 diag(sgn).
     CK(launch_signs(U1, l, n, l, S1, sgn, s));
@@ -813,11 +851,10 @@ cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, i
     CK(launch_convert<double>(Uf, l, m, k, U, k, s));
     CK(launch_convert<double>(U1, l, n, k, V, k, s));
     CK(launch_convert<double>(S1, l, 1, k, S, k, s));
-    CK(launch_count_positive(S1, k, &sts[si].rank, s));
+    CK(launch_count_positive(S1, k, &pst->rank, s));
     return cudaSuccess;
 }
 
-// Thin-SVD adjoint for storage type T; all arithmetic in FP64.
 template <typename T>
 int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, const T *V,
                    const T *dU, const T *dS, const T *dV, T *dA, tssvd_opts *opts)
@@ -984,7 +1021,7 @@ size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_o
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(64);
     lowrank_core(nullptr, m, n, n, l, l, 0, nullptr, nullptr, nullptr, nullptr, opts->drop_tol,
-                 opts->max_sweeps, sz, nullptr, nullptr);
+                 opts->max_sweeps, sz, nullptr, nullptr, opts->mode);
     return sz.off + 256;
 }
 
@@ -1005,11 +1042,12 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     if (!V) return -11;
     if (!check_opts(opts)) return -12;
     cudaStream_t s = (cudaStream_t)opts->stream;
+    if ((opts->mode == TSSVD_BF16X3 || opts->mode == TSSVD_BF16X6) && l > 256) return -6;
     const int nst = 2 * iters + 3;
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(nst);
     lowrank_core(A, m, n, lda, k, l, iters, Omega, U, S, V, opts->drop_tol, opts->max_sweeps, sz,
-                 nullptr, s);
+                 nullptr, s, opts->mode);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
@@ -1018,7 +1056,7 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     DevStatus *sts = ws.take<DevStatus>(nst);
     if (cudaMemsetAsync(sts, 0, sizeof(DevStatus) * nst, s) != cudaSuccess) return TSSVD_ECUDA;
     cudaError_t e = lowrank_core(A, m, n, lda, k, l, iters, Omega, U, S, V, opts->drop_tol,
-                                 opts->max_sweeps, ws, sts, s);
+                                 opts->max_sweeps, ws, sts, s, opts->mode);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
@@ -1032,6 +1070,7 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
         return TSSVD_ECUDA;
     }
     int code = TSSVD_OK;
+    if (h[nst - 1].err) return TSSVD_ETIMEOUT;  // the products' own waits
     for (int i = 0; i < nst - 1; i++) {
         if (h[i].err) return TSSVD_ETIMEOUT;
         const int solves = (i < 2 * iters) ? 1 : 3;

@@ -110,6 +110,14 @@ size_t oz_row_image_bytes(i64 m, int K);
 template <typename T>
 cudaError_t launch_oz_gram(const T *X, i64 ldx, i64 m, int n, const int *ex, int splits,
                            uint8_t *gimg, double *P, DevStatus *st, cudaStream_t s);
+// A^T B from column digit images (see launch_oz_col_image): partials
+// P[split][i][j] (M x N) over the rows of A (m x M) and B (m x N).
+int oz_tn_splits(i64 m, int M, int N);
+cudaError_t launch_oz_col_image(const double *X, i64 ldx, i64 m, int n, const int *ex,
+                                uint8_t *img, cudaStream_t s);
+cudaError_t launch_oz_tn(const uint8_t *aimg, const int *exa, int M, const uint8_t *bimg,
+                         const int *exb, int N, i64 m, int splits, double *P, DevStatus *st,
+                         cudaStream_t s);
 // Digit image of diag(2^-pk) M (K x N) and its column exponents em.
 cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *pk, int *em,
                             uint8_t *img, cudaStream_t s);
@@ -123,6 +131,14 @@ template <typename T, typename TC>
 cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
                          uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
                          DevStatus *st, cudaStream_t s);
+// The two halves of launch_oz_nn: A's row digit image, and the product
+// from a prebuilt image (to reuse one image of A for several products).
+template <typename T>
+cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
+                                uint8_t *aimg, cudaStream_t s);
+template <typename TC>
+cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
+                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s);
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s);
 // pk[j] = round(log2(sc[j])) (0 for sc[j] <= 0).
 cudaError_t launch_oz_pow2_of(const double *sc, int n, int *pk, cudaStream_t s);

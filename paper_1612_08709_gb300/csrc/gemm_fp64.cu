@@ -319,13 +319,37 @@ int tn_splits(i64 K, i64 M, i64 N, bool upper_only)
 {
     const int tm = ceil_div_i(M, TB), tn = ceil_div_i(N, TB);
     const i64 tiles = upper_only ? (i64)tm * (tm + 1) / 2 : (i64)tm * tn;
-    i64 target = (i64)num_sms() * 4;
-    i64 sp = (target + tiles - 1) / tiles;
-    i64 max_sp = (K + 255) / 256;  // at least 256 rows per split
-    if (sp > max_sp) sp = max_sp;
-    if (sp < 1) sp = 1;
-    if (sp > 65535) sp = 65535;
-    return (int)sp;
+    // CTAs of the partial kernel resident per SM (looked up once).
+    static int per_sm = 0;
+    if (!per_sm) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tn_partial_kernel<double, double>,
+                                                          NTHR, 0) != cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        per_sm = b;
+    }
+    // About four waves' worth of CTAs, the count whose last wave is fullest
+    // (waves / splits smallest, smaller counts winning within 3%), each
+    // split keeping at least 256 rows.
+    const i64 slots = (i64)num_sms() * per_sm;
+    i64 max_sp = (K + 255) / 256;
+    i64 cap = (4 * slots + tiles - 1) / tiles;
+    if (cap > max_sp) cap = max_sp;
+    if (cap > 65535) cap = 65535;
+    if (cap < 1) cap = 1;
+    i64 best = 1;
+    double best_cost = (double)((tiles + slots - 1) / slots);
+    for (i64 sp = 2; sp <= cap; sp++) {
+        const double cost = (double)((tiles * sp + slots - 1) / slots) / (double)sp;
+        if (cost < best_cost * 0.97) {
+            best_cost = cost;
+            best = sp;
+        }
+    }
+    return (int)best;
 }
 
 template <typename TA, typename TB_>

@@ -313,12 +313,15 @@ __global__ void oz_row_image_kernel(const T *__restrict__ A, i64 lda, i64 m, int
     }
 }
 
-// ----------------------------------------------------------------- Gram
-// P[split][i][j] (n x n, FP64) for the (i, j) of the CTA's tile from the
-// Gram digit image: sum over the split's rows of X[k][i] X[k][j].
+// ------------------------------------------------------------ A^T B / Gram
+// P[split][i][j] (M x N, FP64) for the (i, j) of the CTA's tile: sum over
+// the split's rows k of X[k][i] Y[k][j], from the column digit images of X
+// (m x M, exponents exa) and Y (m x N, exponents exb).  With upper (X = Y,
+// the Gram matrix) only tiles holding some i <= j are computed.
 __global__ void __launch_bounds__(kOzThreads, 1)
-    oz_gram_kernel(const uint8_t *__restrict__ img, i64 m, int n, const int *__restrict__ ex,
-                   i64 rows_per_split, double *__restrict__ P, DevStatus *st)
+    oz_tn_kernel(const uint8_t *__restrict__ aimg, const int *__restrict__ exa, int M,
+                 const uint8_t *__restrict__ bimg, const int *__restrict__ exb, int N, int upper,
+                 i64 m, i64 rows_per_split, double *__restrict__ P, DevStatus *st)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
@@ -328,10 +331,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *err = &st->err;
     int ti = 0, tj = 0;
-    gram_tile(blockIdx.x, n, ti, tj);
+    if (upper) {
+        gram_tile(blockIdx.x, M, ti, tj);
+    } else {
+        const int TJ = (N + kNT - 1) / kNT;
+        ti = blockIdx.x / TJ;
+        tj = blockIdx.x % TJ;
+    }
     const int i0 = ti * 128, j0 = tj * kNT;
-    const int npad = gram_npad(n);
-    const uint32_t half = (uint32_t)npad * 32;
+    const uint32_t half_a = (uint32_t)gram_npad(M) * 32, half_b = (uint32_t)gram_npad(N) * 32;
     const i64 kb0 = (i64)blockIdx.y * (rows_per_split / kBK);
     const i64 kbm = (m + kBK - 1) / kBK;
     i64 kb1 = kb0 + rows_per_split / kBK;
@@ -364,16 +372,18 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, err)) break;
                 uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
                 mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-                const uint8_t *blk = img + (size_t)(kb0 + kb) * kDig * 2 * half;
+                const uint8_t *ablk = aimg + (size_t)(kb0 + kb) * kDig * 2 * half_a;
+                const uint8_t *bblk = bimg + (size_t)(kb0 + kb) * kDig * 2 * half_b;
 #pragma unroll 1
                 for (int d = 0; d < kDig; d++)
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
-                        const uint8_t *src = blk + (size_t)(d * 2 + h) * half;
-                        bulk_g2s(stage + d * kATerm + h * (kATerm / 2), src + (size_t)(i0 / 8) * 256,
+                        bulk_g2s(stage + d * kATerm + h * (kATerm / 2),
+                                 ablk + (size_t)(d * 2 + h) * half_a + (size_t)(i0 / 8) * 256,
                                  kATerm / 2, &full_bar[s]);
                         bulk_g2s(stage + kDig * kATerm + d * kBTerm + h * (kBTerm / 2),
-                                 src + (size_t)(j0 / 8) * 256, kBTerm / 2, &full_bar[s]);
+                                 bblk + (size_t)(d * 2 + h) * half_b + (size_t)(j0 / 8) * 256,
+                                 kBTerm / 2, &full_bar[s]);
                     }
                 last = kb;
             }
@@ -400,13 +410,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (ok) {
             const int il = warp * 32 + lane;
             const int i = i0 + il;
-            if (i < n) {
-                double *Prow = P + (i64)blockIdx.y * n * n + (i64)i * n;
-                const int ei = ex[i];
+            if (i < M) {
+                double *Prow = P + (i64)blockIdx.y * M * N + (i64)i * N;
+                const int ei = exa[i];
 #pragma unroll
                 for (int jj = 0; jj < kNT; jj++) {
                     const int j = j0 + jj;
-                    if (j < n) Prow[j] = ldexp(acc[jj], ei + ex[j] - 14);
+                    if (j < N) Prow[j] = ldexp(acc[jj], ei + exb[j] - 14);
                 }
             }
         }
@@ -732,14 +742,30 @@ int oz_gram_tiles(int n)
     return c;
 }
 
-int oz_gram_splits(i64 m, int n)
+// Row splits for a grid of `tiles` output tiles at one CTA per SM: the
+// count whose last wave is fullest (waves / splits smallest), smaller counts
+// winning within 3%, each split keeping at least 1024 rows.
+static int balanced_splits(i64 m, int tiles)
 {
-    const int tiles = oz_gram_tiles(n);
-    i64 sp = ((i64)num_sms() + tiles - 1) / tiles;
-    const i64 max_sp = (m + 255) / 256;
-    if (sp > max_sp) sp = max_sp;
-    return sp < 1 ? 1 : (int)sp;
+    const int sms = num_sms();
+    i64 cap = ((i64)sms + tiles - 1) / tiles;
+    if (cap < 16) cap = 16;
+    const i64 max_rows = (m + 1023) / 1024;
+    if (cap > max_rows) cap = max_rows;
+    if (cap < 1) cap = 1;
+    int best = 1;
+    double best_cost = (double)(((i64)tiles + sms - 1) / sms);
+    for (i64 sp = 2; sp <= cap; sp++) {
+        const double cost = (double)(((i64)tiles * sp + sms - 1) / sms) / (double)sp;
+        if (cost < best_cost * 0.97) {
+            best_cost = cost;
+            best = (int)sp;
+        }
+    }
+    return best;
 }
+
+int oz_gram_splits(i64 m, int n) { return balanced_splits(m, oz_gram_tiles(n)); }
 
 size_t oz_image_bytes(int K, int N)
 {
@@ -762,27 +788,57 @@ size_t oz_row_image_bytes(i64 m, int K)
 }
 
 template <typename T>
+cudaError_t oz_col_image(const T *X, i64 ldx, i64 m, int n, const int *ex, uint8_t *img, cudaStream_t s)
+{
+    const i64 total = (m + kBK - 1) / kBK * (kBK / 8) * gram_npad(n);
+    ProfScope ps_("oz_gram_image", s);
+    oz_gram_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(X, ldx, m, n, ex, img);
+    return cudaGetLastError();
+}
+
+cudaError_t oz_tn_run(const uint8_t *aimg, const int *exa, int M, const uint8_t *bimg,
+                      const int *exb, int N, bool upper, i64 m, int splits, double *P,
+                      DevStatus *st, cudaStream_t s)
+{
+    // whole 32-row blocks per split
+    const i64 kbs = ((m + kBK - 1) / kBK + splits - 1) / splits;
+    const size_t smem = (size_t)kStages * kStageBytes;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(oz_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const int tiles = upper ? oz_gram_tiles(M) : ((M + 127) / 128) * ((N + kNT - 1) / kNT);
+    ProfScope ps_(upper ? "oz_gram" : "oz_tn", s);
+    oz_tn_kernel<<<dim3(tiles, splits), kOzThreads, smem, s>>>(aimg, exa, M, bimg, exb, N,
+                                                              upper ? 1 : 0, m, kbs * kBK, P, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_oz_gram(const T *X, i64 ldx, i64 m, int n, const int *ex, int splits,
                            uint8_t *gimg, double *P, DevStatus *st, cudaStream_t s)
 {
-    cudaError_t e;
-    {
-        const i64 total = (m + kBK - 1) / kBK * (kBK / 8) * gram_npad(n);
-        ProfScope ps_("oz_gram_image", s);
-        oz_gram_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(X, ldx, m, n, ex, gimg);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    // whole 32-row blocks per split
-    i64 kbs = ((m + kBK - 1) / kBK + splits - 1) / splits;
-    const i64 rows = kbs * kBK;
-    const size_t smem = (size_t)kStages * kStageBytes;
-    if ((e = cudaFuncSetAttribute(oz_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-        return e;
-    ProfScope ps_("oz_gram", s);
-    oz_gram_kernel<<<dim3(oz_gram_tiles(n), splits), kOzThreads, smem, s>>>(gimg, m, n, ex, rows,
-                                                                          P, st);
-    return cudaGetLastError();
+    cudaError_t e = oz_col_image<T>(X, ldx, m, n, ex, gimg, s);
+    if (e != cudaSuccess) return e;
+    return oz_tn_run(gimg, ex, n, gimg, ex, n, true, m, splits, P, st, s);
+}
+
+int oz_tn_splits(i64 m, int M, int N)
+{
+    return balanced_splits(m, ((M + 127) / 128) * ((N + kNT - 1) / kNT));
+}
+
+cudaError_t launch_oz_col_image(const double *X, i64 ldx, i64 m, int n, const int *ex,
+                                uint8_t *img, cudaStream_t s)
+{
+    return oz_col_image<double>(X, ldx, m, n, ex, img, s);
+}
+
+cudaError_t launch_oz_tn(const uint8_t *aimg, const int *exa, int M, const uint8_t *bimg,
+                         const int *exb, int N, i64 m, int splits, double *P, DevStatus *st,
+                         cudaStream_t s)
+{
+    return oz_tn_run(aimg, exa, M, bimg, exb, N, false, m, splits, P, st, s);
 }
 
 cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *pk, int *em,
@@ -811,21 +867,24 @@ cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, i
     return cudaGetLastError();
 }
 
-template <typename T, typename TC>
-cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
-                         uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
-                         DevStatus *st, cudaStream_t s)
+template <typename T>
+cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
+                                uint8_t *aimg, cudaStream_t s)
 {
-    cudaError_t e;
-    {
-        const int KP = (K + 15) / 16 * 16;
-        const i64 total = (m + 127) / 128 * 128 * ((KP + kBK - 1) / kBK) * (kBK / 8);
-        ProfScope ps_("oz_row_image", s);
-        oz_row_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(A, lda, m, K, pk, er, aimg);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    const int KP = (K + 15) / 16 * 16;
+    const i64 total = (m + 127) / 128 * 128 * ((KP + kBK - 1) / kBK) * (kBK / 8);
+    ProfScope ps_("oz_row_image", s);
+    oz_row_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(A, lda, m, K, pk, er, aimg);
+    return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
+                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s)
+{
     const size_t smem = (size_t)kStages * kStageBytes;
     auto k = oz_nn_kernel<TC>;
+    cudaError_t e;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
@@ -835,6 +894,22 @@ cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const
     k<<<grid, kOzThreads, smem, s>>>(aimg, m, K, er, bimg, em, N, C, ldc, st);
     return cudaGetLastError();
 }
+
+template <typename T, typename TC>
+cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
+                         uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
+                         DevStatus *st, cudaStream_t s)
+{
+    cudaError_t e = launch_oz_row_image<T>(A, lda, m, K, pk, er, aimg, s);
+    if (e != cudaSuccess) return e;
+    return launch_oz_nn_run<TC>(aimg, m, K, er, bimg, em, N, C, ldc, st, s);
+}
+
+template cudaError_t launch_oz_row_image<double>(const double *, i64, i64, int, const int *,
+                                                 const int *, uint8_t *, cudaStream_t);
+template cudaError_t launch_oz_nn_run<double>(const uint8_t *, i64, int, const int *,
+                                              const uint8_t *, const int *, int, double *, i64,
+                                              DevStatus *, cudaStream_t);
 
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s)
 {

@@ -166,9 +166,11 @@ def test_ts_svd_fp32_storage(orc):
 
 
 @gpu
-def test_lowrank_paper_pin_on_gpu(orc):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_lowrank_paper_pin_on_gpu(orc, mode):
     """Algorithm 8 on the GPU reproduces the paper's printed error (sigma_7
-    for l = 20, i = 2) and matches the oracle run with the same Omega."""
+    for l = 20, i = 2) and matches the oracle run with the same Omega, with
+    the products in FP64 FMA or in FP64-accurate tensor-core digits."""
     torch = _torch()
     import paper_1612_08709_gb300 as pkg
     m, n, l = 1500, 400, 20
@@ -176,7 +178,7 @@ def test_lowrank_paper_pin_on_gpu(orc):
     Om = workloads.gaussian(n, l, 4)
     Ur, Sr, Vr, rr, st = orc.lowrank_svd(A, l, l, 2, Om)
     U, S, V, info = pkg.lowrank_svd(torch.as_tensor(A, device="cuda"), l, l, 2,
-                                    torch.as_tensor(Om, device="cuda"))
+                                    torch.as_tensor(Om, device="cuda"), mode=mode)
     U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
     assert info["rank"] == rr == 6
     err = orc.spectral_error(A, U[:, :rr], S[:rr], V[:, :rr])
@@ -185,16 +187,18 @@ def test_lowrank_paper_pin_on_gpu(orc):
 
 
 @gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
 @pytest.mark.parametrize("m,n,k,l,iters,seed", [(3000, 700, 10, 16, 2, 21), (1200, 900, 5, 8, 0, 22),
-                                                (2049, 1000, 30, 40, 1, 23)])
-def test_lowrank_matches_oracle(orc, m, n, k, l, iters, seed):
+                                                (2049, 1000, 30, 40, 1, 23),
+                                                (1000, 2500, 20, 70, 1, 24)])
+def test_lowrank_matches_oracle(orc, m, n, k, l, iters, seed, mode):
     torch = _torch()
     import paper_1612_08709_gb300 as pkg
     A, _, _, _ = workloads.lowrank_plus_noise(m, n, 60, seed)
     Om = workloads.gaussian(n, l, seed + 100)
     Ur, Sr, Vr, rr, st = orc.lowrank_svd(A, k, l, iters, Om, drop_tol=0.0)
     U, S, V, info = pkg.lowrank_svd(torch.as_tensor(A, device="cuda"), k, l, iters,
-                                    torch.as_tensor(Om, device="cuda"), drop_tol=0.0)
+                                    torch.as_tensor(Om, device="cuda"), drop_tol=0.0, mode=mode)
     U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
     assert info["rank"] == rr
     assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
