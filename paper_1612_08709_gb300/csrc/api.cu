@@ -117,6 +117,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     double *cs = ws.take<double>(n);
     int *perm = ws.take<int>(n);
     double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
+    double *B2 = ws.take<double>(nn);
     double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
     const int tsp = terms ? tc_gram_splits(m) : 0;
     double *Ptc = terms ? ws.take<double>((size_t)tsp * nn) : nullptr;
@@ -131,7 +132,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, B, n, s));
         // B = V D V^T (Gram-form Jacobi; B is rotated in place).
-        CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+        CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s));
         // U~ = A V, Sigma = explicit column norms of U~ (Remark "normalizing").
         CK(launch_nn<T, TO>(A, lda, Vt, n, m, n, n, U, ldu, NP, s));
@@ -170,7 +171,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
     }
     // B = V~ D~ V~^T (Gram-form Jacobi; B is rotated in place).
-    CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
@@ -197,7 +198,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
     }
     // Z = W D W^T.
-    CK(launch_jacobi_eig(B, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
     // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
     CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
@@ -257,6 +258,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     double *cs = ws.take<double>(n);
     int *perm = ws.take<int>(n);
     double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
+    double *B2 = ws.take<double>(nn);
     double *Yt = ws.take<double>((size_t)m * n);
     const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
     uint8_t *big = ws.take<uint8_t>(gib > rib ? gib : rib);  // digit images of the tall operand
@@ -282,7 +284,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
     // B = V~ D~ V~^T
-    CK(launch_jacobi_eig(B, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
     // Y~ = (A D^-1) V~ = A (D^-1 V~), with A's columns prescaled by D^-1 for
     // the digit scales (the product is unchanged)
     const double *M1 = Vt;
@@ -322,7 +324,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
     CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
     // Z = W D W^T
-    CK(launch_jacobi_eig(B, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
     // Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W); T = explicit column norms
     CK(launch_oz_pow2_of(sinv, (int)n, pk2, s));
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));

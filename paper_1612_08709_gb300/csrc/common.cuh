@@ -152,17 +152,18 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 // the accumulated rotations: X_in J = X_out with orthogonal columns.
 // ctr must point to at least max_sweeps + 4 zeroed ints of device memory.
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
-                          int max_sweeps, int *ctr, DevStatus *st, int which,
-                          cudaStream_t s);
+                          int max_sweeps, int *ctr, DevStatus *st, int which, cudaStream_t s);
 
-// Eigendecomposition of the symmetric B (n x n row-major, rotated in place)
-// by Gram-form Jacobi, same pair schedule and barrier.  V (n x n,
-// column-major) accumulates the rotations; on return lam holds the
-// eigenvalues (diagonal of the rotated B) in decreasing order and Vout
-// (row-major, ldvo) the matching eigenvectors as columns.  prm: scratch of
-// 4 * ceil(n/2) doubles; perm: n ints; ctr as for launch_jacobi.
-cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *lam, double *Vout,
-                              i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
+// Eigendecomposition of the symmetric B (n x n row-major) by Gram-form
+// Jacobi, same pair schedule and barrier.  V (n x n, column-major)
+// accumulates the rotations; on return lam holds the eigenvalues (diagonal
+// of the rotated B) in decreasing order and Vout (row-major, ldvo) the
+// matching eigenvectors as columns.  B2: a second n x n buffer (ldb) for
+// the one-barrier-per-round form, or NULL for the two-barrier in-place
+// form; either way B's contents are consumed.  prm: scratch of
+// 4 * ceil(n/2) + 2 doubles; perm: n ints; ctr as for launch_jacobi.
+cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv, double *lam,
+                              double *Vout, i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
                               int *perm, DevStatus *st, int which, cudaStream_t s);
 
 // Column norms of the column-major X, stable descending order, and the

@@ -140,14 +140,132 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
     }
 }
 
-template <int NT>
+__device__ __forceinline__ double4 ld4cg(const double4 *p)
+{
+    const double2 a = __ldcg((const double2 *)p), b = __ldcg((const double2 *)p + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ void st4cg(double4 *p, double4 v)
+{
+    __stcg((double2 *)p, make_double2(v.x, v.y));
+    __stcg((double2 *)p + 1, make_double2(v.z, v.w));
+}
+
+__device__ __forceinline__ void circle_pair(int pr, int t, int npad, int &P, int &Q)
+{
+    const int rounds = npad - 1;
+    const int a = pr, b = npad - 1 - pr;
+    P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
+    Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
+    if (P > Q) {
+        int tmp = P;
+        P = Q;
+        Q = tmp;
+    }
+}
+
+// Plane rotation for the 2 x 2 symmetric block [a g; g b] (a Gram block:
+// a = |x_P|^2, b = |x_Q|^2, g = x_P . x_Q).  Returns (c, s, t, 1) with
+// t = s / c the tangent of the angle that annihilates g, or (1, 0, 0, 0)
+// when |g| <= tol * sqrt(|a b|).
+//
+// FP64 on this part has a dependent latency of about 60 cycles per
+// add/multiply and about 600 per division or square root, while FP32 and
+// integer operations are an order of magnitude faster; a rotation sits on
+// the critical path of every round, so it is built from cheap parts:
+//  - the skip test in the log2 domain, 2 log2|g| > 2 log2 tol + log2|a| +
+//    log2|b|, from the exponent fields and an FP32 log2 of the mantissas
+//    (a threshold accurate to about 1e-4 relative);
+//  - the angle in FP32: d = b - a in FP64 (no cancellation loss), then d
+//    and g reduced to FP32 with a common power-of-two scale by integer
+//    operations on their bit patterns, and t = sign(d) g / (|d|/2 +
+//    sqrt(d^2/4 + g^2)), the smaller root of t^2 + 2 (d / 2g) t - 1 = 0;
+//  - c = 1/sqrt(1 + t^2) and s = c t in FP64 from that one t, so the
+//    rotation is orthogonal to working precision whatever t is.  A t with
+//    a relative error near 2^-24 leaves |g'| ~ 2^-24 |g|, which the next
+//    sweep removes.
+// Zeros, subnormals, infinities and angles below FP32's range go through
+// the plain FP64 formula instead.
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// log2|x| for a normal x: exponent plus an FP32 log2 of the top 23
+// mantissa bits.
+__device__ __forceinline__ float log2_abs(double x)
+{
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    const float m = __int_as_float(0x3f800000 | (int)((bits >> 29) & 0x7fffff));
+    return (float)(E - 1023) + __log2f(m);
+}
+
+// x * 2^(-e) as an FP32, by moving x's exponent; 0 below FP32's normal
+// range.  x normal or 0, exp_field(x) <= e.
+__device__ __forceinline__ float scaled_f32(double x, int e)
+{
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    const int fe = E - e + 127;
+    if (E == 0 || fe < 1) return 0.0f;
+    const unsigned sign = (unsigned)((unsigned long long)bits >> 63) << 31;
+    return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((bits >> 29) & 0x7fffff));
+}
+
+__device__ __noinline__ double4 jac_rotation_slow(double a, double b, double g, double tol)
+{
+    if (g != 0.0 && fabs(g) > tol * sqrt(fabs(a * b))) {
+        const double zeta = (b - a) / (2.0 * g);
+        double tt;
+        if (fabs(zeta) > 1e150)
+            tt = 0.5 / zeta;
+        else
+            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + tt * tt);
+        return make_double4(c, c * tt, tt, 1.0);
+    }
+    return make_double4(1.0, 0.0, 0.0, 0.0);
+}
+
+__device__ __forceinline__ double4 jac_rotation(double a, double b, double g, double tol,
+                                                float log2tol)
+{
+    if (g == 0.0) return make_double4(1.0, 0.0, 0.0, 0.0);
+    const int Ea = exp_field(a), Eb = exp_field(b), Eg = exp_field(g);
+    if (Ea == 0 || Eb == 0 || Eg == 0 || Ea == 0x7ff || Eb == 0x7ff || Eg == 0x7ff)
+        return jac_rotation_slow(a, b, g, tol);
+    if (!(2.0f * log2_abs(g) > 2.0f * log2tol + log2_abs(a) + log2_abs(b)))
+        return make_double4(1.0, 0.0, 0.0, 0.0);
+    const double d = b - a;
+    const int Ed = exp_field(d);
+    const int e = Ed > Eg ? Ed : Eg;
+    if (Eg - e < -100) return jac_rotation_slow(a, b, g, tol);
+    const float hf = 0.5f * scaled_f32(d, e), gf = scaled_f32(g, e);
+    float tf = gf / (fabsf(hf) + sqrtf(fmaf(hf, hf, gf * gf)));
+    if (hf < 0.0f) tf = -tf;
+    const double t = (double)tf;
+    const double c = rsqrt(fma(t, t, 1.0));
+    return make_double4(c, c * t, t, 1.0);
+}
+
+// One round per grid barrier: the CTA of pair (P,Q) reduces the three inner
+// products of columns P and Q of X, and rotates those columns of X and J.
+// CH > 0: nr, nc <= CH * NT and each thread keeps its CH entries of the
+// four columns in registers (one read per round); CH = 0: no cache.  FP64
+// issue is scarce (two lanes per clock per SM), so CH is sized to the
+// problem rather than padded.
+template <int NT, int CH>
 __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
 {
+    constexpr int C = CH > 0 ? CH : 1;
     __shared__ double red[3][NT / 32];
     __shared__ double rot_s[3];
     const int npairs = p.npad / 2;
     const int rounds = p.npad - 1;
     const double tol = p.tol;
+    const float log2tol = log2f((float)p.tol);
     int local_rot = 0;
     int done = -1;
     unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
@@ -155,63 +273,73 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
         for (int t = 0; t < rounds; t++) {
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-                const int a = pr, b = p.npad - 1 - pr;
-                int P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
-                int Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
-                if (P > Q) {
-                    int tmp = P;
-                    P = Q;
-                    Q = tmp;
-                }
+                int P, Q;
+                circle_pair(pr, t, p.npad, P, Q);
                 if (Q >= p.nc) continue;  // the padding column of an odd nc
-                double *xp = p.X + (i64)P * p.ldx;
-                double *xq = p.X + (i64)Q * p.ldx;
+                double *xp = p.X + (i64)P * p.ldx, *xq = p.X + (i64)Q * p.ldx;
+                double *jp = p.J + (i64)P * p.ldj, *jq = p.J + (i64)Q * p.ldj;
+                double u[C], v[C], ju[C], jv[C];
                 double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = threadIdx.x; i < p.nr; i += NT) {
-                    const double u = __ldcg(xp + i), v = __ldcg(xq + i);
-                    al = fma(u, u, al);
-                    be = fma(v, v, be);
-                    ga = fma(u, v, ga);
+                if (CH > 0) {
+#pragma unroll
+                    for (int j = 0; j < C; j++) {
+                        const int i = threadIdx.x + j * NT;
+                        u[j] = i < p.nr ? __ldcg(xp + i) : 0.0;
+                        v[j] = i < p.nr ? __ldcg(xq + i) : 0.0;
+                        ju[j] = i < p.nc ? __ldcg(jp + i) : 0.0;
+                        jv[j] = i < p.nc ? __ldcg(jq + i) : 0.0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < C; j++) {
+                        al = fma(u[j], u[j], al);
+                        be = fma(v[j], v[j], be);
+                        ga = fma(u[j], v[j], ga);
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < p.nr; i += NT) {
+                        const double x = __ldcg(xp + i), y = __ldcg(xq + i);
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
                 }
                 block_sum3<NT>(al, be, ga, red);
-                // one thread computes the rotation (FP64 division and square
-                // root are slow on this part), the block reads it from smem
                 if (threadIdx.x == 0) {
-                    double c = 1.0, sn = 0.0, rot = 0.0;
-                    if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-                        // tan(theta) is the smaller root of t^2 + 2 zeta t - 1 = 0,
-                        // which annihilates the (P,Q) inner product.
-                        const double zeta = (be - al) / (2.0 * ga);
-                        double tt;
-                        if (fabs(zeta) > 1e150)
-                            tt = 0.5 / zeta;
-                        else
-                            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
-                        sn = c * tt;
-                        rot = 1.0;
-                    }
-                    rot_s[0] = c;
-                    rot_s[1] = sn;
-                    rot_s[2] = rot;
+                    const double4 r = jac_rotation(al, be, ga, tol, log2tol);
+                    rot_s[0] = r.x;
+                    rot_s[1] = r.y;
+                    rot_s[2] = r.w;
                 }
                 __syncthreads();  // rotation visible; red free for the next pair
-                const double c = rot_s[0], s = rot_s[1];
+                const double c = rot_s[0], sn = rot_s[1];
                 const bool do_rot = rot_s[2] != 0.0;
                 __syncthreads();  // rot_s is rewritten by the next pair
                 if (!do_rot) continue;
                 if (threadIdx.x == 0) local_rot++;
-                for (int i = threadIdx.x; i < p.nr; i += NT) {
-                    const double u = __ldcg(xp + i), v = __ldcg(xq + i);
-                    __stcg(xp + i, c * u - s * v);
-                    __stcg(xq + i, s * u + c * v);
-                }
-                double *jp = p.J + (i64)P * p.ldj;
-                double *jq = p.J + (i64)Q * p.ldj;
-                for (int i = threadIdx.x; i < p.nc; i += NT) {
-                    const double u = __ldcg(jp + i), v = __ldcg(jq + i);
-                    __stcg(jp + i, c * u - s * v);
-                    __stcg(jq + i, s * u + c * v);
+                if (CH > 0) {
+#pragma unroll
+                    for (int j = 0; j < C; j++) {
+                        const int i = threadIdx.x + j * NT;
+                        if (i < p.nr) {
+                            __stcg(xp + i, c * u[j] - sn * v[j]);
+                            __stcg(xq + i, sn * u[j] + c * v[j]);
+                        }
+                        if (i < p.nc) {
+                            __stcg(jp + i, c * ju[j] - sn * jv[j]);
+                            __stcg(jq + i, sn * ju[j] + c * jv[j]);
+                        }
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < p.nr; i += NT) {
+                        const double x = __ldcg(xp + i), y = __ldcg(xq + i);
+                        __stcg(xp + i, c * x - sn * y);
+                        __stcg(xq + i, sn * x + c * y);
+                    }
+                    for (int i = threadIdx.x; i < p.nc; i += NT) {
+                        const double x = __ldcg(jp + i), y = __ldcg(jq + i);
+                        __stcg(jp + i, c * x - sn * y);
+                        __stcg(jq + i, sn * x + c * y);
+                    }
                 }
             }
             if (t == rounds - 1 && threadIdx.x == 0 && local_rot != 0) {
@@ -244,10 +372,12 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
 // the update is in place and race-free.
 struct EigArgs {
     double *B;
+    double *B2;  // second copy of B (single-barrier form)
     i64 ldb;
     double *V;  // column-major n x n
     i64 ldv;
     double4 *prm;  // [npairs] (c, s, t, rotate)
+    double *diag;  // [n] diagonal of the final B (single-barrier form)
     int n, npad;
     int max_sweeps;
     double tol;
@@ -256,31 +386,135 @@ struct EigArgs {
     int which;
 };
 
-__device__ __forceinline__ double4 ld4cg(const double4 *p)
-{
-    const double2 a = __ldcg((const double2 *)p), b = __ldcg((const double2 *)p + 1);
-    return make_double4(a.x, a.y, b.x, b.y);
-}
+// Gram-form Jacobi with one grid barrier per round (npad <= 2 * kEigSmemPairs).
+// B is double-buffered: round t reads Bc and writes every entry of Bn, so a
+// CTA may start round t + 1 while others still read Bc.  Every CTA derives
+// all n/2 rotations of the round from Bc's 2 x 2 diagonal blocks (the same
+// arithmetic on the same values, so all CTAs agree bit for bit) into shared
+// memory; the CTA of pair (P,Q) then writes rows P and Q of J^T B J into Bn
+// and rotates columns P and Q of V in place.
+constexpr int kEigSmemPairs = 1024;
 
-__device__ __forceinline__ void st4cg(double4 *p, double4 v)
+template <int NT>
+__global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
 {
-    __stcg((double2 *)p, make_double2(v.x, v.y));
-    __stcg((double2 *)p + 1, make_double2(v.z, v.w));
-}
-
-__device__ __forceinline__ void circle_pair(int pr, int t, int npad, int &P, int &Q)
-{
-    const int rounds = npad - 1;
-    const int a = pr, b = npad - 1 - pr;
-    P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
-    Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
-    if (P > Q) {
-        int tmp = P;
-        P = Q;
-        Q = tmp;
+    extern __shared__ double4 prm_s[];
+    const int npairs = p.npad / 2;
+    const int rounds = p.npad - 1;
+    const int n = p.n;
+    const i64 ldb = p.ldb, ldv = p.ldv;
+    int local_rot = 0;
+    int done = -1;
+    unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
+    int epoch = 0;
+    const double *Bc = p.B;
+    double *Bn = p.B2;
+    const int tid = threadIdx.x;
+    const float log2tol = log2f((float)p.tol);
+    for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
+        for (int t = 0; t < rounds; t++) {
+            // ---- all rotations of the round
+            for (int k = tid; k < npairs; k += NT) {
+                int K, K2;
+                circle_pair(k, t, p.npad, K, K2);
+                double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
+                if (K2 < n) {
+                    const double a = __ldcg(Bc + (i64)K * ldb + K);
+                    const double b = __ldcg(Bc + (i64)K2 * ldb + K2);
+                    const double g = __ldcg(Bc + (i64)K * ldb + K2);
+                    r = jac_rotation(a, b, g, p.tol, log2tol);
+                    if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                }
+                prm_s[k] = r;
+            }
+            __syncthreads();
+            for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+                int P, Q;
+                circle_pair(pr, t, p.npad, P, Q);
+                const double4 me = prm_s[pr];
+                const bool hasQ = Q < n;
+                const double c = me.x, s = me.y;
+                // ---- columns P and Q of V J
+                if (hasQ && me.w != 0.0) {
+                    double *vp = p.V + (i64)P * ldv, *vq = p.V + (i64)Q * ldv;
+                    for (int i = tid; i < n; i += NT) {
+                        const double u = __ldcg(vp + i), v = __ldcg(vq + i);
+                        __stcg(vp + i, c * u - s * v);
+                        __stcg(vq + i, s * u + c * v);
+                    }
+                }
+                // ---- rows P and Q of J^T B J
+                const double *cP = Bc + (i64)P * ldb;
+                const double *cQ = hasQ ? Bc + (i64)Q * ldb : nullptr;
+                double *nP = Bn + (i64)P * ldb;
+                double *nQ = hasQ ? Bn + (i64)Q * ldb : nullptr;
+                for (int k = tid; k < npairs; k += NT) {
+                    int K, K2;
+                    circle_pair(k, t, p.npad, K, K2);
+                    const bool hasK2 = K2 < n;
+                    if (k == pr) {
+                        // the pair's own 2 x 2 block G^T [a g; g b] G
+                        const double a = __ldcg(cP + P);
+                        if (hasQ) {
+                            const double b = __ldcg(cQ + Q), g = __ldcg(cP + Q);
+                            if (me.w != 0.0) {
+                                const double cc = c * c, ss = s * s, cs = c * s;
+                                const double a1 = fma(cc, a, fma(-2.0 * cs, g, ss * b));
+                                const double b1 = fma(ss, a, fma(2.0 * cs, g, cc * b));
+                                const double g1 = fma(cs, a - b, (cc - ss) * g);
+                                __stcg(nP + P, a1);
+                                __stcg(nQ + Q, b1);
+                                __stcg(nP + Q, g1);
+                                __stcg(nQ + P, g1);
+                            } else {
+                                __stcg(nP + P, a);
+                                __stcg(nQ + Q, b);
+                                __stcg(nP + Q, g);
+                                __stcg(nQ + P, __ldcg(cQ + P));
+                            }
+                        } else {
+                            __stcg(nP + P, a);
+                        }
+                        continue;
+                    }
+                    const double x = __ldcg(cP + K), y = hasK2 ? __ldcg(cP + K2) : 0.0;
+                    const double z = hasQ ? __ldcg(cQ + K) : 0.0;
+                    const double w = (hasQ && hasK2) ? __ldcg(cQ + K2) : 0.0;
+                    const double4 o = prm_s[k];
+                    // rows (own rotation), then columns (the other pair's)
+                    const double x1 = c * x - s * z, y1 = c * y - s * w;
+                    const double z1 = s * x + c * z, w1 = s * y + c * w;
+                    const double ck = o.x, sk = o.y;
+                    __stcg(nP + K, ck * x1 - sk * y1);
+                    if (hasK2) __stcg(nP + K2, sk * x1 + ck * y1);
+                    if (hasQ) {
+                        __stcg(nQ + K, ck * z1 - sk * w1);
+                        if (hasK2) __stcg(nQ + K2, sk * z1 + ck * w1);
+                    }
+                }
+            }
+            if (t == rounds - 1 && local_rot != 0) {
+                atomicAdd(p.rot + sweep, local_rot);
+                local_rot = 0;
+            }
+            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
+            double *tmp = Bn;
+            Bn = const_cast<double *>(Bc);
+            Bc = tmp;
+        }
+        if (ld_acquire(p.rot + sweep) == 0) {
+            done = sweep + 1;
+            break;
+        }
+    }
+    if (blockIdx.x == 0) {
+        for (int i = tid; i < n; i += NT) p.diag[i] = __ldcg(Bc + (i64)i * ldb + i);
+        if (tid == 0) p.st->sweeps[p.which] = done;
     }
 }
 
+// Two-barrier in-place form for npad > 2 * kEigSmemPairs (the rotations
+// of a round do not fit in shared memory).
 template <int NT>
 __global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
 {
@@ -494,11 +728,14 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.which = which;
 
     constexpr int NT = 128;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    const int mx = nr > nc ? nr : nc;
+    const void *kern = mx <= NT       ? (const void *)jacobi_kernel<NT, 1>
+                       : mx <= 2 * NT ? (const void *)jacobi_kernel<NT, 2>
+                       : mx <= 4 * NT ? (const void *)jacobi_kernel<NT, 4>
+                       : mx <= 8 * NT ? (const void *)jacobi_kernel<NT, 8>
+                                      : (const void *)jacobi_kernel<NT, 0>;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<NT>, NT, 0)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0)) != cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     int npairs = a.npad / 2;
@@ -506,12 +743,11 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     if (blocks > npairs) blocks = npairs;
     void *args[] = {&a};
     ProfScope ps_("jacobi_svd", s);
-    return cudaLaunchCooperativeKernel((const void *)jacobi_kernel<NT>, dim3(blocks), dim3(NT),
-                                       args, 0, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, 0, s);
 }
 
-cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *lam, double *Vout,
-                              i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
+cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv, double *lam,
+                              double *Vout, i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
                               int *perm, DevStatus *st, int which, cudaStream_t s)
 {
     cudaError_t e;
@@ -527,44 +763,51 @@ cudaError_t launch_jacobi_eig(double *B, i64 ldb, double *V, i64 ldv, double *la
     if ((e = cudaMemsetAsync(ctr, 0, sizeof(int) * (size_t)(max_sweeps + 4), s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(&st->bar[0], 0, sizeof(int) * 4, s)) != cudaSuccess) return e;
+    // the rotation-parameter scratch (>= 2n doubles) holds the diagonal after
+    double *dg = prm;
+    const int npad = n + (n & 1);
+    const bool single = B2 != nullptr && npad / 2 <= kEigSmemPairs;
     if (n >= 2) {
         EigArgs a;
         a.B = B;
+        a.B2 = B2;
         a.ldb = ldb;
         a.V = V;
         a.ldv = ldv;
         a.prm = (double4 *)prm;
+        a.diag = dg;
         a.n = n;
-        a.npad = n + (n & 1);
+        a.npad = npad;
         a.max_sweeps = max_sweeps;
         a.tol = (double)n * 0x1p-53;
         a.rot = ctr;
         a.st = st;
         a.which = which;
         constexpr int NT = 128;
+        const void *kern = single ? (const void *)jacobi_eig1_kernel<NT>
+                                  : (const void *)jacobi_eig_kernel<NT>;
+        const size_t smem = single ? sizeof(double4) * (size_t)(npad / 2) : 0;
         int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_eig_kernel<NT>, NT,
-                                                                0)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) !=
+            cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-        int npairs = a.npad / 2;
+        int npairs = npad / 2;
         int blocks = num_sms() * per_sm;
         if (blocks > npairs) blocks = npairs;
         void *args[] = {&a};
         ProfScope ps_("jacobi_eig", s);
-        if ((e = cudaLaunchCooperativeKernel((const void *)jacobi_eig_kernel<NT>, dim3(blocks),
-                                             dim3(NT), args, 0, s)) != cudaSuccess)
+        if ((e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, smem, s)) !=
+            cudaSuccess)
             return e;
     } else {
         if ((e = cudaMemsetAsync(&st->sweeps[which], 0, sizeof(int), s)) != cudaSuccess) return e;
     }
-    // the rotation-parameter scratch (>= 2n doubles) now holds the diagonal
-    double *dg = prm;
-    {
-    ProfScope ps_("diag", s);
-    diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(B, ldb, n, dg);
+    if (!(single && n >= 2)) {
+        ProfScope ps_("diag", s);
+        diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(B, ldb, n, dg);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
     ProfScope ps_("rank_sort", s);
     rank_sort_kernel<<<(n + 255) / 256, 256, 0, s>>>(dg, n, perm);
