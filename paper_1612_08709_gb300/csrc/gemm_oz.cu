@@ -19,14 +19,17 @@
 //    s + t <= 6 (28 pairs; the dropped ones weigh about 2^-49) of
 //    2^(ea+eb-14-7(s+t)) sum_k da_s db_t.  Pairs with the same level
 //    L = s + t share one FP32 accumulator in tensor memory (7 levels x 64
-//    columns).  A row adds at most 129^2 + 2*129*64 + (L-1)*64^2 < 36992
-//    to level L, so over a chunk of 256 rows every level sum stays below
-//    2^24 and is exact.
+//    columns).  A row adds at most 129^2 = 16641 to level 0 and
+//    2*129*64 + (L-1)*64^2 <= 36992 to level L >= 1, so over a chunk of 448
+//    rows every level sum stays below 2^24 and is exact.
 //  * After each chunk the epilogue warps combine the seven level sums with
 //    error-free FP32 transformations (TwoSum) into a double-FP32 value and
-//    add it to an FP64 running sum per output (two FP64 additions per
-//    output and chunk, the only FP64 arithmetic of the product).
-//
+//    add it to an FP64 running sum per output: two FP64 additions per
+//    output and chunk (the FP32 -> FP64 widening and the power-of-two
+//    scales are integer operations on the bit patterns, since FP64 issue
+//    is scarce on this part).  A product with a single chunk (k <= 448)
+//    keeps the double-FP32 values in registers and releases tensor memory
+//    to the next tile before it widens, scales and stores them.
 // Each operand is first cut into a digit image in global memory (once per
 // product), laid out exactly as the shared-memory tiles, so the product
 // kernels only stage tiles with bulk copies (TMA) and issue MMAs.  Stages
@@ -43,11 +46,24 @@ constexpr int kDig = 7;           // digits per value
 constexpr int kLevels = 7;        // levels s + t = 0..6
 constexpr int kNT = 64;           // output columns per CTA tile (N of the MMA)
 constexpr int kBK = 32;           // rows (Gram) or k (A*M) per stage
-constexpr int kChunkStages = 8;   // 256 rows/k per FP32 chunk (levels 0-3 exact)
-constexpr int kStages = 2;
+constexpr int kChunkStages = 14;  // 448 rows/k per FP32 chunk (every level exact)
 constexpr uint32_t kATerm = 128 * kBK * 2;  // 8 KB: one digit of the 128-row operand
 constexpr uint32_t kBTerm = kNT * kBK * 2;  // 4 KB: one digit of the 64-row operand
-constexpr uint32_t kStageBytes = kDig * (kATerm + kBTerm);
+// The products stream 16-deep halves of the 32-deep blocks: a stage holds
+// the seven 4 KB A digits and the 14 KB stacked B digits of one half, and
+// five stages keep four halves in flight ahead of the MMAs.
+constexpr int kStages = 5;
+constexpr uint32_t kStageBytes = kDig * (kATerm / 2) + kDig * (kBTerm / 2);  // 42 KB
+constexpr int kChunkUnits = 2 * kChunkStages;  // halves per FP32 chunk
+// The A*M product runs three stages and stages its 128 x 64 output tile in
+// shared memory (rows padded to 65 eight-byte slots): the drain parks each
+// output's double-FP32 value there (or adds it to an FP64 sum when k spans
+// several chunks), releases tensor memory, and the results then leave as
+// whole 256-byte row segments.  Rolled loops keep the epilogue small (an
+// unrolled one overflows the instruction cache).
+constexpr int kStagesNN = 3;
+constexpr int kStgLd = kNT + 1;
+constexpr size_t kNNSmem = (size_t)kStagesNN * kStageBytes + 128 * kStgLd * sizeof(double);
 
 // Exponent of the bit pattern (unbiased), and the 53-bit significand.
 __device__ __forceinline__ void dsplit(double v, int &ev, unsigned long long &mant, uint32_t &sign)
@@ -79,14 +95,14 @@ __device__ __forceinline__ void fsplit(float v, int &ev, unsigned long long &man
     mant = (unsigned long long)((b & 0x7FFFFFu) | (1u << 23));
 }
 
-// bfloat16 bit pattern of the integer d with |d| <= 255.
+// bfloat16 bit pattern of the integer d with |d| <= 255: d + 1.5 * 2^23 is
+// formed exactly in the FP32 bit pattern, the bias is subtracted in FP32
+// (exact), and an integer of at most 8 significant bits keeps all of them
+// in bfloat16's upper half.
 __device__ __forceinline__ uint32_t bf16_of_int(int d)
 {
-    if (d == 0) return 0;
-    const uint32_t sign = d < 0 ? 1u : 0u;
-    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-    const uint32_t p = 31 - __clz(a);  // 0..7
-    return (sign << 15) | ((127 + p) << 7) | ((a << (7 - p)) & 0x7F);
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
 }
 
 // Seven balanced base-128 digits of a value |v| = mant 2^(q) (q = its
@@ -105,18 +121,24 @@ __device__ __forceinline__ void digits_from(unsigned long long mant, int q, uint
         else if (sh > -64)
             F = (mant + (1ull << (-sh - 1))) >> (-sh);
     }
+    // recode from the least significant end in 32-bit halves: digits 6..3
+    // from the low 28 bits (whose final carry moves up), 2..0 from the rest
+    uint32_t lo = (uint32_t)(F & 0xFFFFFFFull), hi = (uint32_t)(F >> 28);
     int dg[kDig];
 #pragma unroll
-    for (int s = kDig - 1; s >= 1; s--) {
-        int r = (int)(F & 127);
-        F >>= 7;
-        if (r >= 64) {
-            r -= 128;
-            F += 1;
-        }
-        dg[s] = r;
+    for (int s = kDig - 1; s >= 3; s--) {
+        const uint32_t r = lo & 127u, c = r >> 6;
+        dg[s] = (int)r - (int)(c << 7);
+        lo = (lo >> 7) + c;
     }
-    dg[0] = (int)(F & 0xFF);
+    hi += lo;
+#pragma unroll
+    for (int s = 2; s >= 1; s--) {
+        const uint32_t r = hi & 127u, c = r >> 6;
+        dg[s] = (int)r - (int)(c << 7);
+        hi = (hi >> 7) + c;
+    }
+    dg[0] = (int)(hi & 0xFFu);
 #pragma unroll
     for (int s = 0; s < kDig; s++) out[s] = bf16_of_int(vsign ? -dg[s] : dg[s]);
 }
@@ -162,6 +184,32 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &err)
     err = (a - (s - bb)) + (b - bb);
 }
 
+// Exact FP32 -> FP64 widening by integer operations (for zero and normal
+// floats; the level sums and their TwoSum errors are multiples of 2^-42
+// far inside FP32's normal range, so no subnormal reaches this).
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    if ((b & 0x7FFFFFFFu) == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long ex = (unsigned long long)(((b >> 23) & 0xFF) + (1023 - 127));
+    return __longlong_as_double((long long)(sign | (ex << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFF) << 29)));
+}
+
+// x 2^k: an integer add to the exponent field when the result stays
+// normal, else the library scaling.
+__device__ __forceinline__ double scale2k(double x, int k)
+{
+    const long long b = __double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7FF);
+    if (ef == 0) return x;  // zero (subnormals do not occur)
+    const int nf = ef + k;
+    if (nf >= 1 && nf <= 2046 && ef != 0x7FF)
+        return __longlong_as_double(b + ((long long)k << 52));
+    return ldexp(x, k);
+}
+
 // 8 consecutive FP32 TMEM columns of this thread's lane (no wait).
 __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8])
 {
@@ -195,32 +243,68 @@ __device__ __forceinline__ void drain_levels(uint32_t tmem_row, double (&acc)[kN
                 s = t;
                 e += er;
             }
-            acc[g * 8 + c] += (double)s;
-            acc[g * 8 + c] += (double)e;
+            acc[g * 8 + c] += widen(s);
+            acc[g * 8 + c] += widen(e);
         }
     }
 }
 
-// MMAs of one stage: both 16-deep halves, all 28 digit pairs.
+// One 8-column group of the drain: the seven level sums of columns
+// 8g .. 8g+7 of this thread's TMEM lane, combined with TwoSum into
+// double-FP32 values (hi, lo).
+__device__ __forceinline__ void drain_group(uint32_t tmem_row, int g, float (&hi)[8], float (&lo)[8])
+{
+    uint32_t lv[kLevels][8];
+#pragma unroll
+    for (int L = 0; L < kLevels; L++) tmem_ld8_nowait(tmem_row + (uint32_t)(L * kNT + g * 8), lv[L]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        float s = __uint_as_float(lv[kLevels - 1][c]) *
+                  __uint_as_float((uint32_t)(127 - 7 * (kLevels - 1)) << 23);
+        float e = 0.f;
+#pragma unroll
+        for (int L = kLevels - 2; L >= 0; L--) {
+            float t, er;
+            const float w = __uint_as_float((uint32_t)(127 - 7 * L) << 23);
+            two_sum(__uint_as_float(lv[L][c]) * w, s, t, er);
+            s = t;
+            e += er;
+        }
+        hi[c] = s;
+        lo[c] = e;
+    }
+}
+
+// B operand of a 16-deep half: the digit blocks t = 0..6 (64 rows each)
+// stacked into one 448-row K-major operand at t * (kBTerm / 2), so 8-row
+// groups are 256 bytes apart across digit boundaries.  kBHalf is its size
+// (and the stride between halves in the B digit image of oz_image).
+constexpr uint32_t kBHalf = kDig * (kBTerm / 2);
+
+// MMAs of one stage (a 16-deep half).  For A digit s one MMA (two when
+// wider than 256) multiplies A_s by the stacked B digits t = 0..6-s into
+// tensor-memory columns (s + t) * 64: level L = s + t receives every
+// A_s B_t with s + t = L, 10 MMAs of N <= 256 instead of 28 of N = 64
+// (the same products, 43% fewer operand bytes read from shared memory).
+// At the first half of a chunk the s = 0 MMAs, which cover all seven
+// levels, overwrite the accumulators; every later MMA accumulates.
 __device__ __forceinline__ void issue_stage(uint32_t abase, uint32_t bbase, uint32_t tmem,
                                             uint32_t &started)
 {
-    const uint32_t idesc = idesc_bf16(128, kNT);
 #pragma unroll
-    for (int h = 0; h < kBK / 16; h++) {
+    for (int s = 0; s < kDig; s++) {
+        const uint64_t ad = sdesc(abase + s * (kATerm / 2), 128, 256);
+        const int width = (kDig - s) * kNT;
 #pragma unroll
-        for (int s = 0; s < kDig; s++) {
-#pragma unroll
-            for (int t = 0; t < kDig - s; t++) {
-                const int L = s + t;
-                const uint64_t ad = sdesc(abase + s * kATerm + h * (128 * 32), 128, 256);
-                const uint64_t bd = sdesc(bbase + t * kBTerm + h * (kNT * 32), 128, 256);
-                const uint32_t acc = (started >> L) & 1u;
-                mma_bf16(tmem + (uint32_t)(L * kNT), ad, bd, idesc, acc);
-                started |= 1u << L;
-            }
+        for (int n0 = 0; n0 < width; n0 += 256) {
+            const int w = width - n0 < 256 ? width - n0 : 256;
+            const uint64_t bd = sdesc(bbase + (uint32_t)(n0 / 8) * 256, 128, 256);
+            const uint32_t acc = (started != 0u || s > 0) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(s * kNT + n0), ad, bd, idesc_bf16(128, w), acc);
         }
     }
+    started = 1u;
 }
 
 // Upper tiles of the Gram: i-blocks of 128 (ti), j-blocks of 64 (tj) that
@@ -345,7 +429,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     i64 kb1 = kb0 + rows_per_split / kBK;
     if (kb1 > kbm) kb1 = kbm;
     const int nkb = kb1 > kb0 ? (int)(kb1 - kb0) : 0;
-    const int nchunks = (nkb + kChunkStages - 1) / kChunkStages;
+    const int nunits = 2 * nkb;
+    const int nchunks = (nunits + kChunkUnits - 1) / kChunkUnits;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -367,25 +452,24 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         // ---------------- bulk-copy producer
         if (lane == 0) {
             int last = -1;
-            for (int kb = 0; kb < nkb; kb++) {
-                const int s = kb % kStages;
-                if (!mbar_wait(&empty_bar[s], ((kb / kStages) & 1) ^ 1, err)) break;
+            for (int u = 0; u < nunits; u++) {
+                const int s = u % kStages;
+                if (!mbar_wait(&empty_bar[s], ((u / kStages) & 1) ^ 1, err)) break;
                 uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
                 mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-                const uint8_t *ablk = aimg + (size_t)(kb0 + kb) * kDig * 2 * half_a;
-                const uint8_t *bblk = bimg + (size_t)(kb0 + kb) * kDig * 2 * half_b;
+                const int h = u & 1;
+                const uint8_t *ablk = aimg + (size_t)(kb0 + (u >> 1)) * kDig * 2 * half_a;
+                const uint8_t *bblk = bimg + (size_t)(kb0 + (u >> 1)) * kDig * 2 * half_b;
 #pragma unroll 1
-                for (int d = 0; d < kDig; d++)
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        bulk_g2s(stage + d * kATerm + h * (kATerm / 2),
-                                 ablk + (size_t)(d * 2 + h) * half_a + (size_t)(i0 / 8) * 256,
-                                 kATerm / 2, &full_bar[s]);
-                        bulk_g2s(stage + kDig * kATerm + d * kBTerm + h * (kBTerm / 2),
-                                 bblk + (size_t)(d * 2 + h) * half_b + (size_t)(j0 / 8) * 256,
-                                 kBTerm / 2, &full_bar[s]);
-                    }
-                last = kb;
+                for (int d = 0; d < kDig; d++) {
+                    bulk_g2s(stage + d * (kATerm / 2),
+                             ablk + (size_t)(d * 2 + h) * half_a + (size_t)(i0 / 8) * 256,
+                             kATerm / 2, &full_bar[s]);
+                    bulk_g2s(stage + kDig * (kATerm / 2) + d * (kBTerm / 2),
+                             bblk + (size_t)(d * 2 + h) * half_b + (size_t)(j0 / 8) * 256,
+                             kBTerm / 2, &full_bar[s]);
+                }
+                last = u;
             }
             if (last >= 0) mbar_wait_drain(&full_bar[last % kStages], (last / kStages) & 1);
         }
@@ -416,14 +500,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
                 for (int jj = 0; jj < kNT; jj++) {
                     const int j = j0 + jj;
-                    if (j < N) Prow[j] = ldexp(acc[jj], ei + exb[j] - 14);
+                    if (j < N) Prow[j] = scale2k(acc[jj], ei + exb[j] - 14);
                 }
             }
         }
     } else {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int kb = 0;
+            int u = 0;
             bool ok = true;
             for (int ch = 0; ch < nchunks && ok; ch++) {
                 if (ch > 0) {
@@ -431,16 +515,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     tc_fence_after();
                 }
                 uint32_t started = 0;
-                const int kb_end = (ch + 1) * kChunkStages < nkb ? (ch + 1) * kChunkStages : nkb;
-                for (; kb < kb_end; kb++) {
-                    const int s = kb % kStages;
-                    if (!mbar_wait(&full_bar[s], (kb / kStages) & 1, err)) {
+                const int u_end = (ch + 1) * kChunkUnits < nunits ? (ch + 1) * kChunkUnits : nunits;
+                for (; u < u_end; u++) {
+                    const int s = u % kStages;
+                    if (!mbar_wait(&full_bar[s], (u / kStages) & 1, err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t base = saddr(smem_raw + (size_t)s * kStageBytes);
-                    issue_stage(base, base + kDig * kATerm, tmem, started);
+                    issue_stage(base, base + kDig * (kATerm / 2), tmem, started);
                     mma_commit(&empty_bar[s]);
                 }
                 if (!ok) break;
@@ -469,7 +553,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                  TC *__restrict__ C, i64 ldc, DevStatus *st)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+    __shared__ __align__(8) uint64_t full_bar[kStagesNN], empty_bar[kStagesNN];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, done_bar;
     __shared__ uint32_t tmem_base_s;
 
@@ -477,7 +561,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     int *err = &st->err;
     const int KP = (K + 15) / 16 * 16;
     const int nkb = (KP + kBK - 1) / kBK;
-    const int nchunks = (nkb + kChunkStages - 1) / kChunkStages;
+    const int nunits = KP / 16;  // 16-deep halves holding some k < K
+    const int nchunks = (nunits + kChunkUnits - 1) / kChunkUnits;
     const int TN = (N + kNT - 1) / kNT;
     const i64 ntiles = (m + 127) / 128 * TN;
     const int my_tiles =
@@ -485,7 +570,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const size_t btile = (size_t)nkb * kDig * kBTerm;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < kStagesNN; s++) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -508,54 +593,91 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 const i64 t = (i64)blockIdx.x + (i64)ti * gridDim.x;
                 const i64 rt = t / TN;
                 const int nt = (int)(t % TN);
-                for (int kb = 0; kb < nkb; kb++, f++) {
-                    const int s = f % kStages;
-                    if (!mbar_wait(&empty_bar[s], ((f / kStages) & 1) ^ 1, err)) {
+                for (int u = 0; u < nunits; u++, f++) {
+                    const int s = f % kStagesNN;
+                    if (!mbar_wait(&empty_bar[s], ((f / kStagesNN) & 1) ^ 1, err)) {
                         ok = false;
                         break;
                     }
                     uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
                     mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-                    bulk_g2s(stage, aimg + ((size_t)rt * nkb + kb) * kDig * kATerm, kDig * kATerm,
-                             &full_bar[s]);
-                    bulk_g2s(stage + kDig * kATerm, bimg + (size_t)nt * btile + (size_t)kb * kDig * kBTerm,
-                             kDig * kBTerm, &full_bar[s]);
+                    const int kb = u >> 1, h = u & 1;
+                    const uint8_t *ablk = aimg + ((size_t)rt * nkb + kb) * kDig * kATerm;
+#pragma unroll 1
+                    for (int d = 0; d < kDig; d++)
+                        bulk_g2s(stage + d * (kATerm / 2), ablk + d * kATerm + h * (kATerm / 2),
+                                 kATerm / 2, &full_bar[s]);
+                    bulk_g2s(stage + kDig * (kATerm / 2),
+                             bimg + (size_t)nt * btile + (size_t)kb * kDig * kBTerm + h * kBHalf,
+                             kBHalf, &full_bar[s]);
                     last = f;
                 }
             }
-            if (last >= 0) mbar_wait_drain(&full_bar[last % kStages], (last / kStages) & 1);
+            if (last >= 0) mbar_wait_drain(&full_bar[last % kStagesNN], (last / kStagesNN) & 1);
         }
         __syncwarp();
     } else if (warp < 4) {
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        // this warp's 32 staging rows (row `lane` is this thread's TMEM lane)
+        double *stg = reinterpret_cast<double *>(smem_raw + (size_t)kStagesNN * kStageBytes) +
+                      warp * 32 * kStgLd;
+        float2 *stg2 = reinterpret_cast<float2 *>(stg);
         int ch_global = 0;
         bool ok = true;
         for (int ti = 0; ti < my_tiles && ok; ti++) {
             const i64 t = (i64)blockIdx.x + (i64)ti * gridDim.x;
-            const i64 row = (t / TN) * 128 + warp * 32 + lane;
+            const i64 row0 = (t / TN) * 128 + warp * 32;
             const int nt = (int)(t % TN);
-            double acc[kNT];
-#pragma unroll
-            for (int j = 0; j < kNT; j++) acc[j] = 0.0;
+            const bool single = nchunks == 1;
+            if (!single)
+                for (int c = 0; c < kNT; c++) stg[lane * kStgLd + c] = 0.0;
             for (int ch = 0; ch < nchunks; ch++, ch_global++) {
                 if (!mbar_wait(&acc_full, ch_global & 1, err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                drain_levels(trow, acc);
+#pragma unroll 1
+                for (int g = 0; g < kNT / 8; g++) {
+                    float hv[8], lv[8];
+                    drain_group(trow, g, hv, lv);
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                        const int col = g * 8 + c;
+                        if (single)
+                            stg2[lane * kStgLd + col] = make_float2(hv[c], lv[c]);
+                        else
+                            stg[lane * kStgLd + col] += widen(hv[c]) + widen(lv[c]);
+                    }
+                }
                 tc_fence_before();
                 mbar_arrive(&acc_empty);
             }
             if (!ok) break;
-            if (row < m) {
-                const int e = er[row];
-#pragma unroll
-                for (int jj = 0; jj < kNT; jj++) {
-                    const int j = nt * kNT + jj;
-                    if (j < N) C[row * ldc + j] = (TC)ldexp(acc[jj], e + em[j] - 14);
+            // tensor memory is free: widen, scale and store row segments
+            __syncwarp();
+#pragma unroll 1
+            for (int c0 = 0; c0 < kNT; c0 += 32) {
+                const int j = nt * kNT + c0 + lane;
+                if (j < N) {
+                    const int ej = em[j] - 14;
+#pragma unroll 4
+                    for (int r = 0; r < 32; r++) {
+                        const i64 row = row0 + r;
+                        if (row < m) {
+                            double v;
+                            if (single) {
+                                const float2 f = stg2[r * kStgLd + c0 + lane];
+                                v = widen(f.x) + widen(f.y);
+                            } else {
+                                v = stg[r * kStgLd + c0 + lane];
+                            }
+                            C[row * ldc + j] = (TC)scale2k(v, er[row] + ej);
+                        }
+                    }
                 }
             }
+            __syncwarp();
         }
     } else {
         if (lane == 0) {
@@ -571,16 +693,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         tc_fence_after();
                     }
                     uint32_t started = 0;
-                    const int kb_end = (ch + 1) * kChunkStages < nkb ? (ch + 1) * kChunkStages : nkb;
-                    for (int kb = ch * kChunkStages; kb < kb_end; kb++, f++) {
-                        const int s = f % kStages;
-                        if (!mbar_wait(&full_bar[s], (f / kStages) & 1, err)) {
+                    const int u_end = (ch + 1) * kChunkUnits < nunits ? (ch + 1) * kChunkUnits : nunits;
+                    for (int u = ch * kChunkUnits; u < u_end; u++, f++) {
+                        const int s = f % kStagesNN;
+                        if (!mbar_wait(&full_bar[s], (f / kStagesNN) & 1, err)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t base = saddr(smem_raw + (size_t)s * kStageBytes);
-                        issue_stage(base, base + kDig * kATerm, tmem, started);
+                        issue_stage(base, base + kDig * (kATerm / 2), tmem, started);
                         mma_commit(&empty_bar[s]);
                     }
                     if (!ok) break;
@@ -628,7 +750,8 @@ __global__ void oz_colexp_kernel(const double *__restrict__ M, i64 ldm, int K, i
 }
 
 // Digit image of diag(2^-pk) M: per column tile nt and 32-deep k block kb,
-// 7 digit blocks of 64 rows (j) x 32 k in the K-major no-swizzle layout.
+// for each 16-deep half the 7 digit blocks of 64 rows (j) x 16 k stacked
+// in the K-major no-swizzle layout (the stage's B operand, see kBHalf).
 __global__ void oz_image_kernel(const double *__restrict__ M, i64 ldm, int K, int N,
                                 const int *__restrict__ pk, const int *__restrict__ em,
                                 uint8_t *__restrict__ img)
@@ -653,9 +776,9 @@ __global__ void oz_image_kernel(const double *__restrict__ M, i64 ldm, int K, in
             digits7(in ? M[(i64)k * ldm + j] : 0.0, ej, (in && pk) ? -pk[k] : 0, d[u]);
         }
         uint8_t *blk = img + ((size_t)nt * nkb + kb) * kDig * kBTerm;
-        const uint32_t off = (uint32_t)(q >> 1) * (kNT * 32) + (uint32_t)(jj >> 3) * 256 +
+        const uint32_t off = (uint32_t)(q >> 1) * kBHalf + (uint32_t)(jj >> 3) * 256 +
                              (uint32_t)(q & 1) * 128 + (uint32_t)(jj & 7) * 16;
-        store_digits8(blk, kBTerm, off, d);
+        store_digits8(blk, kBTerm / 2, off, d);
     }
 }
 
@@ -882,7 +1005,7 @@ template <typename TC>
 cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
                              const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s)
 {
-    const size_t smem = (size_t)kStages * kStageBytes;
+    const size_t smem = kNNSmem;
     auto k = oz_nn_kernel<TC>;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
