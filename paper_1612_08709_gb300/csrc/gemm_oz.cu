@@ -186,28 +186,37 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &err)
 
 // Exact FP32 -> FP64 widening by integer operations (for zero and normal
 // floats; the level sums and their TwoSum errors are multiples of 2^-42
-// far inside FP32's normal range, so no subnormal reaches this).
+// far inside FP32's normal range, so no subnormal reaches this).  Written
+// without branches so that independent widenings interleave.
 __device__ __forceinline__ double widen(float f)
 {
     const uint32_t b = __float_as_uint(f);
-    if ((b & 0x7FFFFFFFu) == 0) return 0.0;
     const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
     const unsigned long long ex = (unsigned long long)(((b >> 23) & 0xFF) + (1023 - 127));
-    return __longlong_as_double((long long)(sign | (ex << 52) |
-                                            ((unsigned long long)(b & 0x7FFFFF) << 29)));
+    const unsigned long long w =
+        sign | (ex << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29);
+    return (b & 0x7FFFFFFFu) ? __longlong_as_double((long long)w) : 0.0;
 }
 
-// x 2^k: an integer add to the exponent field when the result stays
-// normal, else the library scaling.
-__device__ __forceinline__ double scale2k(double x, int k)
+// x 2^k by an integer add to the exponent field, without branches; `bad`
+// is set when the result would leave the normal range (then the caller
+// redoes the value with scale2k_safe).
+__device__ __forceinline__ double scale2k_fast(double x, int k, bool &bad)
 {
     const long long b = __double_as_longlong(x);
     const int ef = (int)((b >> 52) & 0x7FF);
-    if (ef == 0) return x;  // zero (subnormals do not occur)
-    const int nf = ef + k;
-    if (nf >= 1 && nf <= 2046 && ef != 0x7FF)
-        return __longlong_as_double(b + ((long long)k << 52));
-    return ldexp(x, k);
+    bad |= ef != 0 && ((unsigned)(ef + k - 1) >= 2046u || ef == 0x7FF);
+    return ef == 0 ? x : __longlong_as_double(b + ((long long)k << 52));
+}
+
+__device__ __noinline__ double scale2k_safe(double x, int k) { return ldexp(x, k); }
+
+// x 2^k for results written once per tile (the Gram partials).
+__device__ __forceinline__ double scale2k(double x, int k)
+{
+    bool bad = false;
+    const double r = scale2k_fast(x, k, bad);
+    return bad ? scale2k_safe(x, k) : r;
 }
 
 // 8 consecutive FP32 TMEM columns of this thread's lane (no wait).
@@ -230,6 +239,10 @@ __device__ __forceinline__ void drain_levels(uint32_t tmem_row, double (&acc)[kN
         for (int L = 0; L < kLevels; L++) tmem_ld8_nowait(tmem_row + (uint32_t)(L * kNT + g * 8), lv[L]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
+        for (int L = 0; L < kLevels; L++)
+#pragma unroll
+            for (int c = 0; c < 8; c++) asm volatile("" : "+r"(lv[L][c]));
+#pragma unroll
         for (int c = 0; c < 8; c++) {
             // smallest level first; 2^(-7L) is the level's exact weight
             float s = __uint_as_float(lv[kLevels - 1][c]) *
@@ -249,15 +262,36 @@ __device__ __forceinline__ void drain_levels(uint32_t tmem_row, double (&acc)[kN
     }
 }
 
-// One 8-column group of the drain: the seven level sums of columns
-// 8g .. 8g+7 of this thread's TMEM lane, combined with TwoSum into
-// double-FP32 values (hi, lo).
-__device__ __forceinline__ void drain_group(uint32_t tmem_row, int g, float (&hi)[8], float (&lo)[8])
+// The drain of one 8-column group g: load_group issues the loads of the
+// seven level sums of columns 8g .. 8g+7 of this thread's TMEM lane (no
+// wait); park_group combines them with TwoSum into double-FP32 values and
+// parks them in the staging row (or adds them to its FP64 sums).
+__device__ __forceinline__ void load_group(uint32_t tmem_row, int g, uint32_t (&lv)[kLevels][8])
 {
-    uint32_t lv[kLevels][8];
 #pragma unroll
     for (int L = 0; L < kLevels; L++) tmem_ld8_nowait(tmem_row + (uint32_t)(L * kNT + g * 8), lv[L]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Wait for the outstanding TMEM loads, then pass the registers of lv
+// through empty asm statements: their values now depend on code after the
+// wait, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&lv)[kLevels][8])
+{
+    tmem_wait_ld();
+#pragma unroll
+    for (int L = 0; L < kLevels; L++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) asm volatile("" : "+r"(lv[L][c]));
+}
+
+__device__ __forceinline__ void park_group(const uint32_t (&lv)[kLevels][8], int g, bool single,
+                                           double *stg, float2 *stg2, int lane)
+{
 #pragma unroll
     for (int c = 0; c < 8; c++) {
         float s = __uint_as_float(lv[kLevels - 1][c]) *
@@ -271,8 +305,11 @@ __device__ __forceinline__ void drain_group(uint32_t tmem_row, int g, float (&hi
             s = t;
             e += er;
         }
-        hi[c] = s;
-        lo[c] = e;
+        const int col = g * 8 + c;
+        if (single)
+            stg2[lane * kStgLd + col] = make_float2(s, e);
+        else
+            stg[lane * kStgLd + col] += widen(s) + widen(e);
     }
 }
 
@@ -637,43 +674,73 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                // the loads of group g + 1 are in flight while group g is
+                // combined (two register sets, alternating)
+                uint32_t la[kLevels][8], lb[kLevels][8];
+                load_group(trow, 0, la);
+                tmem_wait_ld(la);
 #pragma unroll 1
-                for (int g = 0; g < kNT / 8; g++) {
-                    float hv[8], lv[8];
-                    drain_group(trow, g, hv, lv);
-#pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                        const int col = g * 8 + c;
-                        if (single)
-                            stg2[lane * kStgLd + col] = make_float2(hv[c], lv[c]);
-                        else
-                            stg[lane * kStgLd + col] += widen(hv[c]) + widen(lv[c]);
-                    }
+                for (int g = 0; g < kNT / 8; g += 2) {
+                    load_group(trow, g + 1, lb);
+                    park_group(la, g, single, stg, stg2, lane);
+                    tmem_wait_ld(lb);
+                    if (g + 2 < kNT / 8) load_group(trow, g + 2, la);
+                    park_group(lb, g + 1, single, stg, stg2, lane);
+                    tmem_wait_ld(la);
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty);
             }
             if (!ok) break;
-            // tensor memory is free: widen, scale and store row segments
+            // tensor memory is free: widen, scale and store row segments.
+            // Lane l owns column j = c0 + l; row exponents are loaded once
+            // (lane r holds row r's) and broadcast; eight rows are formed in
+            // registers before their stores, so the chains overlap.
             __syncwarp();
+            const int erl = row0 + lane < m ? er[row0 + lane] : 0;
+            bool bad = false;
 #pragma unroll 1
             for (int c0 = 0; c0 < kNT; c0 += 32) {
                 const int j = nt * kNT + c0 + lane;
-                if (j < N) {
-                    const int ej = em[j] - 14;
-#pragma unroll 4
-                    for (int r = 0; r < 32; r++) {
-                        const i64 row = row0 + r;
-                        if (row < m) {
-                            double v;
-                            if (single) {
-                                const float2 f = stg2[r * kStgLd + c0 + lane];
-                                v = widen(f.x) + widen(f.y);
-                            } else {
-                                v = stg[r * kStgLd + c0 + lane];
-                            }
-                            C[row * ldc + j] = (TC)scale2k(v, er[row] + ej);
+                const int ej = j < N ? em[j] - 14 : 0;
+#pragma unroll 1
+                for (int r0 = 0; r0 < 32; r0 += 8) {
+                    double v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int r = r0 + q;
+                        double x;
+                        if (single) {
+                            const float2 f = stg2[r * kStgLd + c0 + lane];
+                            x = widen(f.x) + widen(f.y);
+                        } else {
+                            x = stg[r * kStgLd + c0 + lane];
                         }
+                        v[q] = scale2k_fast(x, __shfl_sync(0xffffffffu, erl, r) + ej, bad);
+                    }
+                    if (j < N) {
+#pragma unroll
+                        for (int q = 0; q < 8; q++)
+                            if (row0 + r0 + q < m) C[(row0 + r0 + q) * ldc + j] = (TC)v[q];
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, bad)) {
+                // some result left the normal range: redo the tile's stores
+                // with the library scaling (never for data of sane range)
+                for (int c0 = 0; c0 < kNT; c0 += 32) {
+                    const int j = nt * kNT + c0 + lane;
+                    const int ej = j < N ? em[j] - 14 : 0;
+                    for (int r = 0; r < 32; r++) {
+                        double x;
+                        if (single) {
+                            const float2 f = stg2[r * kStgLd + c0 + lane];
+                            x = widen(f.x) + widen(f.y);
+                        } else {
+                            x = stg[r * kStgLd + c0 + lane];
+                        }
+                        const int k = __shfl_sync(0xffffffffu, erl, r) + ej;
+                        if (j < N && row0 + r < m) C[(row0 + r) * ldc + j] = (TC)scale2k_safe(x, k);
                     }
                 }
             }
