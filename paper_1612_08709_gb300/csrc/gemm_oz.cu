@@ -50,9 +50,7 @@ constexpr int kChunkStages = 14;  // 448 rows/k per FP32 chunk (every level exac
 constexpr uint32_t kATerm = 128 * kBK * 2;  // 8 KB: one digit of the 128-row operand
 constexpr uint32_t kBTerm = kNT * kBK * 2;  // 4 KB: one digit of the 64-row operand
 // The products stream 16-deep halves of the 32-deep blocks: a stage holds
-// the seven 4 KB A digits and the 14 KB stacked B digits of one half, and
-// five stages keep four halves in flight ahead of the MMAs.
-constexpr int kStages = 5;
+// the seven 4 KB A digits and the 14 KB stacked B digits of one half.
 constexpr uint32_t kStageBytes = kDig * (kATerm / 2) + kDig * (kBTerm / 2);  // 42 KB
 constexpr int kChunkUnits = 2 * kChunkStages;  // halves per FP32 chunk
 // The A*M product runs three stages and stages its 128 x 64 output tile in
@@ -64,6 +62,10 @@ constexpr int kChunkUnits = 2 * kChunkStages;  // halves per FP32 chunk
 constexpr int kStagesNN = 3;
 constexpr int kStgLd = kNT + 1;
 constexpr size_t kNNSmem = (size_t)kStagesNN * kStageBytes + 128 * kStgLd * sizeof(double);
+// The Gram-type product (oz_tn) uses the same three stages and staging tile
+// (its drain parks each chunk's double-FP32 values there).
+constexpr int kStagesTN = 3;
+constexpr size_t kTNSmem = (size_t)kStagesTN * kStageBytes + 128 * kStgLd * sizeof(double);
 
 // Exponent of the bit pattern (unbiased), and the 53-bit significand.
 __device__ __forceinline__ void dsplit(double v, int &ev, unsigned long long &mant, uint32_t &sign)
@@ -226,40 +228,6 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
                    "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
-}
-
-// Drain: add sum_L acc_L 2^-7L (the level sums in TMEM) to the FP64
-// running sums of this thread's row, 64 columns.
-__device__ __forceinline__ void drain_levels(uint32_t tmem_row, double (&acc)[kNT])
-{
-#pragma unroll
-    for (int g = 0; g < kNT / 8; g++) {
-        uint32_t lv[kLevels][8];
-#pragma unroll
-        for (int L = 0; L < kLevels; L++) tmem_ld8_nowait(tmem_row + (uint32_t)(L * kNT + g * 8), lv[L]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int L = 0; L < kLevels; L++)
-#pragma unroll
-            for (int c = 0; c < 8; c++) asm volatile("" : "+r"(lv[L][c]));
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            // smallest level first; 2^(-7L) is the level's exact weight
-            float s = __uint_as_float(lv[kLevels - 1][c]) *
-                      __uint_as_float((uint32_t)(127 - 7 * (kLevels - 1)) << 23);
-            float e = 0.f;
-#pragma unroll
-            for (int L = kLevels - 2; L >= 0; L--) {
-                float t, er;
-                const float w = __uint_as_float((uint32_t)(127 - 7 * L) << 23);
-                two_sum(__uint_as_float(lv[L][c]) * w, s, t, er);
-                s = t;
-                e += er;
-            }
-            acc[g * 8 + c] += widen(s);
-            acc[g * 8 + c] += widen(e);
-        }
-    }
 }
 
 // The drain of one 8-column group g: load_group issues the loads of the
@@ -445,7 +413,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                  i64 m, i64 rows_per_split, double *__restrict__ P, DevStatus *st)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages];
+    __shared__ __align__(8) uint64_t full_bar[kStagesTN], empty_bar[kStagesTN];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, done_bar;
     __shared__ uint32_t tmem_base_s;
 
@@ -470,7 +438,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int nchunks = (nunits + kChunkUnits - 1) / kChunkUnits;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < kStagesTN; s++) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -490,8 +458,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (lane == 0) {
             int last = -1;
             for (int u = 0; u < nunits; u++) {
-                const int s = u % kStages;
-                if (!mbar_wait(&empty_bar[s], ((u / kStages) & 1) ^ 1, err)) break;
+                const int s = u % kStagesTN;
+                if (!mbar_wait(&empty_bar[s], ((u / kStagesTN) & 1) ^ 1, err)) break;
                 uint8_t *stage = smem_raw + (size_t)s * kStageBytes;
                 mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
                 const int h = u & 1;
@@ -508,15 +476,21 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 }
                 last = u;
             }
-            if (last >= 0) mbar_wait_drain(&full_bar[last % kStages], (last / kStages) & 1);
+            if (last >= 0) mbar_wait_drain(&full_bar[last % kStagesTN], (last / kStagesTN) & 1);
         }
         __syncwarp();
     } else if (warp < 4) {
-        // ---------------- epilogue
+        // ---------------- epilogue: per chunk, drain the level sums into
+        // this thread's staging row as double-FP32 values, release tensor
+        // memory, then add the row into the FP64 running sums (overlapping
+        // the next chunk's MMAs)
         double acc[kNT];
 #pragma unroll
         for (int j = 0; j < kNT; j++) acc[j] = 0.0;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        double *stg = reinterpret_cast<double *>(smem_raw + (size_t)kStagesTN * kStageBytes) +
+                      warp * 32 * kStgLd;
+        float2 *stg2 = reinterpret_cast<float2 *>(stg);
         bool ok = true;
         for (int ch = 0; ch < nchunks; ch++) {
             if (!mbar_wait(&acc_full, ch & 1, err)) {
@@ -524,9 +498,26 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 break;
             }
             tc_fence_after();
-            drain_levels(trow, acc);
+            uint32_t la[kLevels][8], lb[kLevels][8];
+            load_group(trow, 0, la);
+            tmem_wait_ld(la);
+#pragma unroll 1
+            for (int g = 0; g < kNT / 8; g += 2) {
+                load_group(trow, g + 1, lb);
+                park_group(la, g, true, stg, stg2, lane);
+                tmem_wait_ld(lb);
+                if (g + 2 < kNT / 8) load_group(trow, g + 2, la);
+                park_group(lb, g + 1, true, stg, stg2, lane);
+                tmem_wait_ld(la);
+            }
             tc_fence_before();
             mbar_arrive(&acc_empty);
+#pragma unroll
+            for (int c = 0; c < kNT; c++) {
+                const float2 f = stg2[lane * kStgLd + c];
+                acc[c] += widen(f.x);
+                acc[c] += widen(f.y);
+            }
         }
         if (ok) {
             const int il = warp * 32 + lane;
@@ -554,8 +545,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 uint32_t started = 0;
                 const int u_end = (ch + 1) * kChunkUnits < nunits ? (ch + 1) * kChunkUnits : nunits;
                 for (; u < u_end; u++) {
-                    const int s = u % kStages;
-                    if (!mbar_wait(&full_bar[s], (u / kStages) & 1, err)) {
+                    const int s = u % kStagesTN;
+                    if (!mbar_wait(&full_bar[s], (u / kStagesTN) & 1, err)) {
                         ok = false;
                         break;
                     }
@@ -992,7 +983,7 @@ cudaError_t oz_tn_run(const uint8_t *aimg, const int *exa, int M, const uint8_t 
 {
     // whole 32-row blocks per split
     const i64 kbs = ((m + kBK - 1) / kBK + splits - 1) / splits;
-    const size_t smem = (size_t)kStages * kStageBytes;
+    const size_t smem = kTNSmem;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(oz_tn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
