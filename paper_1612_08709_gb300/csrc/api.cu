@@ -116,7 +116,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
     double *cs = ws.take<double>(n);
     int *perm = ws.take<int>(n);
-    double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
+    double *prm = ws.take<double>(jacobi_prm_doubles(n));
     double *B2 = ws.take<double>(nn);
     double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
     const int tsp = terms ? tc_gram_splits(m) : 0;
@@ -212,7 +212,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     // R = P Sigma V^T by one-sided Jacobi on R^T (R row-major = R^T
     // column-major): R^T P = X, Sigma = column norms, V = X Sigma^-1.
     CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 2, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
     CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
@@ -257,7 +257,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
     double *cs = ws.take<double>(n);
     int *perm = ws.take<int>(n);
-    double *prm = ws.take<double>(4 * (size_t)((n + 1) / 2) + 2);
+    double *prm = ws.take<double>(jacobi_prm_doubles(n));
     double *B2 = ws.take<double>(nn);
     double *Yt = ws.take<double>((size_t)m * n);
     const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
@@ -343,7 +343,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
     CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, st, 2, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
     CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));

@@ -150,9 +150,12 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 // one cooperative kernel with a bounded grid barrier.  X is nr x nc
 // column-major (column j at X + j*ldx), J (nc x nc, column-major) receives
 // the accumulated rotations: X_in J = X_out with orthogonal columns.
-// ctr must point to at least max_sweeps + 4 zeroed ints of device memory.
+// ctr must point to at least max_sweeps + 4 zeroed ints of device memory;
+// prm to jacobi_prm_doubles(nc) doubles of scratch.
+inline size_t jacobi_prm_doubles(i64 nc) { return 8 * (size_t)((nc + 1) / 2) + 8; }
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
-                          int max_sweeps, int *ctr, DevStatus *st, int which, cudaStream_t s);
+                          int max_sweeps, int *ctr, double *prm, DevStatus *st, int which,
+                          cudaStream_t s);
 
 // Eigendecomposition of the symmetric B (n x n row-major) by Gram-form
 // Jacobi, same pair schedule and barrier.  V (n x n, column-major)

@@ -89,11 +89,51 @@ __device__ bool grid_barrier(unsigned long long *count, int &epoch, int *err)
     return s_ok != 0;
 }
 
+// The same barrier in two halves, so that work no other CTA waits for can
+// run while the barrier completes: grid_arrive publishes this CTA's writes
+// (release) and counts it in; grid_wait returns once every CTA has arrived
+// (acquire), or false when the call must be abandoned.
+__device__ __forceinline__ void grid_arrive(unsigned long long *count, int &epoch)
+{
+    __syncthreads();
+    epoch++;
+    if (threadIdx.x == 0) red_release_add64(count, 1ull);
+}
+
+__device__ bool grid_wait(unsigned long long *count, int epoch, int *err)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+        int spins = 0;
+        unsigned long long t0 = 0;
+        while (ld_acquire64(count) < target) {
+            if (++spins < 256) continue;
+            if (t0 == 0) t0 = global_ns();
+            if (ld_volatile(err) != 0) {
+                ok = 0;
+                break;
+            }
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+                atomicCAS(err, 0, TSSVD_ETIMEOUT);
+                ok = 0;
+                break;
+            }
+            spins = 200;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 struct JacobiArgs {
     double *X;
     i64 ldx;
     double *J;
     i64 ldj;
+    double4 *prm;  // [2][npairs] published (c, s, 0, rotate) of the last two rounds
     int nr, nc, npad;
     int max_sweeps;
     double tol;
@@ -154,10 +194,15 @@ __device__ __forceinline__ void st4cg(double4 *p, double4 v)
 
 __device__ __forceinline__ void circle_pair(int pr, int t, int npad, int &P, int &Q)
 {
+    // positions a - 1 + t and b - 1 + t stay below 2 * rounds, so one
+    // conditional subtraction reduces them (no integer division)
     const int rounds = npad - 1;
     const int a = pr, b = npad - 1 - pr;
-    P = (a == 0) ? 0 : 1 + (a - 1 + t) % rounds;
-    Q = (b == 0) ? 0 : 1 + (b - 1 + t) % rounds;
+    int x = a - 1 + t, y = b - 1 + t;
+    if (x >= rounds) x -= rounds;
+    if (y >= rounds) y -= rounds;
+    P = (a == 0) ? 0 : 1 + x;
+    Q = (b == 0) ? 0 : 1 + y;
     if (P > Q) {
         int tmp = P;
         P = Q;
@@ -250,18 +295,50 @@ __device__ __forceinline__ double4 jac_rotation(double a, double b, double g, do
     return make_double4(c, c * t, t, 1.0);
 }
 
+// Rows of an accumulated rotation matrix held in shared memory (rows x nc,
+// row-major; the CTA's own rows) take all rotations of round t: columns
+// K and K' of pair k turn by (c, s) = (prm[k].x, prm[k].y).
+__device__ __forceinline__ void rotate_rows_s(double *R, int rows, int nc, const double4 *prm,
+                                              int npad, int t)
+{
+    for (int k = threadIdx.x; k < npad / 2; k += blockDim.x) {
+        const double4 o = prm[k];
+        if (o.w == 0.0) continue;
+        int K, K2;
+        circle_pair(k, t, npad, K, K2);
+        for (int li = 0; li < rows; li++) {
+            const double u = R[li * nc + K], v = R[li * nc + K2];
+            R[li * nc + K] = o.x * u - o.y * v;
+            R[li * nc + K2] = o.y * u + o.x * v;
+        }
+    }
+}
+
 // One round per grid barrier: the CTA of pair (P,Q) reduces the three inner
 // products of columns P and Q of X, and rotates those columns of X and J.
 // CH > 0: nr, nc <= CH * NT and each thread keeps its CH entries of the
 // four columns in registers (one read per round); CH = 0: no cache.  FP64
 // issue is scarce (two lanes per clock per SM), so CH is sized to the
 // problem rather than padded.
-template <int NT, int CH>
+template <int NT, int CH, bool JS>
 __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
 {
     constexpr int C = CH > 0 ? CH : 1;
     __shared__ double red[3][NT / 32];
     __shared__ double rot_s[3];
+    // JS: this CTA's rows of J (row i for i = blockIdx.x mod gridDim.x) live
+    // in shared memory after the round's rotations; the rotations of round
+    // t reach them in round t + 1 between arrival and wait.
+    extern __shared__ double js_raw[];
+    double4 *prev_s = reinterpret_cast<double4 *>(js_raw);
+    double *J_s = js_raw + 4 * (size_t)(p.npad / 2);
+    const int jrows = JS ? (p.nc - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (JS) {
+        for (int e = threadIdx.x; e < jrows * p.nc; e += NT) {
+            const int li = e / p.nc, c = e % p.nc;
+            J_s[e] = (blockIdx.x + li * gridDim.x == c) ? 1.0 : 0.0;
+        }
+    }
     const int npairs = p.npad / 2;
     const int rounds = p.npad - 1;
     const double tol = p.tol;
@@ -270,12 +347,24 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
     int done = -1;
     unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
     int epoch = 0;
+    int gr = 0;  // rounds completed
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
-        for (int t = 0; t < rounds; t++) {
+        for (int t = 0; t < rounds; t++, gr++) {
+            double4 *pub = p.prm + (size_t)(gr & 1) * npairs;
+            // the previous round's rotations (for J's rows), loaded after
+            // this round's columns and parked in shared memory before the
+            // arrival, so that no wait on them sits in the critical path
+            const double4 *prev_g = p.prm + (size_t)((gr - 1) & 1) * npairs;
+            const bool want_prev = JS && gr > 0 && (int)threadIdx.x < npairs;
+            double4 pv = make_double4(1.0, 0.0, 0.0, 0.0);
+            bool pv_loaded = false;
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
                 int P, Q;
                 circle_pair(pr, t, p.npad, P, Q);
-                if (Q >= p.nc) continue;  // the padding column of an odd nc
+                if (Q >= p.nc) {  // the padding column of an odd nc
+                    if (JS && threadIdx.x == 0) st4cg(pub + pr, make_double4(1.0, 0.0, 0.0, 0.0));
+                    continue;
+                }
                 double *xp = p.X + (i64)P * p.ldx, *xq = p.X + (i64)Q * p.ldx;
                 double *jp = p.J + (i64)P * p.ldj, *jq = p.J + (i64)Q * p.ldj;
                 double u[C], v[C], ju[C], jv[C];
@@ -286,8 +375,12 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         const int i = threadIdx.x + j * NT;
                         u[j] = i < p.nr ? __ldcg(xp + i) : 0.0;
                         v[j] = i < p.nr ? __ldcg(xq + i) : 0.0;
-                        ju[j] = i < p.nc ? __ldcg(jp + i) : 0.0;
-                        jv[j] = i < p.nc ? __ldcg(jq + i) : 0.0;
+                        ju[j] = (!JS && i < p.nc) ? __ldcg(jp + i) : 0.0;
+                        jv[j] = (!JS && i < p.nc) ? __ldcg(jq + i) : 0.0;
+                    }
+                    if (want_prev && !pv_loaded) {
+                        pv = ld4cg(prev_g + threadIdx.x);
+                        pv_loaded = true;
                     }
 #pragma unroll
                     for (int j = 0; j < C; j++) {
@@ -314,6 +407,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                 const double c = rot_s[0], sn = rot_s[1];
                 const bool do_rot = rot_s[2] != 0.0;
                 __syncthreads();  // rot_s is rewritten by the next pair
+                if (JS && threadIdx.x == 0)
+                    st4cg(pub + pr, make_double4(c, sn, 0.0, do_rot ? 1.0 : 0.0));
                 if (!do_rot) continue;
                 if (threadIdx.x == 0) local_rot++;
                 if (CH > 0) {
@@ -324,7 +419,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                             __stcg(xp + i, c * u[j] - sn * v[j]);
                             __stcg(xq + i, sn * u[j] + c * v[j]);
                         }
-                        if (i < p.nc) {
+                        if (!JS && i < p.nc) {
                             __stcg(jp + i, c * ju[j] - sn * jv[j]);
                             __stcg(jq + i, sn * ju[j] + c * jv[j]);
                         }
@@ -335,22 +430,42 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         __stcg(xp + i, c * x - sn * y);
                         __stcg(xq + i, sn * x + c * y);
                     }
-                    for (int i = threadIdx.x; i < p.nc; i += NT) {
-                        const double x = __ldcg(jp + i), y = __ldcg(jq + i);
-                        __stcg(jp + i, c * x - sn * y);
-                        __stcg(jq + i, sn * x + c * y);
-                    }
+                    if (!JS)
+                        for (int i = threadIdx.x; i < p.nc; i += NT) {
+                            const double x = __ldcg(jp + i), y = __ldcg(jq + i);
+                            __stcg(jp + i, c * x - sn * y);
+                            __stcg(jq + i, sn * x + c * y);
+                        }
                 }
             }
             if (t == rounds - 1 && threadIdx.x == 0 && local_rot != 0) {
                 atomicAdd(p.rot + sweep, local_rot);
                 local_rot = 0;
             }
-            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
+            if (want_prev) prev_s[threadIdx.x] = pv_loaded ? pv : ld4cg(prev_g + threadIdx.x);
+            if (JS && gr > 0)
+                for (int k = threadIdx.x + NT; k < npairs; k += NT) prev_s[k] = ld4cg(prev_g + k);
+            grid_arrive(bar_count, epoch);
+            if (JS && gr > 0) rotate_rows_s(J_s, jrows, p.nc, prev_s, p.npad, (t + rounds - 1) % rounds);
+            if (!grid_wait(bar_count, epoch, &p.st->err)) return;
         }
         if (ld_acquire(p.rot + sweep) == 0) {
             done = sweep + 1;
             break;
+        }
+    }
+    if (JS) {
+        // the last round's rotations, then J's rows to global memory
+        if (gr > 0) {
+            for (int k = threadIdx.x; k < npairs; k += NT)
+                prev_s[k] = ld4cg(p.prm + (size_t)((gr - 1) & 1) * npairs + k);
+            __syncthreads();
+            rotate_rows_s(J_s, jrows, p.nc, prev_s, p.npad, rounds - 1);
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < jrows * p.nc; e += NT) {
+            const int li = e / p.nc, c = e % p.nc;
+            p.J[(i64)c * p.ldj + blockIdx.x + li * gridDim.x] = J_s[e];
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) p.st->sweeps[p.which] = done;
@@ -391,11 +506,25 @@ struct EigArgs {
 // CTA may start round t + 1 while others still read Bc.  Every CTA derives
 // all n/2 rotations of the round from Bc's 2 x 2 diagonal blocks (the same
 // arithmetic on the same values, so all CTAs agree bit for bit) into shared
-// memory; the CTA of pair (P,Q) then writes rows P and Q of J^T B J into Bn
-// and rotates columns P and Q of V in place.
-constexpr int kEigSmemPairs = 1024;
+// memory; the CTA of pair (P,Q) then writes rows P and Q of J^T B J into Bn.
+// V's rotations are applied by rows (see VS) or, for large n, to columns P
+// and Q by the pair's CTA.
+// Block {pr, pr + d mod npairs} of the symmetric B is formed by pair pr
+// when 1 <= d <= npairs / 2, except that for an even count the opposite
+// pair (d = npairs / 2) is taken by the smaller index only: every unordered
+// pair of pairs exactly once.
+__device__ __forceinline__ bool block_mine(int pr, int d, int npairs)
+{
+    if (d < 1 || d > npairs / 2) return false;
+    if (2 * d == npairs) return pr < d;
+    return true;
+}
 
-template <int NT>
+constexpr int kEigSmemPairs = 1024;
+// Largest shared-memory footprint for rotation rows held by a CTA.
+constexpr size_t kRowsSmemMax = 96 * 1024;
+
+template <int NT, bool VS>
 __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
 {
     extern __shared__ double4 prm_s[];
@@ -403,6 +532,17 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
     const int rounds = p.npad - 1;
     const int n = p.n;
     const i64 ldb = p.ldb, ldv = p.ldv;
+    // VS: this CTA's rows of V (row i for i = blockIdx.x mod gridDim.x) live
+    // in shared memory and take each round's rotations while the barrier
+    // completes; they are written out at the end.
+    double *V_s = reinterpret_cast<double *>(prm_s + npairs);
+    const int vrows = VS ? (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (VS) {
+        for (int e = threadIdx.x; e < vrows * n; e += NT) {
+            const int li = e / n, c = e % n;
+            V_s[e] = (blockIdx.x + li * gridDim.x == c) ? 1.0 : 0.0;
+        }
+    }
     int local_rot = 0;
     int done = -1;
     unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
@@ -413,8 +553,47 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
     const float log2tol = log2f((float)p.tol);
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
         for (int t = 0; t < rounds; t++) {
+            // ---- issue the loads first: the 2 x 2 block of pair k = tid
+            // (for the rotations) and the first off-diagonal block this
+            // thread updates, so both wait on memory together
+            int K0 = 0, K20 = 0;
+            double a0 = 0.0, b0 = 0.0, g0 = 0.0;
+            if (tid < npairs) {
+                circle_pair(tid, t, p.npad, K0, K20);
+                if (K20 < n) {
+                    a0 = __ldcg(Bc + (i64)K0 * ldb + K0);
+                    b0 = __ldcg(Bc + (i64)K20 * ldb + K20);
+                    g0 = __ldcg(Bc + (i64)K0 * ldb + K20);
+                }
+            }
+            const int pr0 = blockIdx.x;
+            int P0, Q0;
+            circle_pair(pr0, t, p.npad, P0, Q0);
+            int k0 = pr0 + 1 + tid;
+            if (k0 >= npairs) k0 -= npairs;
+            const bool pf = block_mine(pr0, 1 + tid, npairs);
+            int KB0 = 0, KB20 = 0;
+            double x0 = 0.0, y0 = 0.0, z0 = 0.0, w0 = 0.0;
+            if (pf) {
+                circle_pair(k0, t, p.npad, KB0, KB20);
+                const double *cP = Bc + (i64)P0 * ldb, *cQ = Bc + (i64)Q0 * ldb;
+                x0 = __ldcg(cP + KB0);
+                if (KB20 < n) y0 = __ldcg(cP + KB20);
+                if (Q0 < n) {
+                    z0 = __ldcg(cQ + KB0);
+                    if (KB20 < n) w0 = __ldcg(cQ + KB20);
+                }
+            }
             // ---- all rotations of the round
-            for (int k = tid; k < npairs; k += NT) {
+            if (tid < npairs) {
+                double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
+                if (K20 < n) {
+                    r = jac_rotation(a0, b0, g0, p.tol, log2tol);
+                    if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                }
+                prm_s[tid] = r;
+            }
+            for (int k = tid + NT; k < npairs; k += NT) {
                 int K, K2;
                 circle_pair(k, t, p.npad, K, K2);
                 double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
@@ -429,13 +608,14 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             }
             __syncthreads();
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+                const bool first = pr == pr0;
                 int P, Q;
                 circle_pair(pr, t, p.npad, P, Q);
                 const double4 me = prm_s[pr];
                 const bool hasQ = Q < n;
                 const double c = me.x, s = me.y;
-                // ---- columns P and Q of V J
-                if (hasQ && me.w != 0.0) {
+                // ---- columns P and Q of V J (when V is not held by rows)
+                if (!VS && hasQ && me.w != 0.0) {
                     double *vp = p.V + (i64)P * ldv, *vq = p.V + (i64)Q * ldv;
                     for (int i = tid; i < n; i += NT) {
                         const double u = __ldcg(vp + i), v = __ldcg(vq + i);
@@ -443,53 +623,90 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                         __stcg(vq + i, s * u + c * v);
                     }
                 }
-                // ---- rows P and Q of J^T B J
                 const double *cP = Bc + (i64)P * ldb;
                 const double *cQ = hasQ ? Bc + (i64)Q * ldb : nullptr;
                 double *nP = Bn + (i64)P * ldb;
                 double *nQ = hasQ ? Bn + (i64)Q * ldb : nullptr;
-                for (int k = tid; k < npairs; k += NT) {
-                    int K, K2;
-                    circle_pair(k, t, p.npad, K, K2);
-                    const bool hasK2 = K2 < n;
-                    if (k == pr) {
-                        // the pair's own 2 x 2 block G^T [a g; g b] G
-                        const double a = __ldcg(cP + P);
+                // ---- the pair's own 2 x 2 block G^T [a g; g b] G, by the
+                // thread that loaded it as rotation input (pair index mod NT)
+                if (tid == pr % NT) {
+                    double a, b = 0.0, g = 0.0;
+                    if (first && pr < NT && K20 < n) {
+                        a = a0;
+                        b = b0;
+                        g = g0;
+                    } else {
+                        a = __ldcg(cP + P);
                         if (hasQ) {
-                            const double b = __ldcg(cQ + Q), g = __ldcg(cP + Q);
-                            if (me.w != 0.0) {
-                                const double cc = c * c, ss = s * s, cs = c * s;
-                                const double a1 = fma(cc, a, fma(-2.0 * cs, g, ss * b));
-                                const double b1 = fma(ss, a, fma(2.0 * cs, g, cc * b));
-                                const double g1 = fma(cs, a - b, (cc - ss) * g);
-                                __stcg(nP + P, a1);
-                                __stcg(nQ + Q, b1);
-                                __stcg(nP + Q, g1);
-                                __stcg(nQ + P, g1);
-                            } else {
-                                __stcg(nP + P, a);
-                                __stcg(nQ + Q, b);
-                                __stcg(nP + Q, g);
-                                __stcg(nQ + P, __ldcg(cQ + P));
-                            }
+                            b = __ldcg(cQ + Q);
+                            g = __ldcg(cP + Q);
+                        }
+                    }
+                    if (hasQ) {
+                        if (me.w != 0.0) {
+                            const double cc = c * c, ss = s * s, cs = c * s;
+                            const double a1 = fma(cc, a, fma(-2.0 * cs, g, ss * b));
+                            const double b1 = fma(ss, a, fma(2.0 * cs, g, cc * b));
+                            const double g1 = fma(cs, a - b, (cc - ss) * g);
+                            __stcg(nP + P, a1);
+                            __stcg(nQ + Q, b1);
+                            __stcg(nP + Q, g1);
+                            __stcg(nQ + P, g1);
                         } else {
                             __stcg(nP + P, a);
+                            __stcg(nQ + Q, b);
+                            __stcg(nP + Q, g);
+                            __stcg(nQ + P, g);
                         }
-                        continue;
+                    } else {
+                        __stcg(nP + P, a);
                     }
-                    const double x = __ldcg(cP + K), y = hasK2 ? __ldcg(cP + K2) : 0.0;
-                    const double z = hasQ ? __ldcg(cQ + K) : 0.0;
-                    const double w = (hasQ && hasK2) ? __ldcg(cQ + K2) : 0.0;
+                }
+                // ---- off-diagonal blocks of rows P, Q: B is symmetric, so
+                // each block {pr, k} is formed once, by the CTA for which k
+                // lies in the next half of the pair circle, and written
+                // together with its transpose (rows K, K' of the new B)
+                for (int d = 1 + tid; d <= npairs / 2; d += NT) {
+                    if (!block_mine(pr, d, npairs)) continue;
+                    int k = pr + d;
+                    if (k >= npairs) k -= npairs;
+                    int K, K2;
+                    double x, y, z, w;
+                    if (first && d == 1 + tid) {
+                        K = KB0;
+                        K2 = KB20;
+                        x = x0;
+                        y = y0;
+                        z = z0;
+                        w = w0;
+                    } else {
+                        circle_pair(k, t, p.npad, K, K2);
+                        x = __ldcg(cP + K);
+                        y = K2 < n ? __ldcg(cP + K2) : 0.0;
+                        z = hasQ ? __ldcg(cQ + K) : 0.0;
+                        w = (hasQ && K2 < n) ? __ldcg(cQ + K2) : 0.0;
+                    }
+                    const bool hasK2 = K2 < n;
                     const double4 o = prm_s[k];
                     // rows (own rotation), then columns (the other pair's)
                     const double x1 = c * x - s * z, y1 = c * y - s * w;
                     const double z1 = s * x + c * z, w1 = s * y + c * w;
                     const double ck = o.x, sk = o.y;
-                    __stcg(nP + K, ck * x1 - sk * y1);
-                    if (hasK2) __stcg(nP + K2, sk * x1 + ck * y1);
+                    const double pk = ck * x1 - sk * y1, pk2 = sk * x1 + ck * y1;
+                    __stcg(nP + K, pk);
+                    __stcg(Bn + (i64)K * ldb + P, pk);
+                    if (hasK2) {
+                        __stcg(nP + K2, pk2);
+                        __stcg(Bn + (i64)K2 * ldb + P, pk2);
+                    }
                     if (hasQ) {
-                        __stcg(nQ + K, ck * z1 - sk * w1);
-                        if (hasK2) __stcg(nQ + K2, sk * z1 + ck * w1);
+                        const double qk = ck * z1 - sk * w1, qk2 = sk * z1 + ck * w1;
+                        __stcg(nQ + K, qk);
+                        __stcg(Bn + (i64)K * ldb + Q, qk);
+                        if (hasK2) {
+                            __stcg(nQ + K2, qk2);
+                            __stcg(Bn + (i64)K2 * ldb + Q, qk2);
+                        }
                     }
                 }
             }
@@ -497,7 +714,9 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                 atomicAdd(p.rot + sweep, local_rot);
                 local_rot = 0;
             }
-            if (!grid_barrier(bar_count, epoch, &p.st->err)) return;
+            grid_arrive(bar_count, epoch);
+            if (VS) rotate_rows_s(V_s, vrows, n, prm_s, p.npad, t);
+            if (!grid_wait(bar_count, epoch, &p.st->err)) return;
             double *tmp = Bn;
             Bn = const_cast<double *>(Bc);
             Bc = tmp;
@@ -505,6 +724,12 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
         if (ld_acquire(p.rot + sweep) == 0) {
             done = sweep + 1;
             break;
+        }
+    }
+    if (VS) {
+        for (int e = tid; e < vrows * n; e += NT) {
+            const int li = e / n, c = e % n;
+            p.V[(i64)c * ldv + blockIdx.x + li * gridDim.x] = V_s[e];
         }
     }
     if (blockIdx.x == 0) {
@@ -693,7 +918,7 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
 }  // namespace
 
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc, int max_sweeps,
-                          int *ctr, DevStatus *st, int which, cudaStream_t s)
+                          int *ctr, double *prm, DevStatus *st, int which, cudaStream_t s)
 {
     cudaError_t e;
     {
@@ -718,6 +943,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.ldx = ldx;
     a.J = J;
     a.ldj = ldj;
+    a.prm = (double4 *)prm;
     a.nr = nr;
     a.nc = nc;
     a.npad = nc + (nc & 1);
@@ -728,22 +954,42 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.which = which;
 
     constexpr int NT = 128;
+    const int npairs = a.npad / 2;
+    // J's rows in shared memory when they fit (at most one CTA per SM is
+    // assumed for the row count, an upper bound)
+    const int b0 = npairs < num_sms() ? npairs : num_sms();
+    const size_t js_bytes = sizeof(double4) * (size_t)npairs +
+                            sizeof(double) * (size_t)((nc + b0 - 1) / b0) * nc;
+    const bool js = js_bytes <= kRowsSmemMax;
     const int mx = nr > nc ? nr : nc;
-    const void *kern = mx <= NT       ? (const void *)jacobi_kernel<NT, 1>
-                       : mx <= 2 * NT ? (const void *)jacobi_kernel<NT, 2>
-                       : mx <= 4 * NT ? (const void *)jacobi_kernel<NT, 4>
-                       : mx <= 8 * NT ? (const void *)jacobi_kernel<NT, 8>
-                                      : (const void *)jacobi_kernel<NT, 0>;
+    const int ch = mx <= NT ? 1 : mx <= 2 * NT ? 2 : mx <= 4 * NT ? 4 : mx <= 8 * NT ? 8 : 0;
+    const void *kern;
+    switch (ch * 2 + (js ? 1 : 0)) {
+        case 2: kern = (const void *)jacobi_kernel<NT, 1, false>; break;
+        case 3: kern = (const void *)jacobi_kernel<NT, 1, true>; break;
+        case 4: kern = (const void *)jacobi_kernel<NT, 2, false>; break;
+        case 5: kern = (const void *)jacobi_kernel<NT, 2, true>; break;
+        case 8: kern = (const void *)jacobi_kernel<NT, 4, false>; break;
+        case 9: kern = (const void *)jacobi_kernel<NT, 4, true>; break;
+        case 16: kern = (const void *)jacobi_kernel<NT, 8, false>; break;
+        case 17: kern = (const void *)jacobi_kernel<NT, 8, true>; break;
+        case 1: kern = (const void *)jacobi_kernel<NT, 0, true>; break;
+        default: kern = (const void *)jacobi_kernel<NT, 0, false>; break;
+    }
+    const size_t smem = js ? js_bytes : 0;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess)
         return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    int npairs = a.npad / 2;
     int blocks = num_sms() * per_sm;
     if (blocks > npairs) blocks = npairs;
     void *args[] = {&a};
     ProfScope ps_("jacobi_svd", s);
-    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, 0, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, smem, s);
 }
 
 cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv, double *lam,
@@ -784,9 +1030,19 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         a.st = st;
         a.which = which;
         constexpr int NT = 128;
-        const void *kern = single ? (const void *)jacobi_eig1_kernel<NT>
-                                  : (const void *)jacobi_eig_kernel<NT>;
-        const size_t smem = single ? sizeof(double4) * (size_t)(npad / 2) : 0;
+        const int npairs0 = npad / 2;
+        const int b0 = npairs0 < num_sms() ? npairs0 : num_sms();
+        const size_t vs_bytes = sizeof(double4) * (size_t)npairs0 +
+                                sizeof(double) * (size_t)((n + b0 - 1) / b0) * n;
+        const bool vs = single && vs_bytes <= kRowsSmemMax;
+        const void *kern = !single ? (const void *)jacobi_eig_kernel<NT>
+                           : vs    ? (const void *)jacobi_eig1_kernel<NT, true>
+                                   : (const void *)jacobi_eig1_kernel<NT, false>;
+        const size_t smem = !single ? 0 : vs ? vs_bytes : sizeof(double4) * (size_t)npairs0;
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
         int per_sm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) !=
             cudaSuccess)
