@@ -29,30 +29,60 @@ __device__ __forceinline__ double ld_as_double(const T *p)
 }
 
 // ------------------------------------------------------------- colmax
+// Column maxima of |A| as bit patterns: non-negative doubles order like
+// their bit patterns, so the maxima are integer maxima of the patterns with
+// the sign cleared (no FP64 compare, which is slow on this part).  Each
+// warp covers 32 columns; rows are strided over the 8 warps, four loads in
+// flight per thread.
+__device__ __forceinline__ unsigned long long abs_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// |v| as the bit pattern of the double of the same value, by integer
+// operations (FP32 subnormals go through the conversion).
+__device__ __forceinline__ unsigned long long abs_bits(float v)
+{
+    const uint32_t b = __float_as_uint(v) & 0x7FFFFFFFu;
+    const uint32_t ef = b >> 23;
+    if (ef == 0) return b == 0 ? 0ull : abs_bits((double)__uint_as_float(b));
+    if (ef == 0xFF) return 0x7FF0000000000000ull | ((unsigned long long)(b & 0x7FFFFF) << 29);
+    return ((unsigned long long)(ef + (1023 - 127)) << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) colmax_kernel(const T *__restrict__ A, i64 m, i64 n,
                                                      i64 lda, i64 rows_per_chunk,
                                                      unsigned long long *bits)
 {
-    __shared__ double red[8][33];
+    __shared__ unsigned long long red[8][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const i64 c = (i64)blockIdx.x * 32 + lane;
     const i64 r0 = (i64)blockIdx.y * rows_per_chunk;
     const i64 r1 = r0 + rows_per_chunk < m ? r0 + rows_per_chunk : m;
-    double mx = 0.0;
+    unsigned long long mx = 0;
     if (c < n) {
-        for (i64 r = r0 + warp; r < r1; r += 8) {
-            double v = fabs(ld_as_double(A + r * lda + c));
-            mx = v > mx ? v : mx;
+        i64 r = r0 + warp;
+        for (; r + 24 < r1; r += 32) {
+            const unsigned long long a = abs_bits(__ldg(A + r * lda + c));
+            const unsigned long long b = abs_bits(__ldg(A + (r + 8) * lda + c));
+            const unsigned long long d = abs_bits(__ldg(A + (r + 16) * lda + c));
+            const unsigned long long f = abs_bits(__ldg(A + (r + 24) * lda + c));
+            const unsigned long long ab = a > b ? a : b, df = d > f ? d : f;
+            const unsigned long long x = ab > df ? ab : df;
+            mx = x > mx ? x : mx;
+        }
+        for (; r < r1; r += 8) {
+            const unsigned long long a = abs_bits(__ldg(A + r * lda + c));
+            mx = a > mx ? a : mx;
         }
     }
     red[warp][lane] = mx;
     __syncthreads();
     if (warp == 0 && c < n) {
-        double v = red[0][lane];
+        unsigned long long v = red[0][lane];
         for (int w = 1; w < 8; w++) v = red[w][lane] > v ? red[w][lane] : v;
-        // Non-negative doubles order like their bit patterns.
-        atomicMax(bits + c, (unsigned long long)__double_as_longlong(v));
+        atomicMax(bits + c, v);
     }
 }
 

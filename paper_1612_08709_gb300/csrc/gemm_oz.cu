@@ -97,21 +97,19 @@ __device__ __forceinline__ void fsplit(float v, int &ev, unsigned long long &man
     mant = (unsigned long long)((b & 0x7FFFFFu) | (1u << 23));
 }
 
-// bfloat16 bit pattern of the integer d with |d| <= 255: d + 1.5 * 2^23 is
-// formed exactly in the FP32 bit pattern, the bias is subtracted in FP32
-// (exact), and an integer of at most 8 significant bits keeps all of them
-// in bfloat16's upper half.
-__device__ __forceinline__ uint32_t bf16_of_int(int d)
-{
-    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
-}
-
 // Seven balanced base-128 digits of a value |v| = mant 2^(q) (q = its
 // exponent minus the significand bits), prescaled by 2^p, relative to 2^e:
-// F = round(|v| 2^(p - e) 2^49) is recoded from the least significant end
-// into digits in [-64, 63] (the leading digit takes the carry, <= 129), so
-// the dropped digit pairs and the rounding of F carry no sign bias.
+// F = round(|v| 2^(p - e) 2^49) is written as sum_s d_s 2^(7(6-s)) with the
+// six low digits in [-64, 63] (the leading digit takes the carry, <= 129),
+// so the dropped digit pairs and the rounding of F carry no sign bias.
+// The recoding is one addition: with B = 64 (1 + 2^7 + ... + 2^35),
+// F + B = sum (d_s + 64) 2^(7(6-s)) + d_0 2^42, so each low digit is a
+// 7-bit field of F + B minus 64.  Each digit then becomes a bfloat16 bit
+// pattern: d + 1.5 * 2^23 is formed exactly in the FP32 bit pattern, the
+// bias is subtracted in FP32 (exact), and an integer of at most 8
+// significant bits keeps all of them in bfloat16's upper half; the value's
+// sign is the bfloat16 sign bit (a zero digit of a negative value becomes
+// -0, which multiplies like 0).
 __device__ __forceinline__ void digits_from(unsigned long long mant, int q, uint32_t vsign, int e,
                                            int p, uint32_t (&out)[kDig])
 {
@@ -123,26 +121,15 @@ __device__ __forceinline__ void digits_from(unsigned long long mant, int q, uint
         else if (sh > -64)
             F = (mant + (1ull << (-sh - 1))) >> (-sh);
     }
-    // recode from the least significant end in 32-bit halves: digits 6..3
-    // from the low 28 bits (whose final carry moves up), 2..0 from the rest
-    uint32_t lo = (uint32_t)(F & 0xFFFFFFFull), hi = (uint32_t)(F >> 28);
-    int dg[kDig];
+    const unsigned long long G = F + 0x20408102040ull;
+    const uint32_t sgn = vsign << 15;
 #pragma unroll
-    for (int s = kDig - 1; s >= 3; s--) {
-        const uint32_t r = lo & 127u, c = r >> 6;
-        dg[s] = (int)r - (int)(c << 7);
-        lo = (lo >> 7) + c;
+    for (int s = 1; s < kDig; s++) {
+        const int d = (int)((G >> (7 * (kDig - 1 - s))) & 127u) - 64;
+        out[s] = (__float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16) ^ sgn;
     }
-    hi += lo;
-#pragma unroll
-    for (int s = 2; s >= 1; s--) {
-        const uint32_t r = hi & 127u, c = r >> 6;
-        dg[s] = (int)r - (int)(c << 7);
-        hi = (hi >> 7) + c;
-    }
-    dg[0] = (int)(hi & 0xFFu);
-#pragma unroll
-    for (int s = 0; s < kDig; s++) out[s] = bf16_of_int(vsign ? -dg[s] : dg[s]);
+    const int d0 = (int)((G >> 42) & 0xFFu);
+    out[0] = (__float_as_uint(__int_as_float(0x4B400000 + d0) - 12582912.0f) >> 16) ^ sgn;
 }
 
 __device__ __forceinline__ void digits7(double v, int e, int p, uint32_t (&out)[kDig])
