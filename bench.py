@@ -336,7 +336,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest total event time in the
     # timed region): algorithmic flops or bytes per launch / mean duration
-    roof = roofline(kernels, m, n, ms, args, A.element_size())
+    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rows = min(args.cpu_rows, m)
@@ -348,13 +348,15 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.mode == "fp64" else args.mode + "+f64", "data": "synthetic",
+           "dtype": {"fp64": "f64", "fp64_tc": "bf16 digits+fp32+f64"}.get(args.mode, "bf16+fp32+f64"),
+           "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "passes": 2, "scale": 1,
                       "mode": args.mode, "drop_tol": 0.0,
                       "sigma": "geometric 1..%g" % w["lo"],
                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 8 / 1e9),
                       "parallelism": "replicas" if world > 1 else "single"},
-           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+           "roofline": roof, "roofline_kernels": roof_all, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(launches),
            "fp64_path": fp64_path,
            "clocks": clk,
            "accuracy": {"sigma_err_normwise": sig_err, "orth_U": orth_u, "orth_V": orth_v,
@@ -388,48 +390,76 @@ def bf16_peak(sustained=True):
         return (1700.0 if sustained else 1900.0), "fallback"
 
 
-def roofline(kernels, m, n, ms, args, esize):
-    """Roofline entry of the dominant kernel.
+def kernel_models(m, n, esize, sweeps):
+    """Algorithmic work per launch of each kernel of the two-pass TS-SVD.
 
-    FP64 DFMA kernels are bound by the FP64 pipe ("alu"): algorithmic flops
-    2mn^2 (tall A*M) or mn(n+1) (Gram).  The tensor-core kernels are bound
-    by HBM at these shapes: algorithmic bytes = the input read once (and
-    the FP64 output written once for A*M).
+    Returns {kernel: (bound, amount, unit)}: FP64 flops for the FP64-pipe
+    kernels ("alu"), bf16 digit-product flops for the tensor-core digit
+    products ("tensor"), bytes for the streaming kernels ("hbm").
+      nn_tall   A*M, m x n by n x n:          2 m n^2 flops
+      tn_gram   Gram of m x n (symmetric):     m n (n + 1) flops
+      jacobi_eig  Gram-form Jacobi, per round the symmetric update of B
+                  (24 flops per 2 x 2 block, n^2 / 8 blocks) and of V (6n
+                  per rotation, n / 2 rotations): 6 n^2 per round, n - 1
+                  rounds per sweep, the step's mean sweep count
+      jacobi_svd  one-sided Jacobi: per pair 3n FMAs (dots) and 2n outputs
+                  of X and of J at 3 flops: 18n, n / 2 pairs: 9 n^2 per round
+      oz_nn, oz_gram  28 bf16 digit-pair products per FP64-accurate product
+      oz_*_image  read the tall operand once, write 7 bf16 digits per entry
+      colmax, oz_rowexp  read the tall operand once; colsumsq reads m n FP64
     """
-    if not kernels:
-        return None
-    name, (cnt, tot_ms) = max(kernels.items(), key=lambda kv: kv[1][1])
+    rounds = n - 1 + (n & 1)
+    mdl = {"nn_tall": ("alu", 2.0 * m * n * n), "tn_gram": ("alu", float(m) * n * (n + 1)),
+           "oz_nn": ("tensor", 28 * 2.0 * m * n * n), "oz_gram": ("tensor", 28.0 * m * n * (n + 1)),
+           "tc_gram": ("hbm", float(esize) * m * n), "tc_nn": ("hbm", float(esize) * m * n + 8.0 * m * n),
+           "oz_gram_image": ("hbm", (esize + 14.0) * m * n), "oz_row_image": ("hbm", (8 + 14.0) * m * n),
+           "colmax": ("hbm", float(esize) * m * n), "oz_rowexp": ("hbm", 8.0 * m * n),
+           "colsumsq": ("hbm", 8.0 * m * n)}
+    if sweeps and len(sweeps) >= 3 and min(sweeps[:3]) > 0:
+        mdl["jacobi_eig"] = ("alu", (sweeps[0] + sweeps[1]) / 2.0 * rounds * 6.0 * n * n)
+        mdl["jacobi_svd"] = ("alu", float(sweeps[2]) * rounds * 9.0 * n * n)
+    return mdl
+
+
+def roofline_entry(name, cnt, tot_ms, model, step_ms, args):
     per_launch_s = tot_ms / max(cnt, 1) * 1e-3
-    share = tot_ms / (ms * args.steps) if ms > 0 else None
+    bound, amount = model
     traffic = load_traffic(name, args.workload, args.mode)
-    alu = {"nn_tall": 2.0 * m * n * n, "tn_gram": float(m) * n * (n + 1)}
-    hbm = {"tc_gram": float(esize) * m * n, "tc_nn": float(esize) * m * n + 8.0 * m * n}
-    # digit-sliced FP64-accurate products: 28 bf16 digit-pair products per
-    # FP64 product, on the tensor cores
-    tensor = {"oz_nn": 28 * 2.0 * m * n * n, "oz_gram": 28 * float(m) * n * (n + 1)}
-    if name in alu:
-        ach = alu[name] / per_launch_s / 1e12
+    e = {"bound": bound, "kernel": name, "launches_per_step": cnt / max(args.steps, 1),
+         "share_of_step": tot_ms / (step_ms * args.steps) if step_ms > 0 else None,
+         "traffic": traffic}
+    if bound == "alu":
         peak = FP64_PEAK_GFLOPS / 1e3
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived)",
-                "share_of_step": share}
-    if name in tensor:
-        ach = tensor[name] / per_launch_s / 1e12
+        e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s",
+                 peak_source="FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)")
+    elif bound == "tensor":
         peak, src = bf16_peak(sustained=True)
-        return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic, "peak_source": src,
-                "share_of_step": share,
-                "note": "bf16 digit-pair products (28 per FP64-accurate product)"}
-    if name in hbm:
-        ach = hbm[name] / per_launch_s / 1e9
+        e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s", peak_source=src)
+    else:
         peak, src = hbm_peak()
-        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": traffic, "peak_source": src,
-                "share_of_step": share}
-    return {"bound": "latency", "kernel": name, "achieved": None, "peak": None, "unit": None,
-            "frac": None, "traffic": None, "share_of_step": share,
-            "note": "grid-barrier-bound n x n Jacobi solve; no throughput roofline applies"}
+        e.update(achieved=amount / per_launch_s / 1e9, peak=peak, unit="GB/s", peak_source=src)
+    e["frac"] = e["achieved"] / e["peak"]
+    if name.startswith("jacobi"):
+        e["note"] = ("latency-bound: one grid barrier and a chain of dependent FP64 "
+                     "operations per round; the fraction is of the FP64 pipe")
+    return e
+
+
+def roofline(kernels, m, n, ms, args, esize, sweeps=None):
+    """Roofline of the dominant kernel (largest event time in the timed
+    region) and of every other modelled kernel with a share above 1%:
+    algorithmic work per launch (kernel_models) / mean launch duration."""
+    if not kernels:
+        return None, []
+    mdl = kernel_models(m, n, esize, sweeps)
+    ranked = sorted(kernels.items(), key=lambda kv: -kv[1][1])
+    entries = []
+    for name, (cnt, tot) in ranked:
+        if name in mdl and tot >= 0.01 * ms * args.steps:
+            entries.append(roofline_entry(name, cnt, tot, mdl[name], ms, args))
+    top = ranked[0][0]
+    dom = next((e for e in entries if e["kernel"] == top), entries[0] if entries else None)
+    return dom, entries
 
 
 def read_profile(L):
