@@ -52,6 +52,10 @@ WORKLOADS = {
     # with sigma_j = 1/j plus 1e-4 Gaussian noise), k = 50, l = 60, 2 power steps
     "lowrank_100k_x_20k": dict(kind="lowrank", m=100_000, n=20_000, r=200, k=50, l=60, iters=2,
                                seed=4),
+    # forward and backward of the differentiable TS-SVD: 500,000 x 512 FP32,
+    # sigma_j = 1 + (n - j)/n, loss sum_j w_j sigma_j + ||U_k^T B||_F^2 with
+    # k = 64, B 500,000 x 8
+    "grad_500k_x_512": dict(kind="grad", m=500_000, n=512, k=64, nb=8, seed=6),
 }
 
 # FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the
@@ -612,6 +616,61 @@ def run_lowrank(args):
     print(json.dumps(out), flush=True)
 
 
+def run_grad(args):
+    """One step = forward TS-SVD (FP32 storage), the loss, and its backward
+    through the thin-SVD adjoint (TSSVD autograd).  Nominal flops: 8mn^2
+    forward + 8mn^2 for the adjoint's tall products (U recomputed, U^T dU,
+    [U | dU] times an n x n pair)."""
+    import numpy as np
+    import torch
+
+    import paper_1612_08709_gb300 as pkg
+    import workloads
+    w = WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    m, n, k, nb = w["m"], w["n"], w["k"], w["nb"]
+    s = workloads.sigma_distinct_gaps(n)
+    A = workloads.known_spectrum_torch(m, n, s, w["seed"], dev)[0].float()
+    rng = np.random.default_rng(w["seed"] + 1)
+    wv = torch.as_tensor(rng.standard_normal(n), dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(w["seed"] + 2)
+    B = torch.randn(m, nb, generator=g, device=dev, dtype=torch.float32)
+    mode = args.mode if args.mode in ("fp64", "fp64_tc") else "fp64_tc"
+    out = {}
+
+    def step():
+        Ag = A.detach().requires_grad_(True)
+        U, S, V = pkg.TSSVD.apply(Ag, 2, True, 0.0, mode)
+        L = (wv * S).sum() + ((U[:, :k].T @ B) ** 2).sum()
+        L.backward()
+        out["S"], out["U"], out["G"] = S.detach(), U.detach(), Ag.grad
+    for _ in range(args.warmup):
+        step()
+    L_ = pkg.lib()
+    clocks = ClockSampler(0)
+    clocks.start()
+    n0 = L_.tssvd_launch_count()
+    ms = _timed(torch, step, args.steps)
+    launches = L_.tssvd_launch_count() - n0
+    clk = clocks.stop()
+    st = torch.as_tensor(s, device=dev)
+    U = out["U"].double()
+    res = {"metric": METRIC, "value": 16.0 * m * n * n / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "fp32 storage; " + ("bf16 digits+fp32+f64" if mode == "fp64_tc" else "f64"),
+           "data": "synthetic",
+           "config": {"workload": args.workload, "m": m, "n": n, "k": k, "mode": mode,
+                      "flops": "16mn^2 (8mn^2 forward + 8mn^2 adjoint)",
+                      "l2": "inputs larger than L2 (A is %.1f GB FP32)" % (m * n * 4 / 1e9)},
+           "gpu_launches": int(launches), "clocks": clk,
+           "accuracy": {"sigma_err_normwise": float((out["S"].double() - st).abs().max() / st[0]),
+                        "orth_U": float((U.T @ U - torch.eye(n, dtype=U.dtype, device=dev)).abs().max()),
+                        "grad_norm": float(out["G"].double().norm())}}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -620,6 +679,8 @@ def main():
         run_batched(args)
     elif WORKLOADS[args.workload]["kind"] == "lowrank":
         run_lowrank(args)
+    elif WORKLOADS[args.workload]["kind"] == "grad":
+        run_grad(args)
     else:
         run_ours(args)
 

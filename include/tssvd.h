@@ -166,6 +166,9 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
  *   dA = U [ (F o (J - J^T)) S + diag(dS) + S (F o (K - K^T)) - J S^-1 ] V^T
  *        + dU S^-1 V^T.
  * This is the standard thin-SVD adjoint (it is not part of the paper).
+ * opts->mode TSSVD_FP64_TC runs the three tall products (U, U^T dU and dA)
+ * on the FP64-accurate digit-sliced tensor-core kernels; other modes use
+ * FP64 FMA.  Returns 3 if a device wait expired.
  * Errors: -1 A, -2 m, -3 n, -4 lda, -5 S, -6 V, -10 dA, -11 opts.
  */
 int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const double *S,

@@ -308,9 +308,10 @@ def ts_svd_batched_workspace_size(shapes, dtype=torch.float64, passes=2, scale=T
                                                    ctypes.byref(o)))
 
 
-def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=None):
+def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, mode="fp64", stream=None, workspace=None):
     """dA of the thin SVD (see include/tssvd.h, ts_svd_backward); FP64 or
-    FP32 storage (all tensors of A's dtype)."""
+    FP32 storage (all tensors of A's dtype); mode "fp64" or "fp64_tc" for
+    the tall products."""
     A = _as_matrix(A)
     m, n = A.shape
     dt = A.dtype
@@ -319,7 +320,7 @@ def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None, stream=None, workspace=N
     for x in c:
         if x is not None and x.dtype != dt:
             raise TsSvdError("ts_svd_backward: all tensors must have A's dtype")
-    o = _opts(stream=stream, workspace=workspace)
+    o = _opts(mode=mode, stream=stream, workspace=workspace)
     f = lib().ts_svd_backward if dt == torch.float64 else lib().ts_svd_backward_f32
     with torch.cuda.device(A.device):
         rc = f(_ptr(A), m, n, A.stride(0), *[_ptr(x) for x in c], _ptr(dA), ctypes.byref(o))
@@ -335,10 +336,11 @@ class TSSVD(torch.autograd.Function):
     def forward(ctx, A, passes=2, scale=True, drop_tol=0.0, mode="fp64"):
         U, S, V, info = ts_svd(A, passes=passes, scale=scale, drop_tol=drop_tol, mode=mode)
         ctx.save_for_backward(A, S, V)
+        ctx.mode = "fp64_tc" if mode == "fp64_tc" else "fp64"
         return U, S, V
 
     @staticmethod
     def backward(ctx, gU, gS, gV):
         A, S, V = ctx.saved_tensors
-        dA = ts_svd_backward(A, S, V, dU=gU, dS=gS, dV=gV)
+        dA = ts_svd_backward(A, S, V, dU=gU, dS=gS, dV=gV, mode=ctx.mode)
         return dA, None, None, None, None

@@ -876,10 +876,39 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
     const int sp = spJ > spK ? spJ : spK;
     const int gy = nn_grid_rows(m, n);
     const bool dbl = sizeof(T) == sizeof(double);
+    // FP64_TC: the three tall products (U = A V S^-1, J = U^T dU, dA =
+    // [U | dU] BB) on the digit-sliced tensor-core kernels
+    const bool oz = opts->mode == TSSVD_FP64_TC;
+    const int spO = oz ? oz_tn_splits(m, (int)n, (int)n) : 0;
     struct Bufs {
         double *Ub, *sinv, *M0, *J, *K, *Mc, *Vtr, *BB, *P, *NP, *Sd, *Vd, *dSd, *dVd, *dAd;
+        DevStatus *st;
+        int *er, *emM, *emB, *exU, *exD;
+        unsigned long long *bits;
+        uint8_t *big, *bimg;
+        double *PO;
     } b;
+    const size_t gib = oz ? oz_gram_image_bytes(m, (int)n) : 0;
+    size_t bigb = 0;
+    if (oz) {
+        const size_t r1 = oz_row_image_bytes(m, (int)n), r2 = oz_row_image_bytes(m, 2 * (int)n);
+        bigb = 2 * ((gib + 255) / 256 * 256);
+        if (r1 > bigb) bigb = r1;
+        if (r2 > bigb) bigb = r2;
+    }
     auto carve = [&](Bump &w) {
+        b.st = w.take<DevStatus>(1);
+        if (oz) {
+            b.er = w.take<int>(m);
+            b.emM = w.take<int>(n);
+            b.emB = w.take<int>(n);
+            b.exU = w.take<int>(n);
+            b.exD = w.take<int>(n);
+            b.bits = w.take<unsigned long long>(2 * n);
+            b.big = w.take<uint8_t>(bigb);
+            b.bimg = w.take<uint8_t>(oz_image_bytes(2 * (int)n, (int)n));
+            b.PO = w.take<double>((size_t)spO * nn);
+        }
         b.Ub = w.take<double>((size_t)m * 2 * n);
         b.sinv = w.take<double>(n);
         b.M0 = w.take<double>(nn);
@@ -906,6 +935,7 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
     carve(ws);
     if (ws.overflow) return TSSVD_ENOMEM;
     auto body = [&]() -> cudaError_t {
+        CK(cudaMemsetAsync(b.st, 0, sizeof(DevStatus), s));
         // FP64 copies of the small operands
         CK(launch_to_double<T>(S, n, 1, n, b.Sd, n, s));
         CK(launch_to_double<T>(V, n, n, n, b.Vd, n, s));
@@ -915,13 +945,34 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
         CK(launch_discard(b.Sd, n, 0.0, b.sinv, nullptr, s));
         // U = A V S^-1 (recomputed), the left half of [U | dU]
         CK(launch_scale2(b.Vd, n, n, n, nullptr, b.sinv, b.M0, n, s));
-        CK(launch_nn<T, double>(A, lda, b.M0, n, m, n, n, b.Ub, 2 * n, b.NP, s));
+        if (oz) {
+            CK(launch_oz_rowexp<T>(A, lda, m, (int)n, nullptr, b.er, s));
+            CK(launch_oz_row_image<T>(A, lda, m, (int)n, nullptr, b.er, b.big, s));
+            CK(launch_oz_image(b.M0, n, (int)n, (int)n, nullptr, b.emM, b.bimg, s));
+            CK(launch_oz_nn_run<double>(b.big, m, (int)n, b.er, b.bimg, b.emM, (int)n, b.Ub, 2 * n,
+                                        b.st, s));
+        } else {
+            CK(launch_nn<T, double>(A, lda, b.M0, n, m, n, n, b.Ub, 2 * n, b.NP, s));
+        }
         if (dU) {
             CK(launch_to_double<T>(dU, n, m, n, b.Ub + n, 2 * n, s));
             // J = U^T dU
-            CK(launch_tn_partial<double, double>(b.Ub, 2 * n, b.Ub + n, 2 * n, m, n, n, spJ,
-                                                 false, b.P, s));
-            CK(launch_tn_reduce(b.P, spJ, n, n, nullptr, nullptr, false, b.J, n, s));
+            if (oz) {
+                uint8_t *imgD = b.big + (gib + 255) / 256 * 256;
+                CK(cudaMemsetAsync(b.bits, 0, sizeof(unsigned long long) * 2 * n, s));
+                CK(launch_colmax<double>(b.Ub, m, n, 2 * n, b.bits, s));
+                CK(launch_colmax<double>(b.Ub + n, m, n, 2 * n, b.bits + n, s));
+                CK(launch_oz_exp_from_bits(b.bits, (int)n, b.exU, s));
+                CK(launch_oz_exp_from_bits(b.bits + n, (int)n, b.exD, s));
+                CK(launch_oz_col_image(b.Ub, 2 * n, m, (int)n, b.exU, b.big, s));
+                CK(launch_oz_col_image(b.Ub + n, 2 * n, m, (int)n, b.exD, imgD, s));
+                CK(launch_oz_tn(b.big, b.exU, (int)n, imgD, b.exD, (int)n, m, spO, b.PO, b.st, s));
+                CK(launch_tn_reduce(b.PO, spO, n, n, nullptr, nullptr, false, b.J, n, s));
+            } else {
+                CK(launch_tn_partial<double, double>(b.Ub, 2 * n, b.Ub + n, 2 * n, m, n, n, spJ,
+                                                     false, b.P, s));
+                CK(launch_tn_reduce(b.P, spJ, n, n, nullptr, nullptr, false, b.J, n, s));
+            }
         } else {
             CK(cudaMemset2DAsync(b.Ub + n, sizeof(double) * 2 * n, 0, sizeof(double) * n, m, s));
         }
@@ -937,7 +988,13 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
         CK(launch_nn<double, double>(b.Mc, n, b.Vtr, n, n, n, n, b.BB, n, b.NP, s));
         CK(launch_transpose(b.Vd, n, n, n, b.sinv, b.BB + nn, n, s));
         // dA = [U | dU] BB
-        if (dbl) {
+        if (oz) {
+            CK(launch_oz_rowexp<double>(b.Ub, 2 * n, m, 2 * (int)n, nullptr, b.er, s));
+            CK(launch_oz_row_image<double>(b.Ub, 2 * n, m, 2 * (int)n, nullptr, b.er, b.big, s));
+            CK(launch_oz_image(b.BB, n, 2 * (int)n, (int)n, nullptr, b.emB, b.bimg, s));
+            CK(launch_oz_nn_run<T>(b.big, m, 2 * (int)n, b.er, b.bimg, b.emB, (int)n, dA, n, b.st,
+                                   s));
+        } else if (dbl) {
             CK(launch_nn<double, T>(b.Ub, 2 * n, b.BB, n, m, 2 * n, n, dA, n, b.NP, s));
         } else {
             CK(launch_nn<double, double>(b.Ub, 2 * n, b.BB, n, m, 2 * n, n, b.dAd, n, b.NP, s));
@@ -951,11 +1008,13 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
         cudaGetLastError();
         return TSSVD_ECUDA;
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
+    int err = 0;
+    if (cudaMemcpyAsync(&err, &b.st->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return TSSVD_ECUDA;
     }
-    return TSSVD_OK;
+    return err ? TSSVD_ETIMEOUT : TSSVD_OK;
 }
 
 }  // namespace

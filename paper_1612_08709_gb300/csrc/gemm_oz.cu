@@ -1078,6 +1078,11 @@ template cudaError_t launch_oz_row_image<double>(const double *, i64, i64, int, 
 template cudaError_t launch_oz_nn_run<double>(const uint8_t *, i64, int, const int *,
                                               const uint8_t *, const int *, int, double *, i64,
                                               DevStatus *, cudaStream_t);
+template cudaError_t launch_oz_nn_run<float>(const uint8_t *, i64, int, const int *,
+                                             const uint8_t *, const int *, int, float *, i64,
+                                             DevStatus *, cudaStream_t);
+template cudaError_t launch_oz_row_image<float>(const float *, i64, i64, int, const int *,
+                                                const int *, uint8_t *, cudaStream_t);
 
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s)
 {

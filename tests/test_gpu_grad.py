@@ -97,3 +97,36 @@ def test_fp32_forward_autograd_runs_on_the_workload_loss():
     _loss(torch, pkg, A32, w64.float(), B64.float(), k).backward()
     g64, g32 = Ag.grad, A32.grad.double()
     assert float((g32 - g64).abs().max()) <= 1e-3 * float(g64.abs().max())
+
+
+@gpu
+def test_backward_fp64_tc_matches_oracle_gradient(orc):
+    """The adjoint with its three tall products on the FP64-accurate
+    digit-sliced tensor-core kernels: FP64 storage within 1e-10 of the
+    oracle's analytic gradient (as the FP64 FMA path), FP32 storage within
+    FP32 accuracy; autograd through TSSVD in that mode matches FP64's."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    m, n, k = 6000, 96, 8
+    A, w, Bm, A_h, w_h, B_h = _setup(m, n, k, 8, 53, torch.float64)
+    U, S, V, info = pkg.ts_svd(A, drop_tol=0.0, mode="fp64_tc")
+    Uh = U.cpu().numpy()
+    dU = np.zeros((m, n))
+    dU[:, :k] = 2.0 * B_h @ (B_h.T @ Uh[:, :k])
+    dV = np.random.default_rng(54).standard_normal((n, n))
+    ref = orc.ts_svd_backward(A_h, S.cpu().numpy(), V.cpu().numpy(), dU=dU, dS=w_h, dV=dV)
+    g = pkg.ts_svd_backward(A, S, V, dU=torch.as_tensor(dU, device="cuda"), dS=w,
+                            dV=torch.as_tensor(dV, device="cuda"), mode="fp64_tc").cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-10 * np.abs(ref).max()
+    A32 = A.float()
+    U32, S32, V32, info = pkg.ts_svd(A32, drop_tol=0.0, mode="fp64_tc")
+    g32 = pkg.ts_svd_backward(A32, S32, V32, dU=torch.as_tensor(dU, dtype=torch.float32, device="cuda"),
+                              dS=w.float(), mode="fp64_tc").double().cpu().numpy()
+    ref32 = orc.ts_svd_backward(A_h, S.cpu().numpy(), V.cpu().numpy(), dU=dU, dS=w_h)
+    assert np.abs(g32 - ref32).max() <= 1e-3 * np.abs(ref32).max()
+    Ag = A.clone().requires_grad_(True)
+    U2, S2, V2 = pkg.TSSVD.apply(Ag, 2, True, 0.0, "fp64_tc")
+    ((w * S2).sum() + ((U2[:, :k].T @ Bm) ** 2).sum()).backward()
+    Af = A.clone().requires_grad_(True)
+    _loss(torch, pkg, Af, w, Bm, k).backward()
+    assert float((Ag.grad - Af.grad).abs().max()) <= 1e-9 * float(Af.grad.abs().max())

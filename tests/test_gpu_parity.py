@@ -252,3 +252,24 @@ def test_gram_matches_oracle(orc, m, n, seed):
     Br = orc.gram(A)
     assert np.abs(B - Br).max() <= 1e-13 * np.abs(Br).max()
     assert np.array_equal(B, B.T)
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_repeated_singular_values_match_oracle(orc, mode):
+    """Appendix B's spectrum (many repeated singular values and a zero): the
+    GPU matches the oracle in the values and, for each repeated value, in
+    the column subspace of U and V (individual vectors are not defined)."""
+    n = 96
+    s = workloads.sigma_devils_staircase(n)
+    A, _, s0, _ = workloads.known_spectrum(5000, n, s, 43)
+    Ur, Sr, Vr, rr, st = orc.ts_svd(A, drop_tol=0.0)
+    (U, S, V), info = run_gpu(A, drop_tol=0.0, mode=mode)
+    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    k = int((s0 > 0).sum())
+    assert orth(U[:, :k]) <= 1e-12 and orth(V[:, :k]) <= 1e-12
+    for X, Y in ((U, Ur), (V, Vr)):
+        for v in np.unique(s0[:k]):
+            idx = np.where(s0[:k] == v)[0]
+            d = np.abs(X[:, idx] @ X[:, idx].T - Y[:, idx] @ Y[:, idx].T).max()
+            assert d <= 1e-10, (v, d)

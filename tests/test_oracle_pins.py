@@ -393,3 +393,58 @@ def test_backward_dv_term_finite_differences(orc):
     fd = (loss(A + h * E) - loss(A - h * E)) / (2 * h)
     an = float(np.sum(dA * E))
     assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (fd, an)
+
+
+# --------------------------------------------------------------------------
+# Repeated singular values (the paper's Appendix B spectrum)
+# --------------------------------------------------------------------------
+
+
+def cluster_projector_errors(s_ref, X, Y):
+    """For each group of equal reference values, max |X_g X_g^T - Y_g Y_g^T|
+    (the column subspace of a repeated singular value is what is defined)."""
+    vals = np.unique(s_ref)
+    errs = []
+    for v in vals:
+        idx = np.where(s_ref == v)[0]
+        Px = X[:, idx] @ X[:, idx].T
+        Py = Y[:, idx] @ Y[:, idx].T
+        errs.append(np.abs(Px - Py).max())
+    return np.array(errs)
+
+
+def test_devils_staircase_spectrum_shape():
+    """Appendix B: values in [0, 1] from the six-digit binary recoding,
+    1 and 0 reached for k = n = 2000 (the size the appendix plots), many
+    repeats of varying multiplicity."""
+    s = workloads.sigma_devils_staircase(2000)
+    assert s.shape == (2000,) and np.all(np.diff(s) <= 0)
+    assert s[0] == 1.0 and s[-1] == 0.0
+    vals, counts = np.unique(s, return_counts=True)
+    assert np.allclose(vals * 63, np.round(vals * 63))  # multiples of 1/63
+    assert len(vals) < 64 and counts.max() > 100 and len(set(counts)) > 5
+    # the octal-to-binary recoding, checked on exact integers for k = 512
+    # (j 8^6 / 512 = 512 j exactly, so no rounding is involved)
+    s512 = workloads.sigma_devils_staircase(512)
+    brute = []
+    for j in range(512):
+        x = 512 * j
+        b = int("".join("1" if c != "0" else "0" for c in format(x, "o")), 2)
+        brute.append(b / 63.0)
+    assert np.array_equal(s512, np.sort(brute)[::-1])
+
+
+def test_ts_svd_repeated_singular_values(orc):
+    """Algorithm 4 on a known spectrum with repeated values and a zero
+    (Appendix B): the singular values, and the subspace of each repeated
+    value in U and V, match the construction."""
+    n = 96
+    s = workloads.sigma_devils_staircase(n)
+    A, U0, s0, V0 = workloads.known_spectrum(4000, n, s, 41)
+    U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0)
+    assert np.abs(S - s0).max() <= 1e-13 * s0[0]
+    pos = s0 > 0
+    k = int(pos.sum())
+    assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 1e-13
+    assert cluster_projector_errors(s0[:k], U[:, :k], U0[:, :k]).max() <= 1e-12
+    assert cluster_projector_errors(s0[:k], V[:, :k], V0[:, :k]).max() <= 1e-12

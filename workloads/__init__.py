@@ -13,7 +13,9 @@ Recipes (sizes and distributions of the workloads the method is run on):
   * the paper's test matrix (eq. "originalmat" with "testS"/"testSl"):
     U, V orthonormal DCT-II bases, sigma_j = 10^(-20 (j-1)/(p-1));
   * the low-rank workload  A = U_r diag(1/j) V_r^T + 1e-4 G / sqrt(m);
-  * batches of uneven tall problems with log-uniform spectra.
+  * batches of uneven tall problems with log-uniform spectra;
+  * the Devil's-staircase spectrum of the paper's Appendix B (many
+    repeated singular values of varying multiplicity, and zeros).
 """
 import math
 
@@ -52,6 +54,27 @@ def sigma_distinct_gaps(n):
 # --------------------------------------------------------------------------
 # Orthonormal factors
 # --------------------------------------------------------------------------
+
+
+def sigma_devils_staircase(k):
+    """The "Devil's staircase" spectrum of the paper's Appendix B: for
+    j = 0..k-1, the real number j/k is rounded to six octal digits
+    (round(j * 8^6 / k), evaluated in single precision with half-up
+    rounding), every nonzero octal digit becomes the binary digit 1, the
+    resulting six-bit binary number is divided by 2^6 - 1 = 63, and the k
+    values are sorted in decreasing order.  Values lie in [0, 1] with many
+    repeats (multiplicities vary) and include zeros."""
+    q = np.float32(8.0 ** 6) / np.float32(k)
+    out = np.empty(k, dtype=np.float64)
+    for j in range(k):
+        x = int(np.floor(np.float32(np.float32(j) * q) + np.float32(0.5)))
+        bits = 0
+        for pos in range(7):  # at most seven octal digits (8^6 itself)
+            digit = (x >> (3 * pos)) & 7
+            if digit:
+                bits |= 1 << pos
+        out[j] = bits / 63.0
+    return np.sort(out)[::-1].copy()
 
 
 def orthonormal(rows, cols, rng):
