@@ -282,19 +282,22 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     }
     // B = (A D^-1)^T (A D^-1)
     CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
+    // A's row image for Y~ = A (D^-1 V~) (A's columns prescaled by D^-1
+    // for the digit scales; the product is unchanged).  Building the row
+    // images beside the Jacobi kernels on a second stream was tried and
+    // slowed the latency-bound solves 2.5x (L2 and issue contention).
+    CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
+    CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
     // B = V~ D~ V~^T
     CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
-    // Y~ = (A D^-1) V~ = A (D^-1 V~), with A's columns prescaled by D^-1 for
-    // the digit scales (the product is unchanged)
     const double *M1 = Vt;
     if (sc) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
         M1 = M;
     }
-    CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
     CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
-    CK(launch_oz_nn<T, double>(A, lda, m, (int)n, pkA, er, big, img, em, (int)n, Yt, n, st, s));
+    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Yt, n, st, s));
 
     if (passes == 1) {
         // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
@@ -322,18 +325,20 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
     CK(launch_diag_sqrt(G2, n, n, sig, s));
     CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+    // Y~'s row image for Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W) and for
+    // the final U (both prescaled by pk2 = round(log2 Sigma~^-1))
+    CK(launch_oz_pow2_of(sinv, (int)n, pk2, s));
+    CK(launch_oz_rowexp<double>(Yt, n, m, (int)n, pk2, er, s));
+    CK(launch_oz_row_image<double>(Yt, n, m, (int)n, pk2, er, big, s));
     CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
     // Z = W D W^T
     CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
-    // Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W); T = explicit column norms
-    CK(launch_oz_pow2_of(sinv, (int)n, pk2, s));
+    // Q~; T = explicit column norms
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
-    CK(launch_oz_rowexp<double>(Yt, n, m, (int)n, pk2, er, s));
     CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
     double *Qb = u_is_double ? (double *)U : Qt;
     const i64 ldq = u_is_double ? ldu : n;
-    CK(launch_oz_nn<double, double>(Yt, n, m, (int)n, pk2, er, big, img, em, (int)n, Qb, ldq, st,
-                                    s));
+    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Qb, ldq, st, s));
     CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
     CK(launch_norms_reduce(NP, gcs, n, Tn, s));
     CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
@@ -351,7 +356,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
     CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
     CK(launch_oz_image(M3, n, (int)n, (int)n, pk2, em, img, s));
-    CK(launch_oz_nn<double, TO>(Yt, n, m, (int)n, pk2, er, big, img, em, (int)n, U, ldu, st, s));
+    // (Y~'s row image from the Q~ product is still in place)
+    CK(launch_oz_nn_run<TO>(big, m, (int)n, er, img, em, (int)n, U, ldu, st, s));
     CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
     CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
     return cudaSuccess;

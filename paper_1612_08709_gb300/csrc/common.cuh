@@ -121,10 +121,11 @@ cudaError_t launch_oz_tn(const uint8_t *aimg, const int *exa, int M, const uint8
 // Digit image of diag(2^-pk) M (K x N) and its column exponents em.
 cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *pk, int *em,
                             uint8_t *img, cudaStream_t s);
-// er[r] = exponent bounding row r of A diag(2^pk).
+// er[r] = exponent bounding row r of A diag(2^pk).  per_sm caps the grid
+// at that many CTAs per SM (small when it runs beside a Jacobi solve).
 template <typename T>
 cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, int *er,
-                             cudaStream_t s);
+                             cudaStream_t s, int per_sm = 16);
 // C = A M with A prescaled by 2^pk (see launch_oz_image), row exponents er;
 // aimg: scratch of oz_row_image_bytes(m, K) for A's digit image.
 template <typename T, typename TC>
@@ -135,7 +136,7 @@ cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const
 // from a prebuilt image (to reuse one image of A for several products).
 template <typename T>
 cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
-                                uint8_t *aimg, cudaStream_t s);
+                                uint8_t *aimg, cudaStream_t s, int per_sm = 16);
 template <typename TC>
 cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
                              const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s);

@@ -832,27 +832,28 @@ template <typename T>
 __global__ void oz_rowexp_kernel(const T *__restrict__ A, i64 lda, i64 m, int K,
                                  const int *__restrict__ pk, int *__restrict__ er)
 {
-    const i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (r >= m) return;
-    int mx = -100000;
-    for (int k = lane; k < K; k += 32) {
-        int ev;
-        unsigned long long mant;
-        uint32_t sign;
-        dsplit((double)A[r * lda + k], ev, mant, sign);
-        if (mant) {
-            const int e = (mant == (1ull << 52)) ? ev : ev + 1;
-            const int eff = e + (pk ? pk[k] : 0);
-            mx = eff > mx ? eff : mx;
+    const i64 warps = (i64)gridDim.x * (blockDim.x >> 5);
+    for (i64 r = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < m; r += warps) {
+        int mx = -100000;
+        for (int k = lane; k < K; k += 32) {
+            int ev;
+            unsigned long long mant;
+            uint32_t sign;
+            dsplit((double)A[r * lda + k], ev, mant, sign);
+            if (mant) {
+                const int e = (mant == (1ull << 52)) ? ev : ev + 1;
+                const int eff = e + (pk ? pk[k] : 0);
+                mx = eff > mx ? eff : mx;
+            }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int v = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = v > mx ? v : mx;
+        for (int o = 16; o > 0; o >>= 1) {
+            const int v = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = v > mx ? v : mx;
+        }
+        if (lane == 0) er[r] = mx < -1000 ? 0 : mx;
     }
-    if (lane == 0) er[r] = mx < -1000 ? 0 : mx;
 }
 
 // Exponents from MaxEntry bit patterns: ex[j] = log2 of the smallest power
@@ -1027,22 +1028,21 @@ cudaError_t launch_oz_image(const double *M, i64 ldm, int K, int N, const int *p
 
 template <typename T>
 cudaError_t launch_oz_rowexp(const T *A, i64 lda, i64 m, int K, const int *pk, int *er,
-                             cudaStream_t s)
+                             cudaStream_t s, int per_sm)
 {
     ProfScope ps_("oz_rowexp", s);
-    const i64 threads = m * 32;
-    oz_rowexp_kernel<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(A, lda, m, K, pk, er);
+    oz_rowexp_kernel<T><<<grid_cap(m * 32, per_sm), 256, 0, s>>>(A, lda, m, K, pk, er);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
-                                uint8_t *aimg, cudaStream_t s)
+                                uint8_t *aimg, cudaStream_t s, int per_sm)
 {
     const int KP = (K + 15) / 16 * 16;
     const i64 total = (m + 127) / 128 * 128 * ((KP + kBK - 1) / kBK) * (kBK / 8);
     ProfScope ps_("oz_row_image", s);
-    oz_row_image_kernel<T><<<grid_cap(total, 16), 256, 0, s>>>(A, lda, m, K, pk, er, aimg);
+    oz_row_image_kernel<T><<<grid_cap(total, per_sm), 256, 0, s>>>(A, lda, m, K, pk, er, aimg);
     return cudaGetLastError();
 }
 
@@ -1068,13 +1068,13 @@ cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const
                          uint8_t *aimg, const uint8_t *bimg, const int *em, int N, TC *C, i64 ldc,
                          DevStatus *st, cudaStream_t s)
 {
-    cudaError_t e = launch_oz_row_image<T>(A, lda, m, K, pk, er, aimg, s);
+    cudaError_t e = launch_oz_row_image<T>(A, lda, m, K, pk, er, aimg, s, 16);
     if (e != cudaSuccess) return e;
     return launch_oz_nn_run<TC>(aimg, m, K, er, bimg, em, N, C, ldc, st, s);
 }
 
 template cudaError_t launch_oz_row_image<double>(const double *, i64, i64, int, const int *,
-                                                 const int *, uint8_t *, cudaStream_t);
+                                                 const int *, uint8_t *, cudaStream_t, int);
 template cudaError_t launch_oz_nn_run<double>(const uint8_t *, i64, int, const int *,
                                               const uint8_t *, const int *, int, double *, i64,
                                               DevStatus *, cudaStream_t);
@@ -1082,7 +1082,7 @@ template cudaError_t launch_oz_nn_run<float>(const uint8_t *, i64, int, const in
                                              const uint8_t *, const int *, int, float *, i64,
                                              DevStatus *, cudaStream_t);
 template cudaError_t launch_oz_row_image<float>(const float *, i64, i64, int, const int *,
-                                                const int *, uint8_t *, cudaStream_t);
+                                                const int *, uint8_t *, cudaStream_t, int);
 
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s)
 {
@@ -1110,9 +1110,9 @@ template cudaError_t launch_oz_gram<double>(const double *, i64, i64, int, const
 template cudaError_t launch_oz_gram<float>(const float *, i64, i64, int, const int *, int,
                                            uint8_t *, double *, DevStatus *, cudaStream_t);
 template cudaError_t launch_oz_rowexp<double>(const double *, i64, i64, int, const int *, int *,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template cudaError_t launch_oz_rowexp<float>(const float *, i64, i64, int, const int *, int *,
-                                             cudaStream_t);
+                                             cudaStream_t, int);
 template cudaError_t launch_oz_nn<double, double>(const double *, i64, i64, int, const int *,
                                                   const int *, uint8_t *, const uint8_t *,
                                                   const int *, int, double *, i64, DevStatus *,
