@@ -245,6 +245,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     double *P = ws.take<double>((size_t)(osp > sp2 ? osp : sp2) * nn);
     const int gcs = colsumsq_rows(m, n);
     const int gys = nn_grid_rows(n, n);
+    const bool fuse = oz_nn_fuses((int)n);  // column maxima from the product epilogue
     double *NP = ws.take<double>((size_t)(gcs > gys ? gcs : gys) * n);
     uint8_t *img = ws.take<uint8_t>(oz_image_bytes((int)n, (int)n));
     double *B = ws.take<double>(nn), *G2 = ws.take<double>(nn), *Jw = ws.take<double>(nn);
@@ -297,7 +298,11 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         M1 = M;
     }
     CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
-    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Yt, n, st, s));
+    // Y~, with its column maxima (the next Gram's digit scales) taken in the
+    // product's epilogue
+    if (fuse) CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Yt, n, st, s,
+                                fuse ? bits : nullptr, nullptr));
 
     if (passes == 1) {
         // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
@@ -318,8 +323,10 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
 
     // Z = Y^T Y with Y = Y~ Sigma~^-1; Sigma~ = explicit column norms of Y~
     // (the diagonal of its Gram matrix)
-    CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
-    CK(launch_colmax<double>(Yt, m, n, n, bits, s));
+    if (!fuse) {
+        CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+        CK(launch_colmax<double>(Yt, m, n, n, bits, s));
+    }
     CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
     CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, big, P, st, s));
     CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
@@ -338,6 +345,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
     double *Qb = u_is_double ? (double *)U : Qt;
     const i64 ldq = u_is_double ? ldu : n;
+    // (the column sums of squares are a separate pass: in the product's
+    // epilogue their FP64 FMAs cost more than the pass they save)
     CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Qb, ldq, st, s));
     CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
     CK(launch_norms_reduce(NP, gcs, n, Tn, s));

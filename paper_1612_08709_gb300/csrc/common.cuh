@@ -137,9 +137,16 @@ cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const
 template <typename T>
 cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk, const int *er,
                                 uint8_t *aimg, cudaStream_t s, int per_sm = 16);
+// Optionally (N <= 512, oz_nn_fuses) with the output's column statistics:
+// colmax_out[j] = max(colmax_out[j], bits of max_i |C_ij|) (zeroed by the
+// caller) and colsq_out[b * N + j] = the sum of C_ij^2 over the rows of
+// CTA b (oz_nn_grid(m, N) rows of partials, reduced by the caller).
+int oz_nn_grid(i64 m, int N);
+bool oz_nn_fuses(int N);
 template <typename TC>
 cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
-                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s);
+                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s,
+                             unsigned long long *colmax_out = nullptr, double *colsq_out = nullptr);
 cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *ex, cudaStream_t s);
 // pk[j] = round(log2(sc[j])) (0 for sc[j] <= 0).
 cudaError_t launch_oz_pow2_of(const double *sc, int n, int *pk, cudaStream_t s);

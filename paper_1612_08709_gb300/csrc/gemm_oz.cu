@@ -62,6 +62,11 @@ constexpr int kChunkUnits = 2 * kChunkStages;  // halves per FP32 chunk
 constexpr int kStagesNN = 3;
 constexpr int kStgLd = kNT + 1;
 constexpr size_t kNNSmem = (size_t)kStagesNN * kStageBytes + 128 * kStgLd * sizeof(double);
+// Optional fused column statistics of the A*M output (N <= kFuseMaxN):
+// per-warp FP64 sums of squares (deterministic order) and column maxima of
+// |C| as bit patterns, in shared memory after the staging tile.
+constexpr int kFuseMaxN = 512;
+constexpr size_t kNNSmemTotal = kNNSmem + (size_t)kFuseMaxN * (4 * sizeof(double) + 8);
 // The Gram-type product (oz_tn) uses the same three stages and staging tile
 // (its drain parks each chunk's double-FP32 values there).
 constexpr int kStagesTN = 3;
@@ -565,7 +570,8 @@ template <typename TC>
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_nn_kernel(const uint8_t *__restrict__ aimg, i64 m, int K, const int *__restrict__ er,
                  const uint8_t *__restrict__ bimg, const int *__restrict__ em, int N,
-                 TC *__restrict__ C, i64 ldc, DevStatus *st)
+                 TC *__restrict__ C, i64 ldc, DevStatus *st, unsigned long long *colmax_out,
+                 double *colsq_out)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStagesNN], empty_bar[kStagesNN];
@@ -583,6 +589,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int my_tiles =
         (i64)blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     const size_t btile = (size_t)nkb * kDig * kBTerm;
+    double *csq = reinterpret_cast<double *>(smem_raw + kNNSmem);  // [4][kFuseMaxN]
+    unsigned long long *cmx = reinterpret_cast<unsigned long long *>(csq + 4 * kFuseMaxN);
+    const bool fuse = (colmax_out || colsq_out) && N <= kFuseMaxN;
+    if (fuse)
+        for (int i = threadIdx.x; i < 5 * kFuseMaxN; i += blockDim.x) {
+            if (i < 4 * kFuseMaxN)
+                csq[i] = 0.0;
+            else
+                cmx[i - 4 * kFuseMaxN] = 0ull;
+        }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStagesNN; s++) {
@@ -681,6 +697,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             for (int c0 = 0; c0 < kNT; c0 += 32) {
                 const int j = nt * kNT + c0 + lane;
                 const int ej = j < N ? em[j] - 14 : 0;
+                double sq = 0.0;
+                unsigned long long mx = 0ull;
 #pragma unroll 1
                 for (int r0 = 0; r0 < 32; r0 += 8) {
                     double v[8];
@@ -699,8 +717,21 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     if (j < N) {
 #pragma unroll
                         for (int q = 0; q < 8; q++)
-                            if (row0 + r0 + q < m) C[(row0 + r0 + q) * ldc + j] = (TC)v[q];
+                            if (row0 + r0 + q < m) {
+                                C[(row0 + r0 + q) * ldc + j] = (TC)v[q];
+                                if (fuse) {
+                                    sq = fma(v[q], v[q], sq);
+                                    const unsigned long long ab =
+                                        (unsigned long long)__double_as_longlong(v[q]) &
+                                        0x7FFFFFFFFFFFFFFFull;
+                                    mx = ab > mx ? ab : mx;
+                                }
+                            }
                     }
+                }
+                if (fuse && j < N) {
+                    csq[warp * kFuseMaxN + j] += sq;
+                    if (mx) atomicMax(cmx + j, mx);
                 }
             }
             if (__any_sync(0xffffffffu, bad)) {
@@ -723,6 +754,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 }
             }
             __syncwarp();
+        }
+        if (fuse) {
+            // the CTA's column statistics (epilogue warps only)
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int jj = threadIdx.x; jj < N; jj += 128) {
+                if (colsq_out)
+                    colsq_out[(i64)blockIdx.x * N + jj] =
+                        ((csq[jj] + csq[kFuseMaxN + jj]) + csq[2 * kFuseMaxN + jj]) +
+                        csq[3 * kFuseMaxN + jj];
+                if (colmax_out && cmx[jj]) atomicMax(colmax_out + jj, cmx[jj]);
+            }
         }
     } else {
         if (lane == 0) {
@@ -1046,11 +1088,20 @@ cudaError_t launch_oz_row_image(const T *A, i64 lda, i64 m, int K, const int *pk
     return cudaGetLastError();
 }
 
+int oz_nn_grid(i64 m, int N)
+{
+    const i64 ntiles = (m + 127) / 128 * ((N + kNT - 1) / kNT);
+    return (int)(ntiles < num_sms() ? ntiles : num_sms());
+}
+
+bool oz_nn_fuses(int N) { return N <= kFuseMaxN; }
+
 template <typename TC>
 cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, const uint8_t *bimg,
-                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s)
+                             const int *em, int N, TC *C, i64 ldc, DevStatus *st, cudaStream_t s,
+                             unsigned long long *colmax_out, double *colsq_out)
 {
-    const size_t smem = kNNSmem;
+    const size_t smem = kNNSmemTotal;
     auto k = oz_nn_kernel<TC>;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -1059,7 +1110,8 @@ cudaError_t launch_oz_nn_run(const uint8_t *aimg, i64 m, int K, const int *er, c
     const i64 ntiles = (m + 127) / 128 * ((N + kNT - 1) / kNT);
     const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
     ProfScope ps_("oz_nn", s);
-    k<<<grid, kOzThreads, smem, s>>>(aimg, m, K, er, bimg, em, N, C, ldc, st);
+    k<<<grid, kOzThreads, smem, s>>>(aimg, m, K, er, bimg, em, N, C, ldc, st, colmax_out,
+                                     colsq_out);
     return cudaGetLastError();
 }
 
@@ -1070,17 +1122,19 @@ cudaError_t launch_oz_nn(const T *A, i64 lda, i64 m, int K, const int *pk, const
 {
     cudaError_t e = launch_oz_row_image<T>(A, lda, m, K, pk, er, aimg, s, 16);
     if (e != cudaSuccess) return e;
-    return launch_oz_nn_run<TC>(aimg, m, K, er, bimg, em, N, C, ldc, st, s);
+    return launch_oz_nn_run<TC>(aimg, m, K, er, bimg, em, N, C, ldc, st, s, nullptr, nullptr);
 }
 
 template cudaError_t launch_oz_row_image<double>(const double *, i64, i64, int, const int *,
                                                  const int *, uint8_t *, cudaStream_t, int);
 template cudaError_t launch_oz_nn_run<double>(const uint8_t *, i64, int, const int *,
                                               const uint8_t *, const int *, int, double *, i64,
-                                              DevStatus *, cudaStream_t);
+                                              DevStatus *, cudaStream_t, unsigned long long *,
+                                              double *);
 template cudaError_t launch_oz_nn_run<float>(const uint8_t *, i64, int, const int *,
                                              const uint8_t *, const int *, int, float *, i64,
-                                             DevStatus *, cudaStream_t);
+                                             DevStatus *, cudaStream_t, unsigned long long *,
+                                             double *);
 template cudaError_t launch_oz_row_image<float>(const float *, i64, i64, int, const int *,
                                                 const int *, uint8_t *, cudaStream_t, int);
 
