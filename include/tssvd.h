@@ -126,6 +126,37 @@ int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double
 int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S,
                float *V, tssvd_opts *opts);
 
+/* Bytes of workspace ts_pca / ts_pca_f32 need: those of ts_svd plus the
+ * centred copy (m x n elements) and the column-sum partials. */
+size_t ts_pca_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts);
+
+/*
+ * Principal component analysis of the m observations (rows) of A: the thin
+ * SVD of the column-centred matrix A - 1 mu^T, mu_j the mean of column j
+ * (the first problem of the paper's abstract, PCA of a highly rectangular
+ * matrix, solved with Algorithm 4 or 3 as opts->passes says).  The means
+ * are FP64 column sums divided by m and rounded once to the storage type;
+ * the centred values A_ij - mu_j are formed explicitly (FP64 difference,
+ * one rounding) in the workspace rather than as a rank-one correction of
+ * the Gram matrix, which cancels catastrophically when |mu| dominates the
+ * spread of the data.  The principal directions are the columns of V, the
+ * scores U diag(S), and the variances S_j^2 / (m - 1).  The centred
+ * matrix has rank at most m - 1, so for m = n the last singular value is 0
+ * (TSSVD_RANKDEF); a matrix whose rows are all equal gives rank 0.
+ *   A   [in]  m x n, row-major, leading dimension lda >= n; not modified.
+ *   mu  [out] n column means.
+ *   U, S, V, opts as for ts_svd, for the centred matrix.
+ * Errors: -1 A NULL, -2 m < n or m < 1, -3 n < 1, -4 lda < n, -5 mu NULL,
+ * -6 U NULL, -7 S NULL, -8 V NULL, -9 opts NULL or invalid field.
+ */
+int ts_pca(const double *A, int64_t m, int64_t n, int64_t lda, double *mu, double *U,
+           double *S, double *V, tssvd_opts *opts);
+
+/* As ts_pca for FP32 storage (means and centred values rounded to FP32;
+ * the SVD as ts_svd_f32). */
+int ts_pca_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *mu, float *U,
+               float *S, float *V, tssvd_opts *opts);
+
 /* Bytes of workspace lowrank_svd needs. */
 size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_opts *opts);
 

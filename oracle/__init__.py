@@ -37,6 +37,10 @@ def lib():
         L.or_ts_svd2.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_int, _dp, _i64, _dp, _dp, _i64, _lp, _lp]
         L.or_ts_svd2.restype = ctypes.c_int
+        L.or_col_means.argtypes = [_dp, _i64, _i64, _i64, _dp]
+        L.or_pca.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_int, _dp, _dp, _i64, _dp, _dp, _i64, _lp]
+        L.or_pca.restype = ctypes.c_int
         L.or_lowrank_svd.argtypes = [_dp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int, _dp,
                                      ctypes.c_double, ctypes.c_int, _dp, _i64, _dp, _dp,
                                      _i64, _lp, _lp]
@@ -156,6 +160,26 @@ def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, max_sweeps=MAX_SWEE
     if return_diag:
         return out + ((diag[0], diag[1]),)
     return out
+
+
+def col_means(A):
+    A = _c(A)
+    m, n = A.shape
+    mu = np.zeros(n)
+    lib().or_col_means(_p(A), m, n, n, _p(mu))
+    return mu
+
+
+def pca(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, max_sweeps=MAX_SWEEPS):
+    """PCA of the rows of A: (mu n, U m x n, S n, V n x n, rank, status) of
+    the SVD of A - 1 mu^T."""
+    A = _c(A)
+    m, n = A.shape
+    mu = np.zeros(n); U = np.zeros((m, n)); S = np.zeros(n); V = np.zeros((n, n))
+    r = ctypes.c_int64(0)
+    st = lib().or_pca(_p(A), m, n, n, int(passes), int(bool(scale)), float(drop_tol),
+                      int(max_sweeps), _p(mu), _p(U), n, _p(S), _p(V), n, ctypes.byref(r))
+    return mu, U, S, V, r.value, st
 
 
 def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, max_sweeps=MAX_SWEEPS,

@@ -39,6 +39,10 @@
  *  - Sign convention: each right singular vector is flipped so that its
  *    entry of largest magnitude (lowest index on ties) is positive; the
  *    matching left singular vector is flipped with it.
+ *  - PCA (the first problem of the abstract; the paper does not spell out
+ *    the centering): the principal components of the rows of A are the
+ *    singular triplets of C = A - 1 mu^T with mu the column means, and C is
+ *    formed explicitly before the TS-SVD.
  *  - The low-rank SVD returns the leading k of the l triplets that the
  *    direct SVD produces; the SVD of B = Q^T A is taken as the two-pass
  *    tall-skinny SVD of B^T = A^T Q (n x l).
@@ -210,6 +214,37 @@ void or_maxentry_scale(const double *A, i64 m, i64 n, i64 lda, double *d)
  * singular value decomposition X = (X_out diag(1/s)) diag(s) J^T
  * (Algorithm 4, SVD of R).
  */
+/* sqrt(|a b|), as sqrt|a| sqrt|b| so that it neither overflows nor
+ * underflows for squared norms near the ends of the exponent range. */
+static double jac_geo(double a, double b)
+{
+    return sqrt(fabs(a)) * sqrt(fabs(b));
+}
+
+/* Rotation angle that annihilates the (p,q) inner product g of two columns
+ * with squared norms a, b: t = tan(theta) is the smaller root of
+ * t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 g), that is
+ * t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).  For |zeta| > 1 the same
+ * value is r / (1 + sqrt(1 + r^2)) with r = 1 / |zeta| = |2 g| / |b - a|,
+ * which neither overflows nor loses the angle when a and b differ by
+ * hundreds of orders of magnitude (zeta itself would overflow there).
+ * The result is 0 only when the angle underflows; the caller then treats
+ * the pair as converged, since the rotation would be the identity. */
+static double jac_tan(double a, double b, double g)
+{
+    const double d = b - a, ad = fabs(d), ag2 = fabs(2.0 * g);
+    double t;
+    if (ad > ag2) {
+        const double r = ag2 / ad;
+        t = r / (1.0 + sqrt(1.0 + r * r));
+    } else {
+        const double z = ad / ag2;
+        t = 1.0 / (z + sqrt(1.0 + z * z));
+    }
+    const int pos = (d == 0.0) || ((d > 0.0) == (g > 0.0));
+    return pos ? t : -t;
+}
+
 int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
               double *s, int max_sweeps)
 {
@@ -229,14 +264,11 @@ int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
                     beta += xq * xq;
                     gamma += xp * xq;
                 }
-                if (gamma == 0.0 || !(fabs(gamma) > tol * sqrt(alpha * beta)))
+                if (gamma == 0.0 || !(fabs(gamma) > tol * jac_geo(alpha, beta)))
                     continue;
+                double t = jac_tan(alpha, beta, gamma);
+                if (t == 0.0) continue;
                 rotations++;
-                /* Rotation angle that annihilates the (p,q) inner product:
-                 * t = tan(theta) is the smaller root of t^2 + 2 zeta t - 1. */
-                double zeta = (beta - alpha) / (2.0 * gamma);
-                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
-                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 double c = 1.0 / sqrt(1.0 + t * t);
                 double sn = c * t;
                 for (i64 i = 0; i < nr; i++) {
@@ -314,11 +346,10 @@ int or_jacobi_eig(double *B, i64 n, i64 ldb, double *V, i64 ldv, double *lam,
         for (i64 p = 0; p < n - 1; p++) {
             for (i64 q = p + 1; q < n; q++) {
                 double a = B[p * ldb + p], b = B[q * ldb + q], g = B[p * ldb + q];
-                if (g == 0.0 || !(fabs(g) > tol * sqrt(fabs(a * b)))) continue;
+                if (g == 0.0 || !(fabs(g) > tol * jac_geo(a, b))) continue;
+                double t = jac_tan(a, b, g);
+                if (t == 0.0) continue;
                 rotations++;
-                double zeta = (b - a) / (2.0 * g);
-                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
-                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 double c = 1.0 / sqrt(1.0 + t * t);
                 double sn = c * t;
                 /* B <- B J (columns p, q), then B <- J^T B (rows p, q). */
@@ -572,6 +603,57 @@ int or_ts_svd2(const double *A, i64 m, i64 n, i64 lda, int scale,
     free(Y); free(Z); free(W); free(mu); free(Qt); free(T); free(Q); free(R);
     free(Rt); free(P); free(sg); free(Uq);
     return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* PCA (abstract, problem 1): SVD of the column-centred matrix.         */
+/* ------------------------------------------------------------------ */
+
+/* mu_j = (sum_i A_ij) / m.  The sum is taken in row order with Neumaier's
+ * compensated summation (a running sum plus a running correction for the
+ * rounding error of each addition), so it is accurate to about one
+ * rounding whatever m and the offset of the column; this accuracy matters
+ * because an error in mu_j perturbs every centred entry of column j. */
+void or_col_means(const double *A, i64 m, i64 n, i64 lda, double *mu)
+{
+    for (i64 j = 0; j < n; j++) {
+        double t = 0.0, corr = 0.0;
+        for (i64 i = 0; i < m; i++) {
+            const double a = A[i * lda + j];
+            const double u = t + a;
+            if (fabs(t) >= fabs(a))
+                corr += (t - u) + a;
+            else
+                corr += (a - u) + t;
+            t = u;
+        }
+        mu[j] = (t + corr) / (double)m;
+    }
+}
+
+/*
+ * Principal components of the rows of A: mu = column means, then the
+ * TS-SVD (Algorithm 4 when passes = 2, else Algorithm 3) of the centred
+ * matrix C = A - 1 mu^T, formed explicitly.  Outputs and status as
+ * or_ts_svd1 / or_ts_svd2, plus mu (n).
+ */
+int or_pca(const double *A, i64 m, i64 n, i64 lda, int passes, int scale,
+           double drop_tol, int max_sweeps, double *mu, double *U, i64 ldu,
+           double *S, double *V, i64 ldv, i64 *rank)
+{
+    double *C = dalloc(m * n);
+    or_col_means(A, m, n, lda, mu);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) C[i * n + j] = A[i * lda + j] - mu[j];
+    int st;
+    if (passes == 1)
+        st = or_ts_svd1(C, m, n, n, drop_tol, max_sweeps, U, ldu, S, V, ldv,
+                        rank);
+    else
+        st = or_ts_svd2(C, m, n, n, scale, drop_tol, max_sweeps, U, ldu, S, V,
+                        ldv, rank, NULL);
+    free(C);
+    return st;
 }
 
 /* ------------------------------------------------------------------ */

@@ -89,6 +89,12 @@ def lib():
         f = getattr(L, name)
         f.argtypes = [vp, i64, i64, i64, vp, vp, vp, op]
         f.restype = ctypes.c_int
+    L.ts_pca_workspace_size.argtypes = [i64, i64, ctypes.c_int, op]
+    L.ts_pca_workspace_size.restype = ctypes.c_size_t
+    for name in ("ts_pca", "ts_pca_f32"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, op]
+        f.restype = ctypes.c_int
     L.lowrank_svd.argtypes = [vp, i64, i64, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp, op]
     L.lowrank_svd.restype = ctypes.c_int
     for name in ("ts_svd_backward", "ts_svd_backward_f32"):
@@ -124,7 +130,8 @@ def exported_symbols():
             "ts_svd_f32", "lowrank_svd_workspace_size", "lowrank_svd", "ts_svd_backward",
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
-            "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size"]
+            "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
+            "ts_pca_workspace_size", "ts_pca", "ts_pca_f32"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -208,6 +215,41 @@ def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sw
         rc = f(_ptr(A), m, n, A.stride(0), _ptr(U), _ptr(S), _ptr(V), ctypes.byref(o))
     _check(rc, "ts_svd")
     return U, S, V, _info(o, rc)
+
+
+def ts_pca_workspace_size(m, n, dtype=torch.float64, **kw):
+    o = _opts(**kw) if torch.cuda.is_available() else None
+    if o is None:
+        o = _Opts()
+        lib().tssvd_default_opts(ctypes.byref(o))
+    return int(lib().ts_pca_workspace_size(m, n, 4 if dtype == torch.float32 else 8,
+                                           ctypes.byref(o)))
+
+
+def ts_pca(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
+           stream=None, workspace=None, out=None):
+    """PCA of the rows of a CUDA tensor A (m x n, float64 or float32): the thin
+    SVD of A - 1 mu^T.  Returns (mu n, U m x n, S n, V n x n, info).  See
+    include/tssvd.h (ts_pca)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    dt = A.dtype
+    if dt not in (torch.float64, torch.float32):
+        raise TsSvdError("A must be float64 or float32")
+    if out is None:
+        mu = torch.empty((n,), dtype=dt, device=A.device)
+        U = torch.empty((m, n), dtype=dt, device=A.device)
+        S = torch.empty((n,), dtype=dt, device=A.device)
+        V = torch.empty((n, n), dtype=dt, device=A.device)
+    else:
+        mu, U, S, V = out
+    o = _opts(passes, scale, drop_tol, mode, max_sweeps, stream, workspace)
+    f = lib().ts_pca if dt == torch.float64 else lib().ts_pca_f32
+    with torch.cuda.device(A.device):
+        rc = f(_ptr(A), m, n, A.stride(0), _ptr(mu), _ptr(U), _ptr(S), _ptr(V),
+               ctypes.byref(o))
+    _check(rc, "ts_pca")
+    return mu, U, S, V, _info(o, rc)
 
 
 def lowrank_svd(A, k, l, iters, Omega, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,

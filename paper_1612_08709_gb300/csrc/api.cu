@@ -209,11 +209,15 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     CK(launch_build_g(sig, sinv, Vt, n, scale ? d : nullptr, n, G, s));
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
-    // R = P Sigma V^T by one-sided Jacobi on R^T (R row-major = R^T
-    // column-major): R^T P = X, Sigma = column norms, V = X Sigma^-1.
-    CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    // R = P Sigma V^T by one-sided Jacobi on the columns of R^T (R
+    // row-major = R^T column-major): R^T P = X, Sigma = column norms,
+    // V = X Sigma^-1.  When the MaxEntry scaling is strongly graded the
+    // Jacobi runs on the columns of R instead (R V = X, P = X Sigma^-1);
+    // the device-side flag in st->orient routes the outputs.
+    CK(launch_orient_copy(scale ? d : nullptr, &st->rank2, R, n, Xw, &st->orient, s));
     CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s,
+                              &st->orient));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Q P = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
@@ -356,9 +360,10 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_build_g(sig, sinv, Vt, n, sc ? d : nullptr, n, G, s));
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
-    CK(cudaMemcpyAsync(Xw, R, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_orient_copy(sc ? d : nullptr, &st->rank2, R, n, Xw, &st->orient, s));
     CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s));
+    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s,
+                              &st->orient));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)), prescaled like Q~
@@ -403,7 +408,10 @@ int summarise(const std::vector<DevStatus> &sts, int nsolves_per, int *rank_out)
 int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mutex> &lk)
 {
     if (o->workspace) {
-        if (o->workspace_bytes < need) return TSSVD_ENOMEM;  // (sizes queried include slack)
+        // the carve-up aligns every piece to 256 bytes from the base, so an
+        // unaligned base costs up to 255 bytes (the queried sizes include them)
+        const size_t pad = (256 - ((size_t)o->workspace & 255)) & 255;
+        if (o->workspace_bytes < need + pad) return TSSVD_ENOMEM;
         *base = o->workspace;
         return TSSVD_OK;
     }
@@ -715,18 +723,23 @@ int check_opts(const tssvd_opts *o)
     return 1;
 }
 
+// ts_svd (mu == nullptr) and ts_pca (mu != nullptr: column means into mu,
+// then the TS-SVD of the centred copy A - 1 mu^T held in the workspace).
+// `pca` shifts the argument numbers of the error codes past mu.
 template <typename T>
 int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V,
-                 tssvd_opts *opts)
+                 tssvd_opts *opts, T *mu = nullptr, bool pca = false)
 {
+    const int sh = pca ? 1 : 0;
     if (!A) return -1;
     if (m < 1 || m < n) return -2;
     if (n < 1 || n > 16384) return -3;
     if (lda < n) return -4;
-    if (!U) return -5;
-    if (!S) return -6;
-    if (!V) return -7;
-    if (!check_opts(opts)) return -8;
+    if (pca && !mu) return -5;
+    if (!U) return -5 - sh;
+    if (!S) return -6 - sh;
+    if (!V) return -7 - sh;
+    if (!check_opts(opts)) return -8 - sh;
     if ((opts->mode == TSSVD_BF16X3 || opts->mode == TSSVD_BF16X6) && n > 256) {
         fprintf(stderr, "tssvd: the mixed-precision modes take n <= 256 (n = %lld)\n",
                 (long long)n);
@@ -736,6 +749,10 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
 
     Bump sz(nullptr, 0);
     sz.take<DevStatus>(1);
+    if (pca) {
+        sz.take<T>((size_t)m * n);
+        sz.take<double>((size_t)colsum_rows(m, n) * n);
+    }
     ts_any<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
                  opts->max_sweeps, sz, nullptr, s, opts->mode);
     void *base = nullptr;
@@ -745,8 +762,21 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
     Bump ws(base, sz.off + 256);
     DevStatus *st = ws.take<DevStatus>(1);
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
-    cudaError_t e = ts_any<T, T>(A, m, n, lda, U, n, S, V, n, opts->passes, opts->scale,
-                                 opts->drop_tol, opts->max_sweeps, ws, st, s, opts->mode);
+    const T *X = A;
+    i64 ldx = lda;
+    cudaError_t e = cudaSuccess;
+    if (pca) {
+        T *C = ws.take<T>((size_t)m * n);
+        double *P = ws.take<double>((size_t)colsum_rows(m, n) * n);
+        if (ws.overflow) return TSSVD_ENOMEM;
+        e = launch_col_means<T>(A, lda, m, n, P, mu, s);
+        if (e == cudaSuccess) e = launch_center<T>(A, lda, m, n, mu, C, s);
+        X = C;
+        ldx = n;
+    }
+    if (e == cudaSuccess)
+        e = ts_any<T, T>(X, m, n, ldx, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
+                         opts->max_sweeps, ws, st, s, opts->mode);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
@@ -1089,6 +1119,26 @@ int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, floa
                tssvd_opts *opts)
 {
     return ts_svd_entry<float>(A, m, n, lda, U, S, V, opts);
+}
+
+size_t ts_pca_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts)
+{
+    if (!opts || m < 1 || n < 1) return 0;
+    const size_t eb = elem_bytes == 4 ? 4 : 8;
+    return ts_svd_workspace_size(m, n, elem_bytes, opts) + (size_t)m * n * eb +
+           sizeof(double) * (size_t)colsum_rows(m, n) * n + 512;
+}
+
+int ts_pca(const double *A, int64_t m, int64_t n, int64_t lda, double *mu, double *U, double *S,
+           double *V, tssvd_opts *opts)
+{
+    return ts_svd_entry<double>(A, m, n, lda, U, S, V, opts, mu, true);
+}
+
+int ts_pca_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *mu, float *U, float *S,
+               float *V, tssvd_opts *opts)
+{
+    return ts_svd_entry<float>(A, m, n, lda, U, S, V, opts, mu, true);
 }
 
 size_t lowrank_svd_workspace_size(int64_t m, int64_t n, int64_t l, const tssvd_opts *opts)

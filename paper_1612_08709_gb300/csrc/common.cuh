@@ -21,7 +21,8 @@ struct DevStatus {
     int rank;      // nonzero singular values returned
     int sweeps[4]; // Jacobi sweeps per solve (-1 = cap reached)
     int bar[4];    // scratch for the Jacobi grid barrier (bar[0..1]: 64-bit count)
-    int pad[4];
+    int orient;    // 1: the small SVD ran on the columns of R (else of R^T)
+    int pad[3];
 };
 
 // Number of SMs of the current device (cached per device).
@@ -78,6 +79,15 @@ int nn_grid_rows(i64 m, i64 N);
 // g < colsumsq_rows(m, n); sum them with launch_norms_reduce.
 int colsumsq_rows(i64 m, i64 n);
 cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, cudaStream_t s);
+// Column means mu = A^T 1 / m (FP64 sums of the deviations from the first
+// row, rounded once to T): P holds colsum_rows(m, n) * n doubles of
+// partials.
+int colsum_rows(i64 m, i64 n);
+template <typename T>
+cudaError_t launch_col_means(const T *A, i64 lda, i64 m, i64 n, double *P, T *mu, cudaStream_t s);
+// C = A - 1 mu^T, C dense (leading dimension n).
+template <typename T>
+cudaError_t launch_center(const T *A, i64 lda, i64 m, i64 n, const T *mu, T *C, cudaStream_t s);
 
 // out[j] = sqrt(sum_g NP[g][j]) in fixed order.
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
@@ -181,9 +191,12 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
 // sorted outputs.  Eigen mode: Vout (nc x nc row-major, column r = J
 // column perm[r]) and lam[r].  SVD mode additionally: Uout (nr x nc
 // row-major, column r = X column perm[r] / sigma_r, 0 when sigma_r = 0).
+// (orient non-null and *orient != 0, nr == nc: the J and X/s outputs trade
+// places, for a Jacobi run on the columns of R instead of R^T.)
 cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, double *norms, int *perm, double *Jout, i64 ldjo,
-                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s);
+                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s,
+                                   const int *orient = nullptr);
 
 // ---------------------------------------------------------- small ops
 // Discard rule: smax = max sig; r = 1 + last j with sig_j > 0 and not
@@ -209,6 +222,15 @@ cudaError_t launch_diag_sqrt(const double *G, i64 ldg, i64 n, double *out, cudaS
 // out[j] = keep[j] != 0 ? val[j] : 0 (val null: 1).
 cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
                            cudaStream_t s);
+// X = R or R^T (n x n, dense) for the one-sided Jacobi SVD of R; *orient
+// receives 1 for R^T storage (Jacobi on the columns of R).  Columns of R are
+// chosen when the MaxEntry scaling d (null: none) spans more than
+// kOrientBits binary orders of magnitude and no row of R was discarded
+// (*rank2 == n): R = B diag(d), and one-sided Jacobi converges in a few
+// sweeps on column-graded matrices but slowly on their transposes.
+constexpr int kOrientBits = 12;
+cudaError_t launch_orient_copy(const double *d, const int *rank2, const double *R, i64 n,
+                               double *X, int *orient, cudaStream_t s);
 // dst[j][i] = src[i][j] * rs[j] (rs may be null); src rows x cols.
 cudaError_t launch_transpose(const double *src, i64 lds, i64 rows, i64 cols, const double *rs,
                              double *dst, i64 ldd, cudaStream_t s);

@@ -259,15 +259,27 @@ __device__ __forceinline__ float scaled_f32(double x, int e)
     return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((bits >> 29) & 0x7fffff));
 }
 
+// FP64 rotation for the pairs the FP32-angle form cannot take (subnormal or
+// non-finite inputs, or g far below |b - a|).  The test is taken against
+// sqrt|a| sqrt|b| and the angle as tan = r / (1 + sqrt(1 + r^2)),
+// r = |2g| / |b - a| (when |b - a| > |2g|; else from z = 1 / r), so that
+// neither overflows or underflows when a and b are hundreds of orders of
+// magnitude apart.  An angle that underflows to 0 is no rotation (it would
+// be the identity, and counting it would keep the sweep loop going).
 __device__ __noinline__ double4 jac_rotation_slow(double a, double b, double g, double tol)
 {
-    if (g != 0.0 && fabs(g) > tol * sqrt(fabs(a * b))) {
-        const double zeta = (b - a) / (2.0 * g);
+    if (g != 0.0 && fabs(g) > tol * (sqrt(fabs(a)) * sqrt(fabs(b)))) {
+        const double d = b - a, ad = fabs(d), ag2 = fabs(2.0 * g);
         double tt;
-        if (fabs(zeta) > 1e150)
-            tt = 0.5 / zeta;
-        else
-            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        if (ad > ag2) {
+            const double r = ag2 / ad;
+            tt = r / (1.0 + sqrt(fma(r, r, 1.0)));
+        } else {
+            const double z = ad / ag2;
+            tt = 1.0 / (z + sqrt(fma(z, z, 1.0)));
+        }
+        if (tt == 0.0) return make_double4(1.0, 0.0, 0.0, 0.0);
+        if (!(d == 0.0 || ((d > 0.0) == (g > 0.0)))) tt = -tt;
         const double c = 1.0 / sqrt(1.0 + tt * tt);
         return make_double4(c, c * tt, tt, 1.0);
     }
@@ -762,18 +774,8 @@ __global__ void __launch_bounds__(NT) jacobi_eig_kernel(EigArgs p)
                         const double a = __ldcg(p.B + (i64)P * p.ldb + P);
                         const double b = __ldcg(p.B + (i64)Q * p.ldb + Q);
                         const double g = __ldcg(p.B + (i64)P * p.ldb + Q);
-                        if (g != 0.0 && fabs(g) > p.tol * sqrt(fabs(a * b))) {
-                            const double zeta = (b - a) / (2.0 * g);
-                            double tt;
-                            if (fabs(zeta) > 1e150)
-                                tt = 0.5 / zeta;
-                            else
-                                tt = (zeta >= 0.0 ? 1.0 : -1.0) /
-                                     (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                            const double c = 1.0 / sqrt(1.0 + tt * tt);
-                            r = make_double4(c, c * tt, tt, 1.0);
-                            local_rot++;
-                        }
+                        r = jac_rotation_slow(a, b, g, p.tol);
+                        if (r.w != 0.0) local_rot++;
                     }
                     st4cg(p.prm + pr, r);
                 }
@@ -892,8 +894,17 @@ __global__ void rank_sort_kernel(const double *norms, int nc, int *perm)
 
 __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, const double *norms, const int *perm, double *Jout,
-                                   i64 ldjo, double *lam, double *Xout, i64 ldxo)
+                                   i64 ldjo, double *lam, double *Xout, i64 ldxo,
+                                   const int *orient)
 {
+    if (orient && Xout && nr == nc && *orient != 0) {
+        double *tp = Jout;
+        Jout = Xout;
+        Xout = tp;
+        const i64 tl = ldjo;
+        ldjo = ldxo;
+        ldxo = tl;
+    }
     const i64 tj = (i64)nc * nc;
     const i64 tx = Xout ? (i64)nr * nc : 0;
     for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tj + tx;
@@ -1076,14 +1087,15 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         if (blocks < 1) blocks = 1;
         ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(nullptr, 0, V, ldv, 0, n, dg, perm,
-                                                            Vout, ldvo, lam, nullptr, 0);
+                                                            Vout, ldvo, lam, nullptr, 0, nullptr);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, double *norms, int *perm, double *Jout, i64 ldjo,
-                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s)
+                                   double *lam, double *Xout, i64 ldxo, cudaStream_t s,
+                                   const int *orient)
 {
     cudaError_t e;
     {
@@ -1105,7 +1117,7 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
         if (blocks < 1) blocks = 1;
         ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, J, ldj, nr, nc, norms, perm,
-                                                            Jout, ldjo, lam, Xout, ldxo);
+                                                            Jout, ldjo, lam, Xout, ldxo, orient);
     }
     return cudaGetLastError();
 }

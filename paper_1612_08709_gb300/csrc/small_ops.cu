@@ -220,7 +220,50 @@ __global__ void adjoint_core_kernel(const double *J, const double *K, const doub
     }
 }
 
+// Every block derives the orientation itself (n exponents: cheap), so one
+// launch both decides and copies.
+__global__ void orient_copy_kernel(const double *d, const int *rank2, const double *R, i64 n,
+                                   double *X, int *orient)
+{
+    __shared__ int lo_s, hi_s;
+    if (threadIdx.x == 0) {
+        lo_s = 1 << 20;
+        hi_s = -1;
+    }
+    __syncthreads();
+    if (d) {
+        int lo = 1 << 20, hi = -1;
+        for (i64 j = threadIdx.x; j < n; j += blockDim.x) {
+            const int e = (int)((__double_as_longlong(d[j]) >> 52) & 0x7ff);
+            lo = e < lo ? e : lo;
+            hi = e > hi ? e : hi;
+        }
+        atomicMin(&lo_s, lo);
+        atomicMax(&hi_s, hi);
+    }
+    __syncthreads();
+    const int flip = (d && *rank2 == n && hi_s - lo_s > kOrientBits) ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *orient = flip;
+    const i64 nn = n * n;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (i64)gridDim.x * blockDim.x) {
+        const i64 i = e / n, j = e - i * n;
+        X[e] = flip ? R[j * n + i] : R[e];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_orient_copy(const double *d, const int *rank2, const double *R, i64 n,
+                               double *X, int *orient, cudaStream_t s)
+{
+    i64 blocks = (n * n + 255) / 256;
+    if (blocks > (i64)num_sms() * 4) blocks = (i64)num_sms() * 4;
+    if (blocks < 1) blocks = 1;
+    ProfScope ps_("orient_copy", s);
+    orient_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, rank2, R, n, X, orient);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_diag_sqrt(const double *G, i64 ldg, i64 n, double *out, cudaStream_t s)
 {

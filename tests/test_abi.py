@@ -76,3 +76,29 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     L.tssvd_default_opts(ctypes.byref(o))
     assert L.lowrank_svd(p, 10, 8, 8, 5, 4, 2, p, p, p, p, ctypes.byref(o)) == -5
     assert L.lowrank_svd(p, 10, 8, 8, 2, 9, 2, p, p, p, p, ctypes.byref(o)) == -6
+
+
+def test_pca_argument_validation_without_gpu():
+    """ts_pca rejects each invalid argument with its number before it
+    touches the device (the pointers below are never dereferenced)."""
+    import paper_1612_08709_gb300 as pkg
+    from paper_1612_08709_gb300._binding import _Opts
+    L = pkg.lib()
+    o = _Opts()
+    L.tssvd_default_opts(ctypes.byref(o))
+    f = ctypes.c_void_p(256)
+    assert L.ts_pca(None, 10, 2, 2, f, f, f, f, ctypes.byref(o)) == -1
+    assert L.ts_pca(f, 1, 2, 2, f, f, f, f, ctypes.byref(o)) == -2
+    assert L.ts_pca(f, 10, 0, 2, f, f, f, f, ctypes.byref(o)) == -3
+    assert L.ts_pca(f, 10, 2, 1, f, f, f, f, ctypes.byref(o)) == -4
+    assert L.ts_pca(f, 10, 2, 2, None, f, f, f, ctypes.byref(o)) == -5
+    assert L.ts_pca(f, 10, 2, 2, f, None, f, f, ctypes.byref(o)) == -6
+    assert L.ts_pca(f, 10, 2, 2, f, f, None, f, ctypes.byref(o)) == -7
+    assert L.ts_pca(f, 10, 2, 2, f, f, f, None, ctypes.byref(o)) == -8
+    assert L.ts_pca(f, 10, 2, 2, f, f, f, f, None) == -9
+    o.passes = 3
+    assert L.ts_pca(f, 10, 2, 2, f, f, f, f, ctypes.byref(o)) == -9
+    # the workspace query is host arithmetic: the SVD's plus the centred copy
+    L.tssvd_default_opts(ctypes.byref(o))
+    assert (L.ts_pca_workspace_size(20000, 50, 8, ctypes.byref(o)) >=
+            L.ts_svd_workspace_size(20000, 50, 8, ctypes.byref(o)) + 20000 * 50 * 8)

@@ -116,23 +116,25 @@ def test_ts_svd_small_tall_workload_error_report(orc):
 
 
 @gpu
-def test_ts_svd_leading_dimension(orc):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_ts_svd_leading_dimension(orc, mode):
     m, n = 1500, 37
     A, _, _, _ = workloads.known_spectrum(m, n, workloads.sigma_geometric(n, 1e-4), 11)
     ref = orc.ts_svd(A, drop_tol=0.0)
-    got, info = run_gpu(A, lda_pad=5, drop_tol=0.0)
+    got, info = run_gpu(A, lda_pad=5, drop_tol=0.0, mode=mode)
     compare_svd(A, got, ref[:4])
 
 
 @gpu
-def test_ts_svd_rank_deficient(orc):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_ts_svd_rank_deficient(orc, mode):
     rng = np.random.default_rng(12)
     A = rng.standard_normal((2000, 24))
     A[:, 5] = 0.0
     A[:, 17] = 2.0 * A[:, 3]
     for passes in (1, 2):
         ref = orc.ts_svd(A, passes=passes)
-        got, info = run_gpu(A, passes=passes)
+        got, info = run_gpu(A, passes=passes, mode=mode)
         assert info["rank"] == ref[3] == 22
         assert info["status"] == ref[4] == 2
         compare_svd(A, got, ref[:4],
@@ -141,13 +143,14 @@ def test_ts_svd_rank_deficient(orc):
 
 
 @gpu
-def test_ts_svd_paper_matrix_discard(orc):
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_ts_svd_paper_matrix_discard(orc, mode):
     """The paper's DCT test matrix with the default discard threshold
     sqrt(1e-11): the GPU keeps the same columns as the oracle."""
     A, _, s0, _ = workloads.paper_dct_matrix(3000, 120, 120)
     for passes in (1, 2):
         ref = orc.ts_svd(A, passes=passes, scale=False)
-        got, info = run_gpu(A, passes=passes, scale=False)
+        got, info = run_gpu(A, passes=passes, scale=False, mode=mode)
         assert info["rank"] == ref[3]
         r = ref[3]
         assert np.abs(got[1][:r] - ref[1][:r]).max() <= 1e-11
@@ -273,3 +276,36 @@ def test_repeated_singular_values_match_oracle(orc, mode):
             idx = np.where(s0[:k] == v)[0]
             d = np.abs(X[:, idx] @ X[:, idx].T - Y[:, idx] @ Y[:, idx].T).max()
             assert d <= 1e-10, (v, d)
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_ts_svd_badly_scaled_columns(orc, mode):
+    """Columns scaled from 1e-150 to 1e150 (MaxEntry scaling, Remark
+    "working"'s motivation for scale-aware processing; per-column digit
+    exponents far apart): the two-pass result matches the oracle's relative
+    to each column's scale."""
+    m, n = 3000, 24
+    A, _, _, _ = workloads.known_spectrum(m, n, workloads.sigma_geometric(n, 1e-2), 61)
+    colscale = 10.0 ** np.linspace(-150, 150, n)
+    A = A * colscale
+    Ur, Sr, Vr, rr, st = orc.ts_svd(A, drop_tol=0.0)
+    (U, S, V), info = run_gpu(A, drop_tol=0.0, mode=mode)
+    assert info["rank"] == rr and info["status"] == st == 0
+    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    assert orth(U[:, :rr]) <= 1e-12 and orth(V[:, :rr]) <= 1e-12
+    # residual column by column relative to the column's own scale
+    R = A @ V[:, :rr] - U[:, :rr] * S[:rr]
+    assert np.abs(R).max() <= 1e-10 * Sr[0]
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_ts_svd_three_hundred_columns(orc, mode):
+    """n = 300: several Gram tiles (digit path: 3 row blocks of 128), 150
+    Jacobi pairs over more than one CTA per pair index range."""
+    m, n = 6000, 300
+    A, _, _, _ = workloads.known_spectrum(m, n, workloads.sigma_geometric(n, 1e-6), 62)
+    ref = orc.ts_svd(A, drop_tol=0.0)
+    got, info = run_gpu(A, drop_tol=0.0, mode=mode)
+    compare_svd(A, got, ref[:4])

@@ -448,3 +448,109 @@ def test_ts_svd_repeated_singular_values(orc):
     assert np.abs(U[:, :k].T @ U[:, :k] - np.eye(k)).max() <= 1e-13
     assert cluster_projector_errors(s0[:k], U[:, :k], U0[:, :k]).max() <= 1e-12
     assert cluster_projector_errors(s0[:k], V[:, :k], V0[:, :k]).max() <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# PCA (abstract, problem 1): the SVD of the column-centred matrix
+
+
+def test_col_means_exact_on_dyadic_data(orc):
+    """Integer data with m a power of two: every partial sum and the
+    division by m are exact, so the means equal the exact rational means
+    (a divisor of m - 1, or row means, would not)."""
+    rng = np.random.default_rng(51)
+    A = rng.integers(-1000, 1000, size=(256, 7)).astype(np.float64)
+    mu = orc.col_means(A)
+    exact = [sum(int(v) for v in A[:, j]) / 256 for j in range(7)]
+    assert np.array_equal(mu, np.array(exact))
+
+
+def test_col_means_match_exact_summation(orc):
+    """math.fsum gives the correctly rounded sum; the oracle's mean must be
+    within one rounding of it divided by m, even with column offsets 1e6
+    times the spread (a plain running sum over 100,000 rows is not)."""
+    import math
+    rng = np.random.default_rng(56)
+    m, n = 100000, 3
+    A = 1e6 * np.array([1.0, -3.0, 0.7]) + rng.standard_normal((m, n))
+    mu = orc.col_means(A)
+    for j in range(n):
+        exact = math.fsum(A[:, j]) / m
+        assert abs(mu[j] - exact) <= np.spacing(abs(exact)), j
+
+
+def test_pca_single_column_closed_form(orc):
+    """n = 1, data 0, 1, ..., m-1: mean (m-1)/2 and one singular value
+    sqrt(sum (i - (m-1)/2)^2) = sqrt(m (m^2 - 1) / 12); V = [1]."""
+    m = 8
+    A = np.arange(m, dtype=np.float64).reshape(m, 1)
+    mu, U, S, V, r, st = orc.pca(A)
+    assert mu[0] == 3.5
+    assert abs(S[0] - np.sqrt(m * (m * m - 1) / 12.0)) <= 1e-14 * S[0]
+    assert V[0, 0] == 1.0
+    assert np.abs(U[:, 0] * S[0] - (A[:, 0] - 3.5)).max() <= 1e-14 * S[0]
+
+
+def test_pca_matches_lapack_on_centred_matrix(orc):
+    """Brute force: LAPACK's SVD of A - mean(A) on a small input with column
+    means 1e3 times the spread."""
+    A, c, Q, s0, V0 = workloads.pca_data(300, 6, [5.0, 3.0, 2.0, 1.5, 1.0, 0.5], 52)
+    mu, U, S, V, r, st = orc.pca(A)
+    C = A - A.mean(axis=0)
+    Ur, Sr, Vtr = np.linalg.svd(C, full_matrices=False)
+    assert r == 6 and st == 0
+    assert np.abs(mu - A.mean(axis=0)).max() <= 1e-15 * np.abs(A).max()
+    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    assert match_columns_up_to_sign(V, Vtr.T) <= 1e-10
+    assert match_columns_up_to_sign(U, Ur) <= 1e-10
+    # the construction: the centred part has singular values s0
+    assert np.abs(S - s0).max() <= 1e-11 * s0[0]
+
+
+def test_pca_translation_invariance_and_zero_mean_scores(orc):
+    """Adding a constant row vector b to every observation shifts mu by b and
+    leaves S and V unchanged; the scores U have zero column sums."""
+    A, c, Q, s0, V0 = workloads.pca_data(500, 9, np.linspace(4.0, 0.5, 9), 53, offset=1.0)
+    b = np.random.default_rng(54).integers(-64, 64, size=9).astype(np.float64)
+    mu1, U1, S1, V1, r1, st1 = orc.pca(A)
+    mu2, U2, S2, V2, r2, st2 = orc.pca(A + b)
+    assert np.abs(mu2 - (mu1 + b)).max() <= 1e-13 * (1 + np.abs(b).max())
+    assert np.abs(S2 - S1).max() <= 1e-12 * S1[0]
+    assert np.abs(V2 - V1).max() <= 1e-10
+    assert np.abs(U1.sum(axis=0)).max() <= 1e-12 * np.sqrt(500)
+    # without centring the singular values would change: the pin bites
+    _, S_raw, _, _, _ = orc.ts_svd(A + b)
+    assert np.abs(S_raw - S1).max() > 1e-3
+
+
+def test_pca_rank_limits(orc):
+    """Rows all equal: the centred matrix is 0, rank 0, everything zero.
+    m = n: the centred matrix has rank at most m - 1."""
+    A = np.tile(np.array([1.5, -2.0, 8.0, 0.25]), (64, 1))
+    mu, U, S, V, r, st = orc.pca(A)
+    assert r == 0 and st == 2
+    assert np.array_equal(mu, A[0]) and not S.any() and not U.any() and not V.any()
+    B = np.random.default_rng(55).standard_normal((6, 6))
+    mu, U, S, V, r, st = orc.pca(B)
+    assert r == 5 and st == 2 and S[5] == 0.0
+    Sr = np.linalg.svd(B - B.mean(axis=0), compute_uv=False)
+    assert np.abs(S[:5] - Sr[:5]).max() <= 1e-12 * Sr[0]
+
+
+def test_ts_svd_graded_columns_converge(orc):
+    """Columns scaled from 1e-150 to 1e150: Algorithm 4 with MaxEntry
+    scaling stays backward stable (singular values within 1e-13 sigma_1 of
+    LAPACK's, U and V orthonormal, residual at rounding level) and every
+    Jacobi solve converges; the rotation test and angle must not overflow
+    or underflow for squared norms near the ends of the exponent range."""
+    m, n = 3000, 24
+    A, _, _, _ = workloads.known_spectrum(m, n, workloads.sigma_geometric(n, 1e-2), 61)
+    A = A * 10.0 ** np.linspace(-150, 150, n)
+    Sr = np.linalg.svd(A, compute_uv=False)
+    for scale in (True, False):
+        U, S, V, r, st = orc.ts_svd(A, drop_tol=0.0, scale=scale)
+        assert st == 0 and r == n
+        assert np.abs(S - Sr).max() <= 1e-13 * Sr[0]
+        assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13
+        assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13
+        assert np.abs(A @ V - U * S).max() <= 1e-15 * Sr[0]

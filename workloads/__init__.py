@@ -164,6 +164,26 @@ def lowrank_plus_noise(m, n, r, seed, noise=1e-4):
     return np.ascontiguousarray(A), Ur, s, Vr
 
 
+def pca_data(m, n, sigma, seed, offset=1e3):
+    """Observations with a known centred structure plus large column means:
+    A = Q diag(sigma) V^T + 1 c^T, where Q (m x n) is orthonormal and
+    orthogonal to the all-ones vector (so A - 1 c^T is exactly the centred
+    part and its singular values are sigma) and c_j = offset * N(0, 1).
+
+    Returns (A, c, Q, sigma, V), float64 numpy arrays.
+    """
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((m, n))
+    G -= G.mean(axis=0)  # columns orthogonal to the ones vector
+    Q, R = np.linalg.qr(G)
+    Q *= np.sign(np.diag(R))
+    V = orthonormal(n, n, rng)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    c = offset * rng.standard_normal(n)
+    A = (Q * sigma) @ V.T + c
+    return np.ascontiguousarray(A), c, Q, sigma, V
+
+
 def gaussian(rows, cols, seed):
     """i.i.d. N(0,1) matrix (the starting matrix Omega of the subspace iteration)."""
     return np.random.default_rng(seed).standard_normal((rows, cols))
