@@ -171,7 +171,8 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
     }
     // B = V~ D~ V~^T (Gram-form Jacobi; B is rotated in place).
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s,
+                         true));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
@@ -295,7 +296,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
     // B = V~ D~ V~^T
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s));
+    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s,
+                         passes == 2));
     const double *M1 = Vt;
     if (sc) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));

@@ -286,10 +286,11 @@ __device__ __noinline__ double4 jac_rotation_slow(double a, double b, double g, 
     return make_double4(1.0, 0.0, 0.0, 0.0);
 }
 
+// gmin > 0 adds a normwise floor: pairs with |g| <= gmin are left alone.
 __device__ __forceinline__ double4 jac_rotation(double a, double b, double g, double tol,
-                                                float log2tol)
+                                                float log2tol, double gmin = 0.0)
 {
-    if (g == 0.0) return make_double4(1.0, 0.0, 0.0, 0.0);
+    if (!(fabs(g) > gmin)) return make_double4(1.0, 0.0, 0.0, 0.0);
     const int Ea = exp_field(a), Eb = exp_field(b), Eg = exp_field(g);
     if (Ea == 0 || Eb == 0 || Eg == 0 || Ea == 0x7ff || Eb == 0x7ff || Eg == 0x7ff)
         return jac_rotation_slow(a, b, g, tol);
@@ -506,6 +507,7 @@ struct EigArgs {
     double4 *prm;  // [npairs] (c, s, t, rotate)
     double *diag;  // [n] diagonal of the final B (single-barrier form)
     int n, npad;
+    int normwise;  // 1: rotate only when also |b_PQ| > tol * max_k b_kk
     int max_sweeps;
     double tol;
     int *rot;
@@ -563,7 +565,25 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
     double *Bn = p.B2;
     const int tid = threadIdx.x;
     const float log2tol = log2f((float)p.tol);
+    // Normwise floor: tol times the largest diagonal entry, taken from the
+    // diagonals every CTA loads as rotation inputs (the same values in every
+    // CTA, so all agree on the floor), refreshed once per sweep.
+    __shared__ double dmax_s[NT / 32];
+    double dmx = 0.0, gmin = 0.0;
+    if (p.normwise) {
+        for (int i = tid; i < n; i += NT) dmx = fmax(dmx, __ldcg(Bc + (i64)i * ldb + i));
+    }
     for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
+        if (p.normwise) {
+            for (int o = 16; o > 0; o >>= 1) dmx = fmax(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+            if ((tid & 31) == 0) dmax_s[tid >> 5] = dmx;
+            __syncthreads();
+            double m = 0.0;
+            for (int w = 0; w < NT / 32; w++) m = fmax(m, dmax_s[w]);
+            gmin = p.tol * m;
+            dmx = 0.0;
+            __syncthreads();  // dmax_s is rewritten next sweep
+        }
         for (int t = 0; t < rounds; t++) {
             // ---- issue the loads first: the 2 x 2 block of pair k = tid
             // (for the rotations) and the first off-diagonal block this
@@ -600,8 +620,9 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             if (tid < npairs) {
                 double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
                 if (K20 < n) {
-                    r = jac_rotation(a0, b0, g0, p.tol, log2tol);
+                    r = jac_rotation(a0, b0, g0, p.tol, log2tol, gmin);
                     if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                    if (t == rounds - 1) dmx = fmax(dmx, fmax(a0, b0));
                 }
                 prm_s[tid] = r;
             }
@@ -613,8 +634,9 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                     const double a = __ldcg(Bc + (i64)K * ldb + K);
                     const double b = __ldcg(Bc + (i64)K2 * ldb + K2);
                     const double g = __ldcg(Bc + (i64)K * ldb + K2);
-                    r = jac_rotation(a, b, g, p.tol, log2tol);
+                    r = jac_rotation(a, b, g, p.tol, log2tol, gmin);
                     if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                    if (t == rounds - 1) dmx = fmax(dmx, fmax(a, b));
                 }
                 prm_s[k] = r;
             }
@@ -1005,7 +1027,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
 
 cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv, double *lam,
                               double *Vout, i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
-                              int *perm, DevStatus *st, int which, cudaStream_t s)
+                              int *perm, DevStatus *st, int which, cudaStream_t s, bool normwise)
 {
     cudaError_t e;
     {
@@ -1040,6 +1062,7 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         a.rot = ctr;
         a.st = st;
         a.which = which;
+        a.normwise = normwise ? 1 : 0;
         constexpr int NT = 128;
         const int npairs0 = npad / 2;
         const int b0 = npairs0 < num_sms() ? npairs0 : num_sms();
