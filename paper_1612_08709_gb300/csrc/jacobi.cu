@@ -557,7 +557,6 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             V_s[e] = (blockIdx.x + li * gridDim.x == c) ? 1.0 : 0.0;
         }
     }
-    int local_rot = 0;
     int done = -1;
     unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
     int epoch = 0;
@@ -584,6 +583,7 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             dmx = 0.0;
             __syncthreads();  // dmax_s is rewritten next sweep
         }
+        int sweep_rot = 0;
         for (int t = 0; t < rounds; t++) {
             // ---- issue the loads first: the 2 x 2 block of pair k = tid
             // (for the rotations) and the first off-diagonal block this
@@ -617,11 +617,12 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                 }
             }
             // ---- all rotations of the round
+            int rot_here = 0;
             if (tid < npairs) {
                 double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
                 if (K20 < n) {
                     r = jac_rotation(a0, b0, g0, p.tol, log2tol, gmin);
-                    if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                    rot_here |= r.w != 0.0;
                     if (t == rounds - 1) dmx = fmax(dmx, fmax(a0, b0));
                 }
                 prm_s[tid] = r;
@@ -635,12 +636,16 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                     const double b = __ldcg(Bc + (i64)K2 * ldb + K2);
                     const double g = __ldcg(Bc + (i64)K * ldb + K2);
                     r = jac_rotation(a, b, g, p.tol, log2tol, gmin);
-                    if (blockIdx.x == 0 && r.w != 0.0) local_rot++;
+                    rot_here |= r.w != 0.0;
                     if (t == rounds - 1) dmx = fmax(dmx, fmax(a, b));
                 }
                 prm_s[k] = r;
             }
-            __syncthreads();
+            // A round in which no pair rotates leaves B and V as they are:
+            // every CTA sees the same rotations, so all skip its update and
+            // its barrier together (Bc stays the current copy).
+            if (!__syncthreads_or(rot_here)) continue;
+            sweep_rot = 1;
             for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
                 const bool first = pr == pr0;
                 int P, Q;
@@ -744,10 +749,6 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
                     }
                 }
             }
-            if (t == rounds - 1 && local_rot != 0) {
-                atomicAdd(p.rot + sweep, local_rot);
-                local_rot = 0;
-            }
             grid_arrive(bar_count, epoch);
             if (VS) rotate_rows_s(V_s, vrows, n, prm_s, p.npad, t);
             if (!grid_wait(bar_count, epoch, &p.st->err)) return;
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             Bn = const_cast<double *>(Bc);
             Bc = tmp;
         }
-        if (ld_acquire(p.rot + sweep) == 0) {
+        if (!sweep_rot) {
             done = sweep + 1;
             break;
         }
