@@ -47,6 +47,8 @@ def lib():
         L.or_lowrank_svd.restype = ctypes.c_int
         L.or_ts_svd_backward.argtypes = [_dp, _i64, _i64, _i64, _dp, _dp, _i64, _dp, _i64,
                                          _dp, _dp, _i64, _dp, _i64]
+        L.or_lowrank_svd_backward.argtypes = [_dp, _i64, _i64, _i64, _dp, _dp, _i64, _i64,
+                                              _dp, _i64, _dp, _dp, _i64, _dp, _i64]
         L.or_orth_error.argtypes = [_dp, _i64, _i64, _i64]
         L.or_orth_error.restype = ctypes.c_double
         L.or_spectral_error.argtypes = [_dp, _i64, _i64, _i64, _dp, _i64, _dp, _dp, _i64,
@@ -210,6 +212,24 @@ def ts_svd_backward(A, S, V, dU=None, dS=None, dV=None):
     dA = np.zeros((m, n))
     lib().or_ts_svd_backward(_p(A), m, n, n, _p(S), _p(V), n, _p(dU), n, _p(dS),
                              _p(dV), n, _p(dA), n)
+    return dA
+
+
+def lowrank_svd_backward(U, S, V, dU=None, dS=None, dV=None):
+    """Adjoint of a rank-k SVD (U m x k, S k, V n x k): dA (m x n)."""
+    U, S, V = _c(U), _c(S), _c(V)
+    m, k = U.shape
+    n = V.shape[0]
+    nul = ctypes.POINTER(ctypes.c_double)()
+    dU = _c(dU) if dU is not None else None
+    dS = _c(dS) if dS is not None else None
+    dV = _c(dV) if dV is not None else None
+    pdU = _p(dU) if dU is not None else nul
+    pdS = _p(dS) if dS is not None else nul
+    pdV = _p(dV) if dV is not None else nul
+    dA = np.zeros((m, n))
+    lib().or_lowrank_svd_backward(_p(U), m, k, k, _p(S), _p(V), n, k, pdU, k, pdS, pdV, k,
+                                  _p(dA), n)
     return dA
 
 

@@ -838,6 +838,81 @@ void or_ts_svd_backward(const double *A, i64 m, i64 n, i64 lda,
     free(MVt); free(SVt);
 }
 
+/*
+ * Adjoint of a rank-k SVD A ~ U diag(S) V^T (the output of Algorithm 8):
+ * U (m x k, ldu), S (k, distinct and positive), V (n x k, ldv), cotangents
+ * dU (m x k), dS (k), dV (n x k) (NULL = zero) -> dA (m x n, ldda).  With
+ * J = U^T dU, K = V^T dV and F_ab = 1/(S_b^2 - S_a^2) (a != b, F_aa = 0):
+ *   dA = U [ (F o (J - J^T)) S + diag(dS) + S (F o (K - K^T)) ] V^T
+ *        + (I - U U^T) dU S^{-1} V^T + U S^{-1} dV^T (I - V V^T).
+ * This is the derivative of the leading k singular triplets when A has
+ * rank k (the singular values past k are 0); for other A it leaves out
+ * the coupling with the discarded part of the spectrum.
+ */
+void or_lowrank_svd_backward(const double *U, i64 m, i64 k, i64 ldu,
+                             const double *S, const double *V, i64 n, i64 ldv,
+                             const double *dU, i64 lddu, const double *dS,
+                             const double *dV, i64 lddv, double *dA, i64 ldda)
+{
+    double *J = dalloc(k * k), *K = dalloc(k * k), *C = dalloc(k * k);
+    double *PdU = dalloc(m * k), *PdV = dalloc(n * k);
+    /* J = U^T dU, K = V^T dV */
+    for (i64 a = 0; a < k; a++)
+        for (i64 b = 0; b < k; b++) {
+            double ja = 0.0, ka = 0.0;
+            if (dU)
+                for (i64 i = 0; i < m; i++) ja += U[i * ldu + a] * dU[i * lddu + b];
+            if (dV)
+                for (i64 i = 0; i < n; i++) ka += V[i * ldv + a] * dV[i * lddv + b];
+            J[a * k + b] = ja;
+            K[a * k + b] = ka;
+        }
+    /* the k x k core */
+    for (i64 a = 0; a < k; a++)
+        for (i64 b = 0; b < k; b++) {
+            double v = 0.0;
+            if (a != b) {
+                const double F = 1.0 / (S[b] * S[b] - S[a] * S[a]);
+                v += F * (J[a * k + b] - J[b * k + a]) * S[b];
+                v += S[a] * F * (K[a * k + b] - K[b * k + a]);
+            } else if (dS) {
+                v += dS[a];
+            }
+            C[a * k + b] = v;
+        }
+    /* (I - U U^T) dU = dU - U J and (I - V V^T) dV = dV - V K */
+    for (i64 i = 0; i < m; i++)
+        for (i64 b = 0; b < k; b++) {
+            double v = dU ? dU[i * lddu + b] : 0.0;
+            for (i64 a = 0; a < k; a++) v -= U[i * ldu + a] * J[a * k + b];
+            PdU[i * k + b] = v;
+        }
+    for (i64 i = 0; i < n; i++)
+        for (i64 b = 0; b < k; b++) {
+            double v = dV ? dV[i * lddv + b] : 0.0;
+            for (i64 a = 0; a < k; a++) v -= V[i * ldv + a] * K[a * k + b];
+            PdV[i * k + b] = v;
+        }
+#pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < m; i++) {
+        double *UC = dalloc(k);
+        for (i64 b = 0; b < k; b++) {
+            double v = 0.0;
+            for (i64 a = 0; a < k; a++) v += U[i * ldu + a] * C[a * k + b];
+            UC[b] = v;
+        }
+        for (i64 j = 0; j < n; j++) {
+            double acc = 0.0;
+            for (i64 b = 0; b < k; b++)
+                acc += UC[b] * V[j * ldv + b] + PdU[i * k + b] * V[j * ldv + b] / S[b] +
+                       U[i * ldu + b] * PdV[j * k + b] / S[b];
+            dA[i * ldda + j] = acc;
+        }
+        free(UC);
+    }
+    free(J); free(K); free(C); free(PdU); free(PdV);
+}
+
 /* ------------------------------------------------------------------ */
 /* Error metrics (Table "heads").                                       */
 /* ------------------------------------------------------------------ */

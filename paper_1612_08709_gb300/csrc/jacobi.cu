@@ -773,6 +773,370 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
     }
 }
 
+// Circle-schedule inverse: the pair index that holds column i in round t.
+__device__ __forceinline__ int circle_slot(int i, int t, int npad)
+{
+    const int rounds = npad - 1;
+    int pos = 0;
+    if (i != 0) {
+        int x = i - 1 - t;
+        if (x < 0) x += rounds;
+        pos = x + 1;
+    }
+    return pos < npad / 2 ? pos : npad - 1 - pos;
+}
+
+// Column i of a round's rotation matrix J restricted to its pair (ra, rb):
+// J e_i = ua e_ra + ub e_rb (ra < rb; rb may be the padding column).
+struct JCol {
+    int ra, rb;
+    double ua, ub;
+};
+
+__device__ __forceinline__ JCol jcol_idx(int i, int t, int npad)
+{
+    JCol u;
+    const int pr = circle_slot(i, t, npad);
+    circle_pair(pr, t, npad, u.ra, u.rb);
+    u.ua = 0.0;
+    u.ub = 0.0;
+    return u;
+}
+
+__device__ __forceinline__ void jcol_coef(JCol &u, int i, double4 r)
+{
+    // new column P = c e_P - s e_Q, new column Q = s e_P + c e_Q
+    if (i == u.ra) {
+        u.ua = r.x;
+        u.ub = -r.y;
+    } else {
+        u.ua = r.y;
+        u.ub = r.x;
+    }
+}
+
+// The four entries of the 2 x 2 block B[{ra_i, rb_i}][{ra_j, rb_j}] (zero
+// where an index is the padding column).
+struct Blk4 {
+    double aa, ab, ba, bb;
+};
+
+__device__ __forceinline__ Blk4 load_blk4(const double *Bc, i64 ldb, int n, const JCol &ri,
+                                          const JCol &cj)
+{
+    Blk4 m;
+    const double *ra = Bc + (i64)ri.ra * ldb;
+    m.aa = __ldcg(ra + cj.ra);
+    m.ab = cj.rb < n ? __ldcg(ra + cj.rb) : 0.0;
+    if (ri.rb < n) {
+        const double *rb = Bc + (i64)ri.rb * ldb;
+        m.ba = __ldcg(rb + cj.ra);
+        m.bb = cj.rb < n ? __ldcg(rb + cj.rb) : 0.0;
+    } else {
+        m.ba = 0.0;
+        m.bb = 0.0;
+    }
+    return m;
+}
+
+// u_i^T M u_j: entry (i, j) of J^T B J from the 2 x 2 block M.
+__device__ __forceinline__ double bilin(const JCol &ui, const Blk4 &m, const JCol &uj)
+{
+    const double ta = fma(m.ab, uj.ub, m.aa * uj.ua);
+    const double tb = fma(m.bb, uj.ub, m.ba * uj.ua);
+    return fma(ui.ub, tb, ui.ua * ta);
+}
+
+// Two rounds of the circle schedule per grid barrier (V held by rows in
+// shared memory).  With J = J_t J_t2 (rounds t and t2 = t + 1), every entry
+// of J^T B J depends on one 2 x 2 block of B in each of round t's pairs of
+// its row and column indices, so both rounds are formed from the current
+// copy Bc alone:
+//  - round t's rotations from Bc's diagonal 2 x 2 blocks (as one round);
+//  - round t2's rotation inputs (B'[P][P], B'[Q][Q], B'[P][Q] of
+//    B' = J_t^T B J_t) from those blocks and one more 2 x 2 block per pair;
+//  - rows P, Q of J^T B J for the CTA's round-t2 pair from 4 x 4 blocks of
+//    Bc (16 loads and 40 FP64 operations per output 2 x 2 block, against
+//    two rounds of 4 loads and 16 operations).
+// All loads depend only on the schedule and are issued before any rotation
+// is known.  For an odd round count the last round is taken alone by
+// letting round t2 repeat round t's pairing with identity rotations.
+template <int NT>
+__global__ void __launch_bounds__(NT) jacobi_eig2r_kernel(EigArgs p)
+{
+    extern __shared__ double4 prm_s[];  // [npairs] round t, then [npairs] round t2
+    const int npairs = p.npad / 2;
+    const int rounds = p.npad - 1;
+    const int n = p.n, npad = p.npad;
+    const i64 ldb = p.ldb, ldv = p.ldv;
+    double4 *prm2_s = prm_s + npairs;
+    double *d1_s = reinterpret_cast<double *>(prm_s + 2 * npairs);  // [npad] diag of B'
+    double *g1_s = d1_s + npad;                                     // [npairs] B'[P2][Q2]
+    double *V_s = g1_s + npairs;
+    const int vrows = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < vrows * n; e += NT) {
+        const int li = e / n, c = e % n;
+        V_s[e] = (blockIdx.x + li * gridDim.x == c) ? 1.0 : 0.0;
+    }
+    int done = -1;
+    unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
+    int epoch = 0;
+    const double *Bc = p.B;
+    double *Bn = p.B2;
+    const float log2tol = log2f((float)p.tol);
+    __shared__ double dmax_s[NT / 32];
+    double dmx = 0.0, gmin = 0.0;
+    if (p.normwise) {
+        for (int i = tid; i < n; i += NT) dmx = fmax(dmx, __ldcg(Bc + (i64)i * ldb + i));
+    }
+    for (int sweep = 0; sweep < p.max_sweeps; sweep++) {
+        if (p.normwise) {
+            for (int o = 16; o > 0; o >>= 1) dmx = fmax(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+            if ((tid & 31) == 0) dmax_s[tid >> 5] = dmx;
+            __syncthreads();
+            double m = 0.0;
+            for (int w = 0; w < NT / 32; w++) m = fmax(m, dmax_s[w]);
+            gmin = p.tol * m;
+            dmx = 0.0;
+            __syncthreads();
+        }
+        int sweep_rot = 0;
+        for (int t = 0; t < rounds; t += 2) {
+            const bool has2 = t + 1 < rounds;
+            const int t2 = has2 ? t + 1 : t;
+            const bool last_t = t == rounds - 1, last_t2 = has2 && t2 == rounds - 1;
+            // ---- loads: round t's 2 x 2 block of pair tid, round t2's cross
+            // block of pair tid, and the first output block of this CTA
+            int P0 = 0, Q0 = 0;
+            double a0 = 0.0, b0 = 0.0, g0 = 0.0;
+            JCol xp = {0, 0, 0.0, 0.0}, xq = xp;
+            Blk4 xm = {0.0, 0.0, 0.0, 0.0};
+            int P1 = 0, Q1 = 0;
+            if (tid < npairs) {
+                circle_pair(tid, t, npad, P0, Q0);
+                a0 = __ldcg(Bc + (i64)P0 * ldb + P0);
+                if (Q0 < n) {
+                    b0 = __ldcg(Bc + (i64)Q0 * ldb + Q0);
+                    g0 = __ldcg(Bc + (i64)P0 * ldb + Q0);
+                }
+                if (has2) {
+                    circle_pair(tid, t2, npad, P1, Q1);
+                    if (Q1 < n) {
+                        xp = jcol_idx(P1, t, npad);
+                        xq = jcol_idx(Q1, t, npad);
+                        xm = load_blk4(Bc, ldb, n, xp, xq);
+                    }
+                }
+            }
+            const int prB = blockIdx.x;  // one round-t2 pair per CTA (gridDim == npairs)
+            int PB, QB;
+            circle_pair(prB, t2, npad, PB, QB);
+            const bool hasQB = QB < n;
+            const JCol up0 = jcol_idx(PB, t, npad);
+            const JCol uq0 = hasQB ? jcol_idx(QB, t, npad) : up0;
+            const int d0 = 1 + tid;
+            const bool pf = block_mine(prB, d0, npairs);
+            int KB = 0, K2B = 0;
+            JCol uk0 = up0, uk20 = up0;
+            Blk4 mpk = {0.0, 0.0, 0.0, 0.0}, mpk2 = mpk, mqk = mpk, mqk2 = mpk;
+            if (pf) {
+                int k = prB + d0;
+                if (k >= npairs) k -= npairs;
+                circle_pair(k, t2, npad, KB, K2B);
+                uk0 = jcol_idx(KB, t, npad);
+                mpk = load_blk4(Bc, ldb, n, up0, uk0);
+                if (hasQB) mqk = load_blk4(Bc, ldb, n, uq0, uk0);
+                if (K2B < n) {
+                    uk20 = jcol_idx(K2B, t, npad);
+                    mpk2 = load_blk4(Bc, ldb, n, up0, uk20);
+                    if (hasQB) mqk2 = load_blk4(Bc, ldb, n, uq0, uk20);
+                }
+            }
+            // ---- round t: all rotations, and B''s diagonal
+            int rot_here = 0;
+            for (int k = tid; k < npairs; k += NT) {
+                int P = P0, Q = Q0;
+                double a = a0, b = b0, g = g0;
+                if (k != tid) {
+                    circle_pair(k, t, npad, P, Q);
+                    a = __ldcg(Bc + (i64)P * ldb + P);
+                    b = Q < n ? __ldcg(Bc + (i64)Q * ldb + Q) : 0.0;
+                    g = Q < n ? __ldcg(Bc + (i64)P * ldb + Q) : 0.0;
+                }
+                double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
+                if (Q < n) {
+                    r = jac_rotation(a, b, g, p.tol, log2tol, gmin);
+                    rot_here |= r.w != 0.0;
+                    if (last_t) dmx = fmax(dmx, fmax(a, b));
+                    double a1 = a, b1 = b, g1 = g;
+                    if (r.w != 0.0) {
+                        const double c = r.x, s = r.y;
+                        const double cc = c * c, ss = s * s, cs = c * s;
+                        a1 = fma(cc, a, fma(-2.0 * cs, g, ss * b));
+                        b1 = fma(ss, a, fma(2.0 * cs, g, cc * b));
+                        g1 = fma(cs, a - b, (cc - ss) * g);
+                    }
+                    d1_s[P] = a1;
+                    d1_s[Q] = b1;
+                    if (!has2) g1_s[k] = g1;
+                } else {
+                    if (last_t) dmx = fmax(dmx, a);
+                    d1_s[P] = a;
+                }
+                prm_s[k] = r;
+            }
+            __syncthreads();
+            // ---- round t2: rotations from B' = J_t^T B J_t
+            if (has2) {
+                for (int k = tid; k < npairs; k += NT) {
+                    int P = P1, Q = Q1;
+                    JCol up = xp, uq = xq;
+                    Blk4 m = xm;
+                    if (k != tid) {
+                        circle_pair(k, t2, npad, P, Q);
+                        if (Q < n) {
+                            up = jcol_idx(P, t, npad);
+                            uq = jcol_idx(Q, t, npad);
+                            m = load_blk4(Bc, ldb, n, up, uq);
+                        }
+                    }
+                    double4 r = make_double4(1.0, 0.0, 0.0, 0.0);
+                    if (Q < n) {
+                        jcol_coef(up, P, prm_s[circle_slot(P, t, npad)]);
+                        jcol_coef(uq, Q, prm_s[circle_slot(Q, t, npad)]);
+                        const double a = d1_s[P], b = d1_s[Q], g = bilin(up, m, uq);
+                        g1_s[k] = g;
+                        r = jac_rotation(a, b, g, p.tol, log2tol, gmin);
+                        rot_here |= r.w != 0.0;
+                        if (last_t2) dmx = fmax(dmx, fmax(a, b));
+                    } else if (last_t2) {
+                        dmx = fmax(dmx, d1_s[P]);
+                    }
+                    prm2_s[k] = r;
+                }
+            } else {
+                for (int k = tid; k < npairs; k += NT) prm2_s[k] = make_double4(1.0, 0.0, 0.0, 0.0);
+            }
+            // A double round in which no pair rotates leaves B and V as they
+            // are; every CTA sees the same rotations, so all skip together.
+            if (!__syncthreads_or(rot_here)) continue;
+            sweep_rot = 1;
+            // ---- rows PB, QB of J^T B J
+            {
+                const double4 me = prm2_s[prB];
+                const double c = me.x, s = me.y;
+                double *nP = Bn + (i64)PB * ldb;
+                double *nQ = hasQB ? Bn + (i64)QB * ldb : nullptr;
+                if (tid == 0) {
+                    const double a = d1_s[PB];
+                    if (hasQB) {
+                        const double b = d1_s[QB], g = g1_s[prB];
+                        double a1 = a, b1 = b, g1 = g;
+                        if (me.w != 0.0) {
+                            const double cc = c * c, ss = s * s, cs = c * s;
+                            a1 = fma(cc, a, fma(-2.0 * cs, g, ss * b));
+                            b1 = fma(ss, a, fma(2.0 * cs, g, cc * b));
+                            g1 = fma(cs, a - b, (cc - ss) * g);
+                        }
+                        __stcg(nP + PB, a1);
+                        __stcg(nQ + QB, b1);
+                        __stcg(nP + QB, g1);
+                        __stcg(nQ + PB, g1);
+                    } else {
+                        __stcg(nP + PB, a);
+                    }
+                }
+                JCol up = up0, uq = uq0;
+                jcol_coef(up, PB, prm_s[circle_slot(PB, t, npad)]);
+                if (hasQB) jcol_coef(uq, QB, prm_s[circle_slot(QB, t, npad)]);
+                for (int d = d0; d <= npairs / 2; d += NT) {
+                    if (!block_mine(prB, d, npairs)) continue;
+                    int k = prB + d;
+                    if (k >= npairs) k -= npairs;
+                    int K, K2;
+                    JCol uk, uk2;
+                    Blk4 m1, m2, m3, m4;
+                    if (d == d0) {
+                        K = KB;
+                        K2 = K2B;
+                        uk = uk0;
+                        uk2 = uk20;
+                        m1 = mpk;
+                        m2 = mpk2;
+                        m3 = mqk;
+                        m4 = mqk2;
+                    } else {
+                        circle_pair(k, t2, npad, K, K2);
+                        uk = jcol_idx(K, t, npad);
+                        uk2 = uk;
+                        m1 = load_blk4(Bc, ldb, n, up, uk);
+                        m3 = hasQB ? load_blk4(Bc, ldb, n, uq, uk) : m1;
+                        if (K2 < n) {
+                            uk2 = jcol_idx(K2, t, npad);
+                            m2 = load_blk4(Bc, ldb, n, up, uk2);
+                            m4 = hasQB ? load_blk4(Bc, ldb, n, uq, uk2) : m2;
+                        } else {
+                            m2 = m1;
+                            m4 = m3;
+                        }
+                    }
+                    const bool hasK2 = K2 < n;
+                    jcol_coef(uk, K, prm_s[circle_slot(K, t, npad)]);
+                    if (hasK2) jcol_coef(uk2, K2, prm_s[circle_slot(K2, t, npad)]);
+                    // B' entries, then round t2's rotations: rows (own), columns (pair k)
+                    const double x = bilin(up, m1, uk);
+                    const double y = hasK2 ? bilin(up, m2, uk2) : 0.0;
+                    const double z = hasQB ? bilin(uq, m3, uk) : 0.0;
+                    const double w = (hasQB && hasK2) ? bilin(uq, m4, uk2) : 0.0;
+                    const double4 o = prm2_s[k];
+                    const double x1 = c * x - s * z, y1 = c * y - s * w;
+                    const double z1 = s * x + c * z, w1 = s * y + c * w;
+                    const double ck = o.x, sk = o.y;
+                    const double pk = ck * x1 - sk * y1, pk2 = sk * x1 + ck * y1;
+                    __stcg(nP + K, pk);
+                    __stcg(Bn + (i64)K * ldb + PB, pk);
+                    if (hasK2) {
+                        __stcg(nP + K2, pk2);
+                        __stcg(Bn + (i64)K2 * ldb + PB, pk2);
+                    }
+                    if (hasQB) {
+                        const double qk = ck * z1 - sk * w1, qk2 = sk * z1 + ck * w1;
+                        __stcg(nQ + K, qk);
+                        __stcg(Bn + (i64)K * ldb + QB, qk);
+                        if (hasK2) {
+                            __stcg(nQ + K2, qk2);
+                            __stcg(Bn + (i64)K2 * ldb + QB, qk2);
+                        }
+                    }
+                }
+            }
+            grid_arrive(bar_count, epoch);
+            rotate_rows_s(V_s, vrows, n, prm_s, npad, t);
+            if (has2) {
+                __syncthreads();
+                rotate_rows_s(V_s, vrows, n, prm2_s, npad, t2);
+            }
+            if (!grid_wait(bar_count, epoch, &p.st->err)) return;
+            double *tmp = Bn;
+            Bn = const_cast<double *>(Bc);
+            Bc = tmp;
+        }
+        if (!sweep_rot) {
+            done = sweep + 1;
+            break;
+        }
+    }
+    for (int e = tid; e < vrows * n; e += NT) {
+        const int li = e / n, c = e % n;
+        p.V[(i64)c * ldv + blockIdx.x + li * gridDim.x] = V_s[e];
+    }
+    if (blockIdx.x == 0) {
+        for (int i = tid; i < n; i += NT) p.diag[i] = __ldcg(Bc + (i64)i * ldb + i);
+        if (tid == 0) p.st->sweeps[p.which] = done;
+    }
+}
+
 // Two-barrier in-place form for npad > 2 * kEigSmemPairs (the rotations
 // of a round do not fit in shared memory).
 template <int NT>
@@ -1070,10 +1434,29 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         const size_t vs_bytes = sizeof(double4) * (size_t)npairs0 +
                                 sizeof(double) * (size_t)((n + b0 - 1) / b0) * n;
         const bool vs = single && vs_bytes <= kRowsSmemMax;
-        const void *kern = !single ? (const void *)jacobi_eig_kernel<NT>
-                           : vs    ? (const void *)jacobi_eig1_kernel<NT, true>
-                                   : (const void *)jacobi_eig1_kernel<NT, false>;
-        const size_t smem = !single ? 0 : vs ? vs_bytes : sizeof(double4) * (size_t)npairs0;
+        // two rounds per barrier: one CTA per pair (all resident), V by rows
+        const size_t two_bytes = sizeof(double4) * 2 * (size_t)npairs0 +
+                                 sizeof(double) * (size_t)(npad + npairs0) +
+                                 sizeof(double) * (size_t)((n + npairs0 - 1) / npairs0) * n;
+        bool two = false;
+        if (single && two_bytes <= kRowsSmemMax) {
+            const void *k2 = (const void *)jacobi_eig2r_kernel<NT>;
+            if (two_bytes > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)two_bytes)) != cudaSuccess)
+                return e;
+            int per_sm2 = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k2, NT, two_bytes)) !=
+                cudaSuccess)
+                return e;
+            two = (i64)per_sm2 * num_sms() >= npairs0;
+        }
+        const void *kern = two      ? (const void *)jacobi_eig2r_kernel<NT>
+                           : !single ? (const void *)jacobi_eig_kernel<NT>
+                           : vs      ? (const void *)jacobi_eig1_kernel<NT, true>
+                                     : (const void *)jacobi_eig1_kernel<NT, false>;
+        const size_t smem = two ? two_bytes
+                            : !single ? 0 : vs ? vs_bytes : sizeof(double4) * (size_t)npairs0;
         if (smem > 48 * 1024 &&
             (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess)
@@ -1085,7 +1468,7 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
         int npairs = npad / 2;
         int blocks = num_sms() * per_sm;
-        if (blocks > npairs) blocks = npairs;
+        if (blocks > npairs || two) blocks = npairs;
         void *args[] = {&a};
         ProfScope ps_("jacobi_eig", s);
         if ((e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, smem, s)) !=

@@ -554,3 +554,64 @@ def test_ts_svd_graded_columns_converge(orc):
         assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13
         assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13
         assert np.abs(A @ V - U * S).max() <= 1e-15 * Sr[0]
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the rank-k SVD of Algorithm 8
+# --------------------------------------------------------------------------
+
+
+def _rank_k_matrix(m, n, k, seed):
+    rng = np.random.default_rng(seed)
+    U0 = workloads.orthonormal(m, k, rng)
+    V0 = workloads.orthonormal(n, k, rng)
+    s0 = np.linspace(3.0, 1.0, k) + 0.25 * np.arange(k)[::-1] / k
+    return (U0 * s0) @ V0.T, rng
+
+
+def test_lowrank_backward_matches_finite_differences(orc):
+    """A of rank exactly k: the rank-k adjoint equals the derivative of the
+    leading k triplets.  Central differences of a sign-invariant loss
+    L = sum_j w_j sigma_j + ||U_k^T B||_F^2 + ||V_k^T C||_F^2, taken with
+    LAPACK's SVD truncated to k (an independent forward), along random
+    directions; k < n, so the (I - V V^T) term is exercised."""
+    m, n, k = 50, 30, 4
+    A, rng = _rank_k_matrix(m, n, k, 81)
+    w = rng.standard_normal(k)
+    Bm = rng.standard_normal((m, 2))
+    Cm = rng.standard_normal((n, 2))
+
+    def loss(X):
+        Ux, sx, Vtx = np.linalg.svd(X, full_matrices=False)
+        Uk, Vk = Ux[:, :k], Vtx[:k].T
+        return float(w @ sx[:k] + np.sum((Uk.T @ Bm) ** 2) + np.sum((Vk.T @ Cm) ** 2))
+
+    Ux, sx, Vtx = np.linalg.svd(A, full_matrices=False)
+    U, S, V = Ux[:, :k], sx[:k], Vtx[:k].T
+    dU = 2.0 * Bm @ (Bm.T @ U)
+    dV = 2.0 * Cm @ (Cm.T @ V)
+    dA = orc.lowrank_svd_backward(U, S, V, dU=dU, dS=w, dV=dV)
+    for t in range(3):
+        E = rng.standard_normal((m, n))
+        h = 1e-6
+        fd = (loss(A + h * E) - loss(A - h * E)) / (2 * h)
+        an = float(np.sum(dA * E))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (t, fd, an)
+
+
+def test_lowrank_backward_closed_forms(orc):
+    """dS alone gives U diag(dS) V^T; zero cotangents give 0; with k = n
+    (V square) the rank-k adjoint reduces to the thin-SVD adjoint."""
+    A, rng = _rank_k_matrix(40, 12, 5, 82)
+    Ux, sx, Vtx = np.linalg.svd(A, full_matrices=False)
+    U, S, V = Ux[:, :5], sx[:5], Vtx[:5].T
+    w = rng.standard_normal(5)
+    assert np.abs(orc.lowrank_svd_backward(U, S, V, dS=w) - (U * w) @ V.T).max() < 1e-13
+    assert not orc.lowrank_svd_backward(U, S, V).any()
+    B = rng.standard_normal((60, 7))
+    U, S, V, r, st = orc.ts_svd(B, drop_tol=0.0)
+    dU = rng.standard_normal((60, 7))
+    dV = rng.standard_normal((7, 7))
+    thin = orc.ts_svd_backward(B, S, V, dU=dU, dS=w[:2].tolist() + [0.0] * 5, dV=dV)
+    rk = orc.lowrank_svd_backward(U, S, V, dU=dU, dS=w[:2].tolist() + [0.0] * 5, dV=dV)
+    assert np.abs(thin - rk).max() <= 1e-12 * np.abs(thin).max()
