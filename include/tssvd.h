@@ -206,6 +206,28 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     const double *V, const double *dU, const double *dS, const double *dV,
                     double *dA, tssvd_opts *opts);
 
+/*
+ * Adjoint of the rank-k SVD returned by lowrank_svd (Algorithm 8).  Given
+ * the forward outputs U (m x k), S (k, distinct and positive), V (n x k)
+ * and the gradients dU (m x k), dS (k), dV (n x k) of a loss (any of the
+ * three may be NULL, meaning zero), writes dA (m x n, leading dimension n):
+ *   dA = U [ (F o (J - J^T)) S + diag(dS) + S (F o (K - K^T)) ] V^T
+ *        + (I - U U^T) dU S^-1 V^T + U S^-1 dV^T (I - V V^T),
+ * F, J, K as for ts_svd_backward.  This is the derivative of the leading k
+ * singular triplets when A has rank k; for other A it omits the coupling
+ * with the discarded singular values, which the rank-k factors do not
+ * carry.  A itself is not needed.  All arrays are row-major and dense,
+ * device pointers owned by the caller; dA is fully overwritten.
+ * opts->mode TSSVD_FP64_TC forms the one m x n product, [U | dU] times a
+ * 2k x n factor, on the digit-sliced tensor-core kernels; other modes use
+ * FP64 FMA.  Returns 3 if a device wait expired.
+ * Errors: -1 m < 1, -2 n < 1, -3 k < 1 or k > min(m, n), -4 U, -5 S,
+ * -6 V, -10 dA, -11 opts.
+ */
+int lowrank_svd_backward(int64_t m, int64_t n, int64_t k, const double *U, const double *S,
+                         const double *V, const double *dU, const double *dS, const double *dV,
+                         double *dA, tssvd_opts *opts);
+
 /* As ts_svd_backward for FP32 storage (the FP32 forward of ts_svd_f32);
  * the adjoint is evaluated in FP64 and dA rounded to FP32. */
 int ts_svd_backward_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *S,

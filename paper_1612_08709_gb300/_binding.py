@@ -101,6 +101,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
         f.restype = ctypes.c_int
+    L.lowrank_svd_backward.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, op]
+    L.lowrank_svd_backward.restype = ctypes.c_int
     L.ts_gram_workspace_size.argtypes = [i64, i64]
     L.ts_gram_workspace_size.restype = ctypes.c_size_t
     L.ts_gram.argtypes = [vp, i64, i64, i64, vp, op]
@@ -131,7 +133,7 @@ def exported_symbols():
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
             "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
-            "ts_pca_workspace_size", "ts_pca", "ts_pca_f32"]
+            "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -386,3 +388,45 @@ class TSSVD(torch.autograd.Function):
         A, S, V = ctx.saved_tensors
         dA = ts_svd_backward(A, S, V, dU=gU, dS=gS, dV=gV, mode=ctx.mode)
         return dA, None, None, None, None
+
+
+def lowrank_svd_backward(U, S, V, dU=None, dS=None, dV=None, mode="fp64", stream=None,
+                         workspace=None):
+    """dA (m x n) of the rank-k SVD (U m x k, S k, V n x k, float64 CUDA
+    tensors); see include/tssvd.h (lowrank_svd_backward)."""
+    if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dim() == 2):
+        raise TsSvdError("expected 2-D CUDA tensors")
+    m, k = U.shape
+    n = V.shape[0]
+    c = [x.contiguous() if x is not None else None for x in (U, S, V, dU, dS, dV)]
+    for x in c:
+        if x is not None and x.dtype != torch.float64:
+            raise TsSvdError("lowrank_svd_backward: float64 tensors only")
+    if V.shape != (n, k) or S.shape != (k,):
+        raise TsSvdError("lowrank_svd_backward: U m x k, S k, V n x k")
+    dA = torch.empty((m, n), dtype=torch.float64, device=U.device)
+    o = _opts(mode=mode, stream=stream, workspace=workspace)
+    with torch.cuda.device(U.device):
+        rc = lib().lowrank_svd_backward(m, n, k, *[_ptr(x) for x in c], _ptr(dA),
+                                        ctypes.byref(o))
+    _check(rc, "lowrank_svd_backward")
+    return dA
+
+
+class LowRankSVD(torch.autograd.Function):
+    """Differentiable rank-k SVD: forward by lowrank_svd (Algorithm 8),
+    backward by lowrank_svd_backward (exact for A of rank k).  Omega (the
+    random starting matrix) takes no gradient."""
+
+    @staticmethod
+    def forward(ctx, A, k, l, iters, Omega, drop_tol=0.0, mode="fp64"):
+        U, S, V, info = lowrank_svd(A, k, l, iters, Omega, drop_tol=drop_tol, mode=mode)
+        ctx.save_for_backward(U, S, V)
+        ctx.mode = "fp64_tc" if mode == "fp64_tc" else "fp64"
+        return U, S, V
+
+    @staticmethod
+    def backward(ctx, gU, gS, gV):
+        U, S, V = ctx.saved_tensors
+        dA = lowrank_svd_backward(U, S, V, dU=gU, dS=gS, dV=gV, mode=ctx.mode)
+        return dA, None, None, None, None, None, None

@@ -1064,6 +1064,118 @@ int backward_entry(const T *A, int64_t m, int64_t n, int64_t lda, const T *S, co
     return err ? TSSVD_ETIMEOUT : TSSVD_OK;
 }
 
+// Adjoint of the rank-k SVD of Algorithm 8 (U m x k, S k, V n x k):
+//   dA = [U | dU] [ (Core - S^-1 K^T) V^T + S^-1 dV^T ; S^-1 V^T ]
+// with J = U^T dU, K = V^T dV and Core the thin adjoint's core (including
+// its -J S^-1 term): the (I - U U^T) and (I - V V^T) projections folded into
+// the k x k core and the k x n right factor, so the only m-sized work is
+// one tall product (m x 2k by 2k x n) and J.
+int lowrank_backward_entry(int64_t m, int64_t n, int64_t k, const double *U, const double *S,
+                           const double *V, const double *dU, const double *dS,
+                           const double *dV, double *dA, tssvd_opts *opts)
+{
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (k < 1 || k > m || k > n || k > 16384) return -3;
+    if (!U) return -4;
+    if (!S) return -5;
+    if (!V) return -6;
+    if (!dA) return -10;
+    if (!opts) return -11;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 kk = k * k, k2 = 2 * k;
+    const int spJ = tn_splits(m, k, k, false);
+    const int spK = tn_splits(n, k, k, false);
+    const int sp = spJ > spK ? spJ : spK;
+    const int gy1 = nn_grid_rows(m, n), gy2 = nn_grid_rows(k, n);
+    const int gy = gy1 > gy2 ? gy1 : gy2;
+    const bool oz = opts->mode == TSSVD_FP64_TC;
+    struct Bufs {
+        double *Ub, *Sd, *sinv, *J, *K, *Mc, *Vtr, *BB, *P, *NP;
+        DevStatus *st;
+        int *er, *emB;
+        uint8_t *big, *bimg;
+    } b;
+    auto carve = [&](Bump &w) {
+        b.st = w.take<DevStatus>(1);
+        if (oz) {
+            b.er = w.take<int>(m);
+            b.emB = w.take<int>(n);
+            b.big = w.take<uint8_t>(oz_row_image_bytes(m, (int)k2));
+            b.bimg = w.take<uint8_t>(oz_image_bytes((int)k2, (int)n));
+        }
+        b.Ub = w.take<double>((size_t)m * k2);
+        b.Sd = w.take<double>(k);
+        b.sinv = w.take<double>(k);
+        b.J = w.take<double>(kk);
+        b.K = w.take<double>(kk);
+        b.Mc = w.take<double>(kk);
+        b.Vtr = w.take<double>((size_t)k * n);
+        b.BB = w.take<double>((size_t)k2 * n);
+        b.P = w.take<double>((size_t)sp * kk);
+        b.NP = w.take<double>((size_t)gy * n);
+    };
+    Bump sz(nullptr, 0);
+    carve(sz);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off + 256);
+    carve(ws);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    auto body = [&]() -> cudaError_t {
+        CK(cudaMemsetAsync(b.st, 0, sizeof(DevStatus), s));
+        CK(cudaMemcpyAsync(b.Sd, S, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+        CK(launch_discard(b.Sd, k, 0.0, b.sinv, nullptr, s));
+        // [U | dU]
+        CK(launch_to_double<double>(U, k, m, k, b.Ub, k2, s));
+        if (dU) {
+            CK(launch_to_double<double>(dU, k, m, k, b.Ub + k, k2, s));
+            CK(launch_tn_partial<double, double>(b.Ub, k2, b.Ub + k, k2, m, k, k, spJ, false, b.P,
+                                                 s));
+            CK(launch_tn_reduce(b.P, spJ, k, k, nullptr, nullptr, false, b.J, k, s));
+        } else {
+            CK(cudaMemset2DAsync(b.Ub + k, sizeof(double) * k2, 0, sizeof(double) * k, m, s));
+        }
+        if (dV) {
+            CK(launch_tn_partial<double, double>(V, k, dV, k, n, k, k, spK, false, b.P, s));
+            CK(launch_tn_reduce(b.P, spK, k, k, nullptr, nullptr, false, b.K, k, s));
+        }
+        CK(launch_adjoint_core(dU ? b.J : nullptr, dV ? b.K : nullptr, b.Sd, dS, k, b.Mc, s));
+        if (dV) CK(launch_core_fix(b.Mc, b.K, b.sinv, k, s));
+        // BB = [Mc V^T + S^-1 dV^T ; S^-1 V^T]  (2k x n)
+        CK(launch_transpose(V, k, n, k, nullptr, b.Vtr, n, s));
+        CK(launch_nn<double, double>(b.Mc, k, b.Vtr, n, k, k, n, b.BB, n, b.NP, s));
+        if (dV) CK(launch_add_scaled_t(dV, k, n, k, b.sinv, b.BB, n, s));
+        CK(launch_transpose(V, k, n, k, b.sinv, b.BB + (size_t)k * n, n, s));
+        // dA = [U | dU] BB
+        if (oz) {
+            CK(launch_oz_rowexp<double>(b.Ub, k2, m, (int)k2, nullptr, b.er, s));
+            CK(launch_oz_row_image<double>(b.Ub, k2, m, (int)k2, nullptr, b.er, b.big, s));
+            CK(launch_oz_image(b.BB, n, (int)k2, (int)n, nullptr, b.emB, b.bimg, s));
+            CK(launch_oz_nn_run<double>(b.big, m, (int)k2, b.er, b.bimg, b.emB, (int)n, dA, n,
+                                        b.st, s));
+        } else {
+            CK(launch_nn<double, double>(b.Ub, k2, b.BB, n, m, k2, n, dA, n, b.NP, s));
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e = body();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    int err = 0;
+    if (cudaMemcpyAsync(&err, &b.st->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    return err ? TSSVD_ETIMEOUT : TSSVD_OK;
+}
+
 }  // namespace
 }  // namespace tssvd
 
@@ -1387,6 +1499,13 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     double *dA, tssvd_opts *opts)
 {
     return backward_entry<double>(A, m, n, lda, S, V, dU, dS, dV, dA, opts);
+}
+
+int lowrank_svd_backward(int64_t m, int64_t n, int64_t k, const double *U, const double *S,
+                         const double *V, const double *dU, const double *dS, const double *dV,
+                         double *dA, tssvd_opts *opts)
+{
+    return lowrank_backward_entry(m, n, k, U, S, V, dU, dS, dV, dA, opts);
 }
 
 int ts_svd_backward_f32(const float *A, int64_t m, int64_t n, int64_t lda, const float *S,

@@ -242,6 +242,11 @@ cudaError_t launch_transpose(const double *src, i64 lds, i64 rows, i64 cols, con
 // n x n core of the thin-SVD adjoint (J, K, dS may be null).
 cudaError_t launch_adjoint_core(const double *J, const double *K, const double *sv,
                                 const double *dS, i64 n, double *M, cudaStream_t s);
+// M[a][b] -= K[b][a] * sinv[a] (k x k).
+cudaError_t launch_core_fix(double *M, const double *K, const double *sinv, i64 k, cudaStream_t s);
+// X[a][j] += sinv[a] * D[j][a] (X k x n, D n x k).
+cudaError_t launch_add_scaled_t(const double *D, i64 ldd, i64 n, i64 k, const double *sinv,
+                                double *X, i64 ldx, cudaStream_t s);
 // Conversions to the output type.
 template <typename T>
 cudaError_t launch_convert(const double *src, i64 lds, i64 rows, i64 cols, T *dst, i64 ldd,

@@ -220,6 +220,30 @@ __global__ void adjoint_core_kernel(const double *J, const double *K, const doub
     }
 }
 
+// M[a][b] -= K[b][a] * sinv[a] (k x k): the -S^-1 K^T term of the rank-k
+// adjoint's core.
+__global__ void core_fix_kernel(double *M, const double *K, const double *sinv, i64 k)
+{
+    const i64 total = k * k;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (i64)gridDim.x * blockDim.x) {
+        const i64 a = e / k, b = e - a * k;
+        M[e] -= K[b * k + a] * sinv[a];
+    }
+}
+
+// X[a][j] += sinv[a] * D[j][a] (X k x n, D n x k): adds S^-1 D^T.
+__global__ void add_scaled_t_kernel(const double *D, i64 ldd, i64 n, i64 k, const double *sinv,
+                                    double *X, i64 ldx)
+{
+    const i64 total = k * n;
+    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (i64)gridDim.x * blockDim.x) {
+        const i64 a = e / n, j = e - a * n;
+        X[a * ldx + j] += sinv[a] * D[j * ldd + a];
+    }
+}
+
 // Every block derives the orientation itself (n exponents: cheap), so one
 // launch both decides and copies.
 __global__ void orient_copy_kernel(const double *d, const int *rank2, const double *R, i64 n,
@@ -262,6 +286,21 @@ cudaError_t launch_orient_copy(const double *d, const int *rank2, const double *
     if (blocks < 1) blocks = 1;
     ProfScope ps_("orient_copy", s);
     orient_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(d, rank2, R, n, X, orient);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_core_fix(double *M, const double *K, const double *sinv, i64 k, cudaStream_t s)
+{
+    ProfScope ps_("core_fix", s);
+    core_fix_kernel<<<grid_for(k * k), 256, 0, s>>>(M, K, sinv, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_scaled_t(const double *D, i64 ldd, i64 n, i64 k, const double *sinv,
+                                double *X, i64 ldx, cudaStream_t s)
+{
+    ProfScope ps_("add_scaled_t", s);
+    add_scaled_t_kernel<<<grid_for(k * n), 256, 0, s>>>(D, ldd, n, k, sinv, X, ldx);
     return cudaGetLastError();
 }
 

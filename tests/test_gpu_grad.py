@@ -130,3 +130,75 @@ def test_backward_fp64_tc_matches_oracle_gradient(orc):
     Af = A.clone().requires_grad_(True)
     _loss(torch, pkg, Af, w, Bm, k).backward()
     assert float((Ag.grad - Af.grad).abs().max()) <= 1e-9 * float(Af.grad.abs().max())
+
+
+# --------------------------------------------------------------------------
+# Rank-k adjoint (lowrank_svd_backward) and the LowRankSVD autograd function
+# --------------------------------------------------------------------------
+
+
+def _factors(m, n, k, seed):
+    rng = np.random.default_rng(seed)
+    U = workloads.orthonormal(m, k, rng)
+    V = workloads.orthonormal(n, k, rng)
+    S = np.linspace(4.0, 1.0, k) + 0.1 * rng.random(k)
+    S = np.sort(S)[::-1].copy()
+    return U, S, V, rng
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+@pytest.mark.parametrize("m,n,k,which", [(3000, 700, 20, "all"), (777, 131, 9, "all"),
+                                         (2000, 300, 16, "dU"), (2000, 300, 16, "dV"),
+                                         (20000, 2000, 50, "all")])
+def test_lowrank_backward_matches_oracle(orc, m, n, k, which, mode):
+    """Element by element against the oracle's adjoint; tolerance 1e-11 of
+    max |dA| (both sides evaluate the same formula in FP64, the GPU with
+    the projections folded into one m x 2k by 2k x n product)."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    U, S, V, rng = _factors(m, n, k, 90 + m % 7)
+    dU = rng.standard_normal((m, k)) if which in ("all", "dU") else None
+    dS = rng.standard_normal(k) if which == "all" else None
+    dV = rng.standard_normal((n, k)) if which in ("all", "dV") else None
+    ref = orc.lowrank_svd_backward(U, S, V, dU=dU, dS=dS, dV=dV)
+    t = lambda x: torch.as_tensor(x, device="cuda") if x is not None else None
+    got = pkg.lowrank_svd_backward(t(U), t(S), t(V), dU=t(dU), dS=t(dS), dV=t(dV), mode=mode)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_lowrank_autograd_finite_differences(mode):
+    """LowRankSVD on A of rank exactly k: autograd's dA against central
+    differences of L = sum_j w_j sigma_j + ||U^T B||_F^2 + ||V^T C||_F^2
+    through LAPACK's truncated SVD, along random directions."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    m, n, k, l = 400, 120, 6, 10
+    U0, S0, V0, rng = _factors(m, n, k, 95)
+    A = (U0 * S0) @ V0.T
+    w = rng.standard_normal(k)
+    Bm = rng.standard_normal((m, 2))
+    Cm = rng.standard_normal((n, 2))
+    Omega = rng.standard_normal((n, l))
+    Ad = torch.tensor(A, device="cuda", requires_grad=True)
+    U, S, V = pkg.LowRankSVD.apply(Ad, k, l, 2, torch.as_tensor(Omega, device="cuda"), 0.0, mode)
+    wd, Bd, Cd = (torch.as_tensor(x, device="cuda") for x in (w, Bm, Cm))
+    L = (wd * S).sum() + ((U.T @ Bd) ** 2).sum() + ((V.T @ Cd) ** 2).sum()
+    L.backward()
+    dA = Ad.grad.cpu().numpy()
+
+    def loss(X):
+        Ux, sx, Vtx = np.linalg.svd(X, full_matrices=False)
+        return float(w @ sx[:k] + np.sum((Ux[:, :k].T @ Bm) ** 2) +
+                     np.sum((Vtx[:k] @ Cm) ** 2))
+
+    for _ in range(3):
+        E = rng.standard_normal((m, n))
+        h = 1e-6
+        fd = (loss(A + h * E) - loss(A - h * E)) / (2 * h)
+        an = float(np.sum(dA * E))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (fd, an)
