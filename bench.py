@@ -194,6 +194,28 @@ def run_reference(args):
 
 # -------------------------------------------------------------- our arm
 
+def max_over_ranks(ms, dev):
+    """The slowest rank's time (the whole job's), by an all-reduce over the
+    process group when there is more than one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_rank, world, ms_max):
+    """Whole-job throughput: the work of every rank over the slowest rank's
+    time (replicas: each rank runs its own instance of the workload)."""
+    return flops_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
+def replica_seed(base, rank):
+    """Input seed of a rank's replica (distinct inputs per rank)."""
+    return base + 1000 * rank
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -215,7 +237,7 @@ def run_ours(args):
     # input A = U diag(sigma) V^T, built on the device (torch QR of seeded
     # Gaussians); each rank its own replica seed
     sigma = workloads.sigma_geometric(n, w["lo"])
-    A, U0, s0, V0 = workloads.known_spectrum_torch(m, n, sigma, w["seed"] + 1000 * rank, dev)
+    A, U0, s0, V0 = workloads.known_spectrum_torch(m, n, sigma, replica_seed(w["seed"], rank), dev)
     del U0, V0
     U = torch.empty((m, n), dtype=torch.float64, device=dev)
     S = torch.empty((n,), dtype=torch.float64, device=dev)
@@ -256,12 +278,9 @@ def run_ours(args):
     L.tssvd_profile_enable(0)
     kernels = read_profile(L)
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dev)
     flops = nominal_flops(w)
-    value = flops * world / (ms_max * 1e-3) / 1e9
+    value = job_gflops(flops, world, ms_max)
 
     # accuracy of the last result (outside the timed region)
     with torch.no_grad():
@@ -330,12 +349,10 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e = f0.elapsed_time(f1) / args.e2e_steps
-        te = torch.tensor([ms_e], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": flops * world / (float(te.item()) * 1e-3) / 1e9, "unit": "GFLOP/s",
+        ms_e = max_over_ranks(ms_e, dev)
+        e2e = {"value": job_gflops(flops, world, ms_e), "unit": "GFLOP/s",
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (m * n + n + n * n) * 8,
-               "ms_per_step": float(te.item())}
+               "ms_per_step": ms_e}
         del Ah, Uh, Sh, Vh, Ad
 
     # roofline of the dominant kernel (largest total event time in the
