@@ -79,6 +79,10 @@ int nn_grid_rows(i64 m, i64 N);
 // g < colsumsq_rows(m, n); sum them with launch_norms_reduce.
 int colsumsq_rows(i64 m, i64 n);
 cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, cudaStream_t s);
+// launch_colmax streams whole rows when n <= 32 * kColStatMaxCh, with
+// colstat_blocks(m, n) blocks (0 when n is larger).
+constexpr int kColStatMaxCh = 16;
+int colstat_blocks(i64 m, i64 n);
 // Column means mu = A^T 1 / m (FP64 sums of the deviations from the first
 // row, rounded once to T): P holds colsum_rows(m, n) * n doubles of
 // partials.

@@ -313,16 +313,107 @@ __global__ void norms_reduce_kernel(const double *__restrict__ NP, int g, i64 N,
     out[j] = sqrt(s);
 }
 
+// Row-streaming column maxima (n <= 32 * 16): every warp reads whole rows,
+// which are contiguous, and lane l keeps the maxima of columns l + 32 c in
+// registers, so a warp has 2 * NCH independent loads in flight per step
+// whatever n is.  Warps take interleaved rows of the block's range; the
+// block's maxima (|x| as bit patterns, integer compares only) go to bits
+// by atomicMax.  (Column sums stay on the column-strip kernels: they need
+// FP64 operations per element, which bound them above the HBM time on this
+// part, and those kernels keep more warps resident to issue them.)
+template <typename T, int NCH>
+__global__ void __launch_bounds__(256) colmax_rows_kernel(const T *__restrict__ A, i64 lda, i64 m,
+                                                          int n, i64 rows_per,
+                                                          unsigned long long *__restrict__ bits)
+{
+    __shared__ unsigned long long red[8][32 * NCH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const i64 r0 = (i64)blockIdx.x * rows_per;
+    const i64 r1 = r0 + rows_per < m ? r0 + rows_per : m;
+    unsigned long long mx[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; c++) mx[c] = 0ull;
+    i64 r = r0 + warp;
+    for (; r + 8 < r1; r += 16) {
+        const T *a0 = A + r * lda, *a1 = a0 + 8 * lda;
+        T v0[NCH], v1[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+            const int col = lane + 32 * c;
+            v0[c] = col < n ? a0[col] : (T)0;
+            v1[c] = col < n ? a1[col] : (T)0;
+        }
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+            const unsigned long long b0 = abs_bits(v0[c]), b1 = abs_bits(v1[c]);
+            const unsigned long long b = b0 > b1 ? b0 : b1;
+            mx[c] = b > mx[c] ? b : mx[c];
+        }
+    }
+    if (r < r1) {
+        const T *a0 = A + r * lda;
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+            const int col = lane + 32 * c;
+            const unsigned long long b = abs_bits(col < n ? a0[col] : (T)0);
+            mx[c] = b > mx[c] ? b : mx[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; c++) red[warp][lane + 32 * c] = mx[c];
+    __syncthreads();
+    for (int col = threadIdx.x; col < n; col += 256) {
+        unsigned long long v = 0ull;
+        for (int w = 0; w < 8; w++) v = red[w][col] > v ? red[w][col] : v;
+        atomicMax(bits + col, v);
+    }
+}
+
 inline int ceil_div_i(i64 a, i64 b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
 // ------------------------------------------------------------ launchers
 
+int colstat_blocks(i64 m, i64 n)
+{
+    if (n > 32 * kColStatMaxCh) return 0;
+    // three 256-thread blocks per SM stay resident at up to 85 registers
+    // (n <= 256), one wave
+    i64 g = (i64)num_sms() * 3;
+    const i64 cap = (m + 63) / 64;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+template <typename T>
+cudaError_t launch_colmax_rows(const T *A, i64 lda, i64 m, i64 n, unsigned long long *bits,
+                               cudaStream_t s)
+{
+    const int g = colstat_blocks(m, n);
+    const i64 rows_per = (m + g - 1) / g;
+    const int nch = (int)((n + 31) / 32);
+    ProfScope ps_("colmax", s);
+#define TSSVD_COLMAX(NC) colmax_rows_kernel<T, NC><<<g, 256, 0, s>>>(A, lda, m, (int)n, rows_per, bits)
+    if (nch <= 1)
+        TSSVD_COLMAX(1);
+    else if (nch <= 2)
+        TSSVD_COLMAX(2);
+    else if (nch <= 4)
+        TSSVD_COLMAX(4);
+    else if (nch <= 8)
+        TSSVD_COLMAX(8);
+    else
+        TSSVD_COLMAX(16);
+#undef TSSVD_COLMAX
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_colmax(const T *A, i64 m, i64 n, i64 lda, unsigned long long *bits,
                           cudaStream_t s)
 {
+    if (n <= 32 * kColStatMaxCh) return launch_colmax_rows<T>(A, lda, m, n, bits, s);
     const int cx = ceil_div_i(n, 32);
     i64 target = (i64)num_sms() * 8;
     i64 ry = target / cx;
