@@ -342,24 +342,56 @@ __global__ void oz_gram_image_kernel(const T *__restrict__ X, i64 ldx, i64 m, in
 {
     const int npad = gram_npad(n);
     const i64 nkb = (m + kBK - 1) / kBK;
-    const i64 total = nkb * (kBK / 8) * npad;
-    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (i64)gridDim.x * blockDim.x) {
-        const int c = (int)(e % npad);
-        const int q = (int)((e / npad) % (kBK / 8));
-        const i64 kb = e / ((i64)npad * (kBK / 8));
-        const int ec = c < n ? ex[c] : 0;
-        uint32_t d[8][kDig];
+    const i64 ngrp = nkb * (kBK / 8);  // 8-row groups
+    // (c, group) walk: one 32-bit division per step while the group index
+    // fits, the carry form of it afterwards
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 e0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    i64 g = e0 / npad;
+    int c = (int)(e0 - g * npad);
+    const i64 gstep = stride / npad;
+    const int cstep = (int)(stride - gstep * npad);
+    static_assert(kBK / 8 == 4, "four 8-row groups per block");
+    // the next step's eight values are loaded before this step's digits are
+    // formed, so every thread keeps a group of loads in flight
+    auto load8 = [&](i64 gg, int cc, T (&v)[8]) {
+        const i64 k0 = (gg >> 2) * kBK + 8 * (int)(gg & 3);
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-            const i64 k = kb * kBK + 8 * q + r;
-            const T v = (c < n && k < m) ? X[k * ldx + c] : (T)0;
-            digits7(v, ec, 0, d[r]);
+        for (int r = 0; r < 8; r++)
+            v[r] = (cc < n && k0 + r < m) ? X[(k0 + r) * ldx + cc] : (T)0;
+    };
+    T cur[8];
+    if (g < ngrp) load8(g, c, cur);
+    const uint32_t half = (uint32_t)npad * 32;
+    while (g < ngrp) {
+        i64 gn = g + gstep;
+        int cn = c + cstep;
+        if (cn >= npad) {
+            cn -= npad;
+            gn++;
         }
-        const uint32_t half = (uint32_t)npad * 32;
+        T nxt[8];
+        if (gn < ngrp) load8(gn, cn, nxt);
+        const int q = (int)(g & 3);
+        const i64 kb = g >> 2;
         uint8_t *base = img + (size_t)kb * kDig * 2 * half + (size_t)(q >> 1) * half;
         const uint32_t off = (uint32_t)(c >> 3) * 256 + (uint32_t)(q & 1) * 128 + (uint32_t)(c & 7) * 16;
-        store_digits8(base, 2 * half, off, d);
+        if (c < n) {
+            const int ec = ex[c];
+            uint32_t d[8][kDig];
+#pragma unroll
+            for (int r = 0; r < 8; r++) digits7(cur[r], ec, 0, d[r]);
+            store_digits8(base, 2 * half, off, d);
+        } else {
+            // padding columns: all digits zero
+#pragma unroll
+            for (int sd = 0; sd < kDig; sd++)
+                *reinterpret_cast<uint4 *>(base + (size_t)sd * 2 * half + off) = make_uint4(0, 0, 0, 0);
+        }
+        g = gn;
+        c = cn;
+#pragma unroll
+        for (int r = 0; r < 8; r++) cur[r] = nxt[r];
     }
 }
 
@@ -372,25 +404,53 @@ __global__ void oz_row_image_kernel(const T *__restrict__ A, i64 lda, i64 m, int
 {
     const int KP = (K + 15) / 16 * 16;
     const int nkb = (KP + kBK - 1) / kBK;
-    const i64 total = (m + 127) / 128 * 128 * nkb * (kBK / 8);
-    for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (i64)gridDim.x * blockDim.x) {
-        const int q = (int)(e % (kBK / 8));
-        const i64 row = (e / (kBK / 8)) % ((m + 127) / 128 * 128);
-        const int kb = (int)(e / ((kBK / 8) * ((m + 127) / 128 * 128)));
+    const i64 mpad = (m + 127) / 128 * 128;
+    // e = (kb * mpad + row) * 4 + q; the stride is a multiple of 4, so q
+    // is fixed per thread and (kb, row) advance by carries, not divisions
+    static_assert(kBK / 8 == 4, "four 8-deep groups per k block");
+    const i64 stride4 = (i64)gridDim.x * blockDim.x / 4;
+    const i64 e0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (int)(e0 & 3);
+    const i64 g0 = e0 >> 2;
+    int kb = (int)(g0 / mpad);
+    i64 row = g0 - (i64)kb * mpad;
+    const int kstep = (int)(stride4 / mpad);
+    const i64 rstep = stride4 - (i64)kstep * mpad;
+    // the next step's eight values are loaded before this step's digits
+    auto load8 = [&](int kk, i64 rr, T (&v)[8]) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = kk * kBK + 8 * q + u;
+            v[u] = (rr < m && k < K) ? A[rr * lda + k] : (T)0;
+        }
+    };
+    T cur[8];
+    if (kb < nkb) load8(kb, row, cur);
+    while (kb < nkb) {
+        i64 rn = row + rstep;
+        int kn = kb + kstep;
+        if (rn >= mpad) {
+            rn -= mpad;
+            kn++;
+        }
+        T nxt[8];
+        if (kn < nkb) load8(kn, rn, nxt);
         const int ei = row < m ? er[row] : 0;
         uint32_t d[8][kDig];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             const int k = kb * kBK + 8 * q + u;
-            const bool in = row < m && k < K;
-            digits7(in ? A[row * lda + k] : (T)0, ei, (in && pk) ? pk[k] : 0, d[u]);
+            digits7(cur[u], ei, (pk && k < K) ? pk[k] : 0, d[u]);
         }
         const i64 rt = row >> 7;
         const int r = (int)(row & 127);
         uint8_t *base = img + ((size_t)rt * nkb + kb) * kDig * kATerm + (size_t)(q >> 1) * (kATerm / 2);
         const uint32_t off = (uint32_t)(r >> 3) * 256 + (uint32_t)(q & 1) * 128 + (uint32_t)(r & 7) * 16;
         store_digits8(base, kATerm, off, d);
+        row = rn;
+        kb = kn;
+#pragma unroll
+        for (int u = 0; u < 8; u++) cur[u] = nxt[u];
     }
 }
 
