@@ -667,9 +667,13 @@ def run_grad(args):
     L_ = pkg.lib()
     clocks = ClockSampler(0)
     clocks.start()
+    L_.tssvd_profile_enable(1)
+    L_.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
     n0 = L_.tssvd_launch_count()
     ms = _timed(torch, step, args.steps)
     launches = L_.tssvd_launch_count() - n0
+    L_.tssvd_profile_enable(0)
+    kernels = read_profile(L_)
     clk = clocks.stop()
     st = torch.as_tensor(s, device=dev)
     U = out["U"].double()
@@ -684,7 +688,8 @@ def run_grad(args):
            "gpu_launches": int(launches), "clocks": clk,
            "accuracy": {"sigma_err_normwise": float((out["S"].double() - st).abs().max() / st[0]),
                         "orth_U": float((U.T @ U - torch.eye(n, dtype=U.dtype, device=dev)).abs().max()),
-                        "grad_norm": float(out["G"].double().norm())}}
+                        "grad_norm": float(out["G"].double().norm())},
+           "kernels_ms": kernels}
     print(json.dumps(res), flush=True)
 
 

@@ -187,10 +187,10 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
 // the one-barrier-per-round form, or NULL for the two-barrier in-place
 // form; either way B's contents are consumed.  prm: scratch of
 // 4 * ceil(n/2) + 2 doubles; perm: n ints; ctr as for launch_jacobi.
-// normwise (one-barrier form only): a pair rotates only when |b_PQ| also
-// exceeds tol times the largest diagonal entry (refreshed each sweep), the
-// normwise stopping rule used for the first Gram eigensolve of the
-// two-pass algorithm.
+// normwise (one-barrier forms only): a pair rotates only when |b_PQ| also
+// exceeds 2^-52 times the largest diagonal entry (refreshed each sweep),
+// i.e. is above the rounding already in B; used for the first Gram
+// eigensolve of the two-pass algorithm.
 cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv, double *lam,
                               double *Vout, i64 ldvo, int n, int max_sweeps, int *ctr, double *prm,
                               int *perm, DevStatus *st, int which, cudaStream_t s,

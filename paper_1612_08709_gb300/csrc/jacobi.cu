@@ -507,7 +507,7 @@ struct EigArgs {
     double4 *prm;  // [npairs] (c, s, t, rotate)
     double *diag;  // [n] diagonal of the final B (single-barrier form)
     int n, npad;
-    int normwise;  // 1: rotate only when also |b_PQ| > tol * max_k b_kk
+    int normwise;  // 1: rotate only when also |b_PQ| > 2^-52 max_k b_kk
     int max_sweeps;
     double tol;
     int *rot;
@@ -564,9 +564,12 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
     double *Bn = p.B2;
     const int tid = threadIdx.x;
     const float log2tol = log2f((float)p.tol);
-    // Normwise floor: tol times the largest diagonal entry, taken from the
-    // diagonals every CTA loads as rotation inputs (the same values in every
-    // CTA, so all agree on the floor), refreshed once per sweep.
+    // Normwise floor: one unit of FP64 rounding (2^-52) of the largest
+    // diagonal entry, the level below which B's entries carry no
+    // information (they were formed with rounding errors of at least that
+    // size).  Taken from the diagonals every CTA loads as rotation inputs
+    // (the same values in every CTA, so all agree on the floor), refreshed
+    // once per sweep.
     __shared__ double dmax_s[NT / 32];
     double dmx = 0.0, gmin = 0.0;
     if (p.normwise) {
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(NT) jacobi_eig1_kernel(EigArgs p)
             __syncthreads();
             double m = 0.0;
             for (int w = 0; w < NT / 32; w++) m = fmax(m, dmax_s[w]);
-            gmin = p.tol * m;
+            gmin = 0x1p-52 * m;
             dmx = 0.0;
             __syncthreads();  // dmax_s is rewritten next sweep
         }
@@ -897,7 +900,7 @@ __global__ void __launch_bounds__(NT) jacobi_eig2r_kernel(EigArgs p)
             __syncthreads();
             double m = 0.0;
             for (int w = 0; w < NT / 32; w++) m = fmax(m, dmax_s[w]);
-            gmin = p.tol * m;
+            gmin = 0x1p-52 * m;
             dmx = 0.0;
             __syncthreads();
         }
@@ -1434,7 +1437,9 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         const size_t vs_bytes = sizeof(double4) * (size_t)npairs0 +
                                 sizeof(double) * (size_t)((n + b0 - 1) / b0) * n;
         const bool vs = single && vs_bytes <= kRowsSmemMax;
-        // two rounds per barrier: one CTA per pair (all resident), V by rows
+        // two rounds per barrier: one CTA per pair, each on its own SM (with
+        // two CTAs per SM the doubled FP64 work of a round outweighs the
+        // saved barrier: measured at n = 512), V by rows
         const size_t two_bytes = sizeof(double4) * 2 * (size_t)npairs0 +
                                  sizeof(double) * (size_t)(npad + npairs0) +
                                  sizeof(double) * (size_t)((n + npairs0 - 1) / npairs0) * n;
@@ -1449,7 +1454,7 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k2, NT, two_bytes)) !=
                 cudaSuccess)
                 return e;
-            two = (i64)per_sm2 * num_sms() >= npairs0;
+            two = npairs0 <= num_sms() && (i64)per_sm2 * num_sms() >= npairs0;
         }
         const void *kern = two      ? (const void *)jacobi_eig2r_kernel<NT>
                            : !single ? (const void *)jacobi_eig_kernel<NT>
