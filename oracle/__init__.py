@@ -37,6 +37,11 @@ def lib():
         L.or_ts_svd2.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_int, _dp, _i64, _dp, _dp, _i64, _lp, _lp]
         L.or_ts_svd2.restype = ctypes.c_int
+        L.or_mixing.argtypes = [_i64, _dp, _dp, _lp, _lp, _dp]
+        L.or_householder_qr.argtypes = [_dp, _i64, _i64, _i64, _dp, _i64, _dp, _i64]
+        L.or_ts_svd_tsqr.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_double, _dp,
+                                     _dp, _lp, _lp, ctypes.c_int, _dp, _i64, _dp, _dp, _i64, _lp]
+        L.or_ts_svd_tsqr.restype = ctypes.c_int
         L.or_col_means.argtypes = [_dp, _i64, _i64, _i64, _dp]
         L.or_pca.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, _dp, _dp, _i64, _dp, _dp, _i64, _lp]
@@ -162,6 +167,45 @@ def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, max_sweeps=MAX_SWEE
     if return_diag:
         return out + ((diag[0], diag[1]),)
     return out
+
+
+def _ip(a):
+    return a.ctypes.data_as(_lp)
+
+
+def mixing(theta1, theta2, perm1, perm2):
+    """Real 2h x 2h matrix of Remark "randomness"'s Omega = D F S D~ F S~."""
+    t1, t2 = _c(theta1), _c(theta2)
+    p1 = np.ascontiguousarray(perm1, dtype=np.int64)
+    p2 = np.ascontiguousarray(perm2, dtype=np.int64)
+    h = len(t1)
+    O = np.zeros((2 * h, 2 * h))
+    lib().or_mixing(h, _p(t1), _p(t2), _ip(p1), _ip(p2), _p(O))
+    return O
+
+
+def householder_qr(X):
+    X = _c(X)
+    m, n = X.shape
+    Q = np.zeros((m, n)); R = np.zeros((n, n))
+    lib().or_householder_qr(_p(X), m, n, n, _p(Q), n, _p(R), n)
+    return Q, R
+
+
+def ts_svd_tsqr(A, mix, passes=2, wp=PAPER_DROP_TOL ** 2, max_sweeps=MAX_SWEEPS):
+    """Algorithm 1 (passes=1) or 2 (passes=2): (U, S, V, rank, status).
+    mix = (theta1, theta2, perm1, perm2), each of length h = ceil(n / 2)."""
+    A = _c(A)
+    m, n = A.shape
+    t1, t2 = _c(mix[0]), _c(mix[1])
+    p1 = np.ascontiguousarray(mix[2], dtype=np.int64)
+    p2 = np.ascontiguousarray(mix[3], dtype=np.int64)
+    U = np.zeros((m, n)); S = np.zeros(n); V = np.zeros((n, n))
+    r = ctypes.c_int64(0)
+    st = lib().or_ts_svd_tsqr(_p(A), m, n, n, int(passes), float(wp), _p(t1), _p(t2), _ip(p1),
+                              _ip(p2), int(max_sweeps), _p(U), n, _p(S), _p(V), n,
+                              ctypes.byref(r))
+    return U, S, V, r.value, st
 
 
 def col_means(A):

@@ -606,6 +606,227 @@ int or_ts_svd2(const double *A, i64 m, i64 n, i64 lda, int scale,
 }
 
 /* ------------------------------------------------------------------ */
+/* Algorithms 1 and 2: randomized TS-SVD via TSQR (Remark "randomness") */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The random orthogonal mixing of Remark "randomness",
+ * Omega = D F S D~ F S~ on C^h: D = diag(exp(i th1)), D~ = diag(exp(i th2)),
+ * F the unitary DFT ((F x)_a = sum_b x_b exp(-2 pi i a b / h) / sqrt(h)),
+ * (S x)_a = x_{p1[a]}, (S~ x)_a = x_{p2[a]}.  A real vector of length 2h
+ * is read as h complex numbers (x_{2k} + i x_{2k+1}); O (2h x 2h, row
+ * major) is the real matrix of Omega in that reading:
+ *   O[2j][2k] = Re w, O[2j][2k+1] = -Im w, O[2j+1][2k] = Im w,
+ *   O[2j+1][2k+1] = Re w, with w = Omega_jk.
+ * Column k of Omega is Omega applied to e_k, step by step.
+ */
+static void or_dft(const double *xr, const double *xi, i64 h, double *yr, double *yi)
+{
+    const double pi = 3.14159265358979323846, sc = 1.0 / sqrt((double)h);
+    for (i64 a = 0; a < h; a++) {
+        double sr = 0.0, si = 0.0;
+        for (i64 b = 0; b < h; b++) {
+            const double ang = -2.0 * pi * (double)((a * b) % h) / (double)h;
+            const double c = cos(ang), sn = sin(ang);
+            sr += xr[b] * c - xi[b] * sn;
+            si += xr[b] * sn + xi[b] * c;
+        }
+        yr[a] = sr * sc;
+        yi[a] = si * sc;
+    }
+}
+
+void or_mixing(i64 h, const double *th1, const double *th2, const i64 *p1, const i64 *p2,
+               double *O)
+{
+    double *xr = dalloc(h), *xi = dalloc(h), *yr = dalloc(h), *yi = dalloc(h);
+    const i64 n2 = 2 * h;
+    for (i64 k = 0; k < h; k++) {
+        /* S~ e_k */
+        for (i64 a = 0; a < h; a++) {
+            xr[a] = (p2[a] == k) ? 1.0 : 0.0;
+            xi[a] = 0.0;
+        }
+        or_dft(xr, xi, h, yr, yi); /* F */
+        for (i64 a = 0; a < h; a++) { /* D~ */
+            const double c = cos(th2[a]), sn = sin(th2[a]);
+            const double r = yr[a] * c - yi[a] * sn, im = yr[a] * sn + yi[a] * c;
+            yr[a] = r;
+            yi[a] = im;
+        }
+        for (i64 a = 0; a < h; a++) { /* S */
+            xr[a] = yr[p1[a]];
+            xi[a] = yi[p1[a]];
+        }
+        or_dft(xr, xi, h, yr, yi); /* F */
+        for (i64 j = 0; j < h; j++) { /* D, then the real 2 x 2 blocks */
+            const double c = cos(th1[j]), sn = sin(th1[j]);
+            const double wr = yr[j] * c - yi[j] * sn, wi = yr[j] * sn + yi[j] * c;
+            O[(2 * j) * n2 + 2 * k] = wr;
+            O[(2 * j) * n2 + 2 * k + 1] = -wi;
+            O[(2 * j + 1) * n2 + 2 * k] = wi;
+            O[(2 * j + 1) * n2 + 2 * k + 1] = wr;
+        }
+    }
+    free(xr);
+    free(xi);
+    free(yr);
+    free(yi);
+}
+
+/* sqrt(sum x_i^2) with scaling, so that neither overflows nor underflows. */
+static double scaled_norm(const double *x, i64 cnt, i64 stride)
+{
+    double mx = 0.0;
+    for (i64 i = 0; i < cnt; i++)
+        if (fabs(x[i * stride]) > mx) mx = fabs(x[i * stride]);
+    if (mx == 0.0) return 0.0;
+    double ss = 0.0;
+    for (i64 i = 0; i < cnt; i++) {
+        const double t = x[i * stride] / mx;
+        ss += t * t;
+    }
+    return mx * sqrt(ss);
+}
+
+/*
+ * Householder QR of X (m x n, ldx, m >= n): X = Q R with Q (m x n, ldq)
+ * orthonormal and R (n x n, ldr) upper triangular.  Reflection j is
+ * H_j = I - tau_j v v^T with v_j = 1, chosen so that H_j maps column j
+ * (rows j..m-1) onto beta e_j, beta = -sign(x_jj) |x|; a column that is
+ * already zero below and on the diagonal takes H_j = I.  Q is formed by
+ * applying the reflections to [I; 0] in reverse order.
+ */
+void or_householder_qr(const double *X, i64 m, i64 n, i64 ldx, double *Q, i64 ldq, double *R,
+                       i64 ldr)
+{
+    double *W = dalloc(m * n), *tau = dalloc(n);
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) W[i * n + j] = X[i * ldx + j];
+    for (i64 j = 0; j < n; j++) {
+        const double alpha = W[j * n + j];
+        const double xn = (j + 1 < m) ? scaled_norm(W + (j + 1) * n + j, m - j - 1, n) : 0.0;
+        if (xn == 0.0) {
+            tau[j] = 0.0;
+            continue;
+        }
+        const double beta = -copysign(hypot(alpha, xn), alpha);
+        tau[j] = (beta - alpha) / beta;
+        const double sc = 1.0 / (alpha - beta);
+        for (i64 i = j + 1; i < m; i++) W[i * n + j] *= sc;
+        W[j * n + j] = beta;
+        for (i64 c = j + 1; c < n; c++) {
+            double w = W[j * n + c];
+            for (i64 i = j + 1; i < m; i++) w += W[i * n + j] * W[i * n + c];
+            W[j * n + c] -= tau[j] * w;
+            for (i64 i = j + 1; i < m; i++) W[i * n + c] -= tau[j] * W[i * n + j] * w;
+        }
+    }
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) R[i * ldr + j] = (j >= i) ? W[i * n + j] : 0.0;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) Q[i * ldq + j] = (i == j) ? 1.0 : 0.0;
+    for (i64 j = n - 1; j >= 0; j--) {
+        if (tau[j] == 0.0) continue;
+        for (i64 c = j; c < n; c++) {
+            double w = Q[j * ldq + c];
+            for (i64 i = j + 1; i < m; i++) w += W[i * n + j] * Q[i * ldq + c];
+            Q[j * ldq + c] -= tau[j] * w;
+            for (i64 i = j + 1; i < m; i++) Q[i * ldq + c] -= tau[j] * W[i * n + j] * w;
+        }
+    }
+    free(W);
+    free(tau);
+}
+
+/* The discard step of Algorithms 1 and 2: row j of R (n x n) is dropped,
+ * with column j of Q (m x n), when |R_jj| is below |R_00| times the working
+ * precision wp (or is zero); dropped rows and columns become zero. */
+static void tsqr_discard(double *Q, i64 m, double *R, i64 n, double wp)
+{
+    const double thr = fabs(R[0]) * wp;
+    for (i64 j = 0; j < n; j++) {
+        const double d = fabs(R[j * n + j]);
+        if (d > 0.0 && !(d < thr)) continue;
+        for (i64 c = 0; c < n; c++) R[j * n + c] = 0.0;
+        for (i64 i = 0; i < m; i++) Q[i * n + j] = 0.0;
+    }
+}
+
+/*
+ * Algorithm 1 (passes = 1) or Algorithm 2 (passes = 2) on A (m x n, lda):
+ * B* = A Omega* (each row of A mixed by O; n odd is padded with a zero
+ * column to n' = n + 1), B* = Q R by Householder QR (TSQR computes the
+ * same factorization up to the signs of R's rows), discard, [Q = Q2 R2,
+ * discard, T = R2 R], SVD of T (or R) = U~ Sigma V~^T by one-sided Jacobi
+ * on its transpose's columns, U = Q U~, V = O^T V~ (first n rows).
+ * Returns the leading n triplets; status as or_ts_svd2.
+ */
+int or_ts_svd_tsqr(const double *A, i64 m, i64 n, i64 lda, int passes, double wp,
+                   const double *th1, const double *th2, const i64 *p1, const i64 *p2,
+                   int max_sweeps, double *U, i64 ldu, double *S, double *V, i64 ldv,
+                   i64 *rank)
+{
+    const i64 np = n + (n & 1), h = np / 2;
+    int status = OR_OK;
+    double *O = dalloc(np * np), *Bs = dalloc(m * np), *Q1 = dalloc(m * np);
+    double *R1 = dalloc(np * np), *T = dalloc(np * np), *Tt = dalloc(np * np);
+    double *J = dalloc(np * np), *sg = dalloc(np), *Uf = dalloc(m * np);
+    or_mixing(h, th1, th2, p1, p2, O);
+    /* B* = A_pad O^T: row i of B* is O applied to row i of A */
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < np; j++) {
+            double acc = 0.0;
+            for (i64 k = 0; k < n; k++) acc += A[i * lda + k] * O[j * np + k];
+            Bs[i * np + j] = acc;
+        }
+    or_householder_qr(Bs, m, np, np, Q1, np, R1, np);
+    tsqr_discard(Q1, m, R1, np, wp);
+    double *Qf = Q1;
+    double *Q2 = NULL, *R2 = NULL;
+    if (passes == 2) {
+        Q2 = dalloc(m * np);
+        R2 = dalloc(np * np);
+        or_householder_qr(Q1, m, np, np, Q2, np, R2, np);
+        tsqr_discard(Q2, m, R2, np, wp);
+        for (i64 i = 0; i < np; i++)
+            for (i64 j = 0; j < np; j++) {
+                double acc = 0.0;
+                for (i64 k = 0; k < np; k++) acc += R2[i * np + k] * R1[k * np + j];
+                T[i * np + j] = acc;
+            }
+        Qf = Q2;
+    } else {
+        memcpy(T, R1, sizeof(double) * np * np);
+    }
+    /* T = J Sigma (X / Sigma)^T from one-sided Jacobi on the columns of T^T */
+    for (i64 i = 0; i < np; i++)
+        for (i64 j = 0; j < np; j++) Tt[j * np + i] = T[i * np + j];
+    if (or_jacobi(Tt, np, np, np, J, np, sg, max_sweeps) < 0) status = OR_ENOCONV;
+    /* U = Qf J, V = O^T (X / Sigma) */
+    or_matmul(Qf, m, np, np, J, np, np, Uf, np);
+    i64 r = 0;
+    for (i64 j = 0; j < n; j++)
+        if (sg[j] > 0.0) r = j + 1;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < n; j++) U[i * ldu + j] = (j < r) ? Uf[i * np + j] : 0.0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < n; j++) {
+            double acc = 0.0;
+            if (j < r)
+                for (i64 k = 0; k < np; k++) acc += O[k * np + i] * Tt[k * np + j] / sg[j];
+            V[i * ldv + j] = acc;
+        }
+    for (i64 j = 0; j < n; j++) S[j] = (j < r) ? sg[j] : 0.0;
+    canonical_signs(U, m, ldu, V, n, ldv, r);
+    *rank = r;
+    if (status == OR_OK && r < n) status = OR_RANKDEF;
+    free(O); free(Bs); free(Q1); free(R1); free(T); free(Tt); free(J); free(sg); free(Uf);
+    free(Q2); free(R2);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* PCA (abstract, problem 1): SVD of the column-centred matrix.         */
 /* ------------------------------------------------------------------ */
 

@@ -1031,7 +1031,10 @@ __global__ void __launch_bounds__(NT) jacobi_eig2r_kernel(EigArgs p)
                 const double c = me.x, s = me.y;
                 double *nP = Bn + (i64)PB * ldb;
                 double *nQ = hasQB ? Bn + (i64)QB * ldb : nullptr;
-                if (tid == 0) {
+                // the pair's own 2 x 2 block, by the last thread: with
+                // npairs <= 152 it has no off-diagonal block (those go to
+                // threads 0 .. npairs/2 - 1), so this work is off their path
+                if (tid == NT - 1) {
                     const double a = d1_s[PB];
                     if (hasQB) {
                         const double b = d1_s[QB], g = g1_s[prB];

@@ -615,3 +615,89 @@ def test_lowrank_backward_closed_forms(orc):
     thin = orc.ts_svd_backward(B, S, V, dU=dU, dS=w[:2].tolist() + [0.0] * 5, dV=dV)
     rk = orc.lowrank_svd_backward(U, S, V, dU=dU, dS=w[:2].tolist() + [0.0] * 5, dV=dV)
     assert np.abs(thin - rk).max() <= 1e-12 * np.abs(thin).max()
+
+
+# --------------------------------------------------------------------------
+# Algorithms 1 and 2 (TSQR with the random mixing of Remark "randomness")
+# --------------------------------------------------------------------------
+
+
+def test_mixing_matches_fft_chain(orc):
+    """O is Omega = D F S D~ F S~ on pairs of reals read as complex
+    numbers: numpy's FFT (unitary scaling), phases and permutations applied
+    in that order reproduce O x; O is orthogonal."""
+    for n, seed in ((10, 1), (64, 2), (7, 3)):
+        t1, t2, p1, p2 = workloads.mixing_draws(n, seed)
+        h = len(t1)
+        O = orc.mixing(t1, t2, p1, p2)
+        assert np.abs(O.T @ O - np.eye(2 * h)).max() < 1e-14
+        x = np.random.default_rng(seed + 10).standard_normal(2 * h)
+        z = x[0::2] + 1j * x[1::2]
+        z = np.fft.fft(z[p2]) / np.sqrt(h) * np.exp(1j * t2)
+        z = np.fft.fft(z[p1]) / np.sqrt(h) * np.exp(1j * t1)
+        y = np.empty(2 * h)
+        y[0::2], y[1::2] = z.real, z.imag
+        assert np.abs(O @ x - y).max() < 1e-13
+
+
+def test_householder_qr_against_lapack(orc):
+    """X = Q R, Q orthonormal, R upper triangular; R equals LAPACK's up to
+    the signs of its rows (the factorization is unique up to them)."""
+    X = np.random.default_rng(83).standard_normal((120, 17))
+    Q, R = orc.householder_qr(X)
+    assert np.abs(Q @ R - X).max() < 1e-13
+    assert np.abs(Q.T @ Q - np.eye(17)).max() < 1e-14
+    assert not np.tril(R, -1).any()
+    Rl = np.linalg.qr(X, mode="r")
+    sg = np.sign(np.diag(R)) * np.sign(np.diag(Rl))
+    assert np.abs(R - sg[:, None] * Rl).max() < 1e-12
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("m,n,seed", [(300, 9, 84), (500, 24, 85)])
+def test_tsqr_svd_against_lapack(orc, passes, m, n, seed):
+    """Algorithms 1 and 2 on a known spectrum (odd and even n): singular
+    values within 1e-13 of the construction, vectors within the gap-scaled
+    bound, U and V orthonormal."""
+    s0 = np.linspace(3.0, 1.0, n)
+    A, U0, s0, V0 = workloads.known_spectrum(m, n, s0, seed)
+    U, S, V, r, st = orc.ts_svd_tsqr(A, workloads.mixing_draws(n, seed), passes=passes)
+    assert r == n and st == 0
+    assert np.abs(S - s0).max() <= 1e-13 * s0[0]
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-13
+    assert match_columns_up_to_sign(V, V0) <= 1e-11
+    assert match_columns_up_to_sign(U, U0) <= 1e-11
+
+
+def test_tsqr_on_the_paper_matrix(orc):
+    """The paper's test matrix (DCT U, V; sigma to 1e-20) with the working
+    precision 1e-11: the discard of R's diagonal leaves a spectral error
+    near the singular values below 1e-11 (the tall-skinny tables report
+    9.76e-12 for Algorithms 1 and 2), and U is orthonormal near the machine
+    precision for both.  (The tables' 1e-6 for Algorithm 1 reflects a Q
+    formed as B* R^-1; TSQR's own Q, formed from its reflections, is
+    orthonormal to working precision, which Algorithm 2 keeps.)"""
+    m, n = 3000, 200
+    A, U0, s0, V0 = workloads.paper_dct_matrix(m, n, n)
+    mix = workloads.mixing_draws(n, 86)
+    out = {}
+    for passes in (1, 2):
+        U, S, V, r, st = orc.ts_svd_tsqr(A, mix, passes=passes, wp=1e-11)
+        err = orc.spectral_error(A, U, S, V)
+        out[passes] = (np.abs(U[:, :r].T @ U[:, :r] - np.eye(r)).max(), err, r)
+        cut = s0[s0 < 1e-11][0] if np.any(s0 < 1e-11) else 0.0
+        assert 0.1 * cut <= err <= 10 * cut, (passes, err, cut)
+    assert out[2][0] <= 1e-13 and out[1][0] <= 1e-13
+
+
+def test_tsqr_rank_deficient(orc):
+    """A zero column: R has a zero diagonal entry, the row is discarded and
+    the rank drops by one."""
+    A = np.random.default_rng(87).standard_normal((200, 8))
+    A[:, 3] = 0.0
+    for passes in (1, 2):
+        U, S, V, r, st = orc.ts_svd_tsqr(A, workloads.mixing_draws(8, 88), passes=passes)
+        assert r == 7 and st == 2 and S[7] == 0.0
+        Sr = np.linalg.svd(A, compute_uv=False)
+        assert np.abs(S[:7] - Sr[:7]).max() <= 1e-13 * Sr[0]

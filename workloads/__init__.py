@@ -184,6 +184,20 @@ def pca_data(m, n, sigma, seed, offset=1e3):
     return np.ascontiguousarray(A), c, Q, sigma, V
 
 
+def mixing_draws(n, seed):
+    """The random inputs of Remark "randomness"'s mixing for n real columns
+    (h = ceil(n / 2) complex ones): two sets of phases, uniform on
+    [0, 2 pi), and two uniformly random permutations of h (Fisher-Yates
+    shuffles by numpy's generator).  Returns (theta1, theta2, perm1, perm2)."""
+    h = (n + 1) // 2
+    rng = np.random.default_rng(seed)
+    t1 = rng.uniform(0.0, 2.0 * math.pi, h)
+    t2 = rng.uniform(0.0, 2.0 * math.pi, h)
+    p1 = rng.permutation(h).astype(np.int64)
+    p2 = rng.permutation(h).astype(np.int64)
+    return t1, t2, p1, p2
+
+
 def gaussian(rows, cols, seed):
     """i.i.d. N(0,1) matrix (the starting matrix Omega of the subspace iteration)."""
     return np.random.default_rng(seed).standard_normal((rows, cols))
