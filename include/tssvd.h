@@ -126,6 +126,35 @@ int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double
 int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S,
                float *V, tssvd_opts *opts);
 
+/* Bytes of workspace ts_svd_tsqr needs. */
+size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
+
+/*
+ * Thin SVD by the randomized TSQR methods: Algorithm 1 (opts->passes = 1)
+ * or Algorithm 2 (passes = 2).  Each row of A is mixed by the random
+ * orthogonal Omega = D F S D~ F S~ of Remark "randomness" (pairs of reals
+ * read as complex numbers; F the unitary DFT; n odd is padded with a zero
+ * column to n' = n + 1, h = n'/2), the mixed matrix B* = A Omega* is
+ * factored B* = Q R by Householder TSQR (row blocks of about 4n', a
+ * reduction tree over the stacked R factors, Q formed explicitly from the
+ * reflections), rows of R whose |R_jj| is below |R_00| times the working
+ * precision wp = opts->drop_tol^2 are discarded with Q's columns; passes =
+ * 2 then factors Q = Q2 R2 (same discard) and uses T = R2 R.  The SVD of
+ * T (or R) = U~ Sigma V~^T is one-sided Jacobi; U = Q U~, V = Omega^-1 V~.
+ * The leading n triplets are returned with the sign rule of ts_svd.  All
+ * arithmetic is FP64 (opts->mode is not used; opts->scale is not used).
+ *   A     [in]  m x n row-major, leading dimension lda >= n (device).
+ *   theta [in]  2h phases (device, radians): the diagonal of D (h values)
+ *               then of D~ (h values), drawn uniformly by the caller.
+ *   perm  [in]  2h indices (device): the permutation of S, (S x)_a =
+ *               x_perm[a], then that of S~; each a permutation of 0..h-1.
+ *   U, S, V, opts as for ts_svd.  n <= 4096.
+ * Errors: -1 A, -2 m < n, -3 n, -4 lda, -5 theta, -6 perm NULL or not in
+ * range (detected on the device), -7 U, -8 S, -9 V, -10 opts.
+ */
+int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
+                const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts);
+
 /* Bytes of workspace ts_pca / ts_pca_f32 need: those of ts_svd plus the
  * centred copy (m x n elements) and the column-sum partials. */
 size_t ts_pca_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts);

@@ -101,6 +101,10 @@ def lib():
         f = getattr(L, name)
         f.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, op]
         f.restype = ctypes.c_int
+    L.ts_svd_tsqr_workspace_size.argtypes = [i64, i64, op]
+    L.ts_svd_tsqr_workspace_size.restype = ctypes.c_size_t
+    L.ts_svd_tsqr.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, op]
+    L.ts_svd_tsqr.restype = ctypes.c_int
     L.lowrank_svd_backward.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, op]
     L.lowrank_svd_backward.restype = ctypes.c_int
     L.ts_gram_workspace_size.argtypes = [i64, i64]
@@ -133,7 +137,8 @@ def exported_symbols():
             "tssvd_launch_count", "tssvd_profile_enable", "tssvd_profile_report",
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
             "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
-            "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward"]
+            "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward",
+            "ts_svd_tsqr_workspace_size", "ts_svd_tsqr"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -430,3 +435,30 @@ class LowRankSVD(torch.autograd.Function):
         U, S, V = ctx.saved_tensors
         dA = lowrank_svd_backward(U, S, V, dU=gU, dS=gS, dV=gV, mode=ctx.mode)
         return dA, None, None, None, None, None, None
+
+
+def ts_svd_tsqr(A, theta, perm, passes=2, drop_tol=PAPER_DROP_TOL, max_sweeps=50, stream=None,
+                workspace=None):
+    """Algorithm 1 (passes=1) or 2 (passes=2) on a float64 CUDA tensor A
+    (m x n).  theta: 2h phases, perm: 2h int64 indices (h = ceil(n / 2)),
+    both CUDA tensors: the random mixing of Remark "randomness".  Returns
+    (U, S, V, info).  See include/tssvd.h (ts_svd_tsqr)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    if A.dtype != torch.float64:
+        raise TsSvdError("ts_svd_tsqr: float64 only")
+    h = (n + 1) // 2
+    theta = theta.contiguous()
+    perm = perm.contiguous()
+    if theta.dtype != torch.float64 or perm.dtype != torch.int64 or theta.numel() != 2 * h \
+            or perm.numel() != 2 * h:
+        raise TsSvdError("ts_svd_tsqr: theta float64 and perm int64, 2 * ceil(n / 2) each")
+    U = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    S = torch.empty((n,), dtype=torch.float64, device=A.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    o = _opts(passes, False, drop_tol, "fp64", max_sweeps, stream, workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().ts_svd_tsqr(_ptr(A), m, n, A.stride(0), _ptr(theta), _ptr(perm), _ptr(U),
+                               _ptr(S), _ptr(V), ctypes.byref(o))
+    _check(rc, "ts_svd_tsqr")
+    return U, S, V, _info(o, rc)

@@ -1176,6 +1176,131 @@ int lowrank_backward_entry(int64_t m, int64_t n, int64_t k, const double *U, con
     return err ? TSSVD_ETIMEOUT : TSSVD_OK;
 }
 
+// Algorithm 1 (passes = 1) or 2 (passes = 2): B* = A O^T (O the real
+// form of the random mixing, n odd padded to n' = n + 1), B* = Q R by TSQR,
+// discard of R's diagonal below |R_00| wp, [Q = Q2 R2, discard, T = R2 R],
+// SVD of T by one-sided Jacobi, U = Q U~, V = O^T V~ (leading n rows and
+// triplets).  wp = drop_tol^2 (drop_tol is the square root of the working
+// precision, as for the Gram algorithms).
+int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
+               const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 4096) return -3;
+    if (lda < n) return -4;
+    if (!theta) return -5;
+    if (!perm) return -6;
+    if (!U) return -7;
+    if (!S) return -8;
+    if (!V) return -9;
+    if (!check_opts(opts)) return -10;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 np = n + (n & 1);
+    const int h = (int)(np / 2);
+    const int passes = opts->passes;
+    const double wp = opts->drop_tol * opts->drop_tol;
+    const i64 nn = np * np;
+    const int gy = nn_grid_rows(m, np) > nn_grid_rows(np, np) ? nn_grid_rows(m, np)
+                                                               : nn_grid_rows(np, np);
+    struct Bufs {
+        DevStatus *st;
+        int *bad, *keep, *perm_s;
+        double *Mt, *Bst, *Q1, *R1, *Q2, *R2, *T, *Xw, *Jw, *Pm, *Vo, *Pp, *work, *NP;
+        double *norms, *sigma, *sgn, *prm;
+        int *ctr;
+    } b;
+    auto carve = [&](Bump &w) {
+        b.st = w.take<DevStatus>(1);
+        b.bad = w.take<int>(1);
+        b.keep = w.take<int>(np);
+        b.perm_s = w.take<int>(np);
+        b.Mt = w.take<double>(nn);
+        b.Bst = w.take<double>((size_t)m * np);
+        b.Q1 = w.take<double>((size_t)m * np);
+        b.R1 = w.take<double>(nn);
+        b.Q2 = passes == 2 ? w.take<double>((size_t)m * np) : nullptr;
+        b.R2 = passes == 2 ? w.take<double>(nn) : nullptr;
+        b.T = w.take<double>(nn);
+        b.Xw = w.take<double>(nn);
+        b.Jw = w.take<double>(nn);
+        b.Pm = w.take<double>(nn);
+        b.Vo = w.take<double>(nn);
+        b.Pp = w.take<double>(nn);
+        b.work = w.take<double>(tsqr_workspace_doubles(m, (int)np));
+        b.NP = w.take<double>((size_t)gy * np);
+        b.norms = w.take<double>(np);
+        b.sigma = w.take<double>(np);
+        b.sgn = w.take<double>(np);
+        b.prm = w.take<double>(jacobi_prm_doubles(np));
+        b.ctr = w.take<int>((size_t)opts->max_sweeps + 4);
+    };
+    Bump sz(nullptr, 0);
+    carve(sz);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off + 256);
+    carve(ws);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    DevStatus *st = b.st;
+    auto body = [&]() -> cudaError_t {
+        CK(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+        CK(cudaMemsetAsync(b.bad, 0, sizeof(int), s));
+        CK(launch_mixing(h, theta, perm, b.Mt, b.bad, s));
+        // B* = A O^T = A Mt[0:n, :]
+        CK(launch_nn<double, double>(A, lda, b.Mt, np, m, n, np, b.Bst, np, b.NP, s));
+        CK(launch_tsqr(b.Bst, m, (int)np, b.work, b.R1, b.Q1, s));
+        CK(launch_tsqr_discard(b.R1, b.Q1, m, (int)np, wp, b.keep, s));
+        double *Qf = b.Q1;
+        if (passes == 2) {
+            CK(launch_tsqr(b.Q1, m, (int)np, b.work, b.R2, b.Q2, s));
+            CK(launch_tsqr_discard(b.R2, b.Q2, m, (int)np, wp, b.keep, s));
+            CK(launch_nn<double, double>(b.R2, np, b.R1, np, np, np, np, b.T, np, b.NP, s));
+            Qf = b.Q2;
+        } else {
+            CK(cudaMemcpyAsync(b.T, b.R1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+        }
+        // T = P Sigma V~^T by one-sided Jacobi on the columns of T^T
+        CK(launch_orient_copy(nullptr, &st->rank2, b.T, np, b.Xw, &st->orient, s));
+        CK(launch_jacobi(b.Xw, np, b.Jw, np, (int)np, (int)np, opts->max_sweeps, b.ctr, b.prm, st,
+                         2, s));
+        CK(launch_jacobi_finalize(b.Xw, np, b.Jw, np, (int)np, (int)np, b.norms, b.perm_s, b.Pm,
+                                  np, b.sigma, b.Vo, np, s, &st->orient));
+        // V = (O^T V~)[0:n, 0:n] = Mt[0:n, :] V~[:, 0:n], then the sign rule
+        CK(launch_nn<double, double>(b.Mt, np, b.Vo, np, n, np, n, V, n, b.NP, s));
+        CK(launch_signs(V, n, n, n, b.sigma, b.sgn, s));
+        CK(launch_count_positive(b.sigma, n, &st->rank, s));
+        // U = Q (P[:, 0:n] diag(sgn))
+        CK(launch_scale2(b.Pm, np, np, n, nullptr, b.sgn, b.Pp, n, s));
+        CK(launch_nn<double, double>(Qf, np, b.Pp, n, m, np, n, U, n, b.NP, s));
+        CK(launch_convert<double>(b.sigma, np, 1, n, S, n, s));
+        return cudaSuccess;
+    };
+    cudaError_t e = body();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    DevStatus hst;
+    int hbad = 0;
+    if (cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, b.bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    if (hbad) return -6;
+    if (hst.err) return TSSVD_ETIMEOUT;
+    opts->out_rank = hst.rank;
+    for (int i = 0; i < 4; i++) opts->sweeps[i] = hst.sweeps[i];
+    opts->ranks[0] = opts->ranks[1] = hst.rank;
+    if (hst.sweeps[2] < 0) return TSSVD_ENOCONV;
+    return hst.rank < n ? TSSVD_RANKDEF : TSSVD_OK;
+}
+
 }  // namespace
 }  // namespace tssvd
 
@@ -1499,6 +1624,24 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
                     double *dA, tssvd_opts *opts)
 {
     return backward_entry<double>(A, m, n, lda, S, V, dU, dS, dV, dA, opts);
+}
+
+size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts)
+{
+    if (!opts || m < 1 || n < 1) return 0;
+    const i64 np = n + (n & 1), nn = np * np;
+    const int gy = nn_grid_rows(m, np) > nn_grid_rows(np, np) ? nn_grid_rows(m, np)
+                                                               : nn_grid_rows(np, np);
+    size_t d = 3 * (size_t)m * np + 10 * (size_t)nn + tsqr_workspace_doubles(m, (int)np) +
+               (size_t)gy * np + 4 * (size_t)np + jacobi_prm_doubles(np);
+    return sizeof(double) * d + sizeof(int) * (2 * (size_t)np + opts->max_sweeps + 8) +
+           sizeof(DevStatus) + 32 * 256;
+}
+
+int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
+                const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts)
+{
+    return tsqr_entry(A, m, n, lda, theta, perm, U, S, V, opts);
 }
 
 int lowrank_svd_backward(int64_t m, int64_t n, int64_t k, const double *U, const double *S,

@@ -79,6 +79,19 @@ int nn_grid_rows(i64 m, i64 N);
 // g < colsumsq_rows(m, n); sum them with launch_norms_reduce.
 int colsumsq_rows(i64 m, i64 n);
 cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, cudaStream_t s);
+// Algorithms 1 and 2 (tsqr.cu).  Mt = O^T (2h x 2h) of Remark
+// "randomness"'s mixing from th (2h phases) and perm (2h indices); *bad is
+// set if a permutation entry is out of range.
+cudaError_t launch_mixing(int h, const double *th, const i64 *perm, double *Mt, int *bad,
+                          cudaStream_t s);
+// Householder TSQR of X (m x n, dense, destroyed): R (n x n, upper) and
+// Q (m x n) with X = Q R; work: tsqr_workspace_doubles(m, n) doubles.
+size_t tsqr_workspace_doubles(i64 m, int n);
+cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double *Q,
+                        cudaStream_t s);
+// Discard of R's small diagonal entries (rows of R, columns of Q zeroed).
+cudaError_t launch_tsqr_discard(double *R, double *Q, i64 m, int n, double wp, int *keep,
+                                cudaStream_t s);
 // launch_colmax streams whole rows when n <= 32 * kColStatMaxCh, with
 // colstat_blocks(m, n) blocks (0 when n is larger).
 constexpr int kColStatMaxCh = 16;

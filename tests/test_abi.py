@@ -102,3 +102,24 @@ def test_pca_argument_validation_without_gpu():
     L.tssvd_default_opts(ctypes.byref(o))
     assert (L.ts_pca_workspace_size(20000, 50, 8, ctypes.byref(o)) >=
             L.ts_svd_workspace_size(20000, 50, 8, ctypes.byref(o)) + 20000 * 50 * 8)
+
+
+def test_tsqr_argument_validation_without_gpu():
+    """ts_svd_tsqr rejects NULL or out-of-range arguments before touching
+    the device (the pointers below are never dereferenced)."""
+    import paper_1612_08709_gb300 as pkg
+    from paper_1612_08709_gb300._binding import _Opts
+    L = pkg.lib()
+    o = _Opts()
+    L.tssvd_default_opts(ctypes.byref(o))
+    f = ctypes.c_void_p(256)
+    assert L.ts_svd_tsqr(None, 10, 2, 2, f, f, f, f, f, ctypes.byref(o)) == -1
+    assert L.ts_svd_tsqr(f, 1, 2, 2, f, f, f, f, f, ctypes.byref(o)) == -2
+    assert L.ts_svd_tsqr(f, 10000, 5000, 5000, f, f, f, f, f, ctypes.byref(o)) == -3
+    assert L.ts_svd_tsqr(f, 10, 2, 1, f, f, f, f, f, ctypes.byref(o)) == -4
+    assert L.ts_svd_tsqr(f, 10, 2, 2, None, f, f, f, f, ctypes.byref(o)) == -5
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, None, f, f, f, ctypes.byref(o)) == -6
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, None, f, f, ctypes.byref(o)) == -7
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, None, f, ctypes.byref(o)) == -8
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, None, ctypes.byref(o)) == -9
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, f, None) == -10
