@@ -155,6 +155,28 @@ size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
 int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
                 const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts);
 
+/*
+ * Rank-k approximation by Algorithm 7: randomized subspace iteration
+ * (Algorithm 5) with `iters` power steps orthonormalised by Algorithm 1,
+ * the last by Algorithm 2, then Algorithm 6 with the SVD of B = Q^T A as
+ * the Algorithm 2 TS-SVD of B^T = A^T Q.  Directions discarded by a TS-SVD
+ * are removed (the next step works with the kept width, read back from the
+ * device), as in Algorithms 1 and 2.  Every TS-SVD uses the caller's one
+ * mixing draw for l columns, restricted to its width w (the first
+ * ceil(w/2) phases of each set; each permutation's entries below ceil(w/2)
+ * in their order).  FP64 throughout; the discard compares R's diagonal
+ * with the working precision opts->drop_tol^2.
+ *   A, m, n, lda, k, l, iters, Omega, U, S, V as for lowrank_svd
+ *   (l <= 4096).
+ *   theta, perm: the draw of ts_svd_tsqr for l columns (2 ceil(l/2) each).
+ * Errors: -1 A, -2 m, -3 n, -4 lda, -5 k, -6 l, -7 iters, -8 Omega,
+ * -9 theta, -10 perm (NULL or not a permutation), -11 U, -12 S, -13 V,
+ * -14 opts.
+ */
+int lowrank_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
+                     int iters, const double *Omega, const double *theta, const int64_t *perm,
+                     double *U, double *S, double *V, tssvd_opts *opts);
+
 /* Bytes of workspace ts_pca / ts_pca_f32 need: those of ts_svd plus the
  * centred copy (m x n elements) and the column-sum partials. */
 size_t ts_pca_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts);

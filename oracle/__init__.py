@@ -42,6 +42,10 @@ def lib():
         L.or_ts_svd_tsqr.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_double, _dp,
                                      _dp, _lp, _lp, ctypes.c_int, _dp, _i64, _dp, _dp, _i64, _lp]
         L.or_ts_svd_tsqr.restype = ctypes.c_int
+        L.or_lowrank_svd_tsqr.argtypes = [_dp, _i64, _i64, _i64, _i64, _i64, ctypes.c_int, _dp,
+                                          _dp, _dp, _lp, _lp, ctypes.c_double, ctypes.c_int, _dp,
+                                          _i64, _dp, _dp, _i64, _lp]
+        L.or_lowrank_svd_tsqr.restype = ctypes.c_int
         L.or_col_means.argtypes = [_dp, _i64, _i64, _i64, _dp]
         L.or_pca.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, _dp, _dp, _i64, _dp, _dp, _i64, _lp]
@@ -205,6 +209,23 @@ def ts_svd_tsqr(A, mix, passes=2, wp=PAPER_DROP_TOL ** 2, max_sweeps=MAX_SWEEPS)
     st = lib().or_ts_svd_tsqr(_p(A), m, n, n, int(passes), float(wp), _p(t1), _p(t2), _ip(p1),
                               _ip(p2), int(max_sweeps), _p(U), n, _p(S), _p(V), n,
                               ctypes.byref(r))
+    return U, S, V, r.value, st
+
+
+def lowrank_svd_tsqr(A, k, l, iters, Omega, mix, wp=PAPER_DROP_TOL ** 2,
+                     max_sweeps=MAX_SWEEPS):
+    """Algorithm 7: (U m x k, S k, V n x k, rank, status); mix is the mixing
+    draw for l columns (length ceil(l / 2) each)."""
+    A, Omega = _c(A), _c(Omega)
+    m, n = A.shape
+    t1, t2 = _c(mix[0]), _c(mix[1])
+    p1 = np.ascontiguousarray(mix[2], dtype=np.int64)
+    p2 = np.ascontiguousarray(mix[3], dtype=np.int64)
+    U = np.zeros((m, k)); S = np.zeros(k); V = np.zeros((n, k))
+    r = ctypes.c_int64(0)
+    st = lib().or_lowrank_svd_tsqr(_p(A), m, n, n, int(k), int(l), int(iters), _p(Omega), _p(t1),
+                                   _p(t2), _ip(p1), _ip(p2), float(wp), int(max_sweeps), _p(U), k,
+                                   _p(S), _p(V), k, ctypes.byref(r))
     return U, S, V, r.value, st
 
 

@@ -983,6 +983,125 @@ int or_lowrank_svd(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l,
     return st;
 }
 
+/*
+ * The mixing draw for w columns derived from the draw for l >= w columns
+ * (h = ceil(l/2) complex entries, h' = ceil(w/2)): the first h' phases of
+ * each set, and each permutation restricted to 0..h'-1 (its entries below
+ * h' in their order: the restriction of a uniform random permutation is a
+ * uniform random permutation of the subset).
+ */
+static void restrict_mix(const double *th1, const double *th2, const i64 *p1, const i64 *p2,
+                         i64 h, i64 hw, double *t1w, double *t2w, i64 *p1w, i64 *p2w)
+{
+    for (i64 a = 0; a < hw; a++) {
+        t1w[a] = th1[a];
+        t2w[a] = th2[a];
+    }
+    i64 c1 = 0, c2 = 0;
+    for (i64 a = 0; a < h; a++) {
+        if (p1[a] < hw) p1w[c1++] = p1[a];
+        if (p2[a] < hw) p2w[c2++] = p2[a];
+    }
+}
+
+/* Algorithm 1 or 2 on X (rows x w, ldx) with the draw restricted to w
+ * columns; U (rows x w, ldu), S, V (w x w, ldv); returns the rank. */
+static i64 tsqr_restricted(const double *X, i64 rows, i64 w, i64 ldx, int passes, double wp,
+                           const double *th1, const double *th2, const i64 *p1, const i64 *p2,
+                           i64 h, int max_sweeps, double *U, i64 ldu, double *S, double *V,
+                           i64 ldv, int *st)
+{
+    const i64 hw = (w + 1) / 2;
+    double *t1w = dalloc(hw), *t2w = dalloc(hw), *Xc = dalloc(rows * w);
+    i64 *p1w = (i64 *)malloc(sizeof(i64) * (size_t)hw), *p2w = (i64 *)malloc(sizeof(i64) * (size_t)hw);
+    restrict_mix(th1, th2, p1, p2, h, hw, t1w, t2w, p1w, p2w);
+    for (i64 i = 0; i < rows; i++)
+        for (i64 j = 0; j < w; j++) Xc[i * w + j] = X[i * ldx + j];
+    double *Uc = dalloc(rows * w), *Vc = dalloc(w * w);
+    i64 r = 0;
+    if (or_ts_svd_tsqr(Xc, rows, w, w, passes, wp, t1w, t2w, p1w, p2w, max_sweeps, Uc, w, S, Vc,
+                       w, &r) == OR_ENOCONV)
+        *st = OR_ENOCONV;
+    for (i64 i = 0; i < rows; i++)
+        for (i64 j = 0; j < w; j++) U[i * ldu + j] = Uc[i * w + j];
+    for (i64 i = 0; i < w; i++)
+        for (i64 j = 0; j < w; j++) V[i * ldv + j] = Vc[i * w + j];
+    free(t1w); free(t2w); free(Xc); free(p1w); free(p2w); free(Uc); free(Vc);
+    return r;
+}
+
+/*
+ * Algorithm 7 = Algorithm 6 fed by Algorithm 5, with Algorithm 1 for the
+ * power steps and Algorithm 2 for the last step and for the SVD of B (the
+ * TS-SVD of B^T = A^T Q).  As in Algorithms 1 and 2, discarded directions
+ * are removed: each step continues with the basis width the previous
+ * TS-SVD kept.  The mixing of every TS-SVD comes from the one draw for l
+ * columns (theta1, theta2, perm1, perm2, length ceil(l/2)), restricted to
+ * the current width.  Outputs as or_lowrank_svd.
+ */
+int or_lowrank_svd_tsqr(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, int iters,
+                        const double *Omega, const double *th1, const double *th2,
+                        const i64 *p1, const i64 *p2, double wp, int max_sweeps, double *U,
+                        i64 ldu, double *S, double *V, i64 ldv, i64 *rank)
+{
+    int st = OR_OK;
+    const i64 h = (l + 1) / 2;
+    double *Qt = dalloc(n * l), *Q = dalloc(m * l), *Y = dalloc(m * l), *Yt = dalloc(n * l);
+    double *tS = dalloc(l), *tV = dalloc(l * l);
+    i64 w = l;
+    for (i64 i = 0; i < n * l; i++) Qt[i] = Omega[i];
+    for (int it = 0; it < iters && w > 0; it++) {
+        or_matmul(A, m, n, lda, Qt, w, w, Y, w);
+        w = tsqr_restricted(Y, m, w, w, 1, wp, th1, th2, p1, p2, h, max_sweeps, Q, l, tS, tV, l,
+                            &st);
+        if (w == 0) break;
+        /* Q (m x w) compacted to leading dimension w */
+        for (i64 i = 0; i < m; i++)
+            for (i64 j = 0; j < w; j++) Y[i * w + j] = Q[i * l + j];
+        or_matmul_tn(A, m, n, lda, Y, w, w, Yt, w);
+        const i64 w2 = tsqr_restricted(Yt, n, w, w, 1, wp, th1, th2, p1, p2, h, max_sweeps, Qt,
+                                       l, tS, tV, l, &st);
+        for (i64 i = 0; i < n; i++)
+            for (i64 j = 0; j < w2; j++) Yt[i * w2 + j] = Qt[i * l + j];
+        memcpy(Qt, Yt, sizeof(double) * (size_t)(n * w2));
+        w = w2;
+    }
+    i64 rb = 0;
+    double *Bt = dalloc(n * l), *U1 = dalloc(n * l), *S1 = dalloc(l), *V1 = dalloc(l * l);
+    double *Uf = dalloc(m * l);
+    if (w > 0) {
+        or_matmul(A, m, n, lda, Qt, w, w, Y, w);
+        const i64 wq = tsqr_restricted(Y, m, w, w, 2, wp, th1, th2, p1, p2, h, max_sweeps, Q, l,
+                                       tS, tV, l, &st);
+        if (wq > 0) {
+            for (i64 i = 0; i < m; i++)
+                for (i64 j = 0; j < wq; j++) Y[i * wq + j] = Q[i * l + j];
+            /* Algorithm 6: B^T = A^T Q = U1 S1 V1^T, U~ = V1, V = U1 */
+            or_matmul_tn(A, m, n, lda, Y, wq, wq, Bt, wq);
+            rb = tsqr_restricted(Bt, n, wq, wq, 2, wp, th1, th2, p1, p2, h, max_sweeps, U1, l,
+                                 S1, V1, l, &st);
+            for (i64 i = 0; i < m; i++)
+                for (i64 j = 0; j < wq; j++) {
+                    double acc = 0.0;
+                    for (i64 c = 0; c < wq; c++) acc += Y[i * wq + c] * V1[c * l + j];
+                    Uf[i * l + j] = acc;
+                }
+        }
+    }
+    const i64 kk = k < rb ? k : rb;
+    for (i64 i = 0; i < m; i++)
+        for (i64 j = 0; j < k; j++) U[i * ldu + j] = (j < kk) ? Uf[i * l + j] : 0.0;
+    for (i64 i = 0; i < n; i++)
+        for (i64 j = 0; j < k; j++) V[i * ldv + j] = (j < kk) ? U1[i * l + j] : 0.0;
+    for (i64 j = 0; j < k; j++) S[j] = (j < kk) ? S1[j] : 0.0;
+    canonical_signs(U, m, ldu, V, n, ldv, kk);
+    *rank = kk;
+    if (st == OR_OK && kk < k) st = OR_RANKDEF;
+    free(Qt); free(Q); free(Y); free(Yt); free(tS); free(tV); free(Bt); free(U1); free(S1);
+    free(V1); free(Uf);
+    return st;
+}
+
 /* ------------------------------------------------------------------ */
 /* Thin-SVD adjoint.                                                    */
 /* ------------------------------------------------------------------ */

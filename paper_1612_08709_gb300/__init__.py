@@ -16,4 +16,5 @@ from ._binding import (  # noqa: F401
     ts_matmul, ts_svd_batched, ts_svd_batched_workspace_size,
     ts_svd_workspace_size, lowrank_svd_workspace_size, TSSVD, exported_symbols,
     ts_pca, ts_pca_workspace_size, lowrank_svd_backward, LowRankSVD, ts_svd_tsqr,
+    lowrank_svd_tsqr,
 )

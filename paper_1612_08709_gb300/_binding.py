@@ -103,6 +103,9 @@ def lib():
         f.restype = ctypes.c_int
     L.ts_svd_tsqr_workspace_size.argtypes = [i64, i64, op]
     L.ts_svd_tsqr_workspace_size.restype = ctypes.c_size_t
+    L.lowrank_svd_tsqr.argtypes = [vp, i64, i64, i64, i64, i64, ctypes.c_int, vp, vp, vp, vp, vp,
+                                   vp, op]
+    L.lowrank_svd_tsqr.restype = ctypes.c_int
     L.ts_svd_tsqr.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp, op]
     L.ts_svd_tsqr.restype = ctypes.c_int
     L.lowrank_svd_backward.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, op]
@@ -138,7 +141,7 @@ def exported_symbols():
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
             "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
             "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward",
-            "ts_svd_tsqr_workspace_size", "ts_svd_tsqr"]
+            "ts_svd_tsqr_workspace_size", "ts_svd_tsqr", "lowrank_svd_tsqr"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -461,4 +464,29 @@ def ts_svd_tsqr(A, theta, perm, passes=2, drop_tol=PAPER_DROP_TOL, max_sweeps=50
         rc = lib().ts_svd_tsqr(_ptr(A), m, n, A.stride(0), _ptr(theta), _ptr(perm), _ptr(U),
                                _ptr(S), _ptr(V), ctypes.byref(o))
     _check(rc, "ts_svd_tsqr")
+    return U, S, V, _info(o, rc)
+
+
+def lowrank_svd_tsqr(A, k, l, iters, Omega, theta, perm, drop_tol=PAPER_DROP_TOL, max_sweeps=50,
+                     stream=None, workspace=None):
+    """Algorithm 7 (float64 CUDA tensors): returns (U m x k, S k, V n x k,
+    info).  theta, perm: the mixing draw for l columns (2 ceil(l/2) each).
+    See include/tssvd.h (lowrank_svd_tsqr)."""
+    A = _as_matrix(A)
+    m, n = A.shape
+    Omega = Omega.contiguous()
+    theta = theta.contiguous()
+    perm = perm.contiguous()
+    h = (l + 1) // 2
+    if theta.numel() != 2 * h or perm.numel() != 2 * h or perm.dtype != torch.int64:
+        raise TsSvdError("lowrank_svd_tsqr: theta and perm of 2 * ceil(l / 2) entries")
+    U = torch.empty((m, k), dtype=torch.float64, device=A.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A.device)
+    V = torch.empty((n, k), dtype=torch.float64, device=A.device)
+    o = _opts(2, False, drop_tol, "fp64", max_sweeps, stream, workspace)
+    with torch.cuda.device(A.device):
+        rc = lib().lowrank_svd_tsqr(_ptr(A), m, n, A.stride(0), int(k), int(l), int(iters),
+                                    _ptr(Omega), _ptr(theta), _ptr(perm), _ptr(U), _ptr(S),
+                                    _ptr(V), ctypes.byref(o))
+    _check(rc, "lowrank_svd_tsqr")
     return U, S, V, _info(o, rc)

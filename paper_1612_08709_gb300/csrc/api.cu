@@ -803,6 +803,10 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
 // ------------------------------------------------------------- low rank
 
 // Number of per-sub-call status blocks used by lowrank: 2 per power step + 2.
+cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *Mt, double *U,
+                      i64 ldu, double *S, double *V, i64 ldv, int passes, double wp,
+                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s);
+
 cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, int iters,
                          const double *Omega, double *U, double *S, double *V, double tol,
                          int max_sweeps, Bump &ws, DevStatus *sts, cudaStream_t s,
@@ -1176,12 +1180,65 @@ int lowrank_backward_entry(int64_t m, int64_t n, int64_t k, const double *U, con
     return err ? TSSVD_ETIMEOUT : TSSVD_OK;
 }
 
-// Algorithm 1 (passes = 1) or 2 (passes = 2): B* = A O^T (O the real
-// form of the random mixing, n odd padded to n' = n + 1), B* = Q R by TSQR,
-// discard of R's diagonal below |R_00| wp, [Q = Q2 R2, discard, T = R2 R],
-// SVD of T by one-sided Jacobi, U = Q U~, V = O^T V~ (leading n rows and
-// triplets).  wp = drop_tol^2 (drop_tol is the square root of the working
-// precision, as for the Gram algorithms).
+// Algorithm 1 (passes = 1) or 2 (passes = 2) on X (rows x n, ldx), with
+// the mixing Mt = O^T (n' x n', n' = n + (n & 1)) given: B* = X O^T (n odd
+// padded to n'), B* = Q R by TSQR, discard of R's diagonal below |R_00| wp,
+// [Q = Q2 R2, discard, T = R2 R], SVD of T by one-sided Jacobi, U = Q U~,
+// V = O^T V~ (leading n rows and triplets).  st->rank, st->sweeps[2] and
+// st->err are written.  Sizing when ws has no base.
+cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *Mt, double *U,
+                      i64 ldu, double *S, double *V, i64 ldv, int passes, double wp,
+                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s)
+{
+    const i64 np = n + (n & 1), nn = np * np;
+    const int gy = nn_grid_rows(rows, np) > nn_grid_rows(np, np) ? nn_grid_rows(rows, np)
+                                                                  : nn_grid_rows(np, np);
+    int *keep = ws.take<int>(np), *perm_s = ws.take<int>(np);
+    int *ctr = ws.take<int>((size_t)max_sweeps + 4);
+    double *Bst = ws.take<double>((size_t)rows * np), *Q1 = ws.take<double>((size_t)rows * np);
+    double *R1 = ws.take<double>(nn);
+    double *Q2 = passes == 2 ? ws.take<double>((size_t)rows * np) : nullptr;
+    double *R2 = passes == 2 ? ws.take<double>(nn) : nullptr;
+    double *T = ws.take<double>(nn), *Xw = ws.take<double>(nn), *Jw = ws.take<double>(nn);
+    double *Pm = ws.take<double>(nn), *Vo = ws.take<double>(nn), *Pp = ws.take<double>(nn);
+    double *work = ws.take<double>(tsqr_workspace_doubles(rows, (int)np));
+    double *NP = ws.take<double>((size_t)gy * np);
+    double *norms = ws.take<double>(np), *sigma = ws.take<double>(np), *sgn = ws.take<double>(np);
+    double *prm = ws.take<double>(jacobi_prm_doubles(np));
+    if (ws.sizing()) return cudaSuccess;
+    if (ws.overflow) return cudaErrorMemoryAllocation;
+    // B* = X O^T = X Mt[0:n, :]
+    CK(launch_nn<double, double>(X, ldx, Mt, np, rows, n, np, Bst, np, NP, s));
+    CK(launch_tsqr(Bst, rows, (int)np, work, R1, Q1, s));
+    CK(launch_tsqr_discard(R1, Q1, rows, (int)np, wp, keep, s));
+    double *Qf = Q1;
+    if (passes == 2) {
+        CK(launch_tsqr(Q1, rows, (int)np, work, R2, Q2, s));
+        CK(launch_tsqr_discard(R2, Q2, rows, (int)np, wp, keep, s));
+        CK(launch_nn<double, double>(R2, np, R1, np, np, np, np, T, np, NP, s));
+        Qf = Q2;
+    } else {
+        CK(cudaMemcpyAsync(T, R1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    }
+    // T = P Sigma V~^T by one-sided Jacobi on the columns of T^T
+    CK(launch_orient_copy(nullptr, &st->rank2, T, np, Xw, &st->orient, s));
+    CK(launch_jacobi(Xw, np, Jw, np, (int)np, (int)np, max_sweeps, ctr, prm, st, 2, s));
+    CK(launch_jacobi_finalize(Xw, np, Jw, np, (int)np, (int)np, norms, perm_s, Pm, np, sigma, Vo,
+                              np, s, &st->orient));
+    // V = (O^T V~)[0:n, 0:n] = Mt[0:n, :] V~[:, 0:n], then the sign rule
+    CK(launch_nn<double, double>(Mt, np, Vo, np, n, np, n, V, ldv, NP, s));
+    CK(launch_signs(V, ldv, n, n, sigma, sgn, s));
+    CK(launch_count_positive(sigma, n, &st->rank, s));
+    // U = Q (P[:, 0:n] diag(sgn))
+    CK(launch_scale2(Pm, np, np, n, nullptr, sgn, Pp, n, s));
+    CK(launch_nn<double, double>(Qf, np, Pp, n, rows, np, n, U, ldu, NP, s));
+    CK(launch_convert<double>(sigma, np, 1, n, S, n, s));
+    return cudaSuccess;
+}
+
+// The C entry of Algorithms 1 and 2: the mixing matrix from the caller's
+// random draws, then tsqr_core.  wp = drop_tol^2 (drop_tol is the square
+// root of the working precision, as for the Gram algorithms).
 int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
                const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts)
 {
@@ -1197,97 +1254,36 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     if (!check_opts(opts)) return -10;
     cudaStream_t s = (cudaStream_t)opts->stream;
     const i64 np = n + (n & 1);
-    const int h = (int)(np / 2);
-    const int passes = opts->passes;
     const double wp = opts->drop_tol * opts->drop_tol;
-    const i64 nn = np * np;
-    const int gy = nn_grid_rows(m, np) > nn_grid_rows(np, np) ? nn_grid_rows(m, np)
-                                                               : nn_grid_rows(np, np);
-    struct Bufs {
-        DevStatus *st;
-        int *bad, *keep, *perm_s;
-        double *Mt, *Bst, *Q1, *R1, *Q2, *R2, *T, *Xw, *Jw, *Pm, *Vo, *Pp, *work, *NP;
-        double *norms, *sigma, *sgn, *prm;
-        int *ctr;
-    } b;
-    auto carve = [&](Bump &w) {
-        b.st = w.take<DevStatus>(1);
-        b.bad = w.take<int>(1);
-        b.keep = w.take<int>(np);
-        b.perm_s = w.take<int>(np);
-        b.Mt = w.take<double>(nn);
-        b.Bst = w.take<double>((size_t)m * np);
-        b.Q1 = w.take<double>((size_t)m * np);
-        b.R1 = w.take<double>(nn);
-        b.Q2 = passes == 2 ? w.take<double>((size_t)m * np) : nullptr;
-        b.R2 = passes == 2 ? w.take<double>(nn) : nullptr;
-        b.T = w.take<double>(nn);
-        b.Xw = w.take<double>(nn);
-        b.Jw = w.take<double>(nn);
-        b.Pm = w.take<double>(nn);
-        b.Vo = w.take<double>(nn);
-        b.Pp = w.take<double>(nn);
-        b.work = w.take<double>(tsqr_workspace_doubles(m, (int)np));
-        b.NP = w.take<double>((size_t)gy * np);
-        b.norms = w.take<double>(np);
-        b.sigma = w.take<double>(np);
-        b.sgn = w.take<double>(np);
-        b.prm = w.take<double>(jacobi_prm_doubles(np));
-        b.ctr = w.take<int>((size_t)opts->max_sweeps + 4);
-    };
     Bump sz(nullptr, 0);
-    carve(sz);
+    sz.take<DevStatus>(1);
+    sz.take<int>(1);
+    sz.take<double>((size_t)np * np);
+    tsqr_core(nullptr, m, n, n, nullptr, nullptr, n, nullptr, nullptr, n, opts->passes, wp,
+              opts->max_sweeps, sz, nullptr, s);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
     if (rc) return rc;
     Bump ws(base, sz.off + 256);
-    carve(ws);
-    if (ws.overflow) return TSSVD_ENOMEM;
-    DevStatus *st = b.st;
-    auto body = [&]() -> cudaError_t {
-        CK(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
-        CK(cudaMemsetAsync(b.bad, 0, sizeof(int), s));
-        CK(launch_mixing(h, theta, perm, b.Mt, b.bad, s));
-        // B* = A O^T = A Mt[0:n, :]
-        CK(launch_nn<double, double>(A, lda, b.Mt, np, m, n, np, b.Bst, np, b.NP, s));
-        CK(launch_tsqr(b.Bst, m, (int)np, b.work, b.R1, b.Q1, s));
-        CK(launch_tsqr_discard(b.R1, b.Q1, m, (int)np, wp, b.keep, s));
-        double *Qf = b.Q1;
-        if (passes == 2) {
-            CK(launch_tsqr(b.Q1, m, (int)np, b.work, b.R2, b.Q2, s));
-            CK(launch_tsqr_discard(b.R2, b.Q2, m, (int)np, wp, b.keep, s));
-            CK(launch_nn<double, double>(b.R2, np, b.R1, np, np, np, np, b.T, np, b.NP, s));
-            Qf = b.Q2;
-        } else {
-            CK(cudaMemcpyAsync(b.T, b.R1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-        }
-        // T = P Sigma V~^T by one-sided Jacobi on the columns of T^T
-        CK(launch_orient_copy(nullptr, &st->rank2, b.T, np, b.Xw, &st->orient, s));
-        CK(launch_jacobi(b.Xw, np, b.Jw, np, (int)np, (int)np, opts->max_sweeps, b.ctr, b.prm, st,
-                         2, s));
-        CK(launch_jacobi_finalize(b.Xw, np, b.Jw, np, (int)np, (int)np, b.norms, b.perm_s, b.Pm,
-                                  np, b.sigma, b.Vo, np, s, &st->orient));
-        // V = (O^T V~)[0:n, 0:n] = Mt[0:n, :] V~[:, 0:n], then the sign rule
-        CK(launch_nn<double, double>(b.Mt, np, b.Vo, np, n, np, n, V, n, b.NP, s));
-        CK(launch_signs(V, n, n, n, b.sigma, b.sgn, s));
-        CK(launch_count_positive(b.sigma, n, &st->rank, s));
-        // U = Q (P[:, 0:n] diag(sgn))
-        CK(launch_scale2(b.Pm, np, np, n, nullptr, b.sgn, b.Pp, n, s));
-        CK(launch_nn<double, double>(Qf, np, b.Pp, n, m, np, n, U, n, b.NP, s));
-        CK(launch_convert<double>(b.sigma, np, 1, n, S, n, s));
-        return cudaSuccess;
-    };
-    cudaError_t e = body();
+    DevStatus *st = ws.take<DevStatus>(1);
+    int *bad = ws.take<int>(1);
+    double *Mt = ws.take<double>((size_t)np * np);
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_mixing((int)(np / 2), theta, perm, Mt, bad, s);
+    if (e == cudaSuccess)
+        e = tsqr_core(A, m, n, lda, Mt, U, n, S, V, n, opts->passes, wp, opts->max_sweeps, ws, st,
+                      s);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
-        return TSSVD_ECUDA;
+        return e == cudaErrorMemoryAllocation ? TSSVD_ENOMEM : TSSVD_ECUDA;
     }
     DevStatus hst;
     int hbad = 0;
     if (cudaMemcpyAsync(&hst, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&hbad, b.bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return TSSVD_ECUDA;
@@ -1299,6 +1295,193 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     opts->ranks[0] = opts->ranks[1] = hst.rank;
     if (hst.sweeps[2] < 0) return TSSVD_ENOCONV;
     return hst.rank < n ? TSSVD_RANKDEF : TSSVD_OK;
+}
+
+// Algorithm 7: Algorithm 5 with Algorithm 1 in the power steps and
+// Algorithm 2 in the last step, feeding Algorithm 6 (the SVD of B = Q^T A
+// as the Algorithm 2 TS-SVD of B^T = A^T Q).  Discarded directions are
+// removed: every step continues with the width the previous TS-SVD kept,
+// read back from the device (2 iters + 2 short host synchronisations), and
+// every TS-SVD takes the caller's draw for l columns restricted to its
+// width.
+int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
+                       int iters, const double *Omega, const double *theta,
+                       const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1) return -2;
+    if (n < 1) return -3;
+    if (lda < n) return -4;
+    if (k < 1 || k > l) return -5;
+    if (l < 1 || l > m || l > n || l > 4096) return -6;
+    if (iters < 0 || iters > 30) return -7;
+    if (!Omega) return -8;
+    if (!theta) return -9;
+    if (!perm) return -10;
+    if (!U) return -11;
+    if (!S) return -12;
+    if (!V) return -13;
+    if (!check_opts(opts)) return -14;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 lp = l + (l & 1);
+    const int hl = (int)(lp / 2);
+    const double wp = opts->drop_tol * opts->drop_tol;
+    const int nst = 2 * iters + 2;
+    const i64 big = m > n ? m : n;
+    const int sp = tn_splits(m, n, l, false);
+    const int gy = nn_grid_rows(big, l);
+    struct Bufs {
+        DevStatus *st;
+        int *bad;
+        i64 *permw;
+        double *thw, *Mt, *Qt, *Y, *Q, *Qc, *Bt, *U1, *S1, *V1, *V1s, *Uf, *tS, *tV, *sgn, *P, *NP;
+        char *sub;
+    } b;
+    size_t sub_bytes = 0;
+    {
+        Bump probe(nullptr, 0);
+        tsqr_core(nullptr, big, l, l, nullptr, nullptr, l, nullptr, nullptr, l, 2, wp,
+                  opts->max_sweeps, probe, nullptr, s);
+        sub_bytes = probe.off + 256;
+    }
+    auto carve = [&](Bump &w) {
+        b.st = w.take<DevStatus>(nst);
+        b.bad = w.take<int>(1);
+        b.permw = w.take<i64>(2 * (size_t)hl);
+        b.thw = w.take<double>(2 * (size_t)hl);
+        b.Mt = w.take<double>((size_t)lp * lp);
+        b.Qt = w.take<double>((size_t)n * l);
+        b.Y = w.take<double>((size_t)m * l);
+        b.Q = w.take<double>((size_t)m * l);
+        b.Qc = w.take<double>((size_t)m * l);
+        b.Bt = w.take<double>((size_t)n * l);
+        b.U1 = w.take<double>((size_t)n * l);
+        b.S1 = w.take<double>(l);
+        b.V1 = w.take<double>((size_t)l * l);
+        b.V1s = w.take<double>((size_t)l * l);
+        b.Uf = w.take<double>((size_t)m * l);
+        b.tS = w.take<double>(l);
+        b.tV = w.take<double>((size_t)l * l);
+        b.sgn = w.take<double>(l);
+        b.P = w.take<double>((size_t)sp * n * l);
+        b.NP = w.take<double>((size_t)gy * l);
+        b.sub = w.take<char>(sub_bytes);
+    };
+    Bump sz(nullptr, 0);
+    carve(sz);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off + 256);
+    carve(ws);
+    if (ws.overflow) return TSSVD_ENOMEM;
+    int si = 0, code = TSSVD_OK;
+    // one TS-SVD of X (rows x w, dense): the restricted draw, the mixing
+    // matrix, tsqr_core; returns the kept width (or a negative status)
+    auto ts = [&](const double *X, i64 rows, i64 w, int passes, double *Uo, double *So,
+                  double *Vo) -> i64 {
+        const int hw = (int)((w + 1) / 2);
+        DevStatus *st = b.st + si++;
+        Bump sw(b.sub, sub_bytes);
+        cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+        if (e == cudaSuccess) e = launch_restrict_mix(theta, perm, hl, hw, b.thw, b.permw, b.bad, s);
+        if (e == cudaSuccess) e = launch_mixing(hw, b.thw, b.permw, b.Mt, b.bad, s);
+        if (e == cudaSuccess)
+            e = tsqr_core(X, rows, w, w, b.Mt, Uo, w, So, Vo, w, passes, wp, opts->max_sweeps, sw,
+                          st, s);
+        if (e != cudaSuccess) return -TSSVD_ECUDA;
+        DevStatus h;
+        int hbad = 0;
+        if (cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&hbad, b.bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return -TSSVD_ECUDA;
+        if (hbad) return -100;
+        if (h.err) return -TSSVD_ETIMEOUT;
+        if (h.sweeps[2] < 0) code = TSSVD_ENOCONV;
+        opts->sweeps[2] = h.sweeps[2];
+        return h.rank;
+    };
+    auto fail = [&](i64 r) -> int {
+        cudaGetLastError();
+        return r == -100 ? -10 : (int)-r;
+    };
+    if (cudaMemsetAsync(b.bad, 0, sizeof(int), s) != cudaSuccess) return TSSVD_ECUDA;
+    if (cudaMemcpyAsync(b.Qt, Omega, sizeof(double) * n * l, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return TSSVD_ECUDA;
+    i64 w = l;
+    auto err = [&](cudaError_t e) { return e == cudaSuccess; };
+    for (int it = 0; it < iters && w > 0; it++) {
+        // Y = A Q~ (m x w); Y = Q R (Algorithm 1)
+        if (!err(launch_nn<double, double>(A, lda, b.Qt, w, m, n, w, b.Y, w, b.NP, s)))
+            return TSSVD_ECUDA;
+        i64 r = ts(b.Y, m, w, 1, b.Q, b.tS, b.tV);
+        if (r < 0) return fail(r);
+        if (r == 0) {
+            w = 0;
+            break;
+        }
+        // Q (m x r) compacted, then Y~ = A^T Q (n x r); Y~ = Q~ R~ (Algorithm 1)
+        if (cudaMemcpy2DAsync(b.Qc, sizeof(double) * r, b.Q, sizeof(double) * w,
+                              sizeof(double) * r, m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            !err(launch_tn_partial<double, double>(A, lda, b.Qc, r, m, n, r, sp, false, b.P, s)) ||
+            !err(launch_tn_reduce(b.P, sp, n, r, nullptr, nullptr, false, b.Bt, r, s)))
+            return TSSVD_ECUDA;
+        const i64 r2 = ts(b.Bt, n, r, 1, b.U1, b.tS, b.tV);
+        if (r2 < 0) return fail(r2);
+        if (r2 > 0 && cudaMemcpy2DAsync(b.Qt, sizeof(double) * r2, b.U1, sizeof(double) * r,
+                                        sizeof(double) * r2, n, cudaMemcpyDeviceToDevice,
+                                        s) != cudaSuccess)
+            return TSSVD_ECUDA;
+        w = r2;
+    }
+    i64 rb = 0, wq = 0;
+    if (w > 0) {
+        // Y = A Q~; Y = Q R (Algorithm 2)
+        if (!err(launch_nn<double, double>(A, lda, b.Qt, w, m, n, w, b.Y, w, b.NP, s)))
+            return TSSVD_ECUDA;
+        wq = ts(b.Y, m, w, 2, b.Q, b.tS, b.tV);
+        if (wq < 0) return fail(wq);
+        if (wq > 0) {
+            // Algorithm 6: B^T = A^T Q (n x wq) = U1 S1 V1^T (Algorithm 2); U~ = V1, V = U1
+            if (cudaMemcpy2DAsync(b.Qc, sizeof(double) * wq, b.Q, sizeof(double) * w,
+                                  sizeof(double) * wq, m, cudaMemcpyDeviceToDevice,
+                                  s) != cudaSuccess ||
+                !err(launch_tn_partial<double, double>(A, lda, b.Qc, wq, m, n, wq, sp, false, b.P,
+                                                       s)) ||
+                !err(launch_tn_reduce(b.P, sp, n, wq, nullptr, nullptr, false, b.Bt, wq, s)))
+                return TSSVD_ECUDA;
+            rb = ts(b.Bt, n, wq, 2, b.U1, b.S1, b.V1);
+            if (rb < 0) return fail(rb);
+        }
+    }
+    // outputs: the sign rule on V = U1, U = Q V1 diag(sgn); zeros past rb
+    const i64 kk = k < rb ? k : rb;
+    bool ok = cudaMemsetAsync(U, 0, sizeof(double) * m * k, s) == cudaSuccess &&
+              cudaMemsetAsync(V, 0, sizeof(double) * n * k, s) == cudaSuccess &&
+              cudaMemsetAsync(S, 0, sizeof(double) * k, s) == cudaSuccess;
+    if (ok && kk > 0) {
+        ok = err(launch_signs(b.U1, wq, n, wq, b.S1, b.sgn, s)) &&
+             err(launch_scale2(b.V1, wq, wq, wq, nullptr, b.sgn, b.V1s, wq, s)) &&
+             err(launch_nn<double, double>(b.Qc, wq, b.V1s, wq, m, wq, wq, b.Uf, wq, b.NP, s)) &&
+             cudaMemcpy2DAsync(U, sizeof(double) * k, b.Uf, sizeof(double) * wq,
+                               sizeof(double) * kk, m, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+             cudaMemcpy2DAsync(V, sizeof(double) * k, b.U1, sizeof(double) * wq,
+                               sizeof(double) * kk, n, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+             cudaMemcpyAsync(S, b.S1, sizeof(double) * kk, cudaMemcpyDeviceToDevice, s) ==
+                 cudaSuccess;
+    }
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    opts->out_rank = kk;
+    opts->ranks[0] = (int)w;
+    opts->ranks[1] = (int)wq;
+    if (code == TSSVD_OK && kk < k) code = TSSVD_RANKDEF;
+    return code;
 }
 
 }  // namespace
@@ -1449,6 +1632,13 @@ int lowrank_svd(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, i
     for (int i = 0; i < 4; i++) opts->sweeps[i] = h[nst - 2].sweeps[i];
     if (code == TSSVD_OK && rank < k) code = TSSVD_RANKDEF;
     return code;
+}
+
+int lowrank_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
+                     int iters, const double *Omega, const double *theta, const int64_t *perm,
+                     double *U, double *S, double *V, tssvd_opts *opts)
+{
+    return lowrank_tsqr_entry(A, m, n, lda, k, l, iters, Omega, theta, perm, U, S, V, opts);
 }
 
 size_t ts_svd_batched_workspace_size(const tssvd_desc *descs, int count, int elem_bytes,
@@ -1629,13 +1819,14 @@ int ts_svd_backward(const double *A, int64_t m, int64_t n, int64_t lda, const do
 size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts)
 {
     if (!opts || m < 1 || n < 1) return 0;
-    const i64 np = n + (n & 1), nn = np * np;
-    const int gy = nn_grid_rows(m, np) > nn_grid_rows(np, np) ? nn_grid_rows(m, np)
-                                                               : nn_grid_rows(np, np);
-    size_t d = 3 * (size_t)m * np + 10 * (size_t)nn + tsqr_workspace_doubles(m, (int)np) +
-               (size_t)gy * np + 4 * (size_t)np + jacobi_prm_doubles(np);
-    return sizeof(double) * d + sizeof(int) * (2 * (size_t)np + opts->max_sweeps + 8) +
-           sizeof(DevStatus) + 32 * 256;
+    const i64 np = n + (n & 1);
+    Bump sz(nullptr, 0);
+    sz.take<DevStatus>(1);
+    sz.take<int>(1);
+    sz.take<double>((size_t)np * np);
+    tsqr_core(nullptr, m, n, n, nullptr, nullptr, n, nullptr, nullptr, n, opts->passes,
+              opts->drop_tol * opts->drop_tol, opts->max_sweeps, sz, nullptr, nullptr);
+    return sz.off + 256;
 }
 
 int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,

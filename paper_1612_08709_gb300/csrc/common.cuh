@@ -84,6 +84,9 @@ cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, 
 // set if a permutation entry is out of range.
 cudaError_t launch_mixing(int h, const double *th, const i64 *perm, double *Mt, int *bad,
                           cudaStream_t s);
+// The draw for w columns (hw = ceil(w/2)) from one for h complex entries.
+cudaError_t launch_restrict_mix(const double *th, const i64 *perm, int h, int hw, double *thw,
+                                i64 *permw, int *bad, cudaStream_t s);
 // Householder TSQR of X (m x n, dense, destroyed): R (n x n, upper) and
 // Q (m x n) with X = Q R; work: tsqr_workspace_doubles(m, n) doubles.
 size_t tsqr_workspace_doubles(i64 m, int n);

@@ -251,9 +251,42 @@ __global__ void tsqr_mask_kernel(double *R, double *Q, i64 m, int n, const int *
     }
 }
 
+// The mixing draw for w columns from the draw for l >= w columns (h and hw
+// complex entries): the first hw phases of each set and each permutation
+// restricted to 0..hw-1 (its entries below hw, in their order).  One
+// thread: h is at most a few thousand.  An entry outside [0, h) sets bad.
+__global__ void restrict_mix_kernel(const double *th, const i64 *perm, int h, int hw,
+                                    double *thw, i64 *permw, int *bad)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int a = 0; a < hw; a++) {
+        thw[a] = th[a];
+        thw[hw + a] = th[h + a];
+    }
+    for (int set = 0; set < 2; set++) {
+        int c = 0;
+        for (int a = 0; a < h; a++) {
+            const i64 v = perm[(i64)set * h + a];
+            if (v < 0 || v >= h) {
+                *bad = 1;
+                continue;
+            }
+            if (v < hw && c < hw) permw[(i64)set * hw + c++] = v;
+        }
+        for (; c < hw; c++) permw[(i64)set * hw + c] = c;  // only after a bad entry
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+
+cudaError_t launch_restrict_mix(const double *th, const i64 *perm, int h, int hw, double *thw,
+                                i64 *permw, int *bad, cudaStream_t s)
+{
+    restrict_mix_kernel<<<1, 32, 0, s>>>(th, perm, h, hw, thw, permw, bad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mixing(int h, const double *th, const i64 *perm, double *Mt, int *bad,
                           cudaStream_t s)

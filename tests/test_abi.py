@@ -123,3 +123,23 @@ def test_tsqr_argument_validation_without_gpu():
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, None, f, ctypes.byref(o)) == -8
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, None, ctypes.byref(o)) == -9
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, f, None) == -10
+
+
+def test_lowrank_tsqr_argument_validation_without_gpu():
+    import paper_1612_08709_gb300 as pkg
+    from paper_1612_08709_gb300._binding import _Opts
+    L = pkg.lib()
+    o = _Opts()
+    L.tssvd_default_opts(ctypes.byref(o))
+    f = ctypes.c_void_p(256)
+    args = lambda **kw: [kw.get("A", f), kw.get("m", 100), kw.get("n", 50), kw.get("lda", 50),
+                         kw.get("k", 5), kw.get("l", 8), kw.get("it", 1), kw.get("Om", f),
+                         kw.get("th", f), kw.get("pm", f), kw.get("U", f), kw.get("S", f),
+                         kw.get("V", f), kw.get("o", ctypes.byref(o))]
+    assert L.lowrank_svd_tsqr(*args(A=None)) == -1
+    assert L.lowrank_svd_tsqr(*args(k=9)) == -5
+    assert L.lowrank_svd_tsqr(*args(l=51)) == -6
+    assert L.lowrank_svd_tsqr(*args(th=None)) == -9
+    assert L.lowrank_svd_tsqr(*args(pm=None)) == -10
+    assert L.lowrank_svd_tsqr(*args(V=None)) == -13
+    assert L.lowrank_svd_tsqr(*args(o=None)) == -14

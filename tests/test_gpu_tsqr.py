@@ -84,3 +84,60 @@ def test_tsqr_rank_deficient_and_invalid_permutation(orc):
     p1[3] = 99
     with pytest.raises(pkg.TsSvdError, match="argument 6"):
         run_tsqr(A, (t1, t2, p1, p2))
+
+
+def run_lowrank_tsqr(A, k, l, iters, Om, mix, **kw):
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    t1, t2, p1, p2 = mix
+    theta = torch.as_tensor(np.concatenate([t1, t2]), device="cuda")
+    perm = torch.as_tensor(np.concatenate([p1, p2]).astype(np.int64), device="cuda")
+    U, S, V, info = pkg.lowrank_svd_tsqr(torch.as_tensor(A, device="cuda"), k, l, iters,
+                                         torch.as_tensor(Om, device="cuda"), theta, perm, **kw)
+    torch.cuda.synchronize()
+    return U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy(), info
+
+
+@gpu
+@pytest.mark.parametrize("m,n,k,l,iters,seed", [(3000, 800, 10, 16, 2, 100),
+                                                (2000, 1500, 20, 25, 1, 101),
+                                                (5000, 600, 8, 8, 0, 102)])
+def test_lowrank_tsqr_matches_oracle(orc, m, n, k, l, iters, seed):
+    """Algorithm 7 on a low-rank-plus-noise matrix: S, U, V against the
+    oracle with the same Omega and mixing draw."""
+    A, _, _, _ = workloads.lowrank_plus_noise(m, n, 40, seed)
+    Om = workloads.gaussian(n, l, seed + 1)
+    mix = workloads.mixing_draws(l, seed + 2)
+    Ur, Sr, Vr, rr, st = orc.lowrank_svd_tsqr(A, k, l, iters, Om, mix)
+    U, S, V, info = run_lowrank_tsqr(A, k, l, iters, Om, mix)
+    assert info["rank"] == rr and info["status"] == st
+    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-12
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-12
+    g = np.full(k, np.inf)
+    for j in range(k):
+        if j > 0: g[j] = min(g[j], Sr[j - 1] - Sr[j])
+        if j + 1 < k: g[j] = min(g[j], Sr[j] - Sr[j + 1])
+    tol = np.clip(1e-10 * Sr[0] / g, 1e-13, 1.0)
+    for j in range(k):
+        eu = min(np.abs(U[:, j] - Ur[:, j]).max(), np.abs(U[:, j] + Ur[:, j]).max())
+        ev = min(np.abs(V[:, j] - Vr[:, j]).max(), np.abs(V[:, j] + Vr[:, j]).max())
+        assert eu <= tol[j] and ev <= tol[j], (j, eu, ev, tol[j])
+
+
+@gpu
+def test_lowrank_tsqr_paper_pin_on_gpu(orc):
+    """The paper's matrix for l = 20, i = 2: spectral error sigma_12 =
+    2.64e-12 (Algorithm 7's printed value), ranks as the oracle's."""
+    l = 20
+    m, n = 1500, 400
+    A, U0, s0, V0 = workloads.paper_dct_matrix(m, n, l)
+    Om = workloads.gaussian(n, l, 4)
+    mix = workloads.mixing_draws(l, 11)
+    U, S, V, info = run_lowrank_tsqr(A, l, l, 2, Om, mix)
+    r = info["rank"]
+    ref = orc.lowrank_svd_tsqr(A, l, l, 2, Om, mix)
+    assert r == ref[3] == 11
+    err = orc.spectral_error(A, U[:, :r], S[:r], V[:, :r])
+    assert abs(err - 2.64e-12) < 0.006 * 2.64e-12
+    assert orc.orth_error(U[:, :r]) < 1e-13

@@ -701,3 +701,23 @@ def test_tsqr_rank_deficient(orc):
         assert r == 7 and st == 2 and S[7] == 0.0
         Sr = np.linalg.svd(A, compute_uv=False)
         assert np.abs(S[:7] - Sr[:7]).max() <= 1e-13 * Sr[0]
+
+
+@pytest.mark.parametrize("l,pin,seed", [(20, "alg7_l20_i2_spectral_err", 4)])
+def test_lowrank_tsqr_paper_values(orc, l, pin, seed):
+    """Algorithm 7 (TSQR-based TS-SVDs) with i = 2 on the same matrix: the
+    discard at the working precision itself (not its square root) leaves
+    the spectral error at the first singular value below 1e-11, the
+    paper's printed 2.64e-12 for l = 20.  (For l = 10 the first value below
+    1e-11, 7.74e-12, sits within a factor 1.3 of the threshold, so whether
+    R's diagonal entry for it falls below depends on the random draw; that
+    printed value is not a deterministic pin.)"""
+    pins = paper_pins()
+    m, n = 1500, 400
+    A, U0, s0, V0 = workloads.paper_dct_matrix(m, n, l)
+    Om = workloads.gaussian(n, l, seed)
+    U, S, V, r, st = orc.lowrank_svd_tsqr(A, l, l, 2, Om, workloads.mixing_draws(l, seed + 7))
+    err = orc.spectral_error(A, U[:, :r], S[:r], V[:, :r])
+    assert abs(err - pins[pin]) < 0.006 * pins[pin], (err, pins[pin])
+    assert orc.orth_error(U[:, :r]) < 1e-13
+    assert orc.orth_error(V[:, :r]) < 1e-13
