@@ -52,6 +52,12 @@ WORKLOADS = {
     # with sigma_j = 1/j plus 1e-4 Gaussian noise), k = 50, l = 60, 2 power steps
     "lowrank_100k_x_20k": dict(kind="lowrank", m=100_000, n=20_000, r=200, k=50, l=60, iters=2,
                                seed=4),
+    # Algorithm 2 (randomized TSQR TS-SVD, Remark "randomness" mixing) on the
+    # 200,000 x 200 recipe
+    "tsqr_200k_x_200": dict(kind="tsqr", m=200_000, n=200, lo=1e-8, seed=2, passes=2),
+    # Algorithm 7 (TSQR-based TS-SVDs) on the low-rank workload
+    "lowrank_tsqr_100k_x_20k": dict(kind="lowrank", m=100_000, n=20_000, r=200, k=50, l=60,
+                                    iters=2, seed=4, method="tsqr"),
     # forward and backward of the differentiable TS-SVD: 500,000 x 512 FP32,
     # sigma_j = 1 + (n - j)/n, loss sum_j w_j sigma_j + ||U_k^T B||_F^2 with
     # k = 64, B 500,000 x 8
@@ -605,8 +611,15 @@ def run_lowrank(args):
     del Ur, Vr
     Om = torch.as_tensor(workloads.gaussian(n, l, w["seed"] + 3), device=dev)
     mode = args.mode if args.mode in ("fp64", "fp64_tc") else "fp64"
+    tsqr = w.get("method") == "tsqr"
+    if tsqr:
+        t1, t2, p1, p2 = workloads.mixing_draws(l, w["seed"] + 5)
+        theta = torch.as_tensor(np.concatenate([t1, t2]), device=dev)
+        perm = torch.as_tensor(np.concatenate([p1, p2]).astype(np.int64), device=dev)
 
     def step():
+        if tsqr:
+            return pkg.lowrank_svd_tsqr(A, k, l, it, Om, theta, perm, drop_tol=0.0, mode=mode)
         return pkg.lowrank_svd(A, k, l, it, Om, drop_tol=0.0, mode=mode)
     for _ in range(args.warmup):
         U, S, V, info = step()
@@ -624,12 +637,92 @@ def run_lowrank(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "iters": it,
-                      "mode": mode, "flops": "2(2i+2)mnl",
+                      "mode": mode, "algorithm": 7 if tsqr else 8, "flops": "2(2i+2)mnl",
                       "l2": "inputs larger than L2 (A is %.0f GB)" % (m * n * 8 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
            "accuracy": {"sigma_err_vs_signal_max": float((S - s[:k]).abs().max()),
                         "orth_U": float((U.T @ U - eye).abs().max()),
                         "orth_V": float((V.T @ V - eye).abs().max()), "rank": info["rank"]}}
+    print(json.dumps(out), flush=True)
+
+
+def run_tsqr(args):
+    """Algorithm 1 or 2 (randomized TSQR TS-SVD) on the tall-skinny recipe.
+    Nominal flops 12mn^2 for Algorithm 2 (mixing product 2mn^2, two TSQRs of
+    4mn^2 each: Householder factorization and Q, U = Q P 2mn^2), 8mn^2 for
+    Algorithm 1."""
+    import numpy as np
+    import torch
+
+    import paper_1612_08709_gb300 as pkg
+    import workloads
+    w = WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    m, n, passes = w["m"], w["n"], w["passes"]
+    sigma = workloads.sigma_geometric(n, w["lo"])
+    A, U0, s0, V0 = workloads.known_spectrum_torch(m, n, sigma, w["seed"], dev)
+    del U0, V0
+    t1, t2, p1, p2 = workloads.mixing_draws(n, w["seed"] + 5)
+    theta = torch.as_tensor(np.concatenate([t1, t2]), device=dev)
+    perm = torch.as_tensor(np.concatenate([p1, p2]).astype(np.int64), device=dev)
+
+    mode = args.mode if args.mode in ("fp64", "fp64_tc") else "fp64"
+
+    def step():
+        return pkg.ts_svd_tsqr(A, theta, perm, passes=passes, drop_tol=0.0, mode=mode)
+    for _ in range(args.warmup):
+        U, S, V, info = step()
+    L = pkg.lib()
+    clocks = ClockSampler(0)
+    clocks.start()
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
+    n0 = L.tssvd_launch_count()
+    ms = _timed(torch, step, args.steps)
+    launches = L.tssvd_launch_count() - n0
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
+    clk = clocks.stop()
+    U, S, V, info = step()
+    flops = (12.0 if passes == 2 else 8.0) * m * n * n
+    # the Householder kernels against the FP64 pipe, LAPACK's operation
+    # counts per block of b rows: 2bn^2 - 2n^3/3 to factor it, 4bn^2 - 2n^3 to
+    # apply its reflections to [C; 0] (forming Q), over every level of the
+    # reduction tree (blocks of ceil(rows / b) with b = max(4n, 256), the
+    # stacked n x n R factors the next level)
+    qr_flops, rows = 0.0, m
+    while True:
+        b = max(4 * n if n <= 256 else 2 * n, 256)
+        nb = max(1, -(-rows // b))
+        qr_flops += 6.0 * rows * n * n - nb * (2.0 / 3.0 + 2.0) * n ** 3
+        if nb == 1:
+            break
+        rows = nb * n
+    qr_flops *= passes
+    qr_ms = sum(t for k2, (c, t) in kernels.items()
+                if k2.startswith(("tsqr_geqrf", "tsqr_orgqr"))) / args.steps
+    roof = None
+    if qr_ms > 0:
+        ach = qr_flops / (qr_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "tsqr_geqrf+tsqr_orgqr", "achieved": ach,
+                "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                "share_of_step": qr_ms / ms,
+                "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)"}
+    st = torch.as_tensor(s0, device=dev)
+    eye = torch.eye(n, dtype=U.dtype, device=dev)
+    out = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "m": m, "n": n, "algorithm": passes,
+                      "mode": mode,
+                      "flops": "12mn^2" if passes == 2 else "8mn^2",
+                      "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 8 / 1e9)},
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
+           "accuracy": {"sigma_err_normwise": float((S - st).abs().max() / st[0]),
+                        "orth_U": float((U.T @ U - eye).abs().max()),
+                        "orth_V": float((V.T @ V - eye).abs().max()), "rank": info["rank"]},
+           "kernels_ms": {k2: {"launches": c, "total_ms": t} for k2, (c, t) in kernels.items()}}
     print(json.dumps(out), flush=True)
 
 
@@ -703,6 +796,8 @@ def main():
         run_lowrank(args)
     elif WORKLOADS[args.workload]["kind"] == "grad":
         run_grad(args)
+    elif WORKLOADS[args.workload]["kind"] == "tsqr":
+        run_tsqr(args)
     else:
         run_ours(args)
 

@@ -142,7 +142,10 @@ size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
  * 2 then factors Q = Q2 R2 (same discard) and uses T = R2 R.  The SVD of
  * T (or R) = U~ Sigma V~^T is one-sided Jacobi; U = Q U~, V = Omega^-1 V~.
  * The leading n triplets are returned with the sign rule of ts_svd.  All
- * arithmetic is FP64 (opts->mode is not used; opts->scale is not used).
+ * arithmetic is FP64; opts->mode selects the engine of the two tall
+ * products (B* = A Omega* and U = Q U~): TSSVD_FP64 (FMA) or TSSVD_FP64_TC
+ * (FP64-accurate digit products on the tensor cores).  opts->scale is not
+ * used.
  *   A     [in]  m x n row-major, leading dimension lda >= n (device).
  *   theta [in]  2h phases (device, radians): the diagonal of D (h values)
  *               then of D~ (h values), drawn uniformly by the caller.
@@ -150,7 +153,8 @@ size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
  *               x_perm[a], then that of S~; each a permutation of 0..h-1.
  *   U, S, V, opts as for ts_svd.  n <= 4096.
  * Errors: -1 A, -2 m < n, -3 n, -4 lda, -5 theta, -6 perm NULL or not in
- * range (detected on the device), -7 U, -8 S, -9 V, -10 opts.
+ * range (detected on the device), -7 U, -8 S, -9 V, -10 opts (or a mode
+ * other than TSSVD_FP64 / TSSVD_FP64_TC).
  */
 int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double *theta,
                 const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts);
@@ -164,14 +168,17 @@ int ts_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, const double
  * device), as in Algorithms 1 and 2.  Every TS-SVD uses the caller's one
  * mixing draw for l columns, restricted to its width w (the first
  * ceil(w/2) phases of each set; each permutation's entries below ceil(w/2)
- * in their order).  FP64 throughout; the discard compares R's diagonal
- * with the working precision opts->drop_tol^2.
+ * in their order).  The TS-SVDs are FP64; opts->mode selects the engine
+ * of the tall products A Q~ and A^T Q: TSSVD_FP64 (FMA) or TSSVD_FP64_TC
+ * (FP64-accurate digit products on the tensor cores; other modes are
+ * rejected).  The discard compares R's diagonal with the working
+ * precision opts->drop_tol^2.
  *   A, m, n, lda, k, l, iters, Omega, U, S, V as for lowrank_svd
  *   (l <= 4096).
  *   theta, perm: the draw of ts_svd_tsqr for l columns (2 ceil(l/2) each).
  * Errors: -1 A, -2 m, -3 n, -4 lda, -5 k, -6 l, -7 iters, -8 Omega,
  * -9 theta, -10 perm (NULL or not a permutation), -11 U, -12 S, -13 V,
- * -14 opts.
+ * -14 opts (or a mode other than TSSVD_FP64 / TSSVD_FP64_TC).
  */
 int lowrank_svd_tsqr(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
                      int iters, const double *Omega, const double *theta, const int64_t *perm,

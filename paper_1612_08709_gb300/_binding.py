@@ -441,10 +441,11 @@ class LowRankSVD(torch.autograd.Function):
 
 
 def ts_svd_tsqr(A, theta, perm, passes=2, drop_tol=PAPER_DROP_TOL, max_sweeps=50, stream=None,
-                workspace=None):
+                workspace=None, mode="fp64"):
     """Algorithm 1 (passes=1) or 2 (passes=2) on a float64 CUDA tensor A
     (m x n).  theta: 2h phases, perm: 2h int64 indices (h = ceil(n / 2)),
-    both CUDA tensors: the random mixing of Remark "randomness".  Returns
+    both CUDA tensors: the random mixing of Remark "randomness".  mode
+    "fp64" or "fp64_tc": the engine of the two tall products.  Returns
     (U, S, V, info).  See include/tssvd.h (ts_svd_tsqr)."""
     A = _as_matrix(A)
     m, n = A.shape
@@ -459,7 +460,7 @@ def ts_svd_tsqr(A, theta, perm, passes=2, drop_tol=PAPER_DROP_TOL, max_sweeps=50
     U = torch.empty((m, n), dtype=torch.float64, device=A.device)
     S = torch.empty((n,), dtype=torch.float64, device=A.device)
     V = torch.empty((n, n), dtype=torch.float64, device=A.device)
-    o = _opts(passes, False, drop_tol, "fp64", max_sweeps, stream, workspace)
+    o = _opts(passes, False, drop_tol, mode, max_sweeps, stream, workspace)
     with torch.cuda.device(A.device):
         rc = lib().ts_svd_tsqr(_ptr(A), m, n, A.stride(0), _ptr(theta), _ptr(perm), _ptr(U),
                                _ptr(S), _ptr(V), ctypes.byref(o))
@@ -468,10 +469,11 @@ def ts_svd_tsqr(A, theta, perm, passes=2, drop_tol=PAPER_DROP_TOL, max_sweeps=50
 
 
 def lowrank_svd_tsqr(A, k, l, iters, Omega, theta, perm, drop_tol=PAPER_DROP_TOL, max_sweeps=50,
-                     stream=None, workspace=None):
+                     stream=None, workspace=None, mode="fp64"):
     """Algorithm 7 (float64 CUDA tensors): returns (U m x k, S k, V n x k,
-    info).  theta, perm: the mixing draw for l columns (2 ceil(l/2) each).
-    See include/tssvd.h (lowrank_svd_tsqr)."""
+    info).  theta, perm: the mixing draw for l columns (2 ceil(l/2) each);
+    mode "fp64" or "fp64_tc" (the engine of the tall products).  See
+    include/tssvd.h (lowrank_svd_tsqr)."""
     A = _as_matrix(A)
     m, n = A.shape
     Omega = Omega.contiguous()
@@ -483,7 +485,7 @@ def lowrank_svd_tsqr(A, k, l, iters, Omega, theta, perm, drop_tol=PAPER_DROP_TOL
     U = torch.empty((m, k), dtype=torch.float64, device=A.device)
     S = torch.empty((k,), dtype=torch.float64, device=A.device)
     V = torch.empty((n, k), dtype=torch.float64, device=A.device)
-    o = _opts(2, False, drop_tol, "fp64", max_sweeps, stream, workspace)
+    o = _opts(2, False, drop_tol, mode, max_sweeps, stream, workspace)
     with torch.cuda.device(A.device):
         rc = lib().lowrank_svd_tsqr(_ptr(A), m, n, A.stride(0), int(k), int(l), int(iters),
                                     _ptr(Omega), _ptr(theta), _ptr(perm), _ptr(U), _ptr(S),

@@ -805,7 +805,7 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
 // Number of per-sub-call status blocks used by lowrank: 2 per power step + 2.
 cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *Mt, double *U,
                       i64 ldu, double *S, double *V, i64 ldv, int passes, double wp,
-                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s);
+                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s, bool oz = false);
 
 cudaError_t lowrank_core(const double *A, i64 m, i64 n, i64 lda, i64 k, i64 l, int iters,
                          const double *Omega, double *U, double *S, double *V, double tol,
@@ -1185,10 +1185,12 @@ int lowrank_backward_entry(int64_t m, int64_t n, int64_t k, const double *U, con
 // padded to n'), B* = Q R by TSQR, discard of R's diagonal below |R_00| wp,
 // [Q = Q2 R2, discard, T = R2 R], SVD of T by one-sided Jacobi, U = Q U~,
 // V = O^T V~ (leading n rows and triplets).  st->rank, st->sweeps[2] and
-// st->err are written.  Sizing when ws has no base.
+// st->err are written.  oz: the two tall products (B* and U) as
+// FP64-accurate digit products on the tensor cores.  Sizing when ws has no
+// base.
 cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *Mt, double *U,
                       i64 ldu, double *S, double *V, i64 ldv, int passes, double wp,
-                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s)
+                      int max_sweeps, Bump &ws, DevStatus *st, cudaStream_t s, bool oz)
 {
     const i64 np = n + (n & 1), nn = np * np;
     const int gy = nn_grid_rows(rows, np) > nn_grid_rows(np, np) ? nn_grid_rows(rows, np)
@@ -1205,10 +1207,22 @@ cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *M
     double *NP = ws.take<double>((size_t)gy * np);
     double *norms = ws.take<double>(np), *sigma = ws.take<double>(np), *sgn = ws.take<double>(np);
     double *prm = ws.take<double>(jacobi_prm_doubles(np));
+    int *er = oz ? ws.take<int>(rows) : nullptr, *em = oz ? ws.take<int>(np) : nullptr;
+    uint8_t *aimg = oz ? ws.take<uint8_t>(oz_row_image_bytes(rows, (int)np)) : nullptr;
+    uint8_t *bimg = oz ? ws.take<uint8_t>(oz_image_bytes((int)np, (int)np)) : nullptr;
     if (ws.sizing()) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
+    // C (rows x N) = Xa (rows x K) M (K x N)
+    auto tall = [&](const double *Xa, i64 lda_, i64 K, const double *M, i64 ldm, i64 N, double *C,
+                    i64 ldc) -> cudaError_t {
+        if (!oz) return launch_nn<double, double>(Xa, lda_, M, ldm, rows, K, N, C, ldc, NP, s);
+        CK(launch_oz_rowexp<double>(Xa, lda_, rows, (int)K, nullptr, er, s));
+        CK(launch_oz_image(M, ldm, (int)K, (int)N, nullptr, em, bimg, s));
+        return launch_oz_nn<double, double>(Xa, lda_, rows, (int)K, nullptr, er, aimg, bimg, em,
+                                            (int)N, C, ldc, st, s);
+    };
     // B* = X O^T = X Mt[0:n, :]
-    CK(launch_nn<double, double>(X, ldx, Mt, np, rows, n, np, Bst, np, NP, s));
+    CK(tall(X, ldx, n, Mt, np, np, Bst, np));
     CK(launch_tsqr(Bst, rows, (int)np, work, R1, Q1, s));
     CK(launch_tsqr_discard(R1, Q1, rows, (int)np, wp, keep, s));
     double *Qf = Q1;
@@ -1231,7 +1245,7 @@ cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *M
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Q (P[:, 0:n] diag(sgn))
     CK(launch_scale2(Pm, np, np, n, nullptr, sgn, Pp, n, s));
-    CK(launch_nn<double, double>(Qf, np, Pp, n, rows, np, n, U, ldu, NP, s));
+    CK(tall(Qf, np, np, Pp, n, n, U, ldu));
     CK(launch_convert<double>(sigma, np, 1, n, S, n, s));
     return cudaSuccess;
 }
@@ -1252,6 +1266,8 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     if (!S) return -8;
     if (!V) return -9;
     if (!check_opts(opts)) return -10;
+    if (opts->mode != TSSVD_FP64 && opts->mode != TSSVD_FP64_TC) return -10;
+    const bool oz = opts->mode == TSSVD_FP64_TC;
     cudaStream_t s = (cudaStream_t)opts->stream;
     const i64 np = n + (n & 1);
     const double wp = opts->drop_tol * opts->drop_tol;
@@ -1260,7 +1276,7 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     sz.take<int>(1);
     sz.take<double>((size_t)np * np);
     tsqr_core(nullptr, m, n, n, nullptr, nullptr, n, nullptr, nullptr, n, opts->passes, wp,
-              opts->max_sweeps, sz, nullptr, s);
+              opts->max_sweeps, sz, nullptr, s, oz);
     void *base = nullptr;
     std::unique_lock<std::mutex> lk;
     int rc = acquire_ws(opts, sz.off, &base, lk);
@@ -1274,7 +1290,7 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     if (e == cudaSuccess) e = launch_mixing((int)(np / 2), theta, perm, Mt, bad, s);
     if (e == cudaSuccess)
         e = tsqr_core(A, m, n, lda, Mt, U, n, S, V, n, opts->passes, wp, opts->max_sweeps, ws, st,
-                      s);
+                      s, oz);
     if (e != cudaSuccess) {
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
@@ -1303,7 +1319,9 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
 // removed: every step continues with the width the previous TS-SVD kept,
 // read back from the device (2 iters + 2 short host synchronisations), and
 // every TS-SVD takes the caller's draw for l columns restricted to its
-// width.
+// width.  The tall products A Q~ and A^T Q run in FP64 FMA or, with
+// TSSVD_FP64_TC, on the digit-sliced tensor-core kernels (A's row and
+// column digit images built once per call).
 int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t l,
                        int iters, const double *Omega, const double *theta,
                        const int64_t *perm, double *U, double *S, double *V, tssvd_opts *opts)
@@ -1322,21 +1340,26 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
     if (!S) return -12;
     if (!V) return -13;
     if (!check_opts(opts)) return -14;
+    if (opts->mode != TSSVD_FP64 && opts->mode != TSSVD_FP64_TC) return -14;
     cudaStream_t s = (cudaStream_t)opts->stream;
+    const bool oz = opts->mode == TSSVD_FP64_TC;
     const i64 lp = l + (l & 1);
     const int hl = (int)(lp / 2);
     const double wp = opts->drop_tol * opts->drop_tol;
     const int nst = 2 * iters + 2;
     const i64 big = m > n ? m : n;
-    const int sp = tn_splits(m, n, l, false);
+    const int sp = oz ? oz_tn_splits(m, (int)n, (int)l) : tn_splits(m, n, l, false);
     const int gy = nn_grid_rows(big, l);
     struct Bufs {
         DevStatus *st;
         int *bad;
         i64 *permw;
         double *thw, *Mt, *Qt, *Y, *Q, *Qc, *Bt, *U1, *S1, *V1, *V1s, *Uf, *tS, *tV, *sgn, *P, *NP;
+        unsigned long long *bits;
+        int *exA, *erA, *exQ, *em;
+        uint8_t *rimgA, *cimgA, *cimgQ, *bimg;
         char *sub;
-    } b;
+    } b = {};
     size_t sub_bytes = 0;
     {
         Bump probe(nullptr, 0);
@@ -1345,7 +1368,7 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
         sub_bytes = probe.off + 256;
     }
     auto carve = [&](Bump &w) {
-        b.st = w.take<DevStatus>(nst);
+        b.st = w.take<DevStatus>(nst + 1);
         b.bad = w.take<int>(1);
         b.permw = w.take<i64>(2 * (size_t)hl);
         b.thw = w.take<double>(2 * (size_t)hl);
@@ -1365,6 +1388,17 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
         b.sgn = w.take<double>(l);
         b.P = w.take<double>((size_t)sp * n * l);
         b.NP = w.take<double>((size_t)gy * l);
+        if (oz) {
+            b.bits = w.take<unsigned long long>(n > l ? n : l);
+            b.exA = w.take<int>(n);
+            b.erA = w.take<int>(m);
+            b.exQ = w.take<int>(l);
+            b.em = w.take<int>(l);
+            b.rimgA = w.take<uint8_t>(oz_row_image_bytes(m, (int)n));
+            b.cimgA = w.take<uint8_t>(oz_gram_image_bytes(m, (int)n));
+            b.cimgQ = w.take<uint8_t>(oz_gram_image_bytes(m, (int)l));
+            b.bimg = w.take<uint8_t>(oz_image_bytes((int)n, (int)l));
+        }
         b.sub = w.take<char>(sub_bytes);
     };
     Bump sz(nullptr, 0);
@@ -1413,10 +1447,41 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
         return TSSVD_ECUDA;
     i64 w = l;
     auto err = [&](cudaError_t e) { return e == cudaSuccess; };
+    DevStatus *pst = b.st + nst;  // the digit products' bounded waits
+    if (cudaMemsetAsync(pst, 0, sizeof(DevStatus), s) != cudaSuccess) return TSSVD_ECUDA;
+    // Y = A X (m x c, X n x c dense) and Co = A^T Z (n x c, Z m x c dense)
+    auto AX = [&](const double *X, i64 c, double *Yo) -> cudaError_t {
+        if (!oz) return launch_nn<double, double>(A, lda, X, c, m, n, c, Yo, c, b.NP, s);
+        CK(launch_oz_image(X, c, (int)n, (int)c, nullptr, b.em, b.bimg, s));
+        return launch_oz_nn_run<double>(b.rimgA, m, (int)n, b.erA, b.bimg, b.em, (int)c, Yo, c,
+                                        pst, s);
+    };
+    auto AtZ = [&](const double *Z, i64 c, double *Co) -> cudaError_t {
+        if (!oz) {
+            CK(launch_tn_partial<double, double>(A, lda, Z, c, m, n, c, sp, false, b.P, s));
+        } else {
+            CK(cudaMemsetAsync(b.bits, 0, sizeof(unsigned long long) * c, s));
+            CK(launch_colmax<double>(Z, m, c, c, b.bits, s));
+            CK(launch_oz_exp_from_bits(b.bits, (int)c, b.exQ, s));
+            CK(launch_oz_col_image(Z, c, m, (int)c, b.exQ, b.cimgQ, s));
+            CK(launch_oz_tn(b.cimgA, b.exA, (int)n, b.cimgQ, b.exQ, (int)c, m, sp, b.P, pst, s));
+        }
+        return launch_tn_reduce(b.P, sp, n, c, nullptr, nullptr, false, Co, c, s);
+    };
+    if (oz) {
+        auto images = [&]() -> cudaError_t {
+            CK(cudaMemsetAsync(b.bits, 0, sizeof(unsigned long long) * n, s));
+            CK(launch_colmax<double>(A, m, n, lda, b.bits, s));
+            CK(launch_oz_exp_from_bits(b.bits, (int)n, b.exA, s));
+            CK(launch_oz_rowexp<double>(A, lda, m, (int)n, nullptr, b.erA, s));
+            CK(launch_oz_row_image<double>(A, lda, m, (int)n, nullptr, b.erA, b.rimgA, s));
+            return launch_oz_col_image(A, lda, m, (int)n, b.exA, b.cimgA, s);
+        };
+        if (!err(images())) return TSSVD_ECUDA;
+    }
     for (int it = 0; it < iters && w > 0; it++) {
         // Y = A Q~ (m x w); Y = Q R (Algorithm 1)
-        if (!err(launch_nn<double, double>(A, lda, b.Qt, w, m, n, w, b.Y, w, b.NP, s)))
-            return TSSVD_ECUDA;
+        if (!err(AX(b.Qt, w, b.Y))) return TSSVD_ECUDA;
         i64 r = ts(b.Y, m, w, 1, b.Q, b.tS, b.tV);
         if (r < 0) return fail(r);
         if (r == 0) {
@@ -1426,8 +1491,7 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
         // Q (m x r) compacted, then Y~ = A^T Q (n x r); Y~ = Q~ R~ (Algorithm 1)
         if (cudaMemcpy2DAsync(b.Qc, sizeof(double) * r, b.Q, sizeof(double) * w,
                               sizeof(double) * r, m, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-            !err(launch_tn_partial<double, double>(A, lda, b.Qc, r, m, n, r, sp, false, b.P, s)) ||
-            !err(launch_tn_reduce(b.P, sp, n, r, nullptr, nullptr, false, b.Bt, r, s)))
+            !err(AtZ(b.Qc, r, b.Bt)))
             return TSSVD_ECUDA;
         const i64 r2 = ts(b.Bt, n, r, 1, b.U1, b.tS, b.tV);
         if (r2 < 0) return fail(r2);
@@ -1440,8 +1504,7 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
     i64 rb = 0, wq = 0;
     if (w > 0) {
         // Y = A Q~; Y = Q R (Algorithm 2)
-        if (!err(launch_nn<double, double>(A, lda, b.Qt, w, m, n, w, b.Y, w, b.NP, s)))
-            return TSSVD_ECUDA;
+        if (!err(AX(b.Qt, w, b.Y))) return TSSVD_ECUDA;
         wq = ts(b.Y, m, w, 2, b.Q, b.tS, b.tV);
         if (wq < 0) return fail(wq);
         if (wq > 0) {
@@ -1449,9 +1512,7 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
             if (cudaMemcpy2DAsync(b.Qc, sizeof(double) * wq, b.Q, sizeof(double) * w,
                                   sizeof(double) * wq, m, cudaMemcpyDeviceToDevice,
                                   s) != cudaSuccess ||
-                !err(launch_tn_partial<double, double>(A, lda, b.Qc, wq, m, n, wq, sp, false, b.P,
-                                                       s)) ||
-                !err(launch_tn_reduce(b.P, sp, n, wq, nullptr, nullptr, false, b.Bt, wq, s)))
+                !err(AtZ(b.Qc, wq, b.Bt)))
                 return TSSVD_ECUDA;
             rb = ts(b.Bt, n, wq, 2, b.U1, b.S1, b.V1);
             if (rb < 0) return fail(rb);
@@ -1473,10 +1534,14 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
              cudaMemcpyAsync(S, b.S1, sizeof(double) * kk, cudaMemcpyDeviceToDevice, s) ==
                  cudaSuccess;
     }
-    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+    int perr = 0;
+    if (!ok ||
+        cudaMemcpyAsync(&perr, &pst->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return TSSVD_ECUDA;
     }
+    if (perr) return TSSVD_ETIMEOUT;
     opts->out_rank = kk;
     opts->ranks[0] = (int)w;
     opts->ranks[1] = (int)wq;
@@ -1825,7 +1890,8 @@ size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts)
     sz.take<int>(1);
     sz.take<double>((size_t)np * np);
     tsqr_core(nullptr, m, n, n, nullptr, nullptr, n, nullptr, nullptr, n, opts->passes,
-              opts->drop_tol * opts->drop_tol, opts->max_sweeps, sz, nullptr, nullptr);
+              opts->drop_tol * opts->drop_tol, opts->max_sweeps, sz, nullptr, nullptr,
+              opts->mode == TSSVD_FP64_TC);
     return sz.off + 256;
 }
 

@@ -1,10 +1,20 @@
 // Algorithms 1 and 2 (randomized TS-SVD via TSQR): the random mixing of
 // Remark "randomness" as an explicit orthogonal matrix, Householder TSQR
-// (leaf QRs of row blocks, a reduction tree over the stacked R factors,
+// (blocked QRs of row blocks, a reduction tree over the stacked R factors,
 // and Q formed explicitly back down the tree) and the discard of R's
-// diagonal.  All in FP64 on the CUDA cores: the leaf QRs are bound by the
-// FP64 pipe (2 b n^2 flops per block of b rows).
+// diagonal.  All in FP64 on the CUDA cores: the block QRs are bound by the
+// FP64 pipe (2 b n^2 flops to factor a block of b rows, 4 b n^2 to form its
+// Q).  Panels of up to 16 columns are factored in shared memory; their
+// reflections are applied to the rest of the block in compact WY form
+// (I - V T V^T), register-tiled, so that every panel streams the block
+// through L2 once.  At the upper levels of the tree, where blocks are
+// fewer than SMs, the column tiles of one block are spread over the CTAs
+// of a thread-block cluster.
 #include "common.cuh"
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace tssvd {
 namespace {
@@ -81,147 +91,428 @@ __global__ void mixing_kernel(int h, const double *__restrict__ th, const i64 *_
 }
 
 constexpr int kQrThreads = 256;
+constexpr int kQrWarps = kQrThreads / 32;
+// Columns per tile of the trailing updates (lanes: TC columns x 32/TC rows).
+constexpr int kQrTC = 16;
 
-// Block reduction of one value per thread (all threads get the sum).
-__device__ __forceinline__ double qr_block_sum(double v, double *red)
+// Rows [qr_row0(q), qr_row0(q + 1)) of a tree level with `rows` rows form
+// block q of nblk (an even split: every block has at least n rows).
+__host__ __device__ __forceinline__ i64 qr_row0(i64 rows, int nblk, int q)
+{
+    return (i64)q * rows / nblk;
+}
+
+// Shared memory of the QR kernels, in doubles: the panel P (rbmax x PS),
+// its top NB rows as V with the unit diagonal and zeros made explicit
+// (Vt), the per-row-group partials of W = V^T C (Wp), W (Ws), op(T) W
+// (Wt), T, V^T V (G) and reduction scratch.
+__host__ __device__ constexpr size_t qr_smem_doubles(int nb, int tc, i64 rbmax)
+{
+    return (size_t)rbmax * (nb + 1) + (size_t)nb * (nb + 1) + (size_t)kQrThreads * nb +
+           2 * (size_t)nb * tc + 2 * (size_t)nb * nb + (size_t)kQrWarps * nb + 8 + nb;
+}
+
+template <int NB, int TC>
+struct QrSmem {
+    double *P, *Vt, *Wp, *Ws, *Wt, *Tm, *G, *red, *stp;
+    __device__ QrSmem(double *base, int rbmax)
+    {
+        P = base;
+        Vt = P + (size_t)rbmax * (NB + 1);
+        Wp = Vt + NB * (NB + 1);
+        Ws = Wp + kQrThreads * NB;
+        Wt = Ws + NB * TC;
+        Tm = Wt + NB * TC;
+        G = Tm + NB * NB;
+        red = G + NB * NB;
+        stp = red + kQrWarps * NB;
+    }
+};
+
+// CTA-wide sums of each thread's v[0..K): out[k] (shared) for all threads
+// on return.
+template <int K>
+__device__ __forceinline__ void qr_sum_vec(double (&v)[K], double *red, double *out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) red[warp * K + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < kQrWarps; w++) t += red[w * K + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// CTA-wide maximum of one value per thread, returned to every thread.
+__device__ __forceinline__ double qr_max(double v, double *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
     double t = 0.0;
-    for (int w = 0; w < kQrThreads / 32; w++) t += red[w];
+    for (int w = 0; w < kQrWarps; w++) t = fmax(t, red[w]);
+    __syncthreads();
     return t;
 }
 
-// Householder QR of row block blk of X (rows [r0, r1), n columns, in
-// place): reflection j is I - tau_j v v^T with v_j = 1 and v below the
-// diagonal stored in X; R (upper triangle of the block's first n rows) is
-// copied, with zeros below, into rows [blk n, blk n + n) of Rs.  Each
-// step reduces column j's norm, forms the reflection, then w = v^T X (for
-// the trailing columns, warps on interleaved rows, lanes on columns) and
-// the rank-one update.
-__global__ void __launch_bounds__(kQrThreads) geqr2_kernel(double *__restrict__ X, i64 ldx,
-                                                          i64 m, int n, i64 b, int nblk,
-                                                          double *__restrict__ tau,
-                                                          double *__restrict__ Rs)
+// Euclidean norm of P[i][j] over rows lo <= i < rb: the plain sum of
+// squares, or, when that leaves [2^-960, 2^960] (underflow or overflow
+// possible), the sum of squares of the entries scaled by a power of two
+// near 1 / max |entry|.  Uniform across the CTA; all threads get it.
+template <int PS>
+__device__ double qr_col_norm(const double *P, int lo, int rb, int j, double *red, double *out,
+                              bool *in_range)
 {
-    extern __shared__ double qr_s[];  // [8][n] partial w, then w
-    __shared__ double red[kQrThreads / 32];
-    __shared__ double step_s[2];      // tau_j, 1 / (alpha - beta)
-    const int blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const i64 r0 = (i64)blk * b;
-    const i64 r1 = (blk == nblk - 1) ? m : r0 + b;
-    const i64 rows = r1 - r0;
-    double *Xb = X + r0 * ldx;
-    const int kq = rows < n ? (int)rows : n;
-    for (int j = 0; j < kq; j++) {
-        // ---- the reflection for column j (rows j .. rows-1)
-        double ss = 0.0;
-        for (i64 i = j + 1 + tid; i < rows; i += kQrThreads) {
-            const double x = Xb[i * ldx + j];
-            ss = fma(x, x, ss);
-        }
-        const double xn2 = qr_block_sum(ss, red);
-        if (tid == 0) {
-            const double alpha = Xb[(i64)j * ldx + j];
-            if (xn2 == 0.0) {
-                step_s[0] = 0.0;
-                step_s[1] = 0.0;
-            } else {
-                const double beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
-                step_s[0] = (beta - alpha) / beta;
-                step_s[1] = 1.0 / (alpha - beta);
-                Xb[(i64)j * ldx + j] = beta;
-            }
-            tau[(i64)blk * n + j] = step_s[0];
-        }
-        __syncthreads();
-        const double tj = step_s[0], scv = step_s[1];
-        if (tj == 0.0) continue;  // uniform across the block
-        for (i64 i = j + 1 + tid; i < rows; i += kQrThreads) Xb[i * ldx + j] *= scv;
-        __syncthreads();
-        // ---- w_c = X[j][c] + sum_{i>j} v_i X[i][c], c > j
-        for (int c = j + 1 + lane; c < n; c += 32) {
-            double acc = 0.0;
-            for (i64 i = j + 1 + warp; i < rows; i += kQrThreads / 32)
-                acc = fma(Xb[i * ldx + j], Xb[i * ldx + c], acc);
-            qr_s[warp * n + c] = acc;
-        }
-        __syncthreads();
-        for (int c = j + 1 + tid; c < n; c += kQrThreads) {
-            double w = Xb[(i64)j * ldx + c];
-            for (int q = 0; q < kQrThreads / 32; q++) w += qr_s[q * n + c];
-            qr_s[c] = w;  // row 0 of the partials is no longer needed for c
-        }
-        __syncthreads();
-        // ---- X[i][c] -= tau v_i w_c for i >= j, c > j
-        for (int c = j + 1 + lane; c < n; c += 32) {
-            const double tw = tj * qr_s[c];
-            if (warp == 0) Xb[(i64)j * ldx + c] -= tw;
-            for (i64 i = j + 1 + warp; i < rows; i += kQrThreads / 32)
-                Xb[i * ldx + c] = fma(-tw, Xb[i * ldx + j], Xb[i * ldx + c]);
-        }
-        __syncthreads();
+    const int tid = threadIdx.x;
+    double ss[1] = {0.0};
+    for (int i = lo + tid; i < rb; i += kQrThreads) {
+        const double x = P[i * PS + j];
+        ss[0] = fma(x, x, ss[0]);
     }
-    for (int j = kq; j < n; j++)
-        if (tid == 0) tau[(i64)blk * n + j] = 0.0;
-    // R into the stacked array (zeros below the diagonal and past kq rows)
-    double *R = Rs + (i64)blk * n * n;
-    for (int e = tid; e < n * n; e += kQrThreads) {
-        const int i = e / n, c = e % n;
-        R[e] = (i <= c && i < kq) ? Xb[(i64)i * ldx + c] : 0.0;
+    qr_sum_vec<1>(ss, red, out);
+    const double xs = out[0];
+    if (xs >= 0x1p-960 && xs <= 0x1p960) {
+        *in_range = true;
+        return sqrt(xs);
+    }
+    *in_range = false;
+    double am = 0.0;
+    for (int i = lo + tid; i < rb; i += kQrThreads) am = fmax(am, fabs(P[i * PS + j]));
+    am = qr_max(am, red);
+    if (am == 0.0 || !(am <= 1.79e308)) return am;  // zero column, or inf / nan propagates
+    const int e = ilogb(am);
+    ss[0] = 0.0;
+    for (int i = lo + tid; i < rb; i += kQrThreads) {
+        const double x = ldexp(P[i * PS + j], -e);
+        ss[0] = fma(x, x, ss[0]);
+    }
+    qr_sum_vec<1>(ss, red, out);
+    return ldexp(sqrt(out[0]), e);
+}
+
+// Vt = the top NB rows of the panel's V: unit diagonal, zeros above it and
+// in columns >= jb, P's entries below the diagonal.
+template <int NB>
+__device__ void qr_build_vt(const double *P, int jb, double *Vt)
+{
+    constexpr int PS = NB + 1;
+    for (int e = threadIdx.x; e < NB * NB; e += kQrThreads) {
+        const int i = e / NB, k = e % NB;
+        Vt[i * PS + k] = (k >= jb || i < k) ? 0.0 : (i == k ? 1.0 : P[i * PS + k]);
     }
 }
 
-// Q of row block blk: Y = H_0 ... H_{n-1} [C; 0] with C = rows
-// [blk n, blk n + n) of Cin (the block's slice of the next level's Q, or
-// the identity at the top), written to rows [r0, r1) of Qout.
-__global__ void __launch_bounds__(kQrThreads) org2r_kernel(const double *__restrict__ X, i64 ldx,
-                                                          i64 m, int n, i64 b, int nblk,
-                                                          const double *__restrict__ tau,
-                                                          const double *__restrict__ Cin,
-                                                          double *__restrict__ Qout, i64 ldq)
+// Householder QR of the panel in shared memory: P (rb x NB, row stride
+// NB + 1; columns >= jb are zero) becomes R above the diagonal and the
+// reflection vectors v_k below it (v_k[k] = 1 implicit), reflection k
+// being I - tau_k v_k v_k^T.  Then T (upper triangular, T_kk = tau_k) with
+// H_0 H_1 ... H_{jb-1} = I - V T V^T (the compact WY form), and Vt.
+// Every thread calls this; it ends with a barrier.
+template <int NB>
+__device__ void qr_panel(double *P, int rb, int jb, double *Tm, double *G, double *Vt, double *red,
+                         double *stp)
 {
-    extern __shared__ double qr_s[];
-    const int blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const i64 r0 = (i64)blk * b;
-    const i64 r1 = (blk == nblk - 1) ? m : r0 + b;
-    const i64 rows = r1 - r0;
-    const double *Xb = X + r0 * ldx;
-    double *Y = Qout + r0 * ldq;
-    const int kq = rows < n ? (int)rows : n;
-    for (i64 e = tid; e < rows * n; e += kQrThreads) {
-        const i64 i = e / n;
-        const int c = (int)(e - i * n);
-        Y[i * ldq + c] = (i < n) ? (Cin ? Cin[((i64)blk * n + i) * n + c] : (i == c ? 1.0 : 0.0))
-                                 : 0.0;
+    constexpr int PS = NB + 1;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += kQrThreads) Tm[e] = 0.0;
+    for (int jj = 0; jj < jb; jj++) {
+        bool in_range;
+        const double xn = qr_col_norm<PS>(P, jj + 1, rb, jj, red, stp, &in_range);
+        if (tid == 0) {
+            const double alpha = P[jj * PS + jj];
+            double tau = 0.0, scv = 0.0;
+            if (xn != 0.0) {
+                const double nrm = (in_range && fabs(alpha) < 0x1p480)
+                                       ? sqrt(fma(alpha, alpha, stp[0]))
+                                       : hypot(alpha, xn);
+                const double beta = -copysign(nrm, alpha);
+                tau = (beta - alpha) / beta;
+                scv = 1.0 / (alpha - beta);
+                P[jj * PS + jj] = beta;
+            }
+            Tm[jj * NB + jj] = tau;
+            stp[1] = tau;
+            stp[2] = scv;
+        }
+        __syncthreads();
+        const double tau = stp[1], scv = stp[2];
+        if (tau == 0.0) continue;  // uniform: H_jj = I
+        for (int i = jj + 1 + tid; i < rb; i += kQrThreads) P[i * PS + jj] *= scv;
+        __syncthreads();
+        // w_c = sum_{i >= jj} v_i P[i][c] for the panel's columns c > jj
+        double w[NB];
+#pragma unroll
+        for (int c = 0; c < NB; c++) w[c] = 0.0;
+        for (int i = jj + tid; i < rb; i += kQrThreads) {
+            const double v = (i == jj) ? 1.0 : P[i * PS + jj];
+#pragma unroll
+            for (int c = 0; c < NB; c++)
+                if (c > jj) w[c] = fma(v, P[i * PS + c], w[c]);
+        }
+        qr_sum_vec<NB>(w, red, stp + 4);
+        for (int i = jj + tid; i < rb; i += kQrThreads) {
+            const double tv = tau * ((i == jj) ? 1.0 : P[i * PS + jj]);
+#pragma unroll
+            for (int c = 0; c < NB; c++)
+                if (c > jj) P[i * PS + c] = fma(-tv, stp[4 + c], P[i * PS + c]);
+        }
+        __syncthreads();
+    }
+    // G[k][l] = v_k . v_l (k < l < jb) = P[l][k] + sum_{i > l} P[i][k] P[i][l];
+    // two threads per pair (alternate row pairs), combined by a shuffle
+    {
+        const int npair = jb * (jb - 1) / 2;
+        const int q = tid >> 1, half = tid & 1;
+        int k = 0, l = 1;
+        double sacc = 0.0;
+        if (q < npair) {
+            int base = 0;
+            while (q >= base + l) {
+                base += l;
+                ++l;
+            }
+            k = q - base;
+            double a0 = 0.0, a1 = 0.0;
+            int i = l + 1 + half;
+            for (; i + 2 < rb; i += 4) {
+                a0 = fma(P[i * PS + k], P[i * PS + l], a0);
+                a1 = fma(P[(i + 2) * PS + k], P[(i + 2) * PS + l], a1);
+            }
+            if (i < rb) a0 = fma(P[i * PS + k], P[i * PS + l], a0);
+            sacc = a0 + a1;
+        }
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+        if (q < npair && half == 0) G[k * NB + l] = sacc + P[l * PS + k];
+    }
+    qr_build_vt<NB>(P, jb, Vt);
+    __syncthreads();
+    // T[0:l, l] = -tau_l T[0:l, 0:l] (V^T v_l)[0:l]
+    for (int l = 1; l < jb; l++) {
+        if (tid < l) {
+            double acc = 0.0;
+            for (int k = tid; k < l; k++) acc = fma(Tm[tid * NB + k], G[k * NB + l], acc);
+            Tm[tid * NB + l] = -Tm[l * NB + l] * acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Applies the panel's block reflection to one tile of C (rows 0..rb-1 of C
+// are the panel's rows; columns c0 .. c0 + TC - 1, only those in [clo, chi)
+// changed): C <- C - V op(T) V^T C with op(T) = T^T (TRANS, the transpose
+// of H_0 ... H_{jb-1}: the factorization's trailing update) or T (the
+// product itself: forming Q).  Thread layout: lane = (row group, column),
+// warps and row groups stride the rows; W = V^T C is reduced through
+// shared memory.  Every thread calls this.
+template <int NB, int TC, bool TRANS>
+__device__ void qr_apply_tile(double *C, i64 ldc, int rb, int jb, int c0, int clo, int chi,
+                              const QrSmem<NB, TC> &sm)
+{
+    constexpr int PS = NB + 1, RG = 32 / TC, RS = kQrWarps * RG, U = 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tc = lane % TC, ro = warp * RG + lane / TC;
+    const int c = c0 + tc;
+    const bool cok = c >= clo && c < chi;
+    double acc[NB];
+#pragma unroll
+    for (int k = 0; k < NB; k++) acc[k] = 0.0;
+    for (int i = ro; i < rb; i += RS * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int r = i + u * RS;
+            x[u] = (cok && r < rb) ? __ldcg(C + (i64)r * ldc + c) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int r = i + u * RS;
+            if (r < rb) {
+                const double *v = (r < jb) ? sm.Vt + r * PS : sm.P + r * PS;
+#pragma unroll
+                for (int k = 0; k < NB; k++) acc[k] = fma(v[k], x[u], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; k++) sm.Wp[(ro * NB + k) * TC + tc] = acc[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * TC; e += kQrThreads) {
+        const int k = e / TC, t = e % TC;
+        double s0 = 0.0, s1 = 0.0;
+        for (int r = 0; r < RS; r += 2) {
+            s0 += sm.Wp[(r * NB + k) * TC + t];
+            s1 += sm.Wp[((r + 1) * NB + k) * TC + t];
+        }
+        sm.Ws[e] = s0 + s1;
     }
     __syncthreads();
-    for (int j = kq - 1; j >= 0; j--) {
-        const double tj = tau[(i64)blk * n + j];
-        if (tj == 0.0) continue;
-        for (int c = lane; c < n; c += 32) {
-            double acc = 0.0;
-            for (i64 i = j + 1 + warp; i < rows; i += kQrThreads / 32)
-                acc = fma(Xb[i * ldx + j], Y[i * ldq + c], acc);
-            qr_s[warp * n + c] = acc;
+    for (int e = threadIdx.x; e < NB * TC; e += kQrThreads) {
+        const int k = e / TC, t = e % TC;
+        double s = 0.0;
+        if (TRANS) {
+            for (int q = 0; q <= k; q++) s = fma(sm.Tm[q * NB + k], sm.Ws[q * TC + t], s);
+        } else {
+            for (int q = k; q < NB; q++) s = fma(sm.Tm[k * NB + q], sm.Ws[q * TC + t], s);
+        }
+        sm.Wt[e] = s;
+    }
+    __syncthreads();
+    double w[NB];
+#pragma unroll
+    for (int k = 0; k < NB; k++) w[k] = sm.Wt[k * TC + tc];
+    if (!cok) return;
+    for (int i = ro; i < rb; i += RS * U) {
+        double x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int r = i + u * RS;
+            x[u] = (r < rb) ? __ldcg(C + (i64)r * ldc + c) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int r = i + u * RS;
+            if (r < rb) {
+                const double *v = (r < jb) ? sm.Vt + r * PS : sm.P + r * PS;
+                double y = x[u];
+#pragma unroll
+                for (int k = 0; k < NB; k++) y = fma(-v[k], w[k], y);
+                __stcg(C + (i64)r * ldc + c, y);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void qr_cluster_sync()
+{
+    __threadfence();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Blocked Householder QR of every row block of one tree level (X: rows x
+// n, leading dimension ldx, overwritten by R above and V below the
+// diagonal of each block).  CTA (blk, part), cs parts per block: part owns
+// the column tiles t with t % cs == part and applies every panel's
+// reflection to them; every part factors each panel itself (identical
+// arithmetic, so identical results) after a cluster barrier has made the
+// owner's update of the panel's columns visible.  The factored panel and
+// its T are written back by the owner one step later, once no part reads
+// the panel's columns any more.  Per block: T blocks to Tg, R (n x n,
+// zeros below the diagonal) to rows [blk n, blk n + n) of Rs.
+template <int NB, int TC>
+__global__ void __launch_bounds__(kQrThreads, 1)
+    geqrf_kernel(double *__restrict__ X, i64 ldx, i64 rows, int n, int nblk, int cs, int rbmax,
+                 double *__restrict__ Tg, double *__restrict__ Rs)
+{
+    constexpr int PS = NB + 1;
+    extern __shared__ double qr_smem[];
+    const QrSmem<NB, TC> sm(qr_smem, rbmax);
+    const int blk = blockIdx.x / cs, part = blockIdx.x % cs, tid = threadIdx.x;
+    const i64 r0 = qr_row0(rows, nblk, blk), r1 = qr_row0(rows, nblk, blk + 1);
+    const int rbk = (int)(r1 - r0);
+    const int kq = rbk < n ? rbk : n;
+    const int npan = (kq + NB - 1) / NB, npan_all = (n + NB - 1) / NB;
+    const int ntiles = (n + TC - 1) / TC;
+    double *Xb = X + r0 * ldx;
+    auto write_back = [&](int p) {
+        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        if ((j0 / TC) % cs != part) return;
+        for (int e = tid; e < rb * NB; e += kQrThreads) {
+            const int i = e / NB, k = e % NB;
+            if (k < jb) __stcg(Xb + (i64)(j0 + i) * ldx + j0 + k, sm.P[i * PS + k]);
+        }
+        double *T = Tg + ((i64)blk * npan_all + p) * NB * NB;
+        for (int e = tid; e < NB * NB; e += kQrThreads) T[e] = sm.Tm[e];
+    };
+    for (int p = 0; p < npan; p++) {
+        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        if (p > 0) {
+            write_back(p - 1);
+            __syncthreads();
+        }
+        for (int e = tid; e < rb * NB; e += kQrThreads) {
+            const int i = e / NB, k = e % NB;
+            sm.P[i * PS + k] = (k < jb) ? __ldcg(Xb + (i64)(j0 + i) * ldx + j0 + k) : 0.0;
         }
         __syncthreads();
-        for (int c = tid; c < n; c += kQrThreads) {
-            double w = Y[(i64)j * ldq + c];
-            for (int q = 0; q < kQrThreads / 32; q++) w += qr_s[q * n + c];
-            qr_s[c] = w;
+        qr_panel<NB>(sm.P, rb, jb, sm.Tm, sm.G, sm.Vt, sm.red, sm.stp);
+        const int clo = j0 + jb;
+        for (int t = clo / TC; t < ntiles; t++)
+            if (t % cs == part)
+                qr_apply_tile<NB, TC, true>(Xb + (i64)j0 * ldx, ldx, rb, jb, t * TC, clo, n, sm);
+        if (cs > 1)
+            qr_cluster_sync();
+        else
+            __syncthreads();
+    }
+    if (npan > 0) write_back(npan - 1);
+    __syncthreads();
+    double *R = Rs + (i64)blk * n * n;
+    for (int t = part; t < ntiles; t += cs)
+        for (int e = tid; e < n * TC; e += kQrThreads) {
+            const int i = e / TC, c = t * TC + e % TC;
+            if (c < n) R[(i64)i * n + c] = (i <= c && i < kq) ? __ldcg(Xb + (i64)i * ldx + c) : 0.0;
         }
+}
+
+// Q of every row block of one level: Y = H_0 ... H_{kq-1} [C; 0], C = rows
+// [blk n, blk n + n) of Cin (the next level's Q), or the identity at the
+// top, written to the block's rows of Qout.  Panels are applied last to
+// first; CTA (blk, part) forms the column tiles t % cs == part (no
+// dependence between parts).  With C = I, columns below the panel's first
+// column are still unit vectors and are skipped.
+template <int NB, int TC>
+__global__ void __launch_bounds__(kQrThreads, 1)
+    orgqr_kernel(const double *__restrict__ X, i64 ldx, i64 rows, int n, int nblk, int cs,
+                 int rbmax, const double *__restrict__ Tg, const double *__restrict__ Cin,
+                 double *__restrict__ Qout, i64 ldq)
+{
+    constexpr int PS = NB + 1;
+    extern __shared__ double qr_smem[];
+    const QrSmem<NB, TC> sm(qr_smem, rbmax);
+    const int blk = blockIdx.x / cs, part = blockIdx.x % cs, tid = threadIdx.x;
+    const i64 r0 = qr_row0(rows, nblk, blk), r1 = qr_row0(rows, nblk, blk + 1);
+    const int rbk = (int)(r1 - r0);
+    const int kq = rbk < n ? rbk : n;
+    const int npan = (kq + NB - 1) / NB, npan_all = (n + NB - 1) / NB;
+    const int ntiles = (n + TC - 1) / TC;
+    const double *Xb = X + r0 * ldx;
+    double *Y = Qout + r0 * ldq;
+    for (int t = part; t < ntiles; t += cs)
+        for (int e = tid; e < rbk * TC; e += kQrThreads) {
+            const int i = e / TC, c = t * TC + e % TC;
+            if (c >= n) continue;
+            double y = 0.0;
+            if (i < n) y = Cin ? Cin[((i64)blk * n + i) * n + c] : (i == c ? 1.0 : 0.0);
+            __stcg(Y + (i64)i * ldq + c, y);
+        }
+    __syncthreads();
+    for (int p = npan - 1; p >= 0; p--) {
+        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        for (int e = tid; e < rb * NB; e += kQrThreads) {
+            const int i = e / NB, k = e % NB;
+            sm.P[i * PS + k] = (k < jb) ? Xb[(i64)(j0 + i) * ldx + j0 + k] : 0.0;
+        }
+        const double *T = Tg + ((i64)blk * npan_all + p) * NB * NB;
+        for (int e = tid; e < NB * NB; e += kQrThreads) sm.Tm[e] = T[e];
         __syncthreads();
-        for (int c = lane; c < n; c += 32) {
-            const double tw = tj * qr_s[c];
-            if (warp == 0) Y[(i64)j * ldq + c] -= tw;
-            for (i64 i = j + 1 + warp; i < rows; i += kQrThreads / 32)
-                Y[i * ldq + c] = fma(-tw, Xb[i * ldx + j], Y[i * ldq + c]);
-        }
+        qr_build_vt<NB>(sm.P, jb, sm.Vt);
+        __syncthreads();
+        const int clo = Cin ? 0 : j0;
+        for (int t = part; t < ntiles; t += cs)
+            if ((t + 1) * TC > clo)
+                qr_apply_tile<NB, TC, false>(Y + (i64)j0 * ldq, ldq, rb, jb, t * TC, clo, n, sm);
         __syncthreads();
     }
 }
@@ -302,26 +593,26 @@ cudaError_t launch_mixing(int h, const double *th, const i64 *perm, double *Mt, 
     return cudaGetLastError();
 }
 
-// Row-block size of a TSQR level with `rows` rows: at least n rows per
-// block (so every block has a full n x n R), about 4n.
-i64 tsqr_block_rows(i64 rows, int n)
+// Target rows of a TSQR block: about 4n (2n above n = 256, so that the
+// panel of a block still fits in shared memory), at least 256.
+static i64 tsqr_block_rows(int n)
 {
-    i64 b = 4 * (i64)n;
-    if (b < 256) b = 256;
-    if (b > rows) b = rows;
-    return b;
+    const i64 b = n <= 256 ? 4 * (i64)n : 2 * (i64)n;
+    return b < 256 ? 256 : b;
 }
 
-int tsqr_blocks(i64 rows, int n)
+// Blocks of a level with `rows` rows: ceil(rows / b), rows split evenly, so
+// every block has at most b and (for rows >= b) at least b / 2 >= 2n rows.
+static int tsqr_blocks(i64 rows, int n)
 {
-    const i64 b = tsqr_block_rows(rows, n);
-    i64 nb = rows / b;
+    const i64 b = tsqr_block_rows(n);
+    const i64 nb = (rows + b - 1) / b;
     return nb < 1 ? 1 : (int)nb;
 }
 
 // Levels of the reduction tree: level 0 is X (m rows), level l + 1 the
 // stacked R factors of level l (blocks(l) * n rows), up to one block.
-int tsqr_levels(i64 m, int n, i64 *rows_out, int max_levels)
+static int tsqr_levels(i64 m, int n, i64 *rows_out, int max_levels)
 {
     int L = 0;
     i64 rows = m;
@@ -334,6 +625,17 @@ int tsqr_levels(i64 m, int n, i64 *rows_out, int max_levels)
     return L;
 }
 
+constexpr size_t kQrSmemCap = 220 * 1024;
+
+// Panel width of a level whose blocks have at most rbmax rows: the widest
+// of 16, 8, 4, 2 whose shared memory fits (0: none does).
+static int tsqr_panel_width(i64 rbmax)
+{
+    for (int nb = 16; nb >= 2; nb /= 2)
+        if (qr_smem_doubles(nb, kQrTC, rbmax) * sizeof(double) <= kQrSmemCap) return nb;
+    return 0;
+}
+
 size_t tsqr_workspace_doubles(i64 m, int n)
 {
     i64 rows[64];
@@ -341,11 +643,102 @@ size_t tsqr_workspace_doubles(i64 m, int n)
     size_t d = 0;
     for (int l = 0; l < L; l++) {
         const int nb = tsqr_blocks(rows[l], n);
-        d += (size_t)nb * n;                     // tau
-        d += (size_t)nb * n * n;                 // stacked R (next level's X)
-        if (l > 0) d += (size_t)rows[l] * n;     // Q of this level
+        d += (size_t)nb * ((size_t)n + 16) * 16 + 8;   // T blocks (panel width <= 16)
+        d += (size_t)nb * n * n + 8;                  // stacked R (next level's X)
+        if (l > 0) d += (size_t)rows[l] * n + 8;      // Q of this level
     }
-    return d + 64 * (size_t)L;
+    return d + 64;
+}
+
+template <int NB>
+static cudaError_t launch_geqrf_nb(double *X, i64 rows, int n, int nblk, int cs, int rbmax,
+                                   double *Tg, double *Rs, cudaStream_t s)
+{
+    auto kern = geqrf_kernel<NB, kQrTC>;
+    const size_t smem = qr_smem_doubles(NB, kQrTC, rbmax) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nblk * cs));
+    cfg.blockDim = dim3(kQrThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    // Cluster width: each width's co-resident cluster count gives the waves
+    // a level needs; the cost model is waves x (the widest part's share of
+    // the tile work + a fixed share for the panel chain every part runs).
+    {
+        int best = 1;
+        double best_cost = 1e300;
+        for (int c = cs; c >= 1; c--) {
+            int ncl = 0;
+            if (c > 1) {
+                static std::mutex mu;
+                static std::map<std::tuple<int, int, size_t>, int> cache;
+                const auto key = std::make_tuple(NB, c, smem);
+                std::lock_guard<std::mutex> g(mu);
+                auto it = cache.find(key);
+                if (it != cache.end()) {
+                    ncl = it->second;
+                } else {
+                    cfg.gridDim = dim3((unsigned)(nblk * c));
+                    at[0].val.clusterDim.x = (unsigned)c;
+                    cfg.numAttrs = 1;
+                    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) {
+                        cudaGetLastError();
+                        ncl = 0;
+                    }
+                    cache[key] = ncl;
+                }
+            } else {
+                ncl = num_sms();
+            }
+            if (ncl <= 0) continue;
+            const int waves = (nblk + ncl - 1) / ncl;
+            const double cost = waves * (1.0 / c + 0.1);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = c;
+            }
+        }
+        cs = best;
+    }
+    at[0].val.clusterDim.x = (unsigned)cs;
+    cfg.gridDim = dim3((unsigned)(nblk * cs));
+    cfg.numAttrs = cs > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, X, (i64)n, rows, n, nblk, cs, rbmax, Tg, Rs);
+}
+
+template <int NB>
+static cudaError_t launch_orgqr_nb(const double *X, i64 rows, int n, int nblk, int cs, int rbmax,
+                                   const double *Tg, const double *Cin, double *Q, cudaStream_t s)
+{
+    auto kern = orgqr_kernel<NB, kQrTC>;
+    const size_t smem = qr_smem_doubles(NB, kQrTC, rbmax) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(nblk * cs), kQrThreads, smem, s>>>(X, (i64)n, rows, n, nblk, cs, rbmax, Tg,
+                                                         Cin, Q, (i64)n);
+    return cudaGetLastError();
+}
+
+// Parts per block of a level with nblk blocks: enough CTAs to cover the
+// SMs once, at most one per column tile (and at most 8, a portable
+// cluster, for the factorization, whose parts synchronise).
+static int tsqr_parts(int nblk, int n, int cap)
+{
+    const int ntiles = (n + kQrTC - 1) / kQrTC;
+    int cs = nblk >= num_sms() ? 1 : num_sms() / nblk;
+    if (cs > ntiles) cs = ntiles;
+    if (cs > cap) cs = cap;
+    return cs < 1 ? 1 : cs;
 }
 
 cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double *Q,
@@ -353,34 +746,37 @@ cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double
 {
     i64 rows[64];
     const int L = tsqr_levels(m, n, rows, 64);
-    double *taus[64], *Rst[64], *Qs[64];
+    double *Tgs[64], *Rst[64], *Qs[64];
+    int nbl[64], rbm[64], pw[64];
     double *w = work;
     for (int l = 0; l < L; l++) {
         const int nb = tsqr_blocks(rows[l], n);
-        taus[l] = w;
-        w += (size_t)nb * n + 8;
+        nbl[l] = nb;
+        rbm[l] = (int)((rows[l] + nb - 1) / nb);
+        pw[l] = tsqr_panel_width(rbm[l]);
+        if (pw[l] == 0) return cudaErrorInvalidValue;
+        Tgs[l] = w;
+        w += (size_t)nb * ((size_t)n + 16) * 16 + 8;
         Rst[l] = w;
         w += (size_t)nb * n * n + 8;
         Qs[l] = (l == 0) ? Q : w;
         if (l > 0) w += (size_t)rows[l] * n + 8;
     }
-    const size_t smem = sizeof(double) * (kQrThreads / 32) * (size_t)n;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(geqr2_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(org2r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     // factorization up the tree
     for (int l = 0; l < L; l++) {
         double *Xl = (l == 0) ? X : Rst[l - 1];
-        const int nb = tsqr_blocks(rows[l], n);
-        const i64 b = tsqr_block_rows(rows[l], n);
-        ProfScope ps_("tsqr_geqr2", s);
-        geqr2_kernel<<<nb, kQrThreads, smem, s>>>(Xl, n, rows[l], n, b, nb, taus[l], Rst[l]);
-        cudaError_t e = cudaGetLastError();
+        const int cs = tsqr_parts(nbl[l], n, 8);
+        static const char *const kGeqrfNames[] = {"tsqr_geqrf", "tsqr_geqrf_tree1",
+                                                  "tsqr_geqrf_tree2", "tsqr_geqrf_tree3",
+                                                  "tsqr_geqrf_tree4+"};
+        ProfScope ps_(kGeqrfNames[l < 4 ? l : 4], s);
+        cudaError_t e;
+        switch (pw[l]) {
+        case 16: e = launch_geqrf_nb<16>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
+        case 8: e = launch_geqrf_nb<8>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
+        case 4: e = launch_geqrf_nb<4>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
+        default: e = launch_geqrf_nb<2>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
+        }
         if (e != cudaSuccess) return e;
     }
     // R = the top block's R
@@ -389,13 +785,19 @@ cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double
     if (e != cudaSuccess) return e;
     // Q down the tree
     for (int l = L - 1; l >= 0; l--) {
-        double *Xl = (l == 0) ? X : Rst[l - 1];
-        const int nb = tsqr_blocks(rows[l], n);
-        const i64 b = tsqr_block_rows(rows[l], n);
-        ProfScope ps_("tsqr_org2r", s);
-        org2r_kernel<<<nb, kQrThreads, smem, s>>>(Xl, n, rows[l], n, b, nb, taus[l],
-                                                   l == L - 1 ? nullptr : Qs[l + 1], Qs[l], n);
-        e = cudaGetLastError();
+        const double *Xl = (l == 0) ? X : Rst[l - 1];
+        const double *Cin = (l == L - 1) ? nullptr : Qs[l + 1];
+        const int cs = tsqr_parts(nbl[l], n, 1 << 20);
+        static const char *const kOrgqrNames[] = {"tsqr_orgqr", "tsqr_orgqr_tree1",
+                                                  "tsqr_orgqr_tree2", "tsqr_orgqr_tree3",
+                                                  "tsqr_orgqr_tree4+"};
+        ProfScope ps_(kOrgqrNames[l < 4 ? l : 4], s);
+        switch (pw[l]) {
+        case 16: e = launch_orgqr_nb<16>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
+        case 8: e = launch_orgqr_nb<8>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
+        case 4: e = launch_orgqr_nb<4>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
+        default: e = launch_orgqr_nb<2>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

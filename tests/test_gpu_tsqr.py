@@ -36,8 +36,10 @@ def run_tsqr(A, mix, **kw):
     return (f(U), f(S), f(V)), info
 
 
+# tree shapes: one block (300 x 300), two to six levels (50,000 x 100),
+# panel width 8 (3,000 x 700: blocks of 1,400 rows)
 CASES = [(3000, 24, 90), (2001, 13, 91), (20000, 50, 92), (777, 9, 93), (50000, 100, 94),
-         (300, 300, 95)]
+         (300, 300, 95), (3000, 700, 96)]
 
 
 @gpu
@@ -49,6 +51,20 @@ def test_tsqr_matches_oracle(orc, m, n, seed, passes):
     mix = workloads.mixing_draws(n, seed)
     ref = orc.ts_svd_tsqr(A, mix, passes=passes, wp=0.0)
     got, info = run_tsqr(A, mix, passes=passes, drop_tol=0.0)
+    assert info["rank"] == ref[3] and info["status"] == ref[4]
+    compare_svd(A, got, ref[:4])
+
+
+@gpu
+@pytest.mark.parametrize("m,n,seed", CASES[:6])
+def test_tsqr_fp64_tc_products_match_oracle(orc, m, n, seed):
+    """Algorithm 2 with the two tall products on the FP64-accurate digit
+    kernels: the same bar as the FP64 path."""
+    s = workloads.sigma_geometric(n, 1e-6)
+    A, _, _, _ = workloads.known_spectrum(m, n, s, seed)
+    mix = workloads.mixing_draws(n, seed)
+    ref = orc.ts_svd_tsqr(A, mix, passes=2, wp=0.0)
+    got, info = run_tsqr(A, mix, passes=2, drop_tol=0.0, mode="fp64_tc")
     assert info["rank"] == ref[3] and info["status"] == ref[4]
     compare_svd(A, got, ref[:4])
 
@@ -99,17 +115,19 @@ def run_lowrank_tsqr(A, k, l, iters, Om, mix, **kw):
 
 
 @gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
 @pytest.mark.parametrize("m,n,k,l,iters,seed", [(3000, 800, 10, 16, 2, 100),
                                                 (2000, 1500, 20, 25, 1, 101),
                                                 (5000, 600, 8, 8, 0, 102)])
-def test_lowrank_tsqr_matches_oracle(orc, m, n, k, l, iters, seed):
+def test_lowrank_tsqr_matches_oracle(orc, m, n, k, l, iters, seed, mode):
     """Algorithm 7 on a low-rank-plus-noise matrix: S, U, V against the
-    oracle with the same Omega and mixing draw."""
+    oracle with the same Omega and mixing draw, with the tall products in
+    FP64 FMA or FP64-accurate digit products."""
     A, _, _, _ = workloads.lowrank_plus_noise(m, n, 40, seed)
     Om = workloads.gaussian(n, l, seed + 1)
     mix = workloads.mixing_draws(l, seed + 2)
     Ur, Sr, Vr, rr, st = orc.lowrank_svd_tsqr(A, k, l, iters, Om, mix)
-    U, S, V, info = run_lowrank_tsqr(A, k, l, iters, Om, mix)
+    U, S, V, info = run_lowrank_tsqr(A, k, l, iters, Om, mix, mode=mode)
     assert info["rank"] == rr and info["status"] == st
     assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
     assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-12
