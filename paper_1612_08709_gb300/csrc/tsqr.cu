@@ -95,26 +95,46 @@ constexpr int kQrWarps = kQrThreads / 32;
 // Columns per tile of the trailing updates (lanes: TC columns x 32/TC rows).
 constexpr int kQrTC = 16;
 
-// Rows [qr_row0(q), qr_row0(q + 1)) of a tree level with `rows` rows form
-// block q of nblk (an even split: every block has at least n rows).
-__host__ __device__ __forceinline__ i64 qr_row0(i64 rows, int nblk, int q)
+// Rows [qr_row0(q), qr_row0(q + 1)) of a tree level form block q of nblk:
+// the level's rows / unit units split evenly, unit = 1 at the leaves (every
+// block has at least n rows) and unit = n above them (every block holds
+// whole stacked R factors).
+__host__ __device__ __forceinline__ i64 qr_row0(i64 rows, int unit, int nblk, int q)
 {
-    return (i64)q * rows / nblk;
+    return (i64)q * (rows / unit) / nblk * unit;
+}
+
+// Block row of the panel's active row a.  Dense blocks: every row from the
+// panel's first column j0 down.  Blocks of kR stacked upper triangular R
+// factors (n x n each): column c is zero below row c of every factor, and
+// stays so, so the panel's reflections touch only rows j0 .. j0 + jb - 1 of
+// the first factor and rows 0 .. j0 + jb - 1 of each further factor.
+__device__ __forceinline__ int qr_active_rows(bool stacked, int rbk, int n, int j0, int jb)
+{
+    return stacked ? jb + (rbk / n - 1) * (j0 + jb) : rbk - j0;
+}
+__device__ __forceinline__ int qr_row_of(bool stacked, int n, int j0, int jb, int a)
+{
+    if (!stacked || a < jb) return j0 + a;
+    const int t = a - jb, h = j0 + jb;
+    return (t / h + 1) * n + t % h;
 }
 
 // Shared memory of the QR kernels, in doubles: the panel P (rbmax x PS),
 // its top NB rows as V with the unit diagonal and zeros made explicit
 // (Vt), the per-row-group partials of W = V^T C (Wp), W (Ws), op(T) W
-// (Wt), T, V^T V (G) and reduction scratch.
+// (Wt), T, V^T V (G), reduction scratch and the panel's row map (ints).
 __host__ __device__ constexpr size_t qr_smem_doubles(int nb, int tc, i64 rbmax)
 {
     return (size_t)rbmax * (nb + 1) + (size_t)nb * (nb + 1) + (size_t)kQrThreads * nb +
-           2 * (size_t)nb * tc + 2 * (size_t)nb * nb + (size_t)kQrWarps * nb + 8 + nb;
+           2 * (size_t)nb * tc + 2 * (size_t)nb * nb + (size_t)kQrWarps * nb + 8 + nb +
+           (size_t)(rbmax + 1) / 2;
 }
 
 template <int NB, int TC>
 struct QrSmem {
     double *P, *Vt, *Wp, *Ws, *Wt, *Tm, *G, *red, *stp;
+    int *rmap;
     __device__ QrSmem(double *base, int rbmax)
     {
         P = base;
@@ -126,6 +146,7 @@ struct QrSmem {
         G = Tm + NB * NB;
         red = G + NB * NB;
         stp = red + kQrWarps * NB;
+        rmap = (int *)(stp + 8 + NB);
     }
 };
 
@@ -213,6 +234,48 @@ __device__ void qr_build_vt(const double *P, int jb, double *Vt)
     }
 }
 
+// Reflection JJ of the panel applied to the panel's columns JJ + 1 .. NB - 1
+// (a compile-time range, so no lane computes a column the reflection does
+// not change): w_c = sum_{i >= JJ} v_i P[i][c], P[i][c] -= tau v_i w_c.
+template <int NB, int JJ>
+__device__ __forceinline__ void qr_panel_update(double *P, int rb, double tau, double *red,
+                                                double *stp)
+{
+    constexpr int PS = NB + 1, K = NB - 1 - JJ;
+    if constexpr (K > 0) {
+        const int tid = threadIdx.x;
+        double w[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) w[c] = 0.0;
+        for (int i = JJ + tid; i < rb; i += kQrThreads) {
+            const double v = (i == JJ) ? 1.0 : P[i * PS + JJ];
+#pragma unroll
+            for (int c = 0; c < K; c++) w[c] = fma(v, P[i * PS + JJ + 1 + c], w[c]);
+        }
+        qr_sum_vec<K>(w, red, stp + 4);
+        for (int i = JJ + tid; i < rb; i += kQrThreads) {
+            const double tv = tau * ((i == JJ) ? 1.0 : P[i * PS + JJ]);
+#pragma unroll
+            for (int c = 0; c < K; c++)
+                P[i * PS + JJ + 1 + c] = fma(-tv, stp[4 + c], P[i * PS + JJ + 1 + c]);
+        }
+    }
+    __syncthreads();
+}
+
+// qr_panel_update for a run-time column jj (uniform across the CTA).
+template <int NB, int JJ = 0>
+__device__ __forceinline__ void qr_panel_update_at(int jj, double *P, int rb, double tau,
+                                                   double *red, double *stp)
+{
+    if constexpr (JJ < NB) {
+        if (jj == JJ)
+            qr_panel_update<NB, JJ>(P, rb, tau, red, stp);
+        else
+            qr_panel_update_at<NB, JJ + 1>(jj, P, rb, tau, red, stp);
+    }
+}
+
 // Householder QR of the panel in shared memory: P (rb x NB, row stride
 // NB + 1; columns >= jb are zero) becomes R above the diagonal and the
 // reflection vectors v_k below it (v_k[k] = 1 implicit), reflection k
@@ -250,24 +313,7 @@ __device__ void qr_panel(double *P, int rb, int jb, double *Tm, double *G, doubl
         if (tau == 0.0) continue;  // uniform: H_jj = I
         for (int i = jj + 1 + tid; i < rb; i += kQrThreads) P[i * PS + jj] *= scv;
         __syncthreads();
-        // w_c = sum_{i >= jj} v_i P[i][c] for the panel's columns c > jj
-        double w[NB];
-#pragma unroll
-        for (int c = 0; c < NB; c++) w[c] = 0.0;
-        for (int i = jj + tid; i < rb; i += kQrThreads) {
-            const double v = (i == jj) ? 1.0 : P[i * PS + jj];
-#pragma unroll
-            for (int c = 0; c < NB; c++)
-                if (c > jj) w[c] = fma(v, P[i * PS + c], w[c]);
-        }
-        qr_sum_vec<NB>(w, red, stp + 4);
-        for (int i = jj + tid; i < rb; i += kQrThreads) {
-            const double tv = tau * ((i == jj) ? 1.0 : P[i * PS + jj]);
-#pragma unroll
-            for (int c = 0; c < NB; c++)
-                if (c > jj) P[i * PS + c] = fma(-tv, stp[4 + c], P[i * PS + c]);
-        }
-        __syncthreads();
+        qr_panel_update_at<NB>(jj, P, rb, tau, red, stp);
     }
     // G[k][l] = v_k . v_l (k < l < jb) = P[l][k] + sum_{i > l} P[i][k] P[i][l];
     // two threads per pair (alternate row pairs), combined by a shuffle
@@ -308,11 +354,11 @@ __device__ void qr_panel(double *P, int rb, int jb, double *Tm, double *G, doubl
     }
 }
 
-// Applies the panel's block reflection to one tile of C (rows 0..rb-1 of C
-// are the panel's rows; columns c0 .. c0 + TC - 1, only those in [clo, chi)
-// changed): C <- C - V op(T) V^T C with op(T) = T^T (TRANS, the transpose
-// of H_0 ... H_{jb-1}: the factorization's trailing update) or T (the
-// product itself: forming Q).  Thread layout: lane = (row group, column),
+// Applies the panel's block reflection to one tile of C (the panel's active
+// row a is row sm.rmap[a] of C, a < rb; columns c0 .. c0 + TC - 1, only
+// those in [clo, chi) changed): C <- C - V op(T) V^T C with op(T) = T^T
+// (TRANS, the transpose of H_0 ... H_{jb-1}: the factorization's trailing
+// update) or T (the product itself: forming Q).  Thread layout: lane = (row group, column),
 // warps and row groups stride the rows; W = V^T C is reduced through
 // shared memory.  Every thread calls this.
 template <int NB, int TC, bool TRANS>
@@ -332,7 +378,7 @@ __device__ void qr_apply_tile(double *C, i64 ldc, int rb, int jb, int c0, int cl
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int r = i + u * RS;
-            x[u] = (cok && r < rb) ? __ldcg(C + (i64)r * ldc + c) : 0.0;
+            x[u] = (cok && r < rb) ? __ldcg(C + (i64)sm.rmap[r] * ldc + c) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -377,7 +423,7 @@ __device__ void qr_apply_tile(double *C, i64 ldc, int rb, int jb, int c0, int cl
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int r = i + u * RS;
-            x[u] = (r < rb) ? __ldcg(C + (i64)r * ldc + c) : 0.0;
+            x[u] = (r < rb) ? __ldcg(C + (i64)sm.rmap[r] * ldc + c) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -387,7 +433,7 @@ __device__ void qr_apply_tile(double *C, i64 ldc, int rb, int jb, int c0, int cl
                 double y = x[u];
 #pragma unroll
                 for (int k = 0; k < NB; k++) y = fma(-v[k], w[k], y);
-                __stcg(C + (i64)r * ldc + c, y);
+                __stcg(C + (i64)sm.rmap[r] * ldc + c, y);
             }
         }
     }
@@ -412,45 +458,54 @@ __device__ __forceinline__ void qr_cluster_sync()
 // zeros below the diagonal) to rows [blk n, blk n + n) of Rs.
 template <int NB, int TC>
 __global__ void __launch_bounds__(kQrThreads, 1)
-    geqrf_kernel(double *__restrict__ X, i64 ldx, i64 rows, int n, int nblk, int cs, int rbmax,
-                 double *__restrict__ Tg, double *__restrict__ Rs)
+    geqrf_kernel(double *__restrict__ X, i64 ldx, i64 rows, int unit, int n, int nblk, int cs,
+                 int rbmax, double *__restrict__ Tg, double *__restrict__ Rs)
 {
     constexpr int PS = NB + 1;
     extern __shared__ double qr_smem[];
     const QrSmem<NB, TC> sm(qr_smem, rbmax);
     const int blk = blockIdx.x / cs, part = blockIdx.x % cs, tid = threadIdx.x;
-    const i64 r0 = qr_row0(rows, nblk, blk), r1 = qr_row0(rows, nblk, blk + 1);
+    const i64 r0 = qr_row0(rows, unit, nblk, blk), r1 = qr_row0(rows, unit, nblk, blk + 1);
     const int rbk = (int)(r1 - r0);
+    const bool stacked = unit > 1;
     const int kq = rbk < n ? rbk : n;
     const int npan = (kq + NB - 1) / NB, npan_all = (n + NB - 1) / NB;
     const int ntiles = (n + TC - 1) / TC;
     double *Xb = X + r0 * ldx;
+    // sm.rmap = the active rows of panel p
+    auto map_rows = [&](int j0, int jb, int rb) {
+        for (int a = tid; a < rb; a += kQrThreads) sm.rmap[a] = qr_row_of(stacked, n, j0, jb, a);
+    };
+    // the owner writes panel p (rows in sm.rmap) and its T back
     auto write_back = [&](int p) {
-        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        const int j0 = p * NB, jb = min(NB, kq - j0);
+        const int rb = qr_active_rows(stacked, rbk, n, j0, jb);
         if ((j0 / TC) % cs != part) return;
         for (int e = tid; e < rb * NB; e += kQrThreads) {
             const int i = e / NB, k = e % NB;
-            if (k < jb) __stcg(Xb + (i64)(j0 + i) * ldx + j0 + k, sm.P[i * PS + k]);
+            if (k < jb) __stcg(Xb + (i64)sm.rmap[i] * ldx + j0 + k, sm.P[i * PS + k]);
         }
         double *T = Tg + ((i64)blk * npan_all + p) * NB * NB;
         for (int e = tid; e < NB * NB; e += kQrThreads) T[e] = sm.Tm[e];
     };
     for (int p = 0; p < npan; p++) {
-        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        const int j0 = p * NB, jb = min(NB, kq - j0);
+        const int rb = qr_active_rows(stacked, rbk, n, j0, jb);
         if (p > 0) {
             write_back(p - 1);
             __syncthreads();
         }
+        map_rows(j0, jb, rb);
+        __syncthreads();
         for (int e = tid; e < rb * NB; e += kQrThreads) {
             const int i = e / NB, k = e % NB;
-            sm.P[i * PS + k] = (k < jb) ? __ldcg(Xb + (i64)(j0 + i) * ldx + j0 + k) : 0.0;
+            sm.P[i * PS + k] = (k < jb) ? __ldcg(Xb + (i64)sm.rmap[i] * ldx + j0 + k) : 0.0;
         }
         __syncthreads();
         qr_panel<NB>(sm.P, rb, jb, sm.Tm, sm.G, sm.Vt, sm.red, sm.stp);
         const int clo = j0 + jb;
         for (int t = clo / TC; t < ntiles; t++)
-            if (t % cs == part)
-                qr_apply_tile<NB, TC, true>(Xb + (i64)j0 * ldx, ldx, rb, jb, t * TC, clo, n, sm);
+            if (t % cs == part) qr_apply_tile<NB, TC, true>(Xb, ldx, rb, jb, t * TC, clo, n, sm);
         if (cs > 1)
             qr_cluster_sync();
         else
@@ -469,21 +524,23 @@ __global__ void __launch_bounds__(kQrThreads, 1)
 // Q of every row block of one level: Y = H_0 ... H_{kq-1} [C; 0], C = rows
 // [blk n, blk n + n) of Cin (the next level's Q), or the identity at the
 // top, written to the block's rows of Qout.  Panels are applied last to
-// first; CTA (blk, part) forms the column tiles t % cs == part (no
-// dependence between parts).  With C = I, columns below the panel's first
-// column are still unit vectors and are skipped.
+// first, each to its active rows (those of the factorization); CTA (blk,
+// part) forms the column tiles t % cs == part (no dependence between
+// parts).  With C = I, columns below the panel's first column are still
+// unit vectors and are skipped.
 template <int NB, int TC>
 __global__ void __launch_bounds__(kQrThreads, 1)
-    orgqr_kernel(const double *__restrict__ X, i64 ldx, i64 rows, int n, int nblk, int cs,
-                 int rbmax, const double *__restrict__ Tg, const double *__restrict__ Cin,
+    orgqr_kernel(const double *__restrict__ X, i64 ldx, i64 rows, int unit, int n, int nblk,
+                 int cs, int rbmax, const double *__restrict__ Tg, const double *__restrict__ Cin,
                  double *__restrict__ Qout, i64 ldq)
 {
     constexpr int PS = NB + 1;
     extern __shared__ double qr_smem[];
     const QrSmem<NB, TC> sm(qr_smem, rbmax);
     const int blk = blockIdx.x / cs, part = blockIdx.x % cs, tid = threadIdx.x;
-    const i64 r0 = qr_row0(rows, nblk, blk), r1 = qr_row0(rows, nblk, blk + 1);
+    const i64 r0 = qr_row0(rows, unit, nblk, blk), r1 = qr_row0(rows, unit, nblk, blk + 1);
     const int rbk = (int)(r1 - r0);
+    const bool stacked = unit > 1;
     const int kq = rbk < n ? rbk : n;
     const int npan = (kq + NB - 1) / NB, npan_all = (n + NB - 1) / NB;
     const int ntiles = (n + TC - 1) / TC;
@@ -497,12 +554,15 @@ __global__ void __launch_bounds__(kQrThreads, 1)
             if (i < n) y = Cin ? Cin[((i64)blk * n + i) * n + c] : (i == c ? 1.0 : 0.0);
             __stcg(Y + (i64)i * ldq + c, y);
         }
-    __syncthreads();
     for (int p = npan - 1; p >= 0; p--) {
-        const int j0 = p * NB, jb = min(NB, kq - j0), rb = rbk - j0;
+        const int j0 = p * NB, jb = min(NB, kq - j0);
+        const int rb = qr_active_rows(stacked, rbk, n, j0, jb);
+        __syncthreads();  // the previous panel's readers of sm are done
+        for (int a = tid; a < rb; a += kQrThreads) sm.rmap[a] = qr_row_of(stacked, n, j0, jb, a);
+        __syncthreads();
         for (int e = tid; e < rb * NB; e += kQrThreads) {
             const int i = e / NB, k = e % NB;
-            sm.P[i * PS + k] = (k < jb) ? Xb[(i64)(j0 + i) * ldx + j0 + k] : 0.0;
+            sm.P[i * PS + k] = (k < jb) ? Xb[(i64)sm.rmap[i] * ldx + j0 + k] : 0.0;
         }
         const double *T = Tg + ((i64)blk * npan_all + p) * NB * NB;
         for (int e = tid; e < NB * NB; e += kQrThreads) sm.Tm[e] = T[e];
@@ -512,8 +572,7 @@ __global__ void __launch_bounds__(kQrThreads, 1)
         const int clo = Cin ? 0 : j0;
         for (int t = part; t < ntiles; t += cs)
             if ((t + 1) * TC > clo)
-                qr_apply_tile<NB, TC, false>(Y + (i64)j0 * ldq, ldq, rb, jb, t * TC, clo, n, sm);
-        __syncthreads();
+                qr_apply_tile<NB, TC, false>(Y, ldq, rb, jb, t * TC, clo, n, sm);
     }
 }
 
@@ -593,38 +652,6 @@ cudaError_t launch_mixing(int h, const double *th, const i64 *perm, double *Mt, 
     return cudaGetLastError();
 }
 
-// Target rows of a TSQR block: about 4n (2n above n = 256, so that the
-// panel of a block still fits in shared memory), at least 256.
-static i64 tsqr_block_rows(int n)
-{
-    const i64 b = n <= 256 ? 4 * (i64)n : 2 * (i64)n;
-    return b < 256 ? 256 : b;
-}
-
-// Blocks of a level with `rows` rows: ceil(rows / b), rows split evenly, so
-// every block has at most b and (for rows >= b) at least b / 2 >= 2n rows.
-static int tsqr_blocks(i64 rows, int n)
-{
-    const i64 b = tsqr_block_rows(n);
-    const i64 nb = (rows + b - 1) / b;
-    return nb < 1 ? 1 : (int)nb;
-}
-
-// Levels of the reduction tree: level 0 is X (m rows), level l + 1 the
-// stacked R factors of level l (blocks(l) * n rows), up to one block.
-static int tsqr_levels(i64 m, int n, i64 *rows_out, int max_levels)
-{
-    int L = 0;
-    i64 rows = m;
-    while (L < max_levels) {
-        rows_out[L++] = rows;
-        const int nb = tsqr_blocks(rows, n);
-        if (nb == 1) break;
-        rows = (i64)nb * n;
-    }
-    return L;
-}
-
 constexpr size_t kQrSmemCap = 220 * 1024;
 
 // Panel width of a level whose blocks have at most rbmax rows: the widest
@@ -636,23 +663,80 @@ static int tsqr_panel_width(i64 rbmax)
     return 0;
 }
 
+// The most rows a block may have with 16-column panels.
+static i64 tsqr_rows_cap()
+{
+    i64 lo = 16, hi = 1 << 16;
+    while (lo < hi) {
+        const i64 mid = (lo + hi + 1) / 2;
+        if (qr_smem_doubles(16, kQrTC, mid) * sizeof(double) <= kQrSmemCap)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The reduction tree.  Level 0 (the leaves): X's m rows in nblk blocks of
+// at most max(cap, 2n) rows (cap: the rows a 16-column panel allows),
+// rounded up to whole waves over the SMs when there are at least half as
+// many blocks as SMs and every block keeps 2n rows.  Level l + 1: the
+// nblk(l) stacked n x n R factors of level l, k per block (k = cap / n,
+// between 2 and 8), up to one block.
+struct TsqrPlan {
+    int L;
+    i64 rows[64];
+    int unit[64], nblk[64], rbmax[64];
+};
+
+static void tsqr_plan(i64 m, int n, TsqrPlan &P)
+{
+    const i64 cap = tsqr_rows_cap();
+    const i64 bleaf = cap > 2 * (i64)n ? cap : 2 * (i64)n;
+    i64 nb0 = (m + bleaf - 1) / bleaf;
+    const int sms = num_sms();
+    if (nb0 >= sms / 2) {
+        const i64 r = (nb0 + sms - 1) / sms * sms;
+        if (m / r >= 2 * (i64)n) nb0 = r;
+    }
+    if (nb0 < 1) nb0 = 1;
+    i64 k = cap / n;
+    if (k < 2) k = 2;
+    if (k > 8) k = 8;
+    P.L = 0;
+    i64 rows = m, nb = nb0;
+    int unit = 1;
+    while (P.L < 64) {
+        const int l = P.L++;
+        P.rows[l] = rows;
+        P.unit[l] = unit;
+        P.nblk[l] = (int)nb;
+        const i64 units = rows / unit;
+        P.rbmax[l] = (int)((units + nb - 1) / nb * unit);
+        if (nb == 1) break;
+        rows = nb * n;
+        unit = n;
+        nb = (nb + k - 1) / k;
+    }
+}
+
 size_t tsqr_workspace_doubles(i64 m, int n)
 {
-    i64 rows[64];
-    const int L = tsqr_levels(m, n, rows, 64);
+    TsqrPlan P;
+    tsqr_plan(m, n, P);
     size_t d = 0;
-    for (int l = 0; l < L; l++) {
-        const int nb = tsqr_blocks(rows[l], n);
-        d += (size_t)nb * ((size_t)n + 16) * 16 + 8;   // T blocks (panel width <= 16)
-        d += (size_t)nb * n * n + 8;                  // stacked R (next level's X)
-        if (l > 0) d += (size_t)rows[l] * n + 8;      // Q of this level
+    for (int l = 0; l < P.L; l++) {
+        const int nb = P.nblk[l];
+        d += (size_t)nb * ((size_t)n + 16) * 16 + 8;  // T blocks (panel width <= 16)
+        d += (size_t)nb * n * n + 8;                 // stacked R (next level's X)
+        if (l > 0) d += (size_t)P.rows[l] * n + 8;   // Q of this level
     }
     return d + 64;
 }
 
 template <int NB>
-static cudaError_t launch_geqrf_nb(double *X, i64 rows, int n, int nblk, int cs, int rbmax,
-                                   double *Tg, double *Rs, cudaStream_t s)
+static cudaError_t launch_geqrf_nb(double *X, i64 rows, int unit, int n, int nblk, int cs,
+                                   int rbmax, double *Tg, double *Rs, cudaStream_t s)
 {
     auto kern = geqrf_kernel<NB, kQrTC>;
     const size_t smem = qr_smem_doubles(NB, kQrTC, rbmax) * sizeof(double);
@@ -712,20 +796,21 @@ static cudaError_t launch_geqrf_nb(double *X, i64 rows, int n, int nblk, int cs,
     at[0].val.clusterDim.x = (unsigned)cs;
     cfg.gridDim = dim3((unsigned)(nblk * cs));
     cfg.numAttrs = cs > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, X, (i64)n, rows, n, nblk, cs, rbmax, Tg, Rs);
+    return cudaLaunchKernelEx(&cfg, kern, X, (i64)n, rows, unit, n, nblk, cs, rbmax, Tg, Rs);
 }
 
 template <int NB>
-static cudaError_t launch_orgqr_nb(const double *X, i64 rows, int n, int nblk, int cs, int rbmax,
-                                   const double *Tg, const double *Cin, double *Q, cudaStream_t s)
+static cudaError_t launch_orgqr_nb(const double *X, i64 rows, int unit, int n, int nblk, int cs,
+                                   int rbmax, const double *Tg, const double *Cin, double *Q,
+                                   cudaStream_t s)
 {
     auto kern = orgqr_kernel<NB, kQrTC>;
     const size_t smem = qr_smem_doubles(NB, kQrTC, rbmax) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)(nblk * cs), kQrThreads, smem, s>>>(X, (i64)n, rows, n, nblk, cs, rbmax, Tg,
-                                                         Cin, Q, (i64)n);
+    kern<<<(unsigned)(nblk * cs), kQrThreads, smem, s>>>(X, (i64)n, rows, unit, n, nblk, cs, rbmax,
+                                                         Tg, Cin, Q, (i64)n);
     return cudaGetLastError();
 }
 
@@ -744,38 +829,40 @@ static int tsqr_parts(int nblk, int n, int cap)
 cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double *Q,
                         cudaStream_t s)
 {
-    i64 rows[64];
-    const int L = tsqr_levels(m, n, rows, 64);
+    TsqrPlan P;
+    tsqr_plan(m, n, P);
+    const int L = P.L;
     double *Tgs[64], *Rst[64], *Qs[64];
-    int nbl[64], rbm[64], pw[64];
+    int pw[64];
     double *w = work;
     for (int l = 0; l < L; l++) {
-        const int nb = tsqr_blocks(rows[l], n);
-        nbl[l] = nb;
-        rbm[l] = (int)((rows[l] + nb - 1) / nb);
-        pw[l] = tsqr_panel_width(rbm[l]);
+        const int nb = P.nblk[l];
+        pw[l] = tsqr_panel_width(P.rbmax[l]);
         if (pw[l] == 0) return cudaErrorInvalidValue;
         Tgs[l] = w;
         w += (size_t)nb * ((size_t)n + 16) * 16 + 8;
         Rst[l] = w;
         w += (size_t)nb * n * n + 8;
         Qs[l] = (l == 0) ? Q : w;
-        if (l > 0) w += (size_t)rows[l] * n + 8;
+        if (l > 0) w += (size_t)P.rows[l] * n + 8;
     }
+    static const char *const kGeqrfNames[] = {"tsqr_geqrf", "tsqr_geqrf_tree1", "tsqr_geqrf_tree2",
+                                              "tsqr_geqrf_tree3", "tsqr_geqrf_tree4+"};
+    static const char *const kOrgqrNames[] = {"tsqr_orgqr", "tsqr_orgqr_tree1", "tsqr_orgqr_tree2",
+                                              "tsqr_orgqr_tree3", "tsqr_orgqr_tree4+"};
     // factorization up the tree
     for (int l = 0; l < L; l++) {
         double *Xl = (l == 0) ? X : Rst[l - 1];
-        const int cs = tsqr_parts(nbl[l], n, 8);
-        static const char *const kGeqrfNames[] = {"tsqr_geqrf", "tsqr_geqrf_tree1",
-                                                  "tsqr_geqrf_tree2", "tsqr_geqrf_tree3",
-                                                  "tsqr_geqrf_tree4+"};
+        const int cs = tsqr_parts(P.nblk[l], n, 8);
         ProfScope ps_(kGeqrfNames[l < 4 ? l : 4], s);
         cudaError_t e;
+        const i64 rw = P.rows[l];
+        const int u = P.unit[l], nb = P.nblk[l], rm = P.rbmax[l];
         switch (pw[l]) {
-        case 16: e = launch_geqrf_nb<16>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
-        case 8: e = launch_geqrf_nb<8>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
-        case 4: e = launch_geqrf_nb<4>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
-        default: e = launch_geqrf_nb<2>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Rst[l], s); break;
+        case 16: e = launch_geqrf_nb<16>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Rst[l], s); break;
+        case 8: e = launch_geqrf_nb<8>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Rst[l], s); break;
+        case 4: e = launch_geqrf_nb<4>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Rst[l], s); break;
+        default: e = launch_geqrf_nb<2>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Rst[l], s); break;
         }
         if (e != cudaSuccess) return e;
     }
@@ -787,16 +874,15 @@ cudaError_t launch_tsqr(double *X, i64 m, int n, double *work, double *R, double
     for (int l = L - 1; l >= 0; l--) {
         const double *Xl = (l == 0) ? X : Rst[l - 1];
         const double *Cin = (l == L - 1) ? nullptr : Qs[l + 1];
-        const int cs = tsqr_parts(nbl[l], n, 1 << 20);
-        static const char *const kOrgqrNames[] = {"tsqr_orgqr", "tsqr_orgqr_tree1",
-                                                  "tsqr_orgqr_tree2", "tsqr_orgqr_tree3",
-                                                  "tsqr_orgqr_tree4+"};
+        const int cs = tsqr_parts(P.nblk[l], n, 1 << 20);
         ProfScope ps_(kOrgqrNames[l < 4 ? l : 4], s);
+        const i64 rw = P.rows[l];
+        const int u = P.unit[l], nb = P.nblk[l], rm = P.rbmax[l];
         switch (pw[l]) {
-        case 16: e = launch_orgqr_nb<16>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
-        case 8: e = launch_orgqr_nb<8>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
-        case 4: e = launch_orgqr_nb<4>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
-        default: e = launch_orgqr_nb<2>(Xl, rows[l], n, nbl[l], cs, rbm[l], Tgs[l], Cin, Qs[l], s); break;
+        case 16: e = launch_orgqr_nb<16>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Cin, Qs[l], s); break;
+        case 8: e = launch_orgqr_nb<8>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Cin, Qs[l], s); break;
+        case 4: e = launch_orgqr_nb<4>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Cin, Qs[l], s); break;
+        default: e = launch_orgqr_nb<2>(Xl, rw, u, n, nb, cs, rm, Tgs[l], Cin, Qs[l], s); break;
         }
         if (e != cudaSuccess) return e;
     }
