@@ -327,26 +327,42 @@ def run_ours(args):
                          "speedup_of_headline": ms64 / ms_max}
         del U64, S64, V64
 
-    # end to end: pinned host buffers, copies inside the timed region
+    # end to end: pinned host buffers (placed on the GPU's NUMA node when
+    # the host has several), copies inside the timed region
     e2e = None
     if args.e2e_steps > 0:
-        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
-        Ah.copy_(A)
-        Uh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
-        Sh = torch.empty((n,), dtype=torch.float64, pin_memory=True)
-        Vh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        numa = bind_to_gpu_numa_node(dev)
+        try:
+            Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+            Ah.copy_(A)
+            Uh = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+            Uh.zero_()
+            Sh = torch.empty((n,), dtype=torch.float64, pin_memory=True)
+            Vh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        finally:
+            restore = numa.pop("restore", None)
+            if restore is not None:
+                os.sched_setaffinity(0, restore)
         Ad = torch.empty_like(A)
         kw2 = dict(kw)
+        phases = []
 
         def e2e_step():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
             Ad.copy_(Ah, non_blocking=True)
+            ev[1].record(stream)
             pkg.ts_svd(Ad, **kw2)
+            ev[2].record(stream)
             Uh.copy_(U, non_blocking=True)
             Sh.copy_(S, non_blocking=True)
             Vh.copy_(V, non_blocking=True)
+            ev[3].record(stream)
+            phases.append(ev)
 
         e2e_step()
         torch.cuda.synchronize()
+        phases.clear()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -356,9 +372,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_e = f0.elapsed_time(f1) / args.e2e_steps
         ms_e = max_over_ranks(ms_e, dev)
+        ph = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in phases) / len(phases) for i in range(3)]
         e2e = {"value": job_gflops(flops, world, ms_e), "unit": "GFLOP/s",
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (m * n + n + n * n) * 8,
-               "ms_per_step": ms_e}
+               "ms_per_step": ms_e,
+               "phases_ms": {"h2d": ph[0], "ts_svd": ph[1], "d2h": ph[2]},
+               "host_numa": numa}
         del Ah, Uh, Sh, Vh, Ad
 
     # roofline of the dominant kernel (largest total event time in the
@@ -394,6 +413,42 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bind_to_gpu_numa_node(dev):
+    """On a host with several NUMA nodes that have CPUs, restrict this
+    process to the CPUs of the GPU's node (from sysfs) so that pinned host
+    buffers allocated and first touched now live there; the caller restores
+    the old affinity ("restore") afterwards.  Returns what it found."""
+    import glob
+    info = {"nodes_with_cpus": 0, "gpu_node": None, "bound": False, "restore": None}
+    try:
+        nodes = {}
+        for p in glob.glob("/sys/devices/system/node/node[0-9]*"):
+            cl = open(os.path.join(p, "cpulist")).read().strip()
+            if not cl:
+                continue
+            cpus = set()
+            for part in cl.split(","):
+                a, _, b = part.partition("-")
+                cpus |= set(range(int(a), int(b or a) + 1))
+            nodes[int(os.path.basename(p)[4:])] = cpus
+        info["nodes_with_cpus"] = len(nodes)
+        import torch
+        pr = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        node = int(open("/sys/bus/pci/devices/%s/numa_node" % bus).read().strip())
+        info["gpu_node"] = node
+        if len(nodes) > 1 and node in nodes:
+            allowed = os.sched_getaffinity(0)
+            mine = nodes[node] & allowed
+            if mine and mine != allowed:
+                os.sched_setaffinity(0, mine)
+                info["bound"] = True
+                info["restore"] = allowed
+    except (OSError, ValueError, AttributeError):
+        pass
+    return info
 
 
 # HBM copy bandwidth measured on this pool's GB300s (the recipe's peak file
