@@ -90,6 +90,33 @@ InternalWs g_ws[64];
 // is counted.
 inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSSVD_BF16X3 ? 2 : 0); }
 
+
+// The first Gram eigensolve of Algorithm 4, B = V~ D~ V~^T (B consumed),
+// accurate to the FP64 rounding already in B (the second pass repairs the
+// rest), for a B formed with FP64-accurate products.
+// For n <= kPcholMaxN: pivoted Cholesky P^T B P = R^T R with the floor of
+// launch_pchol, one-sided Jacobi on the columns of R^T (rotation threshold
+// 2^-51: the columns come out orthogonal to rounding), whose normalised
+// columns, sorted by norm and un-pivoted, are the eigenvectors: B = P R^T R
+// P^T and R^T = (X Sigma^-1) Sigma K^T give B = P (X Sigma^-1) Sigma^2
+// (X Sigma^-1)^T P^T.  On a graded B this converges in a third of the
+// sweeps of the Gram-form solver.  Larger n: Gram-form Jacobi with the
+// normwise floor.  Scratch: Xw, Jw, B2, Xn (n x n), norms, lam (n),
+// perm, piv (n ints).
+static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *Jw, double *Xn,
+                             double *lam, double *norms, double *Vt, int max_sweeps, int *ctr,
+                             double *prm, int *perm, int *piv, DevStatus *st, cudaStream_t s)
+{
+    if (n <= kPcholMaxN) {
+        CK(launch_pchol(B, (int)n, Xw, n, piv, s));
+        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
+        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n, s));
+        return launch_row_scatter(Xn, piv, (int)n, Vt, s);
+    }
+    return launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+                             s, true);
+}
+
 template <typename T, typename TO>
 cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                     int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
@@ -115,7 +142,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     double *Tn = ws.take<double>(n), *tinv = ws.take<double>(n), *Tk = ws.take<double>(n);
     double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
     double *cs = ws.take<double>(n);
-    int *perm = ws.take<int>(n);
+    int *perm = ws.take<int>(n), *piv = ws.take<int>(n);
     double *prm = ws.take<double>(jacobi_prm_doubles(n));
     double *B2 = ws.take<double>(nn);
     double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
@@ -170,9 +197,14 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
     }
-    // B = V~ D~ V~^T (Gram-form Jacobi; B is rotated in place).
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s,
-                         true));
+    // B = V~ D~ V~^T (B consumed).  The BF16-split first pass leaves errors
+    // in B far above its FP64 rounding, the floor the Cholesky form assumes:
+    // it keeps the Gram-form solver.
+    if (terms)
+        CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+                             s, true));
+    else
+        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
@@ -262,7 +294,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     double *Tn = ws.take<double>(n), *tinv = ws.take<double>(n), *Tk = ws.take<double>(n);
     double *sgn = ws.take<double>(n), *norms = ws.take<double>(n), *sigma = ws.take<double>(n);
     double *cs = ws.take<double>(n);
-    int *perm = ws.take<int>(n);
+    int *perm = ws.take<int>(n), *piv = ws.take<int>(n);
     double *prm = ws.take<double>(jacobi_prm_doubles(n));
     double *B2 = ws.take<double>(nn);
     double *Yt = ws.take<double>((size_t)m * n);
@@ -295,9 +327,12 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
     CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
-    // B = V~ D~ V~^T
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0, s,
-                         passes == 2));
+    // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm 3)
+    if (passes == 2)
+        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s));
+    else
+        CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+                             s));
     const double *M1 = Vt;
     if (sc) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));

@@ -191,9 +191,21 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 // ctr must point to at least max_sweeps + 4 zeroed ints of device memory;
 // prm to jacobi_prm_doubles(nc) doubles of scratch.
 inline size_t jacobi_prm_doubles(i64 nc) { return 8 * (size_t)((nc + 1) / 2) + 8; }
+// tol: the rotation threshold |x_p . x_q| > tol |x_p| |x_q| (0: nr 2^-53).
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
                           int max_sweeps, int *ctr, double *prm, DevStatus *st, int which,
-                          cudaStream_t s);
+                          cudaStream_t s, double tol = 0.0);
+
+// Pivoted Cholesky of the symmetric W (n x n row-major, consumed) with a
+// floor: P^T W P = R^T R, pivots the largest remaining diagonal entries;
+// once all remaining ones are <= 2^-52 max_i W_ii the trailing block of R
+// is that floor's square root times I (W = 0: R = I).  X = R^T
+// column-major (ldx), piv[i] = the original index of pivoted index i.
+// One CTA; used for n <= kPcholMaxN.
+constexpr int kPcholMaxN = 256;
+cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStream_t s);
+// V[piv[i]][j] = Xn[i][j], n x n row-major.
+cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *V, cudaStream_t s);
 
 // Eigendecomposition of the symmetric B (n x n row-major) by Gram-form
 // Jacobi, same pair schedule and barrier.  V (n x n, column-major)

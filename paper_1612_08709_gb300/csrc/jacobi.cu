@@ -1319,10 +1319,174 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
     }
 }
 
+// Pivoted Cholesky with a floor, one CTA: P^T W P = R^T R with the pivot
+// the largest remaining diagonal entry at each step.  Once every remaining
+// diagonal entry is <= delta = 2^-52 max_i W_ii (the rounding already in a
+// Gram matrix of that size), the trailing block of R is set to sqrt(delta) I
+// (W perturbed by at most 2 delta in norm); W = 0 gives R = I.  W (n x n,
+// row-major, symmetric) is consumed: rows and columns of its trailing
+// block are swapped physically so the rank-one updates stay contiguous.
+// Output: X = R^T column-major (X[k ldx + i] = R[k][i]) and piv (logical
+// index i is original index piv[i]).
+constexpr int kPcholThreads = 1024;
+
+__global__ void __launch_bounds__(kPcholThreads, 1)
+    pchol_kernel(double *__restrict__ W, int n, double *__restrict__ X, i64 ldx,
+                 int *__restrict__ piv)
+{
+    extern __shared__ double pc_s[];
+    double *rk = pc_s;                               // row k of R (n)
+    double *rv = rk + n;                             // reduction values (32)
+    int *ri = (int *)(rv + 32);                      // reduction indices (32)
+    int *pm = ri + 32;                               // permutation (n)
+    __shared__ double sdelta, spiv;
+    __shared__ int sj, sstop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kPcholThreads / 32;
+    for (int i = tid; i < n; i += kPcholThreads) pm[i] = i;
+    for (i64 e = tid; e < (i64)n * n; e += kPcholThreads) {
+        const i64 k = e / n, i = e - k * n;
+        X[k * ldx + i] = 0.0;
+    }
+    // delta = 2^-52 max diag
+    {
+        double v = 0.0;
+        for (int i = tid; i < n; i += kPcholThreads) v = fmax(v, W[(i64)i * n + i]);
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) rv[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; w++) t = fmax(t, rv[w]);
+            sdelta = 0x1p-52 * t;
+        }
+        __syncthreads();
+    }
+    const double delta = sdelta;
+    int k = 0;
+    for (; k < n; k++) {
+        // pivot: the largest remaining diagonal entry (lowest index on ties)
+        double bv = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < n; i += kPcholThreads) {
+            const double v = W[(i64)i * n + i];
+            if (v > bv) {
+                bv = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            rv[warp] = bv;
+            ri[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t = rv[0];
+            int j = ri[0];
+            for (int w = 1; w < nw; w++)
+                if (rv[w] > t || (rv[w] == t && ri[w] < j)) {
+                    t = rv[w];
+                    j = ri[w];
+                }
+            sj = j;
+            sstop = (delta > 0.0 && t > delta) ? 0 : 1;
+            spiv = t;
+        }
+        __syncthreads();
+        if (sstop) break;
+        const int j = sj;
+        if (j != k) {
+            // swap rows k and j of the trailing block, then columns k and j
+            for (int c = k + tid; c < n; c += kPcholThreads) {
+                const double a = W[(i64)k * n + c], b = W[(i64)j * n + c];
+                W[(i64)k * n + c] = b;
+                W[(i64)j * n + c] = a;
+            }
+            // the finished rows of R: entries at logical columns k and j
+            for (int r = tid; r < k; r += kPcholThreads) {
+                const double a = X[(i64)r * ldx + k], b = X[(i64)r * ldx + j];
+                X[(i64)r * ldx + k] = b;
+                X[(i64)r * ldx + j] = a;
+            }
+            __syncthreads();
+            for (int r = k + tid; r < n; r += kPcholThreads) {
+                const double a = W[(i64)r * n + k], b = W[(i64)r * n + j];
+                W[(i64)r * n + k] = b;
+                W[(i64)r * n + j] = a;
+            }
+            if (tid == 0) {
+                const int t = pm[k];
+                pm[k] = pm[j];
+                pm[j] = t;
+            }
+            __syncthreads();
+        }
+        // row k of R
+        const double pv = sqrt(spiv), inv = 1.0 / pv;
+        for (int c = k + tid; c < n; c += kPcholThreads) {
+            const double r = (c == k) ? pv : W[(i64)k * n + c] * inv;
+            rk[c] = r;
+            X[(i64)k * ldx + c] = r;
+        }
+        __syncthreads();
+        // rank-one update of the trailing block (rows and columns > k)
+        const int t = n - k - 1;
+        for (int e = tid; e < t * t; e += kPcholThreads) {
+            const int i = k + 1 + e / t, c = k + 1 + e % t;
+            W[(i64)i * n + c] = fma(-rk[i], rk[c], W[(i64)i * n + c]);
+        }
+        __syncthreads();
+    }
+    // the trailing block below the floor (or all of R when W = 0)
+    const double tail = delta > 0.0 ? sqrt(delta) : 1.0;
+    for (int i = k + tid; i < n; i += kPcholThreads) X[(i64)i * ldx + i] = tail;
+    for (int i = tid; i < n; i += kPcholThreads) piv[i] = pm[i];
+}
+
+// V[piv[i]][j] = Xn[i][j] (n x n row-major): the eigenvectors of the
+// pivoted matrix back in the original order.
+__global__ void row_scatter_kernel(const double *__restrict__ Xn, const int *__restrict__ piv,
+                                   int n, double *__restrict__ V)
+{
+    const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (i64)n * n) return;
+    const i64 i = e / n, j = e - i * n;
+    V[(i64)piv[i] * n + j] = Xn[e];
+}
+
 }  // namespace
 
+cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStream_t s)
+{
+    const size_t smem = sizeof(double) * ((size_t)n + 32) + sizeof(int) * ((size_t)n + 32);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pchol_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    ProfScope ps_("pchol", s);
+    pchol_kernel<<<1, kPcholThreads, smem, s>>>(W, n, X, ldx, piv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *V, cudaStream_t s)
+{
+    const i64 total = (i64)n * n;
+    row_scatter_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Xn, piv, n, V);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc, int max_sweeps,
-                          int *ctr, double *prm, DevStatus *st, int which, cudaStream_t s)
+                          int *ctr, double *prm, DevStatus *st, int which, cudaStream_t s,
+                          double tol)
 {
     cudaError_t e;
     {
@@ -1352,7 +1516,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.nc = nc;
     a.npad = nc + (nc & 1);
     a.max_sweeps = max_sweeps;
-    a.tol = (double)nr * 0x1p-53;
+    a.tol = tol > 0.0 ? tol : (double)nr * 0x1p-53;
     a.rot = ctr;
     a.st = st;
     a.which = which;
