@@ -117,6 +117,21 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
                              s, true);
 }
 
+// The small SVD of Algorithm 4, R = P Sigma V^T (R n x n row-major), by
+// one-sided Jacobi on the columns of R^T, or of R when the MaxEntry scaling
+// D is strongly graded (the device flag st->orient set by
+// launch_orient_copy: column grading is what the one-sided method handles
+// accurately).  Outputs Pm (P), sigma, Vo (V), sorted.
+static cudaError_t final_svd(double *R, i64 n, const double *d, double *Xw, double *Jw,
+                             double *norms, double *Pm, double *sigma, double *Vo, int max_sweeps,
+                             int *ctr, double *prm, int *perm, DevStatus *st, cudaStream_t s)
+{
+    CK(launch_orient_copy(d, &st->rank2, R, n, Xw, &st->orient, s));
+    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
+    return launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n,
+                                  s, &st->orient);
+}
+
 template <typename T, typename TO>
 cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                     int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
@@ -247,10 +262,8 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     // V = X Sigma^-1.  When the MaxEntry scaling is strongly graded the
     // Jacobi runs on the columns of R instead (R V = X, P = X Sigma^-1);
     // the device-side flag in st->orient routes the outputs.
-    CK(launch_orient_copy(scale ? d : nullptr, &st->rank2, R, n, Xw, &st->orient, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s,
-                              &st->orient));
+    CK(final_svd(R, n, scale ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm,
+                 perm, st, s));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Q P = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
@@ -397,10 +410,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_build_g(sig, sinv, Vt, n, sc ? d : nullptr, n, G, s));
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
-    CK(launch_orient_copy(sc ? d : nullptr, &st->rank2, R, n, Xw, &st->orient, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
-    CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n, s,
-                              &st->orient));
+    CK(final_svd(R, n, sc ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm, perm,
+                 st, s));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)), prescaled like Q~

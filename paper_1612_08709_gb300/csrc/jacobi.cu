@@ -1339,7 +1339,7 @@ __global__ void __launch_bounds__(kPcholThreads, 1)
     double *rv = rk + n;                             // reduction values (32)
     int *ri = (int *)(rv + 32);                      // reduction indices (32)
     int *pm = ri + 32;                               // permutation (n)
-    __shared__ double sdelta, spiv;
+    __shared__ double sdelta, spiv, sinv;
     __shared__ int sj, sstop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = kPcholThreads / 32;
@@ -1398,7 +1398,9 @@ __global__ void __launch_bounds__(kPcholThreads, 1)
                 }
             sj = j;
             sstop = (delta > 0.0 && t > delta) ? 0 : 1;
-            spiv = t;
+            // (one thread: FP64 sqrt and divide are long FP64-pipe sequences)
+            spiv = sstop ? 0.0 : sqrt(t);
+            sinv = sstop ? 0.0 : 1.0 / spiv;
         }
         __syncthreads();
         if (sstop) break;
@@ -1430,18 +1432,30 @@ __global__ void __launch_bounds__(kPcholThreads, 1)
             __syncthreads();
         }
         // row k of R
-        const double pv = sqrt(spiv), inv = 1.0 / pv;
+        const double pv = spiv, inv = sinv;
         for (int c = k + tid; c < n; c += kPcholThreads) {
             const double r = (c == k) ? pv : W[(i64)k * n + c] * inv;
             rk[c] = r;
             X[(i64)k * ldx + c] = r;
         }
         __syncthreads();
-        // rank-one update of the trailing block (rows and columns > k)
-        const int t = n - k - 1;
-        for (int e = tid; e < t * t; e += kPcholThreads) {
-            const int i = k + 1 + e / t, c = k + 1 + e % t;
-            W[(i64)i * n + c] = fma(-rk[i], rk[c], W[(i64)i * n + c]);
+        // rank-one update of the trailing block (rows and columns > k): a
+        // warp per row, each lane's columns loaded together (n <= 256: at
+        // most 8 per lane), so a row costs one memory round trip
+        for (int i = k + 1 + warp; i < n; i += nw) {
+            double *row = W + (i64)i * n;
+            const double ri_ = rk[i];
+            double w[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int c = k + 1 + lane + 32 * q;
+                w[q] = c < n ? row[c] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int c = k + 1 + lane + 32 * q;
+                if (c < n) row[c] = fma(-ri_, rk[c], w[q]);
+            }
         }
         __syncthreads();
     }
@@ -1462,6 +1476,7 @@ __global__ void row_scatter_kernel(const double *__restrict__ Xn, const int *__r
     V[(i64)piv[i] * n + j] = Xn[e];
 }
 
+
 }  // namespace
 
 cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStream_t s)
@@ -1472,6 +1487,7 @@ cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStr
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    if (n > 256) return cudaErrorInvalidValue;  // rows held as 8 values per lane
     ProfScope ps_("pchol", s);
     pchol_kernel<<<1, kPcholThreads, smem, s>>>(W, n, X, ldx, piv);
     return cudaGetLastError();

@@ -205,7 +205,8 @@ __device__ double qr_col_norm(const double *P, int lo, int rb, int j, double *re
     const double xs = out[0];
     if (xs >= 0x1p-960 && xs <= 0x1p960) {
         *in_range = true;
-        return sqrt(xs);
+        // only thread 0 uses the norm: one FP64 square root, not one per thread
+        return threadIdx.x == 0 ? sqrt(xs) : 1.0;
     }
     *in_range = false;
     double am = 0.0;
