@@ -472,7 +472,7 @@ def bf16_peak(sustained=True):
         return (1700.0 if sustained else 1900.0), "fallback"
 
 
-def kernel_models(m, n, esize, sweeps):
+def kernel_models(m, n, esize, sweeps, cholesky_first=False):
     """Algorithmic work per launch of each kernel of the two-pass TS-SVD.
 
     Returns {kernel: (bound, amount, unit)}: FP64 flops for the FP64-pipe
@@ -486,6 +486,12 @@ def kernel_models(m, n, esize, sweeps):
                   rounds per sweep, the step's mean sweep count
       jacobi_svd  one-sided Jacobi: per pair 3n FMAs (dots) and 2n outputs
                   of X and of J at 3 flops: 18n, n / 2 pairs: 9 n^2 per round
+      pchol       pivoted Cholesky of the n x n Gram: n^3 / 3 FMAs
+    cholesky_first: the first eigensolve ran as pivoted Cholesky and the
+    one-sided kernel (n <= 256, FP64-accurate modes), so jacobi_eig is the
+    second eigensolve alone (sweeps[1]) and jacobi_svd launches twice, for
+    sweeps[0] and sweeps[2]; otherwise jacobi_eig launches for sweeps[0]
+    and sweeps[1] and jacobi_svd once (sweeps[2]).
       oz_nn, oz_gram  28 bf16 digit-pair products per FP64-accurate product
       oz_*_image  read the tall operand once, write 7 bf16 digits per entry
       colmax, oz_rowexp  read the tall operand once; colsumsq reads m n FP64
@@ -497,9 +503,14 @@ def kernel_models(m, n, esize, sweeps):
            "oz_gram_image": ("hbm", (esize + 14.0) * m * n), "oz_row_image": ("hbm", (8 + 14.0) * m * n),
            "colmax": ("hbm", float(esize) * m * n), "oz_rowexp": ("hbm", 8.0 * m * n),
            "colsumsq": ("hbm", 8.0 * m * n)}
+    mdl["pchol"] = ("alu", 2.0 * n * n * n / 3.0)
     if sweeps and len(sweeps) >= 3 and min(sweeps[:3]) > 0:
-        mdl["jacobi_eig"] = ("alu", (sweeps[0] + sweeps[1]) / 2.0 * rounds * 6.0 * n * n)
-        mdl["jacobi_svd"] = ("alu", float(sweeps[2]) * rounds * 9.0 * n * n)
+        if cholesky_first:
+            mdl["jacobi_eig"] = ("alu", float(sweeps[1]) * rounds * 6.0 * n * n)
+            mdl["jacobi_svd"] = ("alu", (sweeps[0] + sweeps[2]) / 2.0 * rounds * 9.0 * n * n)
+        else:
+            mdl["jacobi_eig"] = ("alu", (sweeps[0] + sweeps[1]) / 2.0 * rounds * 6.0 * n * n)
+            mdl["jacobi_svd"] = ("alu", float(sweeps[2]) * rounds * 9.0 * n * n)
     return mdl
 
 
@@ -524,6 +535,9 @@ def roofline_entry(name, cnt, tot_ms, model, step_ms, args):
     if name.startswith("jacobi"):
         e["note"] = ("latency-bound: one grid barrier and a chain of dependent FP64 "
                      "operations per round; the fraction is of the FP64 pipe")
+    elif name == "pchol":
+        e["note"] = ("one CTA, a barrier-separated chain of n pivot steps; the fraction "
+                     "is of the whole GPU's FP64 pipe")
     return e
 
 
@@ -533,7 +547,7 @@ def roofline(kernels, m, n, ms, args, esize, sweeps=None):
     algorithmic work per launch (kernel_models) / mean launch duration."""
     if not kernels:
         return None, []
-    mdl = kernel_models(m, n, esize, sweeps)
+    mdl = kernel_models(m, n, esize, sweeps, cholesky_first="pchol" in kernels)
     ranked = sorted(kernels.items(), key=lambda kv: -kv[1][1])
     entries = []
     for name, (cnt, tot) in ranked:
