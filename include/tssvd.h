@@ -89,7 +89,10 @@ typedef struct {
     size_t workspace_bytes;
     /* ---- written by the call ---- */
     int64_t out_rank; /* number of nonzero singular values returned */
-    int sweeps[4];    /* Jacobi sweeps: [0] eig of A^T A, [1] eig of Y^T Y, [2] SVD of R */
+    /* Jacobi sweeps: [0] the first eigensolve (of A^T A, D-scaled; with
+     * passes = 2, n <= 256 and an FP64-accurate mode, the one-sided sweeps
+     * on its pivoted Cholesky factor), [1] eig of Y^T Y, [2] SVD of R */
+    int sweeps[4];
     int ranks[2];     /* ranks kept by the first and second discard steps */
 } tssvd_opts;
 
@@ -109,6 +112,12 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
  * passes = 2: Algorithm 4 (Gram of A, eigendecomposition, Y~ = A V~,
  * explicit column norms (Remark "normalizing"), discard, second Gram pass
  * on Y, R = T W^T S~ V~^T, SVD of R, U = Q P).  passes = 1: Algorithm 3.
+ * The eigendecompositions and the SVD of R are Jacobi methods; the first
+ * eigensolve of Algorithm 4 is accurate to the rounding already in the
+ * Gram matrix (the second pass repairs the rest): for n <= 256 in the
+ * FP64-accurate modes it is a pivoted Cholesky factorization followed by
+ * one-sided Jacobi on the factor, otherwise Gram-form Jacobi with a
+ * normwise floor.
  *   A   [in]  m x n, row-major, leading dimension lda >= n; not modified.
  *   U   [out] m x n, row-major (leading dimension n).
  *   S   [out] n.

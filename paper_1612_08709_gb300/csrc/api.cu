@@ -257,11 +257,10 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     CK(launch_build_g(sig, sinv, Vt, n, scale ? d : nullptr, n, G, s));
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
-    // R = P Sigma V^T by one-sided Jacobi on the columns of R^T (R
-    // row-major = R^T column-major): R^T P = X, Sigma = column norms,
-    // V = X Sigma^-1.  When the MaxEntry scaling is strongly graded the
-    // Jacobi runs on the columns of R instead (R V = X, P = X Sigma^-1);
-    // the device-side flag in st->orient routes the outputs.
+    // R = P Sigma V^T by one-sided Jacobi (final_svd): on the columns of
+    // R^T (R row-major = R^T column-major: R^T P = X, Sigma = column norms,
+    // V = X Sigma^-1), or of R when the MaxEntry scaling is strongly graded
+    // (the device-side flag st->orient routes the outputs).
     CK(final_svd(R, n, scale ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm,
                  perm, st, s));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
