@@ -143,3 +143,20 @@ def test_lowrank_tsqr_argument_validation_without_gpu():
     assert L.lowrank_svd_tsqr(*args(pm=None)) == -10
     assert L.lowrank_svd_tsqr(*args(V=None)) == -13
     assert L.lowrank_svd_tsqr(*args(o=None)) == -14
+
+
+def test_tsqr_workspace_query_without_gpu():
+    """Algorithm 2's workspace holds B*, Q and Q2 (m x n' FP64 each) and the
+    reduction tree; the query is host arithmetic (the tree plan) and grows
+    with m."""
+    import paper_1612_08709_gb300 as pkg
+    from paper_1612_08709_gb300._binding import _Opts
+    L = pkg.lib()
+    o = _Opts()
+    L.tssvd_default_opts(ctypes.byref(o))
+    small = L.ts_svd_tsqr_workspace_size(20000, 50, ctypes.byref(o))
+    big = L.ts_svd_tsqr_workspace_size(200000, 200, ctypes.byref(o))
+    odd = L.ts_svd_tsqr_workspace_size(200000, 199, ctypes.byref(o))
+    assert small >= 3 * 20000 * 50 * 8
+    assert big >= 3 * 200000 * 200 * 8 and big > small
+    assert odd >= 3 * 200000 * 200 * 8  # n odd is padded to n + 1
