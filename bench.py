@@ -11,8 +11,9 @@ plain FP64 (DFMA) path is timed beside it on the same input
 
 Prints one JSON line (rank 0).  `value` is GFLOP/s of the algorithm's
 nominal products (8 m n^2 for two passes: Gram A^T A, A V~, Gram Y^T Y,
-Y W and Q P) with A resident in HBM; `e2e` is the same metric through the
-same C-ABI call with host buffers (copies inside the timed region).
+Y W and Q P) with A resident in HBM; `e2e` is the same metric for the same
+C-ABI call with A copied in from pinned host memory and U, S, V copied
+back, both copies inside the timed region (`phases_ms` splits them out).
 `--impl reference` times the FP64 CPU oracle instead (bounded samples of
 the same workload on the host cores).
 
@@ -64,8 +65,8 @@ WORKLOADS = {
     "grad_500k_x_512": dict(kind="grad", m=500_000, n=512, k=64, nb=8, seed=6),
 }
 
-# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the
-# recipe's unit count and maximum SM clock); the DFMA probe measured 1.20.
+# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (GB300's FP64
+# units and maximum SM clock); the DFMA probe measured 1.20.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9
 
 
@@ -451,8 +452,8 @@ def bind_to_gpu_numa_node(dev):
     return info
 
 
-# HBM copy bandwidth measured on the GB300s (the recipe's peak file
-# when present, else the recipe's fallback figure).
+# HBM copy bandwidth: the measured copy rate in MEASURED_PEAKS.json when
+# present, else an earlier GB300 measurement (6.8 TB/s).
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
