@@ -203,8 +203,9 @@ void or_maxentry_scale(const double *A, i64 m, i64 n, i64 lda, double *d)
 /*
  * Orthogonalises the columns of X (nr x nc, ldx) in place by plane
  * rotations, accumulating the rotations in J (nc x nc, ldj, set to I here):
- * on return X_in * J = X_out with mutually orthogonal columns.  The
- * columns of X_out and J are then permuted into order of decreasing norm
+ * on return X_in * J = X_out with mutually orthogonal columns.  J's
+ * columns are then scaled to unit norm (unit_columns), and the
+ * columns of X_out and J are permuted into order of decreasing norm
  * (stable), and s[j] = |X_out column j|.  Returns the number of sweeps
  * taken, or -1 if max_sweeps sweeps all rotated something.
  *
@@ -243,6 +244,24 @@ static double jac_tan(double a, double b, double g)
     }
     const int pos = (d == 0.0) || ((d > 0.0) == (g > 0.0));
     return pos ? t : -t;
+}
+
+/* Divides each column of the n x n matrix J (ldj) by its Euclidean norm.
+ * The accumulated rotations are the eigenvectors (or singular vectors) of
+ * the Jacobi methods, which are unit vectors by definition; each FP64
+ * rotation with c = 1/sqrt(1 + t^2), s = c t has c^2 + s^2 = 1 + O(eps),
+ * biased upward once t^2 is below the rounding unit, so over many
+ * rotations the columns' norms drift above 1 (about 1e-13 at n = 300,
+ * which is what limited the orthonormality of U = Q P in Algorithm 4). */
+static void unit_columns(double *J, i64 n, i64 ldj)
+{
+    for (i64 j = 0; j < n; j++) {
+        double ss = 0.0;
+        for (i64 i = 0; i < n; i++) ss += J[i * ldj + j] * J[i * ldj + j];
+        const double nr = sqrt(ss);
+        if (nr > 0.0)
+            for (i64 i = 0; i < n; i++) J[i * ldj + j] /= nr;
+    }
 }
 
 int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
@@ -288,6 +307,7 @@ int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
             break;
         }
     }
+    unit_columns(J, nc, ldj);
 
     /* Norms and a stable sort by decreasing norm (insertion sort on an
      * index array keeps equal norms in original order). */
@@ -328,7 +348,8 @@ int or_jacobi(double *X, i64 nr, i64 nc, i64 ldx, double *J, i64 ldj,
  * that orthogonalises columns p and q of X, computed from b_pp, b_qq, b_pq
  * and applied as B <- J^T B J (so b_pq becomes 0, b_pp <- b_pp - t b_pq,
  * b_qq <- b_qq + t b_pq).  Rotations accumulate in V (n x n, ldv, set to I
- * here).  Same rotation test and stopping rule as or_jacobi with
+ * here) and are scaled to unit columns at the end (unit_columns).  Same
+ * rotation test and stopping rule as or_jacobi with
  * tol = n * 2^-53 (relative to sqrt(|b_pp b_qq|)).  On return lam holds the
  * diagonal of the rotated B sorted in decreasing order (stable), V's
  * columns are permuted to match, and B holds the rotated matrix (unsorted).
@@ -380,6 +401,7 @@ int or_jacobi_eig(double *B, i64 n, i64 ldb, double *V, i64 ldv, double *lam,
             break;
         }
     }
+    unit_columns(V, n, ldv);
     /* stable sort by decreasing diagonal */
     i64 *idx = (i64 *)malloc((size_t)(n > 0 ? n : 1) * sizeof(i64));
     double *dg = dalloc(n), *tv = dalloc(n * n);

@@ -129,7 +129,7 @@ static cudaError_t final_svd(double *R, i64 n, const double *d, double *Xw, doub
     CK(launch_orient_copy(d, &st->rank2, R, n, Xw, &st->orient, s));
     CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
     return launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n,
-                                  s, &st->orient);
+                                  s, &st->orient, prm);
 }
 
 template <typename T, typename TO>
@@ -1283,7 +1283,7 @@ cudaError_t tsqr_core(const double *X, i64 rows, i64 n, i64 ldx, const double *M
     CK(launch_orient_copy(nullptr, &st->rank2, T, np, Xw, &st->orient, s));
     CK(launch_jacobi(Xw, np, Jw, np, (int)np, (int)np, max_sweeps, ctr, prm, st, 2, s));
     CK(launch_jacobi_finalize(Xw, np, Jw, np, (int)np, (int)np, norms, perm_s, Pm, np, sigma, Vo,
-                              np, s, &st->orient));
+                              np, s, &st->orient, prm));
     // V = (O^T V~)[0:n, 0:n] = Mt[0:n, :] V~[:, 0:n], then the sign rule
     CK(launch_nn<double, double>(Mt, np, Vo, np, n, np, n, V, ldv, NP, s));
     CK(launch_signs(V, ldv, n, n, sigma, sgn, s));

@@ -214,7 +214,9 @@ cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *
 // matching eigenvectors as columns.  B2: a second n x n buffer (ldb) for
 // the one-barrier-per-round form, or NULL for the two-barrier in-place
 // form; either way B's contents are consumed.  prm: scratch of
-// 4 * ceil(n/2) + 2 doubles; perm: n ints; ctr as for launch_jacobi.
+// jacobi_prm_doubles(n) doubles; perm: n ints; ctr as for launch_jacobi.
+// The eigenvectors are returned with unit norms (V's accumulated columns
+// divided by their recomputed norms).
 // normwise (one-barrier forms only): a pair rotates only when |b_PQ| also
 // exceeds 2^-52 times the largest diagonal entry (refreshed each sweep),
 // i.e. is above the rounding already in B; used for the first Gram
@@ -230,10 +232,13 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
 // row-major, column r = X column perm[r] / sigma_r, 0 when sigma_r = 0).
 // (orient non-null and *orient != 0, nr == nc: the J and X/s outputs trade
 // places, for a Jacobi run on the columns of R instead of R^T.)
+// jnorm (nc doubles of scratch, or null): J's columns are divided by their
+// recomputed norms, removing the rounding drift of the accumulated
+// rotations (needed wherever J is a result).
 cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, double *norms, int *perm, double *Jout, i64 ldjo,
                                    double *lam, double *Xout, i64 ldxo, cudaStream_t s,
-                                   const int *orient = nullptr);
+                                   const int *orient = nullptr, double *jnorm = nullptr);
 
 // ---------------------------------------------------------- small ops
 // Discard rule: smax = max sig; r = 1 + last j with sig_j > 0 and not

@@ -1285,10 +1285,18 @@ __global__ void rank_sort_kernel(const double *norms, int nc, int *perm)
     }
 }
 
+// Jout column r = J column perm[r] divided by its norm jnorm[perm[r]]
+// (jnorm may be null: no division).  A product of plane rotations has unit
+// columns in exact arithmetic; in FP64 each rotation with c = 1/sqrt(1 +
+// t^2) and s = c t has c^2 + s^2 = 1 + O(eps) with a positive bias once
+// t^2 falls below the rounding unit, so over thousands of rotations a
+// column's norm drifts upward (1e-13 at n = 300), and that drift, not the
+// convergence test, set the orthonormality of U = Q P.  Dividing by the
+// recomputed norms removes it.
 __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, const double *norms, const int *perm, double *Jout,
                                    i64 ldjo, double *lam, double *Xout, i64 ldxo,
-                                   const int *orient)
+                                   const int *orient, const double *jnorm)
 {
     if (orient && Xout && nr == nc && *orient != 0) {
         double *tp = Jout;
@@ -1306,7 +1314,8 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
             const i64 i = e / nc, r = e % nc;  // row i, output column r
             int src = perm[r];
             if (src < 0 || src >= nc) src = (int)r;
-            Jout[i * ldjo + r] = J[(i64)src * ldj + i];
+            const double jn = jnorm ? jnorm[src] : 1.0;
+            Jout[i * ldjo + r] = jn > 0.0 ? J[(i64)src * ldj + i] / jn : J[(i64)src * ldj + i];
             if (i == 0 && lam) lam[r] = norms[src];
         } else {
             const i64 f = e - tj;
@@ -1675,6 +1684,15 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
     rank_sort_kernel<<<(n + 255) / 256, 256, 0, s>>>(dg, n, perm);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // unit eigenvectors: the norms of V's accumulated columns (prm + n)
+    double *vn = prm + n;
+    {
+        const int warps_per_block = 8;
+        ProfScope ps_("colnorm", s);
+        colnorm_cm_kernel<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
+                            s>>>(V, ldv, n, n, vn);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     {
         i64 total = (i64)n * n;
         i64 blocks = (total + 255) / 256;
@@ -1682,7 +1700,8 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         if (blocks < 1) blocks = 1;
         ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(nullptr, 0, V, ldv, 0, n, dg, perm,
-                                                            Vout, ldvo, lam, nullptr, 0, nullptr);
+                                                            Vout, ldvo, lam, nullptr, 0, nullptr,
+                                                            vn);
     }
     return cudaGetLastError();
 }
@@ -1690,7 +1709,7 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
 cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i64 ldj, int nr,
                                    int nc, double *norms, int *perm, double *Jout, i64 ldjo,
                                    double *lam, double *Xout, i64 ldxo, cudaStream_t s,
-                                   const int *orient)
+                                   const int *orient, double *jnorm)
 {
     cudaError_t e;
     {
@@ -1699,6 +1718,10 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
         ProfScope ps_("colnorm", s);
         colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(X, ldx, nr, nc, norms);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (jnorm) {
+            colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(J, ldj, nc, nc, jnorm);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     {
     ProfScope ps_("rank_sort", s);
@@ -1712,7 +1735,8 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
         if (blocks < 1) blocks = 1;
         ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, J, ldj, nr, nc, norms, perm,
-                                                            Jout, ldjo, lam, Xout, ldxo, orient);
+                                                            Jout, ldjo, lam, Xout, ldxo, orient,
+                                                            jnorm);
     }
     return cudaGetLastError();
 }
