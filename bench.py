@@ -3,19 +3,23 @@
 
 One step = one full call of the hot path on one batch of synthetic input:
 by default the two-pass Gram TS-SVD (Algorithm 4 with MaxEntry scaling) of
-a 2,000,000 x 200 FP64 matrix A = U diag(sigma) V^T with seeded
+a 1,000,000 x 1,000 FP64 matrix A = U diag(sigma) V^T with seeded
 orthonormal factors and sigma geometric from 1 to 1e-8, in the
 FP64-accurate tensor-core mode (digit-sliced products on tcgen05).  The
 plain FP64 (DFMA) path is timed beside it on the same input
-("fp64_path"), with both accuracies, for the comparison at equal accuracy.
+("fp64_path"), with both accuracies, for the comparison at equal accuracy,
+and the 2,000,000 x 200 workload of the same recipe is timed after it
+("also").
 
 Prints one JSON line (rank 0).  `value` is GFLOP/s of the algorithm's
-nominal products (8 m n^2 for two passes: Gram A^T A, A V~, Gram Y^T Y,
-Y W and Q P) with A resident in HBM; `e2e` is the same metric for the same
+nominal products, 6 m n^2 for two passes (Gram A^T A counted as m n^2,
+A V~ 2 m n^2, Gram Y^T Y m n^2, Y W 2 m n^2; the final U = Q P is not
+counted), with A resident in HBM; `e2e` is the same metric for the same
 C-ABI call with A copied in from pinned host memory and U, S, V copied
 back, both copies inside the timed region (`phases_ms` splits them out).
-`--impl reference` times the FP64 CPU oracle instead (bounded samples of
-the same workload on the host cores).
+The FP64 roofline peak is the FP64 FMA rate measured on the same GPU in
+the same run (tssvd_fp64_fma_rate).  `--impl reference` times the FP64 CPU
+oracle instead (bounded samples of the same workload on the host cores).
 
 Multi-GPU (torchrun): every rank runs an independent replica of the
 workload (weak scaling, no collective on the data path).
@@ -65,9 +69,23 @@ WORKLOADS = {
     "grad_500k_x_512": dict(kind="grad", m=500_000, n=512, k=64, nb=8, seed=6),
 }
 
-# FP64 FMA peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (GB300's FP64
-# units and maximum SM clock); the DFMA probe measured 1.20.
+# FP64 FMA peak when it cannot be measured: 152 SMs x 2 DFMA/clk/SM x 2 flop
+# x 2.07 GHz (GB300's FP64 units and maximum SM clock).  run_ours replaces it
+# with the rate measured on the device (set_fp64_peak).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9
+FP64_PEAK_SOURCE = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)"
+
+
+def set_fp64_peak(L):
+    """Measures the device's FP64 FMA rate (tssvd_fp64_fma_rate) and makes
+    it the FP64 roofline peak; keeps the derived figure if that fails."""
+    global FP64_PEAK_GFLOPS, FP64_PEAK_SOURCE
+    v = ctypes.c_double(0.0)
+    if L.tssvd_fp64_fma_rate(ctypes.byref(v), None) == 0 and v.value > 0:
+        FP64_PEAK_GFLOPS = v.value * 1e3
+        FP64_PEAK_SOURCE = ("FP64 FMA rate measured in this run (tssvd_fp64_fma_rate: "
+                            "independent DFMA chains, %.3f TFLOP/s)" % v.value)
+    return FP64_PEAK_GFLOPS / 1e3
 
 
 def parse():
@@ -76,7 +94,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ts_2m_x_200", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ts_1m_x_1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--also", default="ts_2m_x_200",
+                    help="comma-separated tall-skinny workloads timed after the headline "
+                         "(device-resident, same steps; '' to skip)")
     ap.add_argument("--mode", default="fp64_tc", choices=["fp64", "bf16x3", "bf16x6", "fp64_tc"])
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the plain FP64 path reported beside the headline "
@@ -89,8 +110,14 @@ def parse():
 
 
 def nominal_flops(w):
+    """Nominal flops of one two-pass TS-SVD: 6 m n^2 (the Gram matrices
+    counted as m n^2 each, symmetric; A V~ and Y W 2 m n^2 each)."""
     m, n = w["m"], w["n"]
-    return 8.0 * m * n * n
+    return 6.0 * m * n * n
+
+
+FLOP_COUNT = ("6 m n^2 per two-pass TS-SVD: Gram A^T A (m n^2, symmetric), A V~ (2 m n^2), "
+              "Gram Y^T Y (m n^2), Y W (2 m n^2); U = Q P not counted")
 
 
 # ----------------------------------------------------------------- clocks
@@ -158,15 +185,47 @@ def host_sample(w, rows):
     return A
 
 
+# Above this n the oracle's n x n Jacobi solves (serial, plain loops) take
+# minutes each, so its bounded sample is the tall products alone.
+ORACLE_FULL_MAX_N = 256
+
+
+def oracle_sample_text(w, rows):
+    n = w["n"]
+    if n <= ORACLE_FULL_MAX_N:
+        return ("%d x %d rows of the same recipe: one full two-pass TS-SVD (6 m n^2 nominal "
+                "flops)" % (rows, n))
+    return ("%d x %d rows of the same recipe: the oracle's tall products of one pass (Gram "
+            "A^T A and A V~, 3 m n^2 flops); its n x n Jacobi solves at n = %d take minutes "
+            "each and are not in the sample" % (rows, n, n))
+
+
 def time_oracle(w, rows, reps=1):
+    """GFLOP/s of the FP64 CPU oracle on a bounded sample of workload w:
+    the whole two-pass TS-SVD of `rows` rows when n is small, else the
+    tall products of one pass (the oracle's Gram and A V~ on `rows` rows)."""
+    import numpy as np
     import oracle
     A = host_sample(w, rows)
+    n = w["n"]
+    full = n <= ORACLE_FULL_MAX_N
+    V = None if full else np.linalg.qr(np.random.default_rng(7).standard_normal((n, n)))[0]
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+        if full:
+            oracle.ts_svd(A, passes=2, scale=True, drop_tol=0.0)
+        else:
+            oracle.gram(A)
+            oracle.matmul(A, V)
     dt = (time.perf_counter() - t0) / reps
-    flops = 8.0 * rows * w["n"] ** 2
+    flops = (6.0 if full else 3.0) * rows * n ** 2
     return flops / dt / 1e9, dt, oracle.num_threads()
+
+
+def oracle_rows(w, rows):
+    """Rows of the oracle's bounded sample (10-30 s of host work at the
+    default 200,000 rows on 16 cores)."""
+    return min(rows, w["m"])
 
 
 def run_reference(args):
@@ -174,7 +233,9 @@ def run_reference(args):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    rows = min(args.cpu_rows, w["m"])
+    rows = oracle_rows(w, args.cpu_rows)
+    if w["n"] > ORACLE_FULL_MAX_N:
+        rows = max(2000, rows // 4)  # one sample per step: keep the whole run to minutes
     for _ in range(max(0, min(args.warmup, 1))):
         time_oracle(w, min(rows, 20000))
     vals, dts = [], []
@@ -184,14 +245,13 @@ def run_reference(args):
         vals.append(v)
         dts.append(dt)
     value = statistics.mean(vals)
-    sample = "%d x %d rows of the same recipe per step (of %d x %d)" % (rows, w["n"], w["m"],
-                                                                      w["n"])
+    sample = "per step: %s (workload %d x %d)" % (oracle_sample_text(w, rows), w["m"], w["n"])
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * statistics.mean(dts), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "m": w["m"], "n": w["n"], "passes": 2,
-                      "scale": 1, "mode": "fp64-cpu-oracle"},
+                      "scale": 1, "mode": "fp64-cpu-oracle", "flops": FLOP_COUNT},
            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -240,6 +300,7 @@ def run_ours(args):
     w = WORKLOADS[args.workload]
     m, n = w["m"], w["n"]
     L = pkg.lib()
+    fp64_peak = set_fp64_peak(L)
 
     # input A = U diag(sigma) V^T, built on the device (torch QR of seeded
     # Gaussians); each rank its own replica seed
@@ -384,13 +445,23 @@ def run_ours(args):
     # roofline of the dominant kernel (largest total event time in the
     # timed region): algorithmic flops or bytes per launch / mean duration
     roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+    esize = A.element_size()
+    del A, U, S, V, ws
+    torch.cuda.empty_cache()
+
+    # the other tall-skinny workloads of the same recipe, device-resident
+    also = {}
+    for name in [x for x in args.also.split(",") if x and x != args.workload]:
+        if WORKLOADS.get(name, {}).get("kind") != "ts":
+            continue
+        also[name] = measure_ts(torch, pkg, L, WORKLOADS[name], args, dev, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rows = min(args.cpu_rows, m)
+        rows = oracle_rows(w, args.cpu_rows)
         v, dt, cores = time_oracle(w, rows)
         cpu = {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": "%d x %d rows of the same recipe, one two-pass TS-SVD, %.1f s"
-                         % (rows, n, dt)}
+               "sample": "%s, %.1f s" % (oracle_sample_text(w, rows), dt)}
 
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -400,11 +471,14 @@ def run_ours(args):
            "config": {"workload": args.workload, "m": m, "n": n, "passes": 2, "scale": 1,
                       "mode": args.mode, "drop_tol": 0.0,
                       "sigma": "geometric 1..%g" % w["lo"],
-                      "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 8 / 1e9),
+                      "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * esize / 1e9),
+                      "flops": FLOP_COUNT,
                       "parallelism": "replicas" if world > 1 else "single"},
            "roofline": roof, "roofline_kernels": roof_all, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches),
+           "fp64_fma_peak_tflops": fp64_peak,
            "fp64_path": fp64_path,
+           "also": also,
            "clocks": clk,
            "accuracy": {"sigma_err_normwise": sig_err, "orth_U": orth_u, "orth_V": orth_v,
                         "residual_rel": resid, "rank": info["rank"],
@@ -414,6 +488,47 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_ts(torch, pkg, L, w, args, dev, rank):
+    """Device-resident timing of one more tall-skinny workload (same mode,
+    steps and warm-up as the headline): GFLOP/s on the 6 m n^2 count, the
+    accuracy against the known spectrum and the per-kernel event times."""
+    import workloads
+    m, n = w["m"], w["n"]
+    sigma = workloads.sigma_geometric(n, w["lo"])
+    A, U0, s0, V0 = workloads.known_spectrum_torch(m, n, sigma, replica_seed(w["seed"], rank), dev)
+    del U0, V0
+    U = torch.empty((m, n), dtype=torch.float64, device=dev)
+    S = torch.empty((n,), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ws = torch.empty((pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode=args.mode),),
+                     dtype=torch.uint8, device=dev)
+    kw = dict(passes=2, scale=True, drop_tol=0.0, mode=args.mode, workspace=ws, out=(U, S, V))
+    for _ in range(args.warmup):
+        info = pkg.ts_svd(A, **kw)[3]
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
+    ms = _timed(torch, lambda: pkg.ts_svd(A, **kw), args.steps)
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
+    info = pkg.ts_svd(A, **kw)[3]
+    ms = max_over_ranks(ms, dev)
+    with torch.no_grad():
+        s_t = torch.as_tensor(s0, device=dev)
+        eye = torch.eye(n, dtype=U.dtype, device=dev)
+        acc = {"sigma_err_normwise": float((S - s_t).abs().max() / s_t[0]),
+               "orth_U": float((U.T @ U - eye).abs().max()),
+               "orth_V": float((V.T @ V - eye).abs().max()),
+               "rank": info["rank"], "sweeps": info["sweeps"]}
+    roof, _ = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+    out = {"value": nominal_flops(w) / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+           "steps": args.steps, "m": m, "n": n, "mode": args.mode, "accuracy": acc,
+           "roofline": roof,
+           "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()}}
+    del A, U, S, V, ws
+    torch.cuda.empty_cache()
+    return out
 
 
 def bind_to_gpu_numa_node(dev):
@@ -525,7 +640,7 @@ def roofline_entry(name, cnt, tot_ms, model, step_ms, args):
     if bound == "alu":
         peak = FP64_PEAK_GFLOPS / 1e3
         e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s",
-                 peak_source="FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)")
+                 peak_source=FP64_PEAK_SOURCE)
     elif bound == "tensor":
         peak, src = bf16_peak(sustained=True)
         e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s", peak_source=src)
@@ -618,7 +733,7 @@ def run_batched(args):
         del U0, V0
         As.append(A)
         sig.append(torch.as_tensor(s, device=dev))
-    flops = sum(8.0 * m * n * n for m, n in shapes)
+    flops = sum(6.0 * m * n * n for m, n in shapes)
     mode = "auto" if args.mode == "fp64_tc" else args.mode
     outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode)  # tunes + captures
     for _ in range(max(0, args.warmup - 1)):
@@ -778,7 +893,7 @@ def run_tsqr(args):
                 "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
                 "share_of_step": qr_ms / ms,
-                "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)"}
+                "peak_source": FP64_PEAK_SOURCE}
     st = torch.as_tensor(s0, device=dev)
     eye = torch.eye(n, dtype=U.dtype, device=dev)
     out = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
@@ -798,9 +913,9 @@ def run_tsqr(args):
 
 def run_grad(args):
     """One step = forward TS-SVD (FP32 storage), the loss, and its backward
-    through the thin-SVD adjoint (TSSVD autograd).  Nominal flops: 8mn^2
-    forward + 8mn^2 for the adjoint's tall products (U recomputed, U^T dU,
-    [U | dU] times an n x n pair)."""
+    through the thin-SVD adjoint (TSSVD autograd).  Nominal flops 8mn^2:
+    6mn^2 for the forward TS-SVD and 2mn^2 for the adjoint (the count of
+    one m x n by n x n product; its other tall products are not counted)."""
     import numpy as np
     import torch
 
@@ -840,13 +955,13 @@ def run_grad(args):
     clk = clocks.stop()
     st = torch.as_tensor(s, device=dev)
     U = out["U"].double()
-    res = {"metric": METRIC, "value": 16.0 * m * n * n / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+    res = {"metric": METRIC, "value": 8.0 * m * n * n / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "fp32 storage; " + ("bf16 digits+fp32+f64" if mode == "fp64_tc" else "f64"),
            "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "k": k, "mode": mode,
-                      "flops": "16mn^2 (8mn^2 forward + 8mn^2 adjoint)",
+                      "flops": "8mn^2 (6mn^2 forward + 2mn^2 adjoint)",
                       "l2": "inputs larger than L2 (A is %.1f GB FP32)" % (m * n * 4 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
            "accuracy": {"sigma_err_normwise": float((out["S"].double() - st).abs().max() / st[0]),

@@ -44,6 +44,7 @@ extern "C" {
 #define TSSVD_ETIMEOUT 3 /* a bounded device-side wait expired; results undefined */
 #define TSSVD_ECUDA 4    /* a CUDA runtime call failed; results undefined */
 #define TSSVD_ENOMEM 5   /* workspace too small, or the internal one could not grow */
+#define TSSVD_ECOMM 6    /* the caller's all-reduce (tssvd_comm) reported a failure */
 
 /* Arithmetic of the tall products (the passes over the m rows). */
 typedef enum {
@@ -134,6 +135,58 @@ int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double
  * (FP64 arithmetic on the FP32 data, or BF16x3 on the tensor cores). */
 int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S,
                float *V, tssvd_opts *opts);
+
+/*
+ * Row-sharded calls (several GPUs, one process each).  The rows of A are
+ * split over the ranks; each rank holds its row block.  The exchange steps
+ * of the method are all-reductions of small arrays, made through the
+ * caller's collective:
+ *   allreduce(buf, count, dtype, op, stream, ctx)
+ * reduces `count` elements of the DEVICE array buf over all ranks in place
+ * (dtype TSSVD_DT_F64: double, op TSSVD_OP_SUM; dtype TSSVD_DT_U64:
+ * unsigned 64-bit, op TSSVD_OP_MAX), ordered on `stream` (a cudaStream_t)
+ * like the library's own kernels, and returns 0 on success.  Every rank
+ * must receive the same bits (the n x n solves are then repeated
+ * identically on every rank, with no further exchange).  A NCCL all-reduce
+ * on the stream meets this.  rank and size describe the caller's group
+ * (rank in [0, size)).
+ */
+#define TSSVD_DT_F64 0
+#define TSSVD_DT_U64 1
+#define TSSVD_OP_SUM 0
+#define TSSVD_OP_MAX 1
+typedef int (*tssvd_allreduce_fn)(void *buf, int64_t count, int dtype, int op, void *stream,
+                                  void *ctx);
+typedef struct {
+    tssvd_allreduce_fn allreduce;
+    void *ctx;
+    int rank;
+    int size;
+} tssvd_comm;
+
+/*
+ * ts_svd on a row-sharded A: Algorithm 4 (opts->passes = 2) or 3
+ * (passes = 1) where each rank holds rows of A (A_local, m_local x n,
+ * lda), in the form of the paper's Section 2 aggregation of per-partition
+ * Gram matrices: each Gram matrix is formed from the local rows and summed
+ * over the ranks (one all-reduce of n x n doubles per Gram matrix); the
+ * MaxEntry column maxima (one all-reduce of n words, maximum) and every
+ * explicit column norm (one all-reduce of n sums of squares per norm step)
+ * likewise; the eigendecompositions, the discards and the small SVD then
+ * run on every rank on identical data, and the tall products stay local.
+ *   A       [in]  m_local x n, row-major, lda >= n (device).
+ *   U       [out] the rank's m_local rows of U (m_local x n, leading
+ *                 dimension n).
+ *   S, V    [out] n and n x n, identical on every rank.
+ *   comm    [in]  the collective (a NULL allreduce means a single rank).
+ *   opts    as for ts_svd (workspace: ts_svd_workspace_size(m_local, ...)).
+ * m_local >= n on every rank.  Returns as ts_svd, or TSSVD_ECOMM when the
+ * all-reduce failed (results undefined).
+ * Errors: -1 A, -2 m_local < n, -3 n, -4 lda, -5 U, -6 S, -7 V, -8 comm
+ * (NULL, or rank / size out of range), -9 opts.
+ */
+int ts_svd_rowshard(const double *A, int64_t m_local, int64_t n, int64_t lda, double *U,
+                    double *S, double *V, const tssvd_comm *comm, tssvd_opts *opts);
 
 /* Bytes of workspace ts_svd_tsqr needs. */
 size_t ts_svd_tsqr_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
@@ -401,6 +454,15 @@ int ts_gram_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, double *
 long long tssvd_launch_count(void);
 int tssvd_profile_enable(int on);
 size_t tssvd_profile_report(char *buf, size_t len);
+
+/* tssvd_fp64_fma_rate: measures the FP64 fused multiply-add rate of the
+ * current device (the ceiling of the FP64 kernels: the Jacobi solvers, the
+ * Householder factorizations and the FP64 tall products), in TFLOP/s
+ * (2 flops per FMA), by timing a kernel of independent FMA chains with CUDA
+ * events on `stream` (a cudaStream_t; NULL = legacy default stream), best
+ * of four runs after one warm-up (about 1.5 s in all).  Writes *tflops and
+ * returns TSSVD_OK, or -1 (tflops NULL) / TSSVD_ECUDA.  Allocates nothing. */
+int tssvd_fp64_fma_rate(double *tflops, void *stream);
 
 #ifdef __cplusplus
 }

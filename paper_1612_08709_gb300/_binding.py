@@ -20,6 +20,7 @@ TSSVD_RANKDEF = 2
 TSSVD_ETIMEOUT = 3
 TSSVD_ECUDA = 4
 TSSVD_ENOMEM = 5
+TSSVD_ECOMM = 6
 
 _MODES = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp64_tc": 3, "auto": 4}
 _MODE_NAMES = {v: k for k, v in _MODES.items()}
@@ -129,6 +130,10 @@ def lib():
     L.tssvd_profile_enable.restype = ctypes.c_int
     L.tssvd_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.tssvd_profile_report.restype = ctypes.c_size_t
+    L.tssvd_fp64_fma_rate.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    L.tssvd_fp64_fma_rate.restype = ctypes.c_int
+    L.ts_svd_rowshard.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, op]
+    L.ts_svd_rowshard.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -141,7 +146,8 @@ def exported_symbols():
             "ts_gram_workspace_size", "ts_gram", "ts_matmul_workspace_size", "ts_matmul",
             "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
             "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward",
-            "ts_svd_tsqr_workspace_size", "ts_svd_tsqr", "lowrank_svd_tsqr"]
+            "ts_svd_tsqr_workspace_size", "ts_svd_tsqr", "lowrank_svd_tsqr",
+            "tssvd_fp64_fma_rate", "ts_svd_rowshard"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -170,7 +176,7 @@ def _ptr(t):
 def _check(rc, name):
     if rc < 0:
         raise TsSvdError("%s: invalid argument %d" % (name, -rc))
-    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM):
+    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM, TSSVD_ECOMM):
         raise TsSvdError("%s: %s" % (name, lib().tssvd_status_string(rc).decode()))
     return rc
 
@@ -339,7 +345,7 @@ def ts_svd_batched(As, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64
         rc = lib().ts_svd_batched(descs, len(As), eb, ctypes.byref(o))
     if rc < 0:
         raise TsSvdError("ts_svd_batched: invalid argument %d" % (-rc))
-    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM):
+    if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM, TSSVD_ECOMM):
         raise TsSvdError("ts_svd_batched: %s" % lib().tssvd_status_string(rc).decode())
     infos = [{"status": descs[i].status, "rank": int(descs[i].out_rank),
               "mode": _MODE_NAMES.get(descs[i].mode, descs[i].mode)} for i in range(len(As))]

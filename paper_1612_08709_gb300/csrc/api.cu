@@ -81,6 +81,36 @@ InternalWs g_ws[64];
         if (e_ != cudaSuccess) return e_;      \
     } while (0)
 
+// ------------------------------------------------------ row-sharded calls
+
+// Set when the caller's all-reduce fails inside a row-sharded call (the
+// entry point turns it into TSSVD_ECOMM).
+thread_local int t_comm_failed = 0;
+
+// The caller's all-reduce of a device array (a no-op without a collective).
+cudaError_t comm_allreduce(const tssvd_comm *c, void *buf, i64 count, int dtype, int op,
+                           cudaStream_t s)
+{
+    if (!c || !c->allreduce) return cudaSuccess;
+    if (c->allreduce(buf, (int64_t)count, dtype, op, (void *)s, c->ctx) != 0) {
+        t_comm_failed = 1;
+        return cudaErrorUnknown;
+    }
+    return cudaSuccess;
+}
+
+// Explicit column norms from per-block sums of squares NP (g x N): local
+// sums, summed over the ranks, then the square roots.  Without a collective
+// it is launch_norms_reduce (same arithmetic, one kernel).
+cudaError_t shard_norms(const tssvd_comm *c, const double *NP, int g, i64 N, double *out,
+                        cudaStream_t s)
+{
+    if (!c || !c->allreduce) return launch_norms_reduce(NP, g, N, out, s);
+    CK(launch_sumsq_reduce(NP, g, N, out, s));
+    CK(comm_allreduce(c, out, N, TSSVD_DT_F64, TSSVD_OP_SUM, s));
+    return launch_sqrt_inplace(out, N, s);
+}
+
 // ------------------------------------------------------------ TS-SVD core
 
 // Enqueues Algorithm 3 (passes == 1) or Algorithm 4 (passes == 2) on A
@@ -100,9 +130,13 @@ inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSS
 // columns, sorted by norm and un-pivoted, are the eigenvectors: B = P R^T R
 // P^T and R^T = (X Sigma^-1) Sigma K^T give B = P (X Sigma^-1) Sigma^2
 // (X Sigma^-1)^T P^T.  On a graded B this converges in a third of the
-// sweeps of the Gram-form solver.  Larger n: Gram-form Jacobi with the
-// normwise floor.  Scratch: Xw, Jw, B2, Xn (n x n), norms, lam (n),
-// perm, piv (n ints).
+// sweeps of the Gram-form solver.  For kPcholMaxN < n <= kPcholGridMaxN
+// the factorization runs over the whole grid with logical pivoting
+// (launch_pchol_grid; nothing to un-pivot), and the rotations are not
+// accumulated (only the orthogonalised columns are used): 13 sweeps
+// instead of 37 on 1,000,000 x 1,000 with sigma 1 .. 1e-8.  Larger n:
+// Gram-form Jacobi with the normwise floor.  Scratch: Xw, Jw, B2, Xn
+// (n x n), norms, lam (n), perm, piv (n ints).
 static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *Jw, double *Xn,
                              double *lam, double *norms, double *Vt, int max_sweeps, int *ctr,
                              double *prm, int *perm, int *piv, DevStatus *st, cudaStream_t s)
@@ -112,6 +146,13 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
         CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
         CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n, s));
         return launch_row_scatter(Xn, piv, (int)n, Vt, s);
+    }
+    if (n <= kPcholGridMaxN) {
+        CK(launch_pchol_grid(B, (int)n, Xw, n, (unsigned long long *)prm, st, s));
+        CK(launch_jacobi(Xw, n, nullptr, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
+                         0x1p-51));
+        return launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,
+                                      lam, Vt, n, s);
     }
     return launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s, true);
@@ -135,7 +176,7 @@ static cudaError_t final_svd(double *R, i64 n, const double *d, double *Xw, doub
 template <typename T, typename TO>
 cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                     int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                    cudaStream_t s, int mode = TSSVD_FP64)
+                    cudaStream_t s, int mode = TSSVD_FP64, const tssvd_comm *comm = nullptr)
 {
     const int terms = (passes == 2) ? mode_terms(mode) : 0;
     const bool sizing = ws.sizing();
@@ -173,12 +214,13 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         // B = A^T A.
         CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, B, n, s));
+        CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
         // B = V D V^T (Gram-form Jacobi; B is rotated in place).
         CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s));
         // U~ = A V, Sigma = explicit column norms of U~ (Remark "normalizing").
         CK(launch_nn<T, TO>(A, lda, Vt, n, m, n, n, U, ldu, NP, s));
-        CK(launch_norms_reduce(NP, gy, n, sig, s));
+        CK(shard_norms(comm, NP, gy, n, sig, s));
         // Discard, U = U~ Sigma^{-1}, sign convention.
         CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
         CK(launch_scale2(Vt, n, n, n, nullptr, nullptr, Vo, n, s));
@@ -199,6 +241,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         // MaxEntry column scaling D (powers of two, so exact).
         CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
         CK(launch_colmax<T>(A, m, n, lda, bits, s));
+        CK(comm_allreduce(comm, bits, n, TSSVD_DT_U64, TSSVD_OP_MAX, s));
         CK(launch_pow2_scale(bits, n, d, dinv, s));
         rs1 = dinv;
     }
@@ -212,6 +255,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
     }
+    CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     // B = V~ D~ V~^T (B consumed).  The BF16-split first pass leaves errors
     // in B far above its FP64 rounding, the floor the Cholesky form assumes:
     // it keeps the Gram-form solver.
@@ -232,25 +276,27 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         // FP64 Gram matrix, which the second pass forms anyway
         CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, G2, n, s));
+        CK(comm_allreduce(comm, G2, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
         CK(launch_diag_sqrt(G2, n, n, sig, s));
         CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
         CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
     } else {
         CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
-        CK(launch_norms_reduce(NP, gy, n, sig, s));
+        CK(shard_norms(comm, NP, gy, n, sig, s));
         // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
         // products instead of a separate pass over Y.
         CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
         // Z = Y^T Y = Sigma~^-1 (Y~^T Y~) Sigma~^-1.
         CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
         CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
+        CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     }
     // Z = W D W^T.
     CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
     // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
     CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
-    CK(launch_norms_reduce(NP, gy, n, Tn, s));
+    CK(shard_norms(comm, NP, gy, n, Tn, s));
     CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
     CK(launch_keepval(Tn, tinv, n, Tk, s));
     // R = T W^T Sigma~ V~^T D.
@@ -279,7 +325,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
 template <typename T, typename TO>
 cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                        int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                       cudaStream_t s)
+                       cudaStream_t s, const tssvd_comm *comm = nullptr)
 {
     const bool sizing = ws.sizing();
     const i64 nn = n * n;
@@ -320,6 +366,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     // MaxEntry of every column: the Gram's digit scales (and D when scaling)
     CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
     CK(launch_colmax<T>(A, m, n, lda, bits, s));
+    CK(comm_allreduce(comm, bits, n, TSSVD_DT_U64, TSSVD_OP_MAX, s));
     CK(launch_oz_exp_from_bits(bits, (int)n, exA, s));
     const bool sc = (passes == 2) && scale;
     const double *rs1 = nullptr;
@@ -339,6 +386,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
     CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
     CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
+    CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm 3)
     if (passes == 2)
         CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s));
@@ -360,7 +408,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     if (passes == 1) {
         // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
         CK(launch_colsumsq(Yt, n, m, n, NP, s));
-        CK(launch_norms_reduce(NP, gcs, n, sig, s));
+        CK(shard_norms(comm, NP, gcs, n, sig, s));
         CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
         CK(launch_scale2(Vt, n, n, n, nullptr, nullptr, Vo, n, s));
         CK(launch_signs(Vo, n, n, n, sinv, sgn, s));
@@ -383,6 +431,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
     CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, big, P, st, s));
     CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
+    CK(comm_allreduce(comm, G2, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     CK(launch_diag_sqrt(G2, n, n, sig, s));
     CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
     // Y~'s row image for Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W) and for
@@ -402,7 +451,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     // epilogue their FP64 FMAs cost more than the pass they save)
     CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Qb, ldq, st, s));
     CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
-    CK(launch_norms_reduce(NP, gcs, n, Tn, s));
+    CK(shard_norms(comm, NP, gcs, n, Tn, s));
     CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
     CK(launch_keepval(Tn, tinv, n, Tk, s));
     // R = T W^T Sigma~ V~^T D; R = P Sigma V^T
@@ -428,13 +477,13 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
 template <typename T, typename TO>
 cudaError_t ts_any(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                    int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                   cudaStream_t s, int mode)
+                   cudaStream_t s, int mode, const tssvd_comm *comm = nullptr)
 {
     if (mode == TSSVD_FP64_TC)
         return ts_core_oz<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps,
-                                 ws, st, s);
+                                 ws, st, s, comm);
     return ts_core<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps, ws, st,
-                          s, mode);
+                          s, mode, comm);
 }
 
 // Status words are summarised into the ABI's status code.
@@ -773,19 +822,24 @@ int check_opts(const tssvd_opts *o)
 // ts_svd (mu == nullptr) and ts_pca (mu != nullptr: column means into mu,
 // then the TS-SVD of the centred copy A - 1 mu^T held in the workspace).
 // `pca` shifts the argument numbers of the error codes past mu.
+// comm (ts_svd_rowshard): A holds this rank's rows; the exchange steps go
+// through the caller's all-reduce (its argument number is 8, opts 9).
 template <typename T>
 int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V,
-                 tssvd_opts *opts, T *mu = nullptr, bool pca = false)
+                 tssvd_opts *opts, T *mu = nullptr, bool pca = false,
+                 const tssvd_comm *comm = nullptr, bool sharded = false)
 {
-    const int sh = pca ? 1 : 0;
+    const int sh = (pca || sharded) ? 1 : 0;
     if (!A) return -1;
     if (m < 1 || m < n) return -2;
     if (n < 1 || n > 16384) return -3;
     if (lda < n) return -4;
     if (pca && !mu) return -5;
-    if (!U) return -5 - sh;
-    if (!S) return -6 - sh;
-    if (!V) return -7 - sh;
+    if (!U) return -5 - (pca ? 1 : 0);
+    if (!S) return -6 - (pca ? 1 : 0);
+    if (!V) return -7 - (pca ? 1 : 0);
+    if (sharded && (!comm || comm->size < 1 || comm->rank < 0 || comm->rank >= comm->size))
+        return -8;
     if (!check_opts(opts)) return -8 - sh;
     if ((opts->mode == TSSVD_BF16X3 || opts->mode == TSSVD_BF16X6) && n > 256) {
         fprintf(stderr, "tssvd: the mixed-precision modes take n <= 256 (n = %lld)\n",
@@ -821,10 +875,16 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
         X = C;
         ldx = n;
     }
+    t_comm_failed = 0;
     if (e == cudaSuccess)
         e = ts_any<T, T>(X, m, n, ldx, U, n, S, V, n, opts->passes, opts->scale, opts->drop_tol,
-                         opts->max_sweeps, ws, st, s, opts->mode);
+                         opts->max_sweeps, ws, st, s, opts->mode, comm);
     if (e != cudaSuccess) {
+        if (t_comm_failed) {
+            fprintf(stderr, "tssvd: the all-reduce of a row-sharded call failed\n");
+            cudaGetLastError();
+            return TSSVD_ECOMM;
+        }
         fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? TSSVD_ENOMEM : TSSVD_ECUDA;
@@ -1621,6 +1681,7 @@ const char *tssvd_status_string(int st)
     case TSSVD_ETIMEOUT: return "device-side wait timed out";
     case TSSVD_ECUDA: return "CUDA runtime error";
     case TSSVD_ENOMEM: return "workspace too small or allocation failed";
+    case TSSVD_ECOMM: return "the all-reduce of a row-sharded call failed";
     default: return st < 0 ? "invalid argument" : "unknown status";
     }
 }
@@ -1651,6 +1712,12 @@ int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, floa
                tssvd_opts *opts)
 {
     return ts_svd_entry<float>(A, m, n, lda, U, S, V, opts);
+}
+
+int ts_svd_rowshard(const double *A, int64_t m_local, int64_t n, int64_t lda, double *U,
+                    double *S, double *V, const tssvd_comm *comm, tssvd_opts *opts)
+{
+    return ts_svd_entry<double>(A, m_local, n, lda, U, S, V, opts, nullptr, false, comm, true);
 }
 
 size_t ts_pca_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_opts *opts)

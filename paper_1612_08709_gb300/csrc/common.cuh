@@ -111,6 +111,10 @@ cudaError_t launch_center(const T *A, i64 lda, i64 m, i64 n, const T *mu, T *C, 
 
 // out[j] = sqrt(sum_g NP[g][j]) in fixed order.
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
+// The same sums without the square root (row-sharded calls: the squares
+// are summed over the ranks first), and x[j] = sqrt(x[j]).
+cudaError_t launch_sumsq_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s);
+cudaError_t launch_sqrt_inplace(double *x, i64 N, cudaStream_t s);
 
 // ------------------------------------------------- tensor-core products
 // BF16-split products on tcgen05 (gemm_tc.cu).  S = number of bf16 terms
@@ -192,6 +196,7 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 // prm to jacobi_prm_doubles(nc) doubles of scratch.
 inline size_t jacobi_prm_doubles(i64 nc) { return 8 * (size_t)((nc + 1) / 2) + 8; }
 // tol: the rotation threshold |x_p . x_q| > tol |x_p| |x_q| (0: nr 2^-53).
+// J == null: the rotations are not accumulated (only X_out is wanted).
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
                           int max_sweeps, int *ctr, double *prm, DevStatus *st, int which,
                           cudaStream_t s, double tol = 0.0);
@@ -204,6 +209,14 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
 // One CTA; used for n <= kPcholMaxN.
 constexpr int kPcholMaxN = 256;
 cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStream_t s);
+// The same factorization over the whole grid (cooperative launch, one
+// barrier per pivot step) with logical pivoting: W stays in the original
+// order and X's column k is row k of R~ = R P^T (so W = R~^T R~, and X's
+// rows are in the original order: nothing to un-pivot).  key: 3 unsigned
+// 64-bit words of scratch.  n <= kPcholGridMaxN.
+constexpr int kPcholGridMaxN = 2048;
+cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned long long *key,
+                              DevStatus *st, cudaStream_t s);
 // V[piv[i]][j] = Xn[i][j], n x n row-major.
 cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *V, cudaStream_t s);
 

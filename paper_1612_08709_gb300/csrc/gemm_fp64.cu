@@ -304,13 +304,19 @@ __global__ void __launch_bounds__(256) colsumsq_kernel(const double *__restrict_
 }
 
 __global__ void norms_reduce_kernel(const double *__restrict__ NP, int g, i64 N,
-                                    double *__restrict__ out)
+                                    double *__restrict__ out, int take_sqrt)
 {
     i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     double s = 0.0;
     for (int b = 0; b < g; b++) s += NP[(i64)b * N + j];
-    out[j] = sqrt(s);
+    out[j] = take_sqrt ? sqrt(s) : s;
+}
+
+__global__ void sqrt_inplace_kernel(double *x, i64 N)
+{
+    i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) x[j] = sqrt(x[j]);
 }
 
 // Row-streaming column maxima (n <= 32 * 16): every warp reads whole rows,
@@ -546,7 +552,21 @@ cudaError_t launch_colsumsq(const double *X, i64 ldx, i64 m, i64 n, double *NP, 
 cudaError_t launch_norms_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s)
 {
     ProfScope ps_("norms_reduce", s);
-    norms_reduce_kernel<<<ceil_div_i(N, 256), 256, 0, s>>>(NP, g, N, out);
+    norms_reduce_kernel<<<ceil_div_i(N, 256), 256, 0, s>>>(NP, g, N, out, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq_reduce(const double *NP, int g, i64 N, double *out, cudaStream_t s)
+{
+    ProfScope ps_("norms_reduce", s);
+    norms_reduce_kernel<<<ceil_div_i(N, 256), 256, 0, s>>>(NP, g, N, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sqrt_inplace(double *x, i64 N, cudaStream_t s)
+{
+    ProfScope ps_("sqrt", s);
+    sqrt_inplace_kernel<<<ceil_div_i(N, 256), 256, 0, s>>>(x, N);
     return cudaGetLastError();
 }
 

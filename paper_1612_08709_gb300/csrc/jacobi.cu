@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
     const int rounds = p.npad - 1;
     const double tol = p.tol;
     const float log2tol = log2f((float)p.tol);
+    const bool hasJ = p.J != nullptr;  // J == null: no accumulation (X_out alone is wanted)
     int local_rot = 0;
     int done = -1;
     unsigned long long *bar_count = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
@@ -379,7 +380,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                     continue;
                 }
                 double *xp = p.X + (i64)P * p.ldx, *xq = p.X + (i64)Q * p.ldx;
-                double *jp = p.J + (i64)P * p.ldj, *jq = p.J + (i64)Q * p.ldj;
+                double *jp = hasJ ? p.J + (i64)P * p.ldj : nullptr;
+                double *jq = hasJ ? p.J + (i64)Q * p.ldj : nullptr;
                 double u[C], v[C], ju[C], jv[C];
                 double al = 0.0, be = 0.0, ga = 0.0;
                 if (CH > 0) {
@@ -388,8 +390,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         const int i = threadIdx.x + j * NT;
                         u[j] = i < p.nr ? __ldcg(xp + i) : 0.0;
                         v[j] = i < p.nr ? __ldcg(xq + i) : 0.0;
-                        ju[j] = (!JS && i < p.nc) ? __ldcg(jp + i) : 0.0;
-                        jv[j] = (!JS && i < p.nc) ? __ldcg(jq + i) : 0.0;
+                        ju[j] = (!JS && hasJ && i < p.nc) ? __ldcg(jp + i) : 0.0;
+                        jv[j] = (!JS && hasJ && i < p.nc) ? __ldcg(jq + i) : 0.0;
                     }
                     if (want_prev && !pv_loaded) {
                         pv = ld4cg(prev_g + threadIdx.x);
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                             __stcg(xp + i, c * u[j] - sn * v[j]);
                             __stcg(xq + i, sn * u[j] + c * v[j]);
                         }
-                        if (!JS && i < p.nc) {
+                        if (!JS && hasJ && i < p.nc) {
                             __stcg(jp + i, c * ju[j] - sn * jv[j]);
                             __stcg(jq + i, sn * ju[j] + c * jv[j]);
                         }
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         __stcg(xp + i, c * x - sn * y);
                         __stcg(xq + i, sn * x + c * y);
                     }
-                    if (!JS)
+                    if (!JS && hasJ)
                         for (int i = threadIdx.x; i < p.nc; i += NT) {
                             const double x = __ldcg(jp + i), y = __ldcg(jq + i);
                             __stcg(jp + i, c * x - sn * y);
@@ -1306,7 +1308,7 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
         ldjo = ldxo;
         ldxo = tl;
     }
-    const i64 tj = (i64)nc * nc;
+    const i64 tj = J ? (i64)nc * nc : 0;
     const i64 tx = Xout ? (i64)nr * nc : 0;
     for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < tj + tx;
          e += (i64)gridDim.x * blockDim.x) {
@@ -1324,6 +1326,7 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
             if (src < 0 || src >= nc) src = (int)r;
             const double s = norms[src];
             Xout[i * ldxo + r] = (s > 0.0) ? X[(i64)src * ldx + i] / s : 0.0;
+            if (i == 0 && lam && !J) lam[r] = s;
         }
     }
 }
@@ -1474,6 +1477,171 @@ __global__ void __launch_bounds__(kPcholThreads, 1)
     for (int i = tid; i < n; i += kPcholThreads) piv[i] = pm[i];
 }
 
+// Pivoted Cholesky over the whole grid, for n above one CTA's reach:
+// W = R~^T R~ with R~ = R P^T, R the upper-triangular factor of the
+// diagonally pivoted P^T W P (pivot: the largest remaining diagonal entry,
+// lowest index on ties), stopped with the floor of pchol_kernel: once
+// every remaining diagonal entry is <= delta = 2^-52 max_i W_ii, the
+// remaining rows of R~ are sqrt(delta) times unit vectors on the remaining
+// indices in increasing order (W = 0: R~ = I).
+// The pivoting is logical: W stays in the original order, and row k of
+// R~ (the k-th pivot's row, in original column order) is written as
+// column k of X (X[k ldx + c]), so X's rows are in the original order and
+// the eigenvectors found from X need no un-pivoting.
+// Rows of W belong to CTAs round-robin (row i to CTA i mod gridDim.x).
+// Step k: every CTA reads the pivot j (published by an atomic maximum of a
+// packed key) and row j of W, forms row k of R~ in shared memory, and
+// updates its own remaining rows by the rank-one term over the remaining
+// columns (a sorted list, so the loads stay nearly coalesced); then it
+// publishes the largest remaining diagonal entry of its rows for step
+// k + 1 and the grid barrier ends the step.  The key packs the diagonal
+// value's bit pattern (non-negative, so ordered as an unsigned integer)
+// above 11 bits of (2047 - index): ties within the dropped low bits of the
+// value go to the lower index; the pivot value itself is re-read exactly.
+__device__ __forceinline__ unsigned long long pivot_key(double v, int i)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v > 0.0 ? v : 0.0);
+    return (b & ~0x7ffull) | (unsigned long long)(2047 - i);
+}
+
+struct PcholArgs {
+    double *W;  // n x n row-major, consumed
+    double *X;  // column-major: column k = row k of R~
+    i64 ldx;
+    unsigned long long *key;  // [3] pivot keys, zeroed before the launch
+    DevStatus *st;
+    int n;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) pchol_grid_kernel(PcholArgs p)
+{
+    extern __shared__ double pg_s[];
+    const int n = p.n;
+    double *r = pg_s;                              // [n] row k of R~
+    int *act = reinterpret_cast<int *>(r + n);     // [n] remaining columns, increasing
+    unsigned char *done = reinterpret_cast<unsigned char *>(act + n);  // [n]
+    __shared__ unsigned long long s_key[NT / 32];
+    __shared__ double s_piv, s_inv, s_delta;
+    __shared__ int s_j, s_stop, s_nact;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+    const int G = gridDim.x, b = blockIdx.x;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(&p.st->bar[0]);
+    int epoch = 0;
+    for (int c = tid; c < n; c += NT) {
+        done[c] = 0;
+        act[c] = c;
+    }
+    if (tid == 0) s_nact = n;
+    __syncthreads();
+    // publishes this CTA's largest remaining diagonal entry into key slot q
+    auto publish = [&](int q) {
+        unsigned long long k = 0;
+        for (int i = b + tid * G; i < n; i += NT * G)
+            if (!done[i]) {
+                const unsigned long long kk = pivot_key(__ldcg(p.W + (i64)i * n + i), i);
+                k = kk > k ? kk : k;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, k, o);
+            k = t > k ? t : k;
+        }
+        if (lane == 0) s_key[warp] = k;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < NW; w++) t = s_key[w] > t ? s_key[w] : t;
+            if (t != 0) atomicMax(p.key + q, t);
+        }
+    };
+    publish(0);
+    if (!grid_barrier(bar, epoch, &p.st->err)) return;
+    int k = 0;
+    for (; k < n; k++) {
+        if (tid == 0) {
+            const unsigned long long kk = __ldcg(p.key + (k % 3));
+            const int j = 2047 - (int)(kk & 0x7ffull);
+            const double dj = kk ? __ldcg(p.W + (i64)j * n + j) : 0.0;
+            if (k == 0) s_delta = 0x1p-52 * dj;
+            const double delta = s_delta;
+            const int stop = (kk == 0 || !(delta > 0.0 && dj > delta)) ? 1 : 0;
+            s_stop = stop;
+            s_j = j;
+            // (one thread: FP64 square root and divide are long sequences)
+            s_piv = stop ? 0.0 : sqrt(dj);
+            s_inv = stop ? 0.0 : 1.0 / s_piv;
+            if (b == 0) atomicExch(p.key + (k + 2) % 3, 0ull);  // step k + 2's slot, read in k - 1
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int j = s_j, nact = s_nact;
+        const double piv = s_piv, inv = s_inv;
+        // row k of R~ over the remaining columns (others stay 0 in r)
+        const double *wj = p.W + (i64)j * n;
+        for (int t = tid; t < nact; t += NT) {
+            const int c = act[t];
+            r[c] = (c == j) ? piv : __ldcg(wj + c) * inv;
+        }
+        __syncthreads();
+        if (b == 0)
+            for (int c = tid; c < n; c += NT) __stcg(p.X + (i64)k * p.ldx + c, done[c] ? 0.0 : r[c]);
+        // rank-one update of this CTA's remaining rows (i != j) over the
+        // remaining columns, a warp per row, four loads in flight per lane
+        for (int i = b + warp * G; i < n; i += NW * G) {
+            if (done[i] || i == j) continue;
+            double *wi = p.W + (i64)i * n;
+            const double ri = r[i];
+            int t = lane;
+            for (; t + 96 < nact; t += 128) {
+                const int c0 = act[t], c1 = act[t + 32], c2 = act[t + 64], c3 = act[t + 96];
+                const double w0 = __ldcg(wi + c0), w1 = __ldcg(wi + c1);
+                const double w2 = __ldcg(wi + c2), w3 = __ldcg(wi + c3);
+                __stcg(wi + c0, fma(-ri, r[c0], w0));
+                __stcg(wi + c1, fma(-ri, r[c1], w1));
+                __stcg(wi + c2, fma(-ri, r[c2], w2));
+                __stcg(wi + c3, fma(-ri, r[c3], w3));
+            }
+            for (; t < nact; t += 32) {
+                const int c0 = act[t];
+                __stcg(wi + c0, fma(-ri, r[c0], __ldcg(wi + c0)));
+            }
+        }
+        __syncthreads();
+        // j leaves the remaining columns (the list stays increasing)
+        {
+            int pos = -1;
+            for (int t = tid; t < nact; t += NT)
+                if (act[t] == j) pos = t;
+            // at most one thread found it; share through s_j's neighbour
+            __shared__ int s_pos;
+            if (pos >= 0) s_pos = pos;
+            __syncthreads();
+            const int ps = s_pos;
+            int v[(kPcholGridMaxN + NT - 1) / NT];
+            int cnt = 0;
+            for (int t = ps + 1 + tid; t < nact; t += NT) v[cnt++] = act[t];
+            __syncthreads();
+            cnt = 0;
+            for (int t = ps + 1 + tid; t < nact; t += NT) act[t - 1] = v[cnt++];
+            if (tid == 0) {
+                done[j] = 1;
+                s_nact = nact - 1;
+            }
+            __syncthreads();
+        }
+        publish((k + 1) % 3);
+        if (!grid_barrier(bar, epoch, &p.st->err)) return;
+    }
+    // rows k .. n-1 of R~: the floor's square root on the remaining indices
+    // in increasing order (act), spread over the CTAs
+    const double tail = s_delta > 0.0 ? sqrt(s_delta) : 1.0;
+    for (int kk = k + b; kk < n; kk += G) {
+        const int c0 = act[kk - k];
+        for (int c = tid; c < n; c += NT) __stcg(p.X + (i64)kk * p.ldx + c, c == c0 ? tail : 0.0);
+    }
+}
+
 // V[piv[i]][j] = Xn[i][j] (n x n row-major): the eigenvectors of the
 // pivoted matrix back in the original order.
 __global__ void row_scatter_kernel(const double *__restrict__ Xn, const int *__restrict__ piv,
@@ -1502,6 +1670,42 @@ cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStr
     return cudaGetLastError();
 }
 
+cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned long long *key,
+                              DevStatus *st, cudaStream_t s)
+{
+    if (n < 1 || n > kPcholGridMaxN) return cudaErrorInvalidValue;
+    constexpr int NT = 256;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(key, 0, 3 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&st->bar[0], 0, sizeof(int) * 4, s)) != cudaSuccess) return e;
+    const size_t smem = sizeof(double) * (size_t)n + sizeof(int) * (size_t)n + (size_t)n;
+    const void *kern = (const void *)pchol_grid_kernel<NT>;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    // one CTA per SM: every CTA reads the pivot row each step, so more CTAs
+    // only add L2 traffic and barrier arrivals
+    int blocks = num_sms();
+    const int rows_cap = (n + 7) / 8;  // at least 8 rows (a warp each) per CTA
+    if (blocks > rows_cap) blocks = rows_cap;
+    if (blocks < 1) blocks = 1;
+    PcholArgs a;
+    a.W = W;
+    a.X = X;
+    a.ldx = ldx;
+    a.key = key;
+    a.st = st;
+    a.n = n;
+    void *args[] = {&a};
+    ProfScope ps_("pchol_grid", s);
+    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, smem, s);
+}
+
 cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *V, cudaStream_t s)
 {
     const i64 total = (i64)n * n;
@@ -1514,7 +1718,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
                           double tol)
 {
     cudaError_t e;
-    {
+    if (J) {
         i64 total = (i64)nc * nc;
         i64 blocks = (total + 255) / 256;
         if (blocks > 4096) blocks = 4096;
@@ -1553,7 +1757,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     const int b0 = npairs < num_sms() ? npairs : num_sms();
     const size_t js_bytes = sizeof(double4) * (size_t)npairs +
                             sizeof(double) * (size_t)((nc + b0 - 1) / b0) * nc;
-    const bool js = js_bytes <= kRowsSmemMax;
+    const bool js = J != nullptr && js_bytes <= kRowsSmemMax;
     const int mx = nr > nc ? nr : nc;
     const int ch = mx <= NT ? 1 : mx <= 2 * NT ? 2 : mx <= 4 * NT ? 4 : mx <= 8 * NT ? 8 : 0;
     const void *kern;
@@ -1718,7 +1922,7 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
         ProfScope ps_("colnorm", s);
         colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(X, ldx, nr, nc, norms);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (jnorm) {
+        if (jnorm && J) {
             colnorm_cm_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(J, ldj, nc, nc, jnorm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -1729,14 +1933,14 @@ cudaError_t launch_jacobi_finalize(const double *X, i64 ldx, const double *J, i6
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-        i64 total = (i64)nc * nc + (Xout ? (i64)nr * nc : 0);
+        i64 total = (J ? (i64)nc * nc : 0) + (Xout ? (i64)nr * nc : 0);
         i64 blocks = (total + 255) / 256;
         if (blocks > (i64)num_sms() * 8) blocks = (i64)num_sms() * 8;
         if (blocks < 1) blocks = 1;
         ProfScope ps_("permute", s);
         permute_out_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, J, ldj, nr, nc, norms, perm,
                                                             Jout, ldjo, lam, Xout, ldxo, orient,
-                                                            jnorm);
+                                                            J ? jnorm : nullptr);
     }
     return cudaGetLastError();
 }

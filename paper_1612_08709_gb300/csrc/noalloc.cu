@@ -22,6 +22,9 @@
 namespace {
 
 constexpr long long kScratchDoubles = 1LL << 19;  // 4 MiB
+constexpr long long kMaxN = 724;                   // largest n with n * n <= kScratchDoubles
+static_assert(kMaxN * kMaxN <= kScratchDoubles && (kMaxN + 1) * (kMaxN + 1) > kScratchDoubles,
+              "kMaxN must be the largest n whose n x n partial fits the scratch");
 constexpr int kMaxDevices = 64;
 
 // The scratch itself.  In host code this name is only a stand-in for the
@@ -67,7 +70,7 @@ extern "C" int ts_gram_noalloc(const double *A, int64_t m, int64_t n, int64_t ld
     if (!A) return -1;
     if (m < 1) return -2;
     if (n < 1) return -3;
-    if (n * n > kScratchDoubles) {
+    if (n > kMaxN) {  // (compared directly: n * n could overflow for absurd n)
         fprintf(stderr,
                 "ts_gram_noalloc: n = %lld is too large; the fixed 4 MiB scratch holds the "
                 "partial Gram matrices only for n <= 724 (use ts_gram instead)\n",

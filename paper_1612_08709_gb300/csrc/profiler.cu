@@ -74,6 +74,33 @@ ProfScope::~ProfScope()
 
 void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+namespace {
+
+// FP64 fused multiply-add throughput: every thread runs eight independent
+// FMA chains (no memory traffic); the sum is stored only when it takes an
+// impossible value, so the chains are kept without a store per thread.
+__device__ double g_dfma_sink;
+
+__global__ void __launch_bounds__(256) dfma_rate_kernel(int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) x[u] = (double)(threadIdx.x + u);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) x[u] = fma(x[u], a, b);
+        }
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; u++) t += x[u];
+    if (t == -1.0) g_dfma_sink = t;
+}
+
+}  // namespace
+
 }  // namespace tssvd
 
 using namespace tssvd;
@@ -87,6 +114,43 @@ int tssvd_profile_enable(int on)
 }
 
 long long tssvd_launch_count(void) { return g_launches.load(); }
+
+int tssvd_fp64_fma_rate(double *tflops, void *stream)
+{
+    if (!tflops) return -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    // about 0.3 s per run at GB300's rate: long enough for the clocks to
+    // leave their idle state in the warm-up run
+    const int blocks = num_sms() * 8, threads = 256, iters = 10000;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    float best = 0.f;
+    int rc = TSSVD_OK;
+    for (int r = 0; r < 5 && rc == TSSVD_OK; r++) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = TSSVD_ECUDA;
+        dfma_rate_kernel<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-9);
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            rc = TSSVD_ECUDA;
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (rc == TSSVD_OK && r > 0 && (best == 0.f || ms < best)) best = ms;  // first run warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != TSSVD_OK || best <= 0.f) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    const double flops = 2.0 * 64.0 * iters * (double)blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return TSSVD_OK;
+}
 
 size_t tssvd_profile_report(char *buf, size_t len)
 {

@@ -11,10 +11,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_json_line():
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--cpu-rows", "4000"],
-                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+@pytest.mark.parametrize("workload,sample", [
+    (None, "2000 x 1000 rows of the same recipe: the oracle's tall products of one pass"),
+    ("ts_2m_x_200", "4000 x 200 rows of the same recipe: one full two-pass TS-SVD")])
+def test_reference_arm_json_line(workload, sample):
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+           "--steps", "1", "--warmup", "0", "--cpu-rows", "4000"]
+    if workload:
+        cmd += ["--workload", workload]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -25,10 +30,11 @@ def test_reference_arm_json_line():
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["value"] > 0 and d["unit"] == "GFLOP/s" and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "ts_2m_x_200"
+    assert d["config"]["workload"] == (workload or "ts_1m_x_1000")
+    assert d["config"]["flops"].startswith("6 m n^2")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
-    assert "4000 x 200" in cb["sample"]
+    assert sample in cb["sample"], cb["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
 

@@ -1,5 +1,7 @@
 """ts_gram_noalloc (the Gram step for callers that cannot let the library
-allocate device memory) against the allocating ts_gram, through the C ABI.
+allocate device memory) against the allocating ts_gram, through the C ABI,
+and against the FP64 CPU oracle's Gram matrix (an independent check: ts_gram
+runs the same kernels).
 
 Two calls in a row with different shapes, so the second call must not be
 affected by what the first left in the shared fixed scratch.  Same
@@ -41,6 +43,9 @@ def test_gram_noalloc_matches_allocating_gram_two_calls_in_a_row():
         got = B_na.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        import oracle
+        want = oracle.gram(A.cpu().numpy())
+        assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
 
     # sizes beyond the fixed scratch are rejected before any work
     A = torch.zeros((800, 725), dtype=torch.float64, device="cuda")
