@@ -21,8 +21,9 @@ The FP64 roofline peak is the FP64 FMA rate measured on the same GPU in
 the same run (tssvd_fp64_fma_rate).  `--impl reference` times the FP64 CPU
 oracle instead (bounded samples of the same workload on the host cores).
 
-Multi-GPU (torchrun): every rank runs an independent replica of the
-workload (weak scaling, no collective on the data path).
+Multi-GPU (torchrun): the row-sharded TS-SVD (ts_svd_rowshard), each rank
+holding m rows of an (N m) x n matrix with known singular values (weak
+scaling); the method's exchange steps are NCCL all-reduces.
 """
 import argparse
 import ctypes
@@ -488,6 +489,99 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_rowshard(args):
+    """N > 1 ranks (torchrun, one GPU each): the row-sharded TS-SVD
+    (ts_svd_rowshard).  Each rank holds m rows of an (N m) x n matrix with
+    known singular values (weak scaling: the rows per rank stay fixed as N
+    grows); the exchanges are all-reduces over NCCL through the library's
+    callback (n x n doubles per Gram matrix, n per norm step, n words for
+    the column maxima).  value = the N ranks' nominal flops over the
+    slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1612_08709_gb300 as pkg
+    import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl")
+    w = WORKLOADS[args.workload]
+    m, n = w["m"], w["n"]
+    L = pkg.lib()
+    fp64_peak = set_fp64_peak(L)
+    sigma = workloads.sigma_geometric(n, w["lo"])
+    A, s_t, V0 = workloads.known_spectrum_rowblock_torch(m, n, sigma, w["seed"], rank, world, dev)
+    del V0
+    U = torch.empty((m, n), dtype=torch.float64, device=dev)
+    S = torch.empty((n,), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ws = torch.empty((pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode=args.mode),),
+                     dtype=torch.uint8, device=dev)
+    comm = pkg.DistComm()
+    kw = dict(passes=2, scale=True, drop_tol=0.0, mode=args.mode, workspace=ws, out=(U, S, V))
+
+    def step():
+        return pkg.ts_svd_rowshard(A, comm, **kw)[3]
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
+    n0 = L.tssvd_launch_count()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    launches = L.tssvd_launch_count() - n0
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, dev)
+    flops = nominal_flops(w)
+    value = job_gflops(flops, world, ms_max)
+    with torch.no_grad():
+        G = U.T @ U
+        dist.all_reduce(G)
+        eye = torch.eye(n, dtype=U.dtype, device=dev)
+        acc = {"sigma_err_normwise": float((S - s_t).abs().max() / s_t[0]),
+               "orth_U": float((G - eye).abs().max()),
+               "orth_V": float((V.T @ V - eye).abs().max()), "rank": info["rank"],
+               "sweeps": info["sweeps"]}
+    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+    out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "f64", "fp64_tc": "bf16 digits+fp32+f64"}.get(args.mode, "bf16+fp32+f64"),
+           "data": "synthetic",
+           "config": {"workload": args.workload, "m_per_rank": m, "m": m * world, "n": n,
+                      "passes": 2, "scale": 1, "mode": args.mode, "drop_tol": 0.0,
+                      "sigma": "geometric 1..%g" % w["lo"], "flops": FLOP_COUNT,
+                      "l2": "inputs larger than L2 (A is %.1f GB per rank)" % (m * n * 8 / 1e9),
+                      "parallelism": "row-sharded over %d ranks (NCCL all-reduce)" % world},
+           "roofline": roof, "roofline_kernels": roof_all, "cpu_baseline": None,
+           "e2e": None, "gpu_launches": int(launches), "fp64_fma_peak_tflops": fp64_peak,
+           "clocks": clk, "accuracy": acc,
+           "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.destroy_process_group()
 
 
 def measure_ts(torch, pkg, L, w, args, dev, rank):
@@ -983,6 +1077,8 @@ def main():
         run_grad(args)
     elif WORKLOADS[args.workload]["kind"] == "tsqr":
         run_tsqr(args)
+    elif int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        run_rowshard(args)
     else:
         run_ours(args)
 

@@ -1752,27 +1752,54 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
 
     constexpr int NT = 128;
     const int npairs = a.npad / 2;
-    // J's rows in shared memory when they fit (at most one CTA per SM is
-    // assumed for the row count, an upper bound)
-    const int b0 = npairs < num_sms() ? npairs : num_sms();
-    const size_t js_bytes = sizeof(double4) * (size_t)npairs +
-                            sizeof(double) * (size_t)((nc + b0 - 1) / b0) * nc;
-    const bool js = J != nullptr && js_bytes <= kRowsSmemMax;
     const int mx = nr > nc ? nr : nc;
     const int ch = mx <= NT ? 1 : mx <= 2 * NT ? 2 : mx <= 4 * NT ? 4 : mx <= 8 * NT ? 8 : 0;
-    const void *kern;
-    switch (ch * 2 + (js ? 1 : 0)) {
-        case 2: kern = (const void *)jacobi_kernel<NT, 1, false>; break;
-        case 3: kern = (const void *)jacobi_kernel<NT, 1, true>; break;
-        case 4: kern = (const void *)jacobi_kernel<NT, 2, false>; break;
-        case 5: kern = (const void *)jacobi_kernel<NT, 2, true>; break;
-        case 8: kern = (const void *)jacobi_kernel<NT, 4, false>; break;
-        case 9: kern = (const void *)jacobi_kernel<NT, 4, true>; break;
-        case 16: kern = (const void *)jacobi_kernel<NT, 8, false>; break;
-        case 17: kern = (const void *)jacobi_kernel<NT, 8, true>; break;
-        case 1: kern = (const void *)jacobi_kernel<NT, 0, true>; break;
-        default: kern = (const void *)jacobi_kernel<NT, 0, false>; break;
+    auto pick = [&](bool js_) -> const void * {
+        switch (ch * 2 + (js_ ? 1 : 0)) {
+            case 2: return (const void *)jacobi_kernel<NT, 1, false>;
+            case 3: return (const void *)jacobi_kernel<NT, 1, true>;
+            case 4: return (const void *)jacobi_kernel<NT, 2, false>;
+            case 5: return (const void *)jacobi_kernel<NT, 2, true>;
+            case 8: return (const void *)jacobi_kernel<NT, 4, false>;
+            case 9: return (const void *)jacobi_kernel<NT, 4, true>;
+            case 16: return (const void *)jacobi_kernel<NT, 8, false>;
+            case 17: return (const void *)jacobi_kernel<NT, 8, true>;
+            case 1: return (const void *)jacobi_kernel<NT, 0, true>;
+            default: return (const void *)jacobi_kernel<NT, 0, false>;
+        }
+    };
+    // J's rows in shared memory when they fit: a CTA of a grid of g CTAs
+    // holds ceil(nc / g) rows.  First choice: one pair per CTA (every CTA
+    // one pair a round, nothing serialised), sized for that grid, if that
+    // many CTAs fit on the GPU at once; else one CTA per SM (the row count
+    // for at most one CTA per SM, an upper bound).
+    auto js_bytes_for = [&](int g) {
+        return sizeof(double4) * (size_t)npairs + sizeof(double) * (size_t)((nc + g - 1) / g) * nc;
+    };
+    bool js = false, one_pair = false;
+    size_t js_bytes = 0;
+    if (J != nullptr && js_bytes_for(npairs) <= kRowsSmemMax) {
+        const void *k1 = pick(true);
+        const size_t b1 = js_bytes_for(npairs);
+        int ps1 = 0;
+        if (b1 > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1)) !=
+                cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps1, k1, NT, b1)) != cudaSuccess)
+            return e;
+        if ((i64)ps1 * num_sms() >= npairs) {
+            js = true;
+            one_pair = true;
+            js_bytes = b1;
+        }
     }
+    if (J != nullptr && !js) {
+        const int b0 = npairs < num_sms() ? npairs : num_sms();
+        js_bytes = js_bytes_for(b0);
+        js = js_bytes <= kRowsSmemMax;
+    }
+    const void *kern = pick(js);
     const size_t smem = js ? js_bytes : 0;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -1784,6 +1811,7 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     int blocks = num_sms() * per_sm;
     if (blocks > npairs) blocks = npairs;
+    if (one_pair && blocks < npairs) return cudaErrorCooperativeLaunchTooLarge;  // (checked above)
     void *args[] = {&a};
     ProfScope ps_("jacobi_svd", s);
     return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, smem, s);
@@ -1829,9 +1857,25 @@ cudaError_t launch_jacobi_eig(double *B, double *B2, i64 ldb, double *V, i64 ldv
         a.normwise = normwise ? 1 : 0;
         constexpr int NT = 128;
         const int npairs0 = npad / 2;
-        const int b0 = npairs0 < num_sms() ? npairs0 : num_sms();
-        const size_t vs_bytes = sizeof(double4) * (size_t)npairs0 +
-                                sizeof(double) * (size_t)((n + b0 - 1) / b0) * n;
+        // V's rows in shared memory (ceil(n / g) rows for a grid of g CTAs):
+        // sized for one pair per CTA when that grid fits on the GPU at once,
+        // else for one CTA per SM
+        auto vs_bytes_for = [&](int g) {
+            return sizeof(double4) * (size_t)npairs0 + sizeof(double) * (size_t)((n + g - 1) / g) * n;
+        };
+        size_t vs_bytes = vs_bytes_for(npairs0 < num_sms() ? npairs0 : num_sms());
+        if (single && vs_bytes_for(npairs0) <= kRowsSmemMax) {
+            const void *k1 = (const void *)jacobi_eig1_kernel<NT, true>;
+            const size_t b1 = vs_bytes_for(npairs0);
+            int ps1 = 0;
+            if (b1 > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)b1)) != cudaSuccess)
+                return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps1, k1, NT, b1)) != cudaSuccess)
+                return e;
+            if ((i64)ps1 * num_sms() >= npairs0) vs_bytes = b1;
+        }
         const bool vs = single && vs_bytes <= kRowsSmemMax;
         // two rounds per barrier: one CTA per pair, each on its own SM (with
         // two CTAs per SM the doubled FP64 work of a round outweighs the

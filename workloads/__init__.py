@@ -144,6 +144,21 @@ def known_spectrum_torch(m, n, sigma, seed, device, dtype=None):
     return A, U, s, V
 
 
+def known_spectrum_rowblock_torch(m_local, n, sigma, seed, rank, size, device):
+    """Rank `rank`'s block of rows of a row-sharded known-spectrum matrix:
+    A_r = (U_r / sqrt(size)) diag(sigma) V^T with U_r (m_local x n) seeded
+    per rank and V shared.  The stacked U = [U_0; ...] / sqrt(size) has
+    orthonormal columns (U^T U = sum_r U_r^T U_r / size = I), so the whole
+    matrix has singular values sigma and right singular vectors V.
+    Returns (A_r, sigma tensor, V)."""
+    import torch
+    Ur = orthonormal_torch(m_local, n, seed + 7919 * (rank + 1), device)
+    V = orthonormal_torch(n, n, seed + 1000003, device)
+    s = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
+    A = ((Ur * (s / np.sqrt(size))) @ V.T).contiguous()
+    return A, s, V
+
+
 def paper_dct_matrix(m, n, p):
     """The paper's test matrix: DCT-II U (m x p) and V (n x p), sigma of eq.
     testS (p = n) or testSl (p = l), A = U diag(sigma) V^T (m x n)."""
