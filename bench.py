@@ -49,6 +49,9 @@ WORKLOADS = {
     # a 200,000 x 200 case of the same recipe (inputs still larger than L2)
     # for kernel profiling
     "ts_200k_x_200": dict(kind="ts", m=200_000, n=200, lo=1e-8, seed=2),
+    # 20,000 x 1,000 of the 1,000,000 x 1,000 recipe: the same n x n solves
+    # on a 160 MB input, for profiling the Jacobi kernels
+    "ts_20k_x_1000": dict(kind="ts", m=20_000, n=1000, lo=1e-8, seed=3),
     # the small plain case (20,000 x 50, sigma 1..1e-6)
     "ts_20k_x_50": dict(kind="ts", m=20_000, n=50, lo=1e-6, seed=1),
     # 512 uneven tall-skinny SVDs in one graph launch (m in [1e3, 2e5], n in
@@ -75,6 +78,7 @@ WORKLOADS = {
 # with the rate measured on the device (set_fp64_peak).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9
 FP64_PEAK_SOURCE = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (derived)"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def set_fp64_peak(L):
@@ -445,7 +449,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest total event time in the
     # timed region): algorithmic flops or bytes per launch / mean duration
-    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(),
+                               info["sweeps"] + [info.get("sweeps_fp32", 0)])
     esize = A.element_size()
     del A, U, S, V, ws
     torch.cuda.empty_cache()
@@ -483,7 +488,7 @@ def run_ours(args):
            "clocks": clk,
            "accuracy": {"sigma_err_normwise": sig_err, "orth_U": orth_u, "orth_V": orth_v,
                         "residual_rel": resid, "rank": info["rank"],
-                        "sweeps": info["sweeps"]},
+                        "sweeps": info["sweeps"], "sweeps_fp32": info.get("sweeps_fp32", 0)},
            "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()}}
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -563,8 +568,9 @@ def run_rowshard(args):
         acc = {"sigma_err_normwise": float((S - s_t).abs().max() / s_t[0]),
                "orth_U": float((G - eye).abs().max()),
                "orth_V": float((V.T @ V - eye).abs().max()), "rank": info["rank"],
-               "sweeps": info["sweeps"]}
-    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+               "sweeps": info["sweeps"], "sweeps_fp32": info.get("sweeps_fp32", 0)}
+    roof, roof_all = roofline(kernels, m, n, ms, args, A.element_size(),
+                               info["sweeps"] + [info.get("sweeps_fp32", 0)])
     out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -614,8 +620,10 @@ def measure_ts(torch, pkg, L, w, args, dev, rank):
         acc = {"sigma_err_normwise": float((S - s_t).abs().max() / s_t[0]),
                "orth_U": float((U.T @ U - eye).abs().max()),
                "orth_V": float((V.T @ V - eye).abs().max()),
-               "rank": info["rank"], "sweeps": info["sweeps"]}
-    roof, _ = roofline(kernels, m, n, ms, args, A.element_size(), info["sweeps"])
+               "rank": info["rank"], "sweeps": info["sweeps"],
+               "sweeps_fp32": info.get("sweeps_fp32", 0)}
+    roof, _ = roofline(kernels, m, n, ms, args, A.element_size(),
+                               info["sweeps"] + [info.get("sweeps_fp32", 0)])
     out = {"value": nominal_flops(w) / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
            "steps": args.steps, "m": m, "n": n, "mode": args.mode, "accuracy": acc,
            "roofline": roof,
@@ -698,10 +706,14 @@ def kernel_models(m, n, esize, sweeps, cholesky_first=False):
                   of X and of J at 3 flops: 18n, n / 2 pairs: 9 n^2 per round
       pchol       pivoted Cholesky of the n x n Gram: n^3 / 3 FMAs
     cholesky_first: the first eigensolve ran as pivoted Cholesky and the
-    one-sided kernel (n <= 256, FP64-accurate modes), so jacobi_eig is the
+    one-sided kernel (n <= 2048, FP64-accurate modes), so jacobi_eig is the
     second eigensolve alone (sweeps[1]) and jacobi_svd launches twice, for
     sweeps[0] and sweeps[2]; otherwise jacobi_eig launches for sweeps[0]
-    and sweeps[1] and jacobi_svd once (sweeps[2]).
+    and sweeps[1] and jacobi_svd once (sweeps[2]).  Above n = 256 the
+    first eigensolve's one-sided sweeps do not accumulate rotations (6 n^2
+    per round: 3n FMAs of dots and 2n outputs at 3 flops per pair), and
+    both one-sided solves start with the FP32 kernel jacobi_svd32 (9 n^2
+    FP32 flops per round, sweeps[3] summed over its two launches).
       oz_nn, oz_gram  28 bf16 digit-pair products per FP64-accurate product
       oz_*_image  read the tall operand once, write 7 bf16 digits per entry
       colmax, oz_rowexp  read the tall operand once; colsumsq reads m n FP64
@@ -715,9 +727,13 @@ def kernel_models(m, n, esize, sweeps, cholesky_first=False):
            "colsumsq": ("hbm", 8.0 * m * n)}
     mdl["pchol"] = ("alu", 2.0 * n * n * n / 3.0)
     if sweeps and len(sweeps) >= 3 and min(sweeps[:3]) > 0:
+        wide = n > 256
         if cholesky_first:
             mdl["jacobi_eig"] = ("alu", float(sweeps[1]) * rounds * 6.0 * n * n)
-            mdl["jacobi_svd"] = ("alu", (sweeps[0] + sweeps[2]) / 2.0 * rounds * 9.0 * n * n)
+            first = 6.0 if wide else 9.0
+            mdl["jacobi_svd"] = ("alu", (first * sweeps[0] + 9.0 * sweeps[2]) / 2.0 * rounds * n * n)
+            if wide and len(sweeps) >= 4 and sweeps[3] > 0:
+                mdl["jacobi_svd32"] = ("alu32", sweeps[3] / 2.0 * rounds * 9.0 * n * n)
         else:
             mdl["jacobi_eig"] = ("alu", (sweeps[0] + sweeps[1]) / 2.0 * rounds * 6.0 * n * n)
             mdl["jacobi_svd"] = ("alu", float(sweeps[2]) * rounds * 9.0 * n * n)
@@ -735,6 +751,10 @@ def roofline_entry(name, cnt, tot_ms, model, step_ms, args):
         peak = FP64_PEAK_GFLOPS / 1e3
         e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s",
                  peak_source=FP64_PEAK_SOURCE)
+    elif bound == "alu32":
+        e["bound"] = "alu"
+        e.update(achieved=amount / per_launch_s / 1e12, peak=FP32_PEAK_TFLOPS, unit="TFLOP/s",
+                 peak_source="FP32 FMA: 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz (derived)")
     elif bound == "tensor":
         peak, src = bf16_peak(sustained=True)
         e.update(achieved=amount / per_launch_s / 1e12, peak=peak, unit="TFLOP/s", peak_source=src)
@@ -757,7 +777,8 @@ def roofline(kernels, m, n, ms, args, esize, sweeps=None):
     algorithmic work per launch (kernel_models) / mean launch duration."""
     if not kernels:
         return None, []
-    mdl = kernel_models(m, n, esize, sweeps, cholesky_first="pchol" in kernels)
+    mdl = kernel_models(m, n, esize, sweeps,
+                        cholesky_first=("pchol" in kernels or "pchol_grid" in kernels))
     ranked = sorted(kernels.items(), key=lambda kv: -kv[1][1])
     entries = []
     for name, (cnt, tot) in ranked:

@@ -183,7 +183,7 @@ def _check(rc, name):
 
 def _info(o, rc):
     return {"status": rc, "rank": int(o.out_rank), "sweeps": list(o.sweeps)[:3],
-            "ranks": list(o.ranks)}
+            "sweeps_fp32": int(o.sweeps[3]), "ranks": list(o.ranks)}
 
 
 def _as_matrix(A):

@@ -139,7 +139,8 @@ inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSS
 // (n x n), norms, lam (n), perm, piv (n ints).
 static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *Jw, double *Xn,
                              double *lam, double *norms, double *Vt, int max_sweeps, int *ctr,
-                             double *prm, int *perm, int *piv, DevStatus *st, cudaStream_t s)
+                             double *prm, int *perm, int *piv, DevStatus *st, cudaStream_t s,
+                             const JacobiMixedScratch &mw)
 {
     if (n <= kPcholMaxN) {
         CK(launch_pchol(B, (int)n, Xw, n, piv, s));
@@ -149,8 +150,11 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
     }
     if (n <= kPcholGridMaxN) {
         CK(launch_pchol_grid(B, (int)n, Xw, n, (unsigned long long *)prm, st, s));
-        CK(launch_jacobi(Xw, n, nullptr, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
-                         0x1p-51));
+        if (jacobi_mixed_applies(n))
+            CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
+        else
+            CK(launch_jacobi(Xw, n, nullptr, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
+                             0x1p-51));
         return launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,
                                       lam, Vt, n, s);
     }
@@ -165,10 +169,14 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 // accurately).  Outputs Pm (P), sigma, Vo (V), sorted.
 static cudaError_t final_svd(double *R, i64 n, const double *d, double *Xw, double *Jw,
                              double *norms, double *Pm, double *sigma, double *Vo, int max_sweeps,
-                             int *ctr, double *prm, int *perm, DevStatus *st, cudaStream_t s)
+                             int *ctr, double *prm, int *perm, DevStatus *st, cudaStream_t s,
+                             const JacobiMixedScratch &mw)
 {
     CK(launch_orient_copy(d, &st->rank2, R, n, Xw, &st->orient, s));
-    CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
+    if (jacobi_mixed_applies(n))
+        CK(launch_jacobi_mixed(Xw, n, Jw, mw, max_sweeps, ctr, prm, st, 2, s));
+    else
+        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 2, s));
     return launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, Pm, n, sigma, Vo, n,
                                   s, &st->orient, prm);
 }
@@ -263,7 +271,8 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s, true));
     else
-        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s));
+        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s,
+                     JacobiMixedScratch{B2, Jw, W, G, R, P, NP}));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
@@ -308,7 +317,7 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     // V = X Sigma^-1), or of R when the MaxEntry scaling is strongly graded
     // (the device-side flag st->orient routes the outputs).
     CK(final_svd(R, n, scale ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm,
-                 perm, st, s));
+                 perm, st, s, JacobiMixedScratch{B, B2, M3, G, W, P, NP}));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Q P = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
@@ -389,7 +398,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm 3)
     if (passes == 2)
-        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s));
+        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s,
+                     JacobiMixedScratch{B2, Jw, W, G, R, P, NP}));
     else
         CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s));
@@ -459,7 +469,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
     CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
     CK(final_svd(R, n, sc ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm, perm,
-                 st, s));
+                 st, s, JacobiMixedScratch{B, B2, M3, G, W, P, NP}));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
     // U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)), prescaled like Q~

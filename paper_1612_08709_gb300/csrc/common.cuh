@@ -217,6 +217,27 @@ cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStr
 constexpr int kPcholGridMaxN = 2048;
 cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned long long *key,
                               DevStatus *st, cudaStream_t s);
+// One-sided Jacobi in two precisions (jacobi_mixed.cu) for
+// kJacobiMixedMinN < n <= kJacobiMixedMaxN: an FP32 phase (at most
+// kJacobiMixedF32Sweeps sweeps, its count added to st->sweeps[3]) picks an
+// orthogonal basis K (made orthogonal in FP64 by two Newton-Schulz steps),
+// X <- X K, then launch_jacobi in FP64 with threshold tol finishes (its
+// sweeps in st->sweeps[which]).  X is n x n column-major (ldx = n);
+// Jout (n x n column-major, or null) receives K times the FP64 phase's
+// rotations.  Scratch: f32 (n*n doubles, holding two n x n FP32 arrays),
+// K, T, H, X0 (n x n doubles each), P (tn_splits(n, n, n, false) * n * n
+// doubles) and NP (nn_grid_rows(n, n) * n doubles); prm and ctr as for
+// launch_jacobi.
+constexpr int kJacobiMixedMinN = 256;
+constexpr int kJacobiMixedMaxN = 2048;
+constexpr int kJacobiMixedF32Sweeps = 40;
+struct JacobiMixedScratch {
+    double *f32, *K, *T, *H, *X0, *P, *NP;
+};
+bool jacobi_mixed_applies(i64 n);
+cudaError_t launch_jacobi_mixed(double *X, i64 n, double *Jout, const JacobiMixedScratch &w,
+                                int max_sweeps, int *ctr, double *prm, DevStatus *st, int which,
+                                cudaStream_t s, double tol = 0.0);
 // V[piv[i]][j] = Xn[i][j], n x n row-major.
 cudaError_t launch_row_scatter(const double *Xn, const int *piv, int n, double *V, cudaStream_t s);
 

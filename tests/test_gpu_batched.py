@@ -74,3 +74,39 @@ def test_batched_fp32_and_autotuned(orc):
     for A, (U, S, V) in zip(mats, outs):
         Sr = orc.ts_svd(A, drop_tol=0.0)[1]
         assert np.abs(S.cpu().numpy() - Sr).max() <= 1e-11 * Sr[0]
+
+
+_FULL_REF = {}
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64", "fp64_tc"])
+def test_batched_full_ranges_every_member_vs_oracle(orc, mode):
+    """Members drawn from the 512-member workload's ranges (m in [1,000,
+    200,000], n in [16, 256], sigma log-uniform in [1e-6, 1]); every member
+    of the batch is compared with the oracle: sigma, both factors' columns
+    (Davis-Kahan scale), orthonormality, rank.  Several digit-product column
+    tiles per member and Jacobi solves of up to 128 pairs run concurrently
+    on the worker streams."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    from test_gpu_parity import col_err_up_to_sign, gaps
+    shapes = workloads.batch_shapes(8, 17)
+    shapes[0] = (200000, 256)   # the ranges' corners
+    shapes[1] = (1000, 16)
+    mats = [workloads.batch_instance(m, n, 1700 + i)[0] for i, (m, n) in enumerate(shapes)]
+    As = [torch.as_tensor(A, device="cuda") for A in mats]
+    outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode)
+    for i, (A, (U, S, V), info) in enumerate(zip(mats, outs, infos)):
+        n = A.shape[1]
+        if i not in _FULL_REF:
+            _FULL_REF[i] = orc.ts_svd(A, drop_tol=0.0)
+        Ur, Sr, Vr, rr, st = _FULL_REF[i]
+        U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+        assert info["rank"] == rr == n and info["status"] == st
+        assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+        assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-12
+        assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
+        tolv = np.clip(1e-10 * Sr[0] / gaps(Sr), 1e-13, 1.0)
+        assert np.all(col_err_up_to_sign(V, Vr) <= tolv)
+        assert np.all(col_err_up_to_sign(U, Ur) <= tolv)
