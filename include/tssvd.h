@@ -54,10 +54,15 @@ typedef enum {
      * tcgen05 tensor cores with BF16x3 split operands and FP32 accumulation
      * drained to FP64; the second orthonormalisation pass, the eigensolves
      * and all n x n work stay FP64.  Two bf16 terms per value (about 16
-     * significant bits), three term products per product.  n <= 256. */
+     * significant bits), three term products per product.  n <= 256.
+     * Singular values to about 1e-6 of the largest; U orthonormal to 1e-12
+     * for condition numbers up to about 1e5 (beyond that the first pass
+     * leaves Y too ill-conditioned for the second to repair: 3.7e-12 at
+     * 1e6, 3e-11 at 1e8). */
     TSSVD_BF16X3 = 1,
     /* As TSSVD_BF16X3 with three bf16 terms per value (about 24 significant
-     * bits, the accuracy of FP32 inputs) and six term products. n <= 256. */
+     * bits, the accuracy of FP32 inputs) and six term products. n <= 256.
+     * U orthonormal to 1e-12 for condition numbers up to about 1e5. */
     TSSVD_BF16X6 = 2,
     /* FP64-accurate products on the tensor cores: every tall product of
      * both passes is emulated with seven 7-bit integer digits per value
@@ -401,7 +406,8 @@ int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opt
  * (leading dimension n), written in full (both triangles).  Uses
  * opts->stream and opts->workspace (ts_gram_workspace_size bytes) like
  * ts_svd; returns after the stream has finished.  opts->mode selects FP64
- * DFMA or the BF16-split tensor-core product (n <= 256).
+ * DFMA, the BF16-split tensor-core product (n <= 256) or the FP64-accurate
+ * digit-sliced tensor-core product (TSSVD_FP64_TC, any n).
  * Errors: -1 A, -2 m, -3 n, -4 lda, -5 B, -6 opts.
  */
 size_t ts_gram_workspace_size(int64_t m, int64_t n);
@@ -411,8 +417,9 @@ int ts_gram(const double *A, int64_t m, int64_t n, int64_t lda, double *B, tssvd
  * Tall product C = A M: A is m x k (row-major, lda), M is k x n (ldm), C is
  * m x n (ldc), all FP64 device memory.  The product Y~ = A V~ of
  * Algorithms 3 and 4 (and U = Q P, Y = A Q~ of Algorithm 5) as a call of its
- * own.  opts->mode selects FP64 DFMA or the BF16-split tensor-core product
- * (n <= 256).  Uses opts->stream and opts->workspace
+ * own.  opts->mode selects FP64 DFMA, the BF16-split tensor-core product
+ * (n <= 256) or the FP64-accurate digit-sliced tensor-core product
+ * (TSSVD_FP64_TC, any n).  Uses opts->stream and opts->workspace
  * (ts_matmul_workspace_size bytes); returns after the stream has finished.
  * Errors: -1 A, -2 m, -3 k, -4 lda, -5 M, -6 n, -7 ldm, -8 C, -9 ldc,
  * -10 opts.

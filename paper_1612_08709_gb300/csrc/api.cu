@@ -144,8 +144,16 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 {
     if (n <= kPcholMaxN) {
         CK(launch_pchol(B, (int)n, Xw, n, piv, s));
-        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
-        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n, s));
+        if (jacobi_mixed_applies(n)) {
+            CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
+            CK(launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,
+                                      lam, Xn, n, s));
+        } else {
+            CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
+                             0x1p-51));
+            CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n,
+                                      s));
+        }
         return launch_row_scatter(Xn, piv, (int)n, Vt, s);
     }
     if (n <= kPcholGridMaxN) {
@@ -160,6 +168,30 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
     }
     return launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
                              s, true);
+}
+
+// The second eigensolve of Algorithm 4, Z = W D W^T (Z consumed), with
+// the relative rotation test (W must diagonalise Z to working precision:
+// it sets the orthonormality of Q).  For kJacobiMixedMinN < n <=
+// kPcholGridMaxN: Z = R~^T R~ by the grid pivoted Cholesky (Z is well
+// conditioned: the first pass leaves Y with a condition number near 10),
+// then the two-precision one-sided Jacobi on R~^T without accumulation;
+// the orthogonalised columns, normalised, are the eigenvectors.  Its FP64
+// sweeps cost 3.5 n^2 operations a round against the Gram-form solver's
+// 6 n^2, and the FP32 phase takes the first few orders of magnitude.
+// Otherwise the Gram-form solver.
+static cudaError_t second_eig(double *Z, double *Z2, i64 n, double *Xw, double *Jw, double *lam,
+                              double *norms, double *W, int max_sweeps, int *ctr, double *prm,
+                              int *perm, DevStatus *st, cudaStream_t s, const JacobiMixedScratch &mw)
+{
+    if (n > kPcholMaxN && jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
+        CK(launch_pchol_grid(Z, (int)n, Xw, n, (unsigned long long *)prm, st, s));
+        CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 1, s));
+        return launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,
+                                      lam, W, n, s);
+    }
+    return launch_jacobi_eig(Z, Z2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1,
+                             s);
 }
 
 // The small SVD of Algorithm 4, R = P Sigma V^T (R n x n row-major), by
@@ -301,7 +333,8 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     }
     // Z = W D W^T.
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
+    CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, st, s,
+                  JacobiMixedScratch{B2, Jw, G, R, Pm, P, NP}));
     // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
     CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
@@ -451,7 +484,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_oz_row_image<double>(Yt, n, m, (int)n, pk2, er, big, s));
     CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
     // Z = W D W^T
-    CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, W, n, (int)n, max_sweeps, ctr, prm, perm, st, 1, s));
+    CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, st, s,
+                  JacobiMixedScratch{B2, Jw, G, R, Pm, P, NP}));
     // Q~; T = explicit column norms
     CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
     CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));

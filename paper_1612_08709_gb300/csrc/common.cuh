@@ -194,7 +194,7 @@ cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
 // the accumulated rotations: X_in J = X_out with orthogonal columns.
 // ctr must point to at least max_sweeps + 4 zeroed ints of device memory;
 // prm to jacobi_prm_doubles(nc) doubles of scratch.
-inline size_t jacobi_prm_doubles(i64 nc) { return 8 * (size_t)((nc + 1) / 2) + 8; }
+inline size_t jacobi_prm_doubles(i64 nc) { return 8 * (size_t)((nc + 1) / 2) + (size_t)nc + 8; }
 // tol: the rotation threshold |x_p . x_q| > tol |x_p| |x_q| (0: nr 2^-53).
 // J == null: the rotations are not accumulated (only X_out is wanted).
 cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc,
@@ -218,7 +218,7 @@ constexpr int kPcholGridMaxN = 2048;
 cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned long long *key,
                               DevStatus *st, cudaStream_t s);
 // One-sided Jacobi in two precisions (jacobi_mixed.cu) for
-// kJacobiMixedMinN < n <= kJacobiMixedMaxN: an FP32 phase (at most
+// kJacobiMixedMinN <= n <= kJacobiMixedMaxN: an FP32 phase (at most
 // kJacobiMixedF32Sweeps sweeps, its count added to st->sweeps[3]) picks an
 // orthogonal basis K (made orthogonal in FP64 by two Newton-Schulz steps),
 // X <- X K, then launch_jacobi in FP64 with threshold tol finishes (its
@@ -228,7 +228,7 @@ cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned lon
 // K, T, H, X0 (n x n doubles each), P (tn_splits(n, n, n, false) * n * n
 // doubles) and NP (nn_grid_rows(n, n) * n doubles); prm and ctr as for
 // launch_jacobi.
-constexpr int kJacobiMixedMinN = 256;
+constexpr int kJacobiMixedMinN = 64;
 constexpr int kJacobiMixedMaxN = 2048;
 constexpr int kJacobiMixedF32Sweeps = 40;
 struct JacobiMixedScratch {

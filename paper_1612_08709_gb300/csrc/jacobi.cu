@@ -30,6 +30,8 @@ struct JacobiArgs {
     double *J;
     i64 ldj;
     double4 *prm;  // [2][npairs] published (c, s, 0, rotate) of the last two rounds
+    double *nrm;   // [nc] tracked squared column norms (negative: recompute)
+    int track;     // track the norms (wide problems, where FP64 throughput bounds a round)
     int nr, nc, npad;
     int max_sweeps;
     double tol;
@@ -73,6 +75,25 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
             b += red[1][w];
             c += red[2][w];
         }
+    }
+}
+
+// Block sum of one per-thread partial (valid in thread 0), as block_sum3.
+template <int NT>
+__device__ __forceinline__ void block_sum1(double &a, double (*red)[NT / 32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ta = __shfl_down_sync(0xffffffffu, a, o);
+        if (lane < o) a += ta;
+    }
+    if (lane == 0) red[2][warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = red[2][0];
+#pragma unroll
+        for (int w = 1; w < NT / 32; w++) a += red[2][w];
     }
 }
 
@@ -260,6 +281,18 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                 double *xp = p.X + (i64)P * p.ldx, *xq = p.X + (i64)Q * p.ldx;
                 double *jp = hasJ ? p.J + (i64)P * p.ldj : nullptr;
                 double *jq = hasJ ? p.J + (i64)Q * p.ldj : nullptr;
+                // Squared norms: tracked through the rotations (each rotation
+                // gives its two columns' new norms in closed form), so only the
+                // inner product is summed; recomputed in the first two rounds
+                // of every sweep (every column is in a real pair in one of
+                // them, whatever the padding) and after a cancelling update
+                // (flag < 0).
+                double na = -1.0, nb = -1.0;
+                if (p.track && t >= 2) {
+                    na = __ldcg(p.nrm + P);
+                    nb = __ldcg(p.nrm + Q);
+                }
+                const bool need_a = !(na >= 0.0), need_b = !(nb >= 0.0);
                 double u[C], v[C], ju[C], jv[C];
                 double al = 0.0, be = 0.0, ga = 0.0;
                 if (CH > 0) {
@@ -275,11 +308,16 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         pv = ld4cg(prev_g + threadIdx.x);
                         pv_loaded = true;
                     }
+                    if (need_a || need_b) {
 #pragma unroll
-                    for (int j = 0; j < C; j++) {
-                        al = fma(u[j], u[j], al);
-                        be = fma(v[j], v[j], be);
-                        ga = fma(u[j], v[j], ga);
+                        for (int j = 0; j < C; j++) {
+                            al = fma(u[j], u[j], al);
+                            be = fma(v[j], v[j], be);
+                            ga = fma(u[j], v[j], ga);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < C; j++) ga = fma(u[j], v[j], ga);
                     }
                 } else {
                     for (int i = threadIdx.x; i < p.nr; i += NT) {
@@ -289,12 +327,32 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         ga = fma(x, y, ga);
                     }
                 }
-                block_sum3<NT>(al, be, ga, red);
+                if (need_a || need_b || CH == 0)
+                    block_sum3<NT>(al, be, ga, red);
+                else
+                    block_sum1<NT>(ga, red);
                 if (threadIdx.x == 0) {
-                    const double4 r = jac_rotation(al, be, ga, tol, log2tol);
+                    const double a = (need_a || CH == 0) ? al : na;
+                    const double b = (need_b || CH == 0) ? be : nb;
+                    const double4 r = jac_rotation(a, b, ga, tol, log2tol);
                     rot_s[0] = r.x;
                     rot_s[1] = r.y;
                     rot_s[2] = r.w;
+                    double a1 = a, b1 = b;
+                    if (r.w != 0.0) {
+                        // ||c x_P - s x_Q||^2 and ||s x_P + c x_Q||^2; an update
+                        // that cancels below 2^-16 of the inputs is recomputed
+                        const double cc = r.x * r.x, ss = r.y * r.y, cs2 = 2.0 * r.x * r.y;
+                        a1 = fma(cc, a, fma(-cs2, ga, ss * b));
+                        b1 = fma(ss, a, fma(cs2, ga, cc * b));
+                        const double floor = 0x1p-16 * (a + b);
+                        if (!(a1 >= floor)) a1 = -1.0;
+                        if (!(b1 >= floor)) b1 = -1.0;
+                    }
+                    if (p.track && (r.w != 0.0 || need_a || need_b)) {
+                        __stcg(p.nrm + P, a1);
+                        __stcg(p.nrm + Q, b1);
+                    }
                 }
                 __syncthreads();  // rotation visible; red free for the next pair
                 const double c = rot_s[0], sn = rot_s[1];
@@ -1619,6 +1677,11 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.J = J;
     a.ldj = ldj;
     a.prm = (double4 *)prm;
+    a.nrm = prm + 8 * (size_t)((nc + 1) / 2);  // after [2][npairs] double4
+    // Norm tracking saves two of the three inner products per pair; it pays
+    // where the FP64 pipe bounds a round (n = 1000: 12.8 -> 10.5 us), not
+    // where latency does (n = 200: 4.0 -> 4.2 us, the extra loads and stores)
+    a.track = nc > 256 ? 1 : 0;
     a.nr = nr;
     a.nc = nc;
     a.npad = nc + (nc & 1);
