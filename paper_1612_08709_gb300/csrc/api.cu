@@ -144,16 +144,8 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 {
     if (n <= kPcholMaxN) {
         CK(launch_pchol(B, (int)n, Xw, n, piv, s));
-        if (jacobi_mixed_applies(n)) {
-            CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
-            CK(launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,
-                                      lam, Xn, n, s));
-        } else {
-            CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
-                             0x1p-51));
-            CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n,
-                                      s));
-        }
+        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
+        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n, s));
         return launch_row_scatter(Xn, piv, (int)n, Vt, s);
     }
     if (n <= kPcholGridMaxN) {
@@ -172,7 +164,7 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 
 // The second eigensolve of Algorithm 4, Z = W D W^T (Z consumed), with
 // the relative rotation test (W must diagonalise Z to working precision:
-// it sets the orthonormality of Q).  For kJacobiMixedMinN < n <=
+// it sets the orthonormality of Q).  For kJacobiMixedMinN <= n <=
 // kPcholGridMaxN: Z = R~^T R~ by the grid pivoted Cholesky (Z is well
 // conditioned: the first pass leaves Y with a condition number near 10),
 // then the two-precision one-sided Jacobi on R~^T without accumulation;
@@ -184,7 +176,7 @@ static cudaError_t second_eig(double *Z, double *Z2, i64 n, double *Xw, double *
                               double *norms, double *W, int max_sweeps, int *ctr, double *prm,
                               int *perm, DevStatus *st, cudaStream_t s, const JacobiMixedScratch &mw)
 {
-    if (n > kPcholMaxN && jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
+    if (jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
         CK(launch_pchol_grid(Z, (int)n, Xw, n, (unsigned long long *)prm, st, s));
         CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 1, s));
         return launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,

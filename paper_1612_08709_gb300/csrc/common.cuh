@@ -228,7 +228,7 @@ cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned lon
 // K, T, H, X0 (n x n doubles each), P (tn_splits(n, n, n, false) * n * n
 // doubles) and NP (nn_grid_rows(n, n) * n doubles); prm and ctr as for
 // launch_jacobi.
-constexpr int kJacobiMixedMinN = 64;
+constexpr int kJacobiMixedMinN = 257;
 constexpr int kJacobiMixedMaxN = 2048;
 constexpr int kJacobiMixedF32Sweeps = 40;
 struct JacobiMixedScratch {

@@ -31,7 +31,6 @@ struct JacobiArgs {
     i64 ldj;
     double4 *prm;  // [2][npairs] published (c, s, 0, rotate) of the last two rounds
     double *nrm;   // [nc] tracked squared column norms (negative: recompute)
-    int track;     // track the norms (wide problems, where FP64 throughput bounds a round)
     int nr, nc, npad;
     int max_sweeps;
     double tol;
@@ -236,6 +235,11 @@ template <int NT, int CH, bool JS>
 __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
 {
     constexpr int C = CH > 0 ? CH : 1;
+    // Norm tracking saves two of the three inner products per pair; it pays
+    // where the FP64 pipe bounds a round (n > 256, CH >= 4 or uncached;
+    // n = 1000: 12.8 -> 10.5 us), not where latency does (n <= 256, where
+    // this kernel keeps the plain form)
+    constexpr bool kTrack = CH == 0 || CH >= 4;
     __shared__ double red[3][NT / 32];
     __shared__ double rot_s[3];
     // JS: this CTA's rows of J (row i for i = blockIdx.x mod gridDim.x) live
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                 // them, whatever the padding) and after a cancelling update
                 // (flag < 0).
                 double na = -1.0, nb = -1.0;
-                if (p.track && t >= 2) {
+                if (kTrack && t >= 2) {
                     na = __ldcg(p.nrm + P);
                     nb = __ldcg(p.nrm + Q);
                 }
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                     rot_s[1] = r.y;
                     rot_s[2] = r.w;
                     double a1 = a, b1 = b;
-                    if (r.w != 0.0) {
+                    if (kTrack && r.w != 0.0) {
                         // ||c x_P - s x_Q||^2 and ||s x_P + c x_Q||^2; an update
                         // that cancels below 2^-16 of the inputs is recomputed
                         const double cc = r.x * r.x, ss = r.y * r.y, cs2 = 2.0 * r.x * r.y;
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacobiArgs p)
                         if (!(a1 >= floor)) a1 = -1.0;
                         if (!(b1 >= floor)) b1 = -1.0;
                     }
-                    if (p.track && (r.w != 0.0 || need_a || need_b)) {
+                    if (kTrack && (r.w != 0.0 || need_a || need_b)) {
                         __stcg(p.nrm + P, a1);
                         __stcg(p.nrm + Q, b1);
                     }
@@ -1678,10 +1682,6 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
     a.ldj = ldj;
     a.prm = (double4 *)prm;
     a.nrm = prm + 8 * (size_t)((nc + 1) / 2);  // after [2][npairs] double4
-    // Norm tracking saves two of the three inner products per pair; it pays
-    // where the FP64 pipe bounds a round (n = 1000: 12.8 -> 10.5 us), not
-    // where latency does (n = 200: 4.0 -> 4.2 us, the extra loads and stores)
-    a.track = nc > 256 ? 1 : 0;
     a.nr = nr;
     a.nc = nc;
     a.npad = nc + (nc & 1);

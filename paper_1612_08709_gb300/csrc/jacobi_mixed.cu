@@ -21,8 +21,6 @@
 #include "common.cuh"
 #include "jacobi_common.cuh"
 
-#include <cooperative_groups.h>
-
 namespace tssvd {
 
 namespace {
@@ -151,193 +149,6 @@ __global__ void __launch_bounds__(NT) jacobi32_kernel(Jacobi32Args p)
     if (blockIdx.x == 0 && tid == 0) atomicAdd(&p.st->sweeps[3], done > 0 ? done : p.max_sweeps);
 }
 
-// The FP32 phase for n <= 256, resident in one thread-block cluster of
-// four CTAs (a grid barrier costs several microseconds; a cluster barrier
-// a fraction of one, and at this n a round is bound by such latencies, not
-// by arithmetic).  CTAs 0 and 1 hold the top and bottom rows of X in
-// shared memory, CTAs 2 and 3 those of J (each half is at most 128 x 256
-// floats, 128 KB); a pair's column pieces are contiguous (column-major).
-// Round g of the circle schedule:
-//   A. the X CTAs form each pair's three partial inner products over their
-//      rows (8 threads a pair) into part[g & 1]; the J CTAs apply the
-//      rotations of round g - 2 (rot[g & 1]) to their rows of J;
-//   B. cluster barrier;
-//   C. each X CTA adds the other's partials (read from its shared memory
-//      across the cluster; a + b = b + a, so both find the same
-//      rotations), rotates its rows, and CTA 0 stores the rotations into
-//      the J CTAs' rot[g & 1]; at a sweep's last round CTA 0 also stores
-//      the sweep's rotation count in every CTA.
-// The two-round lag makes every buffer's writes and reads fall on opposite
-// sides of a barrier (slot g & 1 is read in A(g + 2), before B(g + 2),
-// and rewritten in C(g + 2), after it).  A sweep with no rotation ends the
-// solve (every CTA reads the count after the next barrier).
-constexpr int kClusterNT = 1024;   // threads of each CTA (128 pair groups of 8)
-constexpr int kClusterMaxN = 256;
-
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterNT, 1)
-    jacobi32_cluster_kernel(const float *X32, float *J32, int n, int max_sweeps, float tol,
-                            DevStatus *st)
-{
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ float cs_mem[];
-    const int rank = (int)cluster.block_rank();
-    const int npad = n + (n & 1), npairs = npad / 2, rounds = npad - 1;
-    const int hr = (n + 1) / 2;                       // rows of the top half
-    const int half = rank & 1;                        // 0 top, 1 bottom
-    const int r0 = half ? hr : 0, nrow = half ? n - hr : hr;
-    float *M = cs_mem;                                // [n][hr] this CTA's rows of X or J
-    float *part = M + (size_t)n * hr;                 // [2][128][3]
-    float *rot = part + 2 * 128 * 3;                  // [2][128][2]
-    int *sweep_rot = reinterpret_cast<int *>(rot + 2 * 128 * 2);  // [2]
-    __shared__ int s_cnt;
-    const int tid = threadIdx.x, k = tid >> 3, l = tid & 7;
-    const bool isX = rank < 2;
-    // load the rows (X from X32; J = I)
-    for (int e = tid; e < n * hr; e += kClusterNT) {
-        const int c = e / hr, r = e - c * hr;
-        float v = 0.0f;
-        if (r < nrow) v = isX ? X32[(i64)c * n + r0 + r] : (c == r0 + r ? 1.0f : 0.0f);
-        M[e] = v;
-    }
-    if (tid == 0) {
-        s_cnt = 0;
-        sweep_rot[0] = sweep_rot[1] = 1;
-    }
-    for (int e = tid; e < 2 * 128 * 2; e += kClusterNT) rot[e] = (e & 1) ? 0.0f : 1.0f;
-    cluster.sync();
-    float *other_part = isX ? cluster.map_shared_rank(part, rank ^ 1) : nullptr;
-    float *jrot2 = cluster.map_shared_rank(rot, 2), *jrot3 = cluster.map_shared_rank(rot, 3);
-    int *flag_of[4];
-    for (int q = 0; q < 4; q++) flag_of[q] = cluster.map_shared_rank(sweep_rot, q);
-    int done = -1, g = 0;
-    for (int sweep = 0; sweep < max_sweeps; sweep++) {
-        for (int t = 0; t < rounds; t++, g++) {
-            const int slot = g & 1;
-            // ---- A
-            if (isX) {
-                // (every lane takes part in the shuffles: a warp may hold
-                // pair groups on both sides of npairs)
-                float a = 0.0f, b = 0.0f, c = 0.0f;
-                if (k < npairs) {
-                    int P, Q;
-                    circle_pair(k, t, npad, P, Q);
-                    if (Q < n) {
-                        const float *xp = M + (size_t)P * hr, *xq = M + (size_t)Q * hr;
-                        for (int r = l; r < nrow; r += 8) {
-                            const float u = xp[r], v = xq[r];
-                            a = fmaf(u, u, a);
-                            b = fmaf(v, v, b);
-                            c = fmaf(u, v, c);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int o = 4; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    c += __shfl_xor_sync(0xffffffffu, c, o);
-                }
-                if (k < npairs && l == 0) {
-                    part[(slot * 128 + k) * 3 + 0] = a;
-                    part[(slot * 128 + k) * 3 + 1] = b;
-                    part[(slot * 128 + k) * 3 + 2] = c;
-                }
-            } else if (g >= 2 && k < npairs) {
-                const int tg = (t + 2 * rounds - 2) % rounds;  // round g - 2 of the schedule
-                const float cc = rot[(slot * 128 + k) * 2], ss = rot[(slot * 128 + k) * 2 + 1];
-                if (ss != 0.0f) {
-                    int P, Q;
-                    circle_pair(k, tg, npad, P, Q);
-                    float *jp = M + (size_t)P * hr, *jq = M + (size_t)Q * hr;
-                    for (int r = l; r < nrow; r += 8) {
-                        const float u = jp[r], v = jq[r];
-                        jp[r] = cc * u - ss * v;
-                        jq[r] = ss * u + cc * v;
-                    }
-                }
-            }
-            // ---- B
-            cluster.sync();
-            if (t == 0 && sweep > 0 && sweep_rot[(sweep - 1) & 1] == 0) {
-                done = sweep;
-                break;
-            }
-            // ---- C
-            if (isX && k < npairs) {
-                int P, Q;
-                circle_pair(k, t, npad, P, Q);
-                float cc = 1.0f, ss = 0.0f;
-                if (Q < n) {
-                    const float *mp = part + (slot * 128 + k) * 3;
-                    const float *op = other_part + (slot * 128 + k) * 3;
-                    const float A = mp[0] + op[0], B = mp[1] + op[1], G = mp[2] + op[2];
-                    if (rot32(A, B, G, tol, cc, ss)) {
-                        float *xp = M + (size_t)P * hr, *xq = M + (size_t)Q * hr;
-                        for (int r = l; r < nrow; r += 8) {
-                            const float u = xp[r], v = xq[r];
-                            xp[r] = cc * u - ss * v;
-                            xq[r] = ss * u + cc * v;
-                        }
-                        if (rank == 0 && l == 0) atomicAdd(&s_cnt, 1);
-                    } else {
-                        cc = 1.0f;
-                        ss = 0.0f;
-                    }
-                }
-                if (rank == 0 && l == 0) {
-                    jrot2[(slot * 128 + k) * 2] = cc;
-                    jrot2[(slot * 128 + k) * 2 + 1] = ss;
-                    jrot3[(slot * 128 + k) * 2] = cc;
-                    jrot3[(slot * 128 + k) * 2 + 1] = ss;
-                }
-            }
-            // the next round's pair groups read columns this round's groups
-            // rotated (another warp's), and CTA 0's count must be complete
-            __syncthreads();
-            if (t == rounds - 1 && rank == 0 && tid == 0) {
-                for (int q = 0; q < 4; q++) flag_of[q][sweep & 1] = s_cnt;
-                s_cnt = 0;
-            }
-        }
-        if (done >= 0) break;
-    }
-    // the J CTAs still owe the last two rounds' rotations (identities when
-    // the last sweep rotated nothing, which is how the loop ends early)
-    for (int e = 0; e < 2; e++, g++) {
-        cluster.sync();
-        if (!isX && g >= 2 && k < npairs && done < 0) {
-            const int slot = g & 1;
-            const int tg = ((g - 2) % rounds + rounds) % rounds;
-            const float cc = rot[(slot * 128 + k) * 2], ss = rot[(slot * 128 + k) * 2 + 1];
-            if (ss != 0.0f) {
-                int P, Q;
-                circle_pair(k, tg, npad, P, Q);
-                float *jp = M + (size_t)P * hr, *jq = M + (size_t)Q * hr;
-                for (int r = l; r < nrow; r += 8) {
-                    const float u = jp[r], v = jq[r];
-                    jp[r] = cc * u - ss * v;
-                    jq[r] = ss * u + cc * v;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (!isX)
-        for (int e = tid; e < n * hr; e += kClusterNT) {
-            const int c = e / hr, r = e - c * hr;
-            if (r < nrow) J32[(i64)c * n + r0 + r] = M[e];
-        }
-    if (rank == 0 && tid == 0) atomicAdd(&st->sweeps[3], done > 0 ? done : max_sweeps);
-    cluster.sync();  // no CTA leaves while another may still read its shared memory
-}
-
-size_t cluster_smem_bytes(int n)
-{
-    const int hr = (n + 1) / 2;
-    return sizeof(float) * ((size_t)n * hr + 2 * 128 * 3 + 2 * 128 * 2) + 2 * sizeof(int);
-}
-
 // Largest |x| of an n x n array as an ordered bit pattern (x != 0 finite).
 __global__ void maxabs_bits_kernel(const double *X, i64 total, unsigned long long *out)
 {
@@ -421,19 +232,7 @@ cudaError_t launch_jacobi_mixed(double *X, i64 n, double *Jout, const JacobiMixe
     if ((e = cudaMemsetAsync(ctr, 0, sizeof(int) * (size_t)(max_sweeps + 4), s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(&st->bar[0], 0, sizeof(int) * 4, s)) != cudaSuccess) return e;
-    if (n <= kClusterMaxN) {
-        const size_t smem = cluster_smem_bytes((int)n);
-        const void *kern = (const void *)jacobi32_cluster_kernel;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        const int sweeps32 =
-            max_sweeps < kJacobiMixedF32Sweeps ? max_sweeps : kJacobiMixedF32Sweeps;
-        ProfScope ps_("jacobi_svd32c", s);
-        jacobi32_cluster_kernel<<<4, kClusterNT, smem, s>>>(X32, J32, (int)n, sweeps32, 0x1p-20f,
-                                                             st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    } else {
+    {
         Jacobi32Args a;
         a.X = X32;
         a.J = J32;

@@ -68,3 +68,33 @@ def test_roofline_accounting_follows_the_first_eigensolve():
     assert dom2["achieved"] == pytest.approx((27 + 19) / 2.0 * rounds * 6.0 * n * n / 15.0e-3 / 1e12)
     for e in allr:
         assert e["frac"] == pytest.approx(e["achieved"] / e["peak"])
+
+
+def test_roofline_accounting_of_the_wide_two_precision_path():
+    """256 < n <= 2048: the FP64 one-sided kernel launches three times
+    (first and second eigensolves without accumulation, 6 n^2 a round; SVD
+    of R with it, 9 n^2), the FP32 kernel three times (sweeps[3] its summed
+    sweeps, 9 n^2 FP32 flops a round against the derived FP32 peak)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        steps = 1
+        workload = "ts_1m_x_1000"
+        mode = "fp64_tc"
+
+    m, n = 1_000_000, 1000
+    sweeps = [4, 19, 4, 43]
+    rounds = n - 1 + (n & 1)
+    kernels = {"jacobi_svd": (3, 283.0), "jacobi_svd32": (3, 191.0), "pchol_grid": (2, 17.7),
+               "oz_nn": (3, 160.0)}
+    mdl = bench.kernel_models(m, n, 8, sweeps, cholesky_first=True)
+    assert "jacobi_eig" not in mdl
+    dom, allr = bench.roofline(kernels, m, n, 755.0, Args, 8, sweeps)
+    assert dom["kernel"] == "jacobi_svd"
+    assert dom["achieved"] == pytest.approx((6.0 * 4 + 6.0 * 19 + 9.0 * 4) / 3.0 * rounds * n * n
+                                            / (283.0 / 3 * 1e-3) / 1e12)
+    f32 = next(e for e in allr if e["kernel"] == "jacobi_svd32")
+    assert f32["bound"] == "alu" and f32["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS)
+    assert f32["achieved"] == pytest.approx(43 / 3.0 * rounds * 9.0 * n * n
+                                            / (191.0 / 3 * 1e-3) / 1e12)
