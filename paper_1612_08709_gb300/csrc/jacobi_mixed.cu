@@ -78,13 +78,20 @@ __global__ void __launch_bounds__(NT) jacobi32_kernel(Jacobi32Args p)
                 if (Q >= n) continue;  // the padding column of an odd n
                 float *xp = p.X + (i64)P * p.ld, *xq = p.X + (i64)Q * p.ld;
                 float *jp = p.J + (i64)P * p.ld, *jq = p.J + (i64)Q * p.ld;
-                float u[CH], v[CH];
+                // J's columns are loaded with X's, so that the rotation's
+                // update waits on no second round trip to L2
+                float u[CH], v[CH], ju[CH], jv[CH];
                 float a = 0.0f, b = 0.0f, g = 0.0f;
 #pragma unroll
                 for (int j = 0; j < CH; j++) {
                     const int i = tid + j * NT;
                     u[j] = i < n ? __ldcg(xp + i) : 0.0f;
                     v[j] = i < n ? __ldcg(xq + i) : 0.0f;
+                    ju[j] = i < n ? __ldcg(jp + i) : 0.0f;
+                    jv[j] = i < n ? __ldcg(jq + i) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < CH; j++) {
                     a = fmaf(u[j], u[j], a);
                     b = fmaf(v[j], v[j], b);
                     g = fmaf(u[j], v[j], g);
@@ -127,9 +134,8 @@ __global__ void __launch_bounds__(NT) jacobi32_kernel(Jacobi32Args p)
                     if (i < n) {
                         __stcg(xp + i, c * u[j] - s * v[j]);
                         __stcg(xq + i, s * u[j] + c * v[j]);
-                        const float ju = __ldcg(jp + i), jv = __ldcg(jq + i);
-                        __stcg(jp + i, c * ju - s * jv);
-                        __stcg(jq + i, s * ju + c * jv);
+                        __stcg(jp + i, c * ju[j] - s * jv[j]);
+                        __stcg(jq + i, s * ju[j] + c * jv[j]);
                     }
                 }
             }
