@@ -114,6 +114,9 @@ def parse():
                     help="comma-separated tall-skinny workloads timed after the headline "
                          "(device-resident, same steps; '' to skip)")
     ap.add_argument("--mode", default="fp64_tc", choices=["fp64", "bf16x3", "bf16x6", "fp64_tc"])
+    ap.add_argument("--passes", type=int, default=2, choices=[2, 3],
+                    help="tall-skinny workloads: 3 runs Algorithm 4's second pass twice "
+                         "(the flop count stays the two-pass 6mn^2)")
     ap.add_argument("--compare-steps", type=int, default=2,
                     help="timed steps of the plain FP64 path reported beside the headline "
                          "(0 to skip)")
@@ -325,9 +328,10 @@ def run_ours(args):
     U = torch.empty((m, n), dtype=torch.float64, device=dev)
     S = torch.empty((n,), dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev)
-    wsb = pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode=args.mode)
+    wsb = pkg.ts_svd_workspace_size(m, n, drop_tol=0.0, mode=args.mode, passes=args.passes)
     ws = torch.empty((wsb,), dtype=torch.uint8, device=dev)
-    kw = dict(passes=2, scale=True, drop_tol=0.0, mode=args.mode, workspace=ws, out=(U, S, V))
+    kw = dict(passes=args.passes, scale=True, drop_tol=0.0, mode=args.mode, workspace=ws,
+              out=(U, S, V))
 
     def step():
         return pkg.ts_svd(A, **kw)[3]
@@ -484,7 +488,7 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": {"fp64": "f64", "fp64_tc": "bf16 digits+fp32+f64"}.get(args.mode, "bf16+fp32+f64"),
            "data": "synthetic",
-           "config": {"workload": args.workload, "m": m, "n": n, "passes": 2, "scale": 1,
+           "config": {"workload": args.workload, "m": m, "n": n, "passes": args.passes, "scale": 1,
                       "mode": args.mode, "drop_tol": 0.0,
                       "sigma": "geometric 1..%g" % w["lo"],
                       "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * esize / 1e9),
@@ -844,6 +848,23 @@ def _timed(torch, fn, steps):
     return e0.elapsed_time(e1) / steps
 
 
+def dominant_tensor_roofline(kernels, steps, bf16_flops_per_step, names=("oz_nn", "oz_tn")):
+    """Roofline of a step's digit products taken together (the dominant
+    kernel class of the low-rank, batched and gradient workloads): their
+    nominal bf16 digit-product flops per step over their summed event time
+    per step, against the sustained bf16 peak."""
+    t = sum(kernels.get(k, (0, 0.0))[1] for k in names) / max(steps, 1)
+    if t <= 0 or bf16_flops_per_step <= 0:
+        return None
+    peak, src = bf16_peak(sustained=True)
+    ach = bf16_flops_per_step / (t * 1e-3) / 1e12
+    top = max(kernels.items(), key=lambda kv: kv[1][1])[0] if kernels else None
+    return {"bound": "tensor", "kernel": "+".join(names), "dominant_by_time": top,
+            "ms_per_step": t, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "peak_source": src, "traffic": None,
+            "note": "28 bf16 digit-pair products per FP64-accurate product"}
+
+
 def run_batched(args):
     """512 uneven members: one ts_svd_batched graph launch per step, against
     one ts_svd call per member (the loop)."""
@@ -890,9 +911,43 @@ def run_batched(args):
                 pkg.ts_svd(A, drop_tol=0.0, mode=md, out=o)
         loop()
         loop_ms = _timed(torch, loop, 1)
+    # Roofline over the whole step (a graph replay's kernels are not timed one
+    # by one): the members' FP64-accurate tall products, 8 m n^2 each (both
+    # Gram matrices, A V~, Y W, U), as 28 digit-pair products on the tensor
+    # cores when every member ran FP64_TC.
+    roof = None
+    if set(modes) == {"fp64_tc"}:
+        peak, src = bf16_peak(sustained=True)
+        ach = 28.0 * sum(8.0 * m * n * n for m, n in shapes) / (ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "whole step (digit products of all members)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": src, "traffic": None,
+                "note": "lower bound of the products' own rate: the step's time includes the "
+                        "members' Jacobi solves"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's two-pass TS-SVD of the first members whose work adds up
+        # to about 2e10 nominal flops (a bounded sample of the same batch)
+        import oracle
+        t_s, f_s, used = 0.0, 0.0, 0
+        for A, (m, n) in zip(As, shapes):
+            Ah = A.cpu().numpy()
+            t0 = time.perf_counter()
+            oracle.ts_svd(Ah, passes=2, scale=True, drop_tol=0.0)
+            t_s += time.perf_counter() - t0
+            f_s += 6.0 * m * n * n
+            used += 1
+            if f_s >= 2e10 or used >= 4:
+                break
+        cpu = {"value": f_s / t_s / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": "two-pass TS-SVD of the batch's first %d members (%.2g nominal flops), "
+                         "%.1f s" % (used, f_s, t_s)}
     out = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "roofline": roof, "cpu_baseline": cpu,
+           "e2e": None, "e2e_note": "not measured: the batch's inputs are 53 GB of pinned host memory",
            "config": {"workload": args.workload, "members": len(shapes),
                       "m_range": list(w["m_range"]), "n_range": list(w["n_range"]),
                       "mode": mode, "modes_chosen": modes, "passes": 2, "scale": 1,
@@ -941,20 +996,77 @@ def run_lowrank(args):
     clocks = ClockSampler(0)
     clocks.start()
     L = pkg.lib()
+    set_fp64_peak(L)
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
     n0 = L.tssvd_launch_count()
     ms = _timed(torch, step, args.steps)
     clk = clocks.stop()
     launches = L.tssvd_launch_count() - n0
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
     U, S, V, info = step()
     flops = 2.0 * (2 * it + 2) * m * n * l
     eye = torch.eye(k, dtype=U.dtype, device=dev)
+    # roofline: the products with A, 2(2i+2) m n l FP64-accurate flops a
+    # step, as 28 digit-pair products on the tensor cores (FP64_TC), or on
+    # the FP64 pipe (FP64)
+    if mode == "fp64_tc":
+        roof = dominant_tensor_roofline(kernels, args.steps, 28.0 * flops)
+    else:
+        t = sum(v[1] for kname, v in kernels.items() if kname.startswith(("nn_", "tn_"))) / args.steps
+        roof = None if t <= 0 else {
+            "bound": "alu", "kernel": "nn_tall+tn_*", "achieved": flops / (t * 1e-3) / 1e12,
+            "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "peak_source": FP64_PEAK_SOURCE,
+            "frac": flops / (t * 1e-3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3), "traffic": None}
+    # end to end: A from pinned host memory, U, S, V back (one step)
+    e2e = None
+    if args.e2e_steps > 0:
+        Ah = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A)
+        Uh = torch.empty((m, k), dtype=torch.float64, pin_memory=True)
+        Sh = torch.empty((k,), dtype=torch.float64, pin_memory=True)
+        Vh = torch.empty((n, k), dtype=torch.float64, pin_memory=True)
+        Ad = torch.empty_like(A)
+
+        def e2e_step():
+            Ad.copy_(Ah, non_blocking=True)
+            if tsqr:
+                Uo, So, Vo, _ = pkg.lowrank_svd_tsqr(Ad, k, l, it, Om, theta, perm, drop_tol=0.0,
+                                                     mode=mode)
+            else:
+                Uo, So, Vo, _ = pkg.lowrank_svd(Ad, k, l, it, Om, drop_tol=0.0, mode=mode)
+            Uh.copy_(Uo, non_blocking=True)
+            Sh.copy_(So, non_blocking=True)
+            Vh.copy_(Vo, non_blocking=True)
+        e2e_step()
+        ms_e = _timed(torch, e2e_step, args.e2e_steps)
+        e2e = {"value": flops / (ms_e * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_e,
+               "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (m * k + k + n * k) * 8}
+        del Ah, Uh, Sh, Vh, Ad
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's Algorithm 8 on a 10,000-row sample of the same recipe
+        # (same n, k, l, power steps; its products are the bulk of its time)
+        import oracle
+        ms_rows = min(10_000, m)
+        As = A[:ms_rows].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.lowrank_svd(As, k, l, it, Om.cpu().numpy(), drop_tol=0.0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2.0 * (2 * it + 2) * ms_rows * n * l / dt / 1e9, "unit": "GFLOP/s",
+               "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "Algorithm 8 on the first %d of %d rows (n = %d, k = %d, l = %d, %d power "
+                         "steps), %.1f s" % (ms_rows, m, n, k, l, it, dt)}
     out = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "k": k, "l": l, "iters": it,
                       "mode": mode, "algorithm": 7 if tsqr else 8, "flops": "2(2i+2)mnl",
                       "l2": "inputs larger than L2 (A is %.0f GB)" % (m * n * 8 / 1e9)},
-           "gpu_launches": int(launches), "clocks": clk,
+           "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "e2e": e2e,
+           "cpu_baseline": cpu,
+           "kernels_ms": {kk: {"launches": c, "total_ms": t} for kk, (c, t) in kernels.items()},
            "accuracy": {"sigma_err_vs_signal_max": float((S - s[:k]).abs().max()),
                         "orth_U": float((U.T @ U - eye).abs().max()),
                         "orth_V": float((V.T @ V - eye).abs().max()), "rank": info["rank"]}}
@@ -1094,6 +1206,14 @@ def run_grad(args):
                       "flops": "8mn^2 (6mn^2 forward + 2mn^2 adjoint)",
                       "l2": "inputs larger than L2 (A is %.1f GB FP32)" % (m * n * 4 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
+           # the step's tall products as executed: forward 8 m n^2 (both Gram
+           # matrices, A V~, Y W, U), adjoint 8 m n^2 (U recomputed, U^T dU,
+           # [U | dU] times a 2n x n factor), 28 digit-pair products each
+           "roofline": (dominant_tensor_roofline(kernels, args.steps, 28.0 * 16.0 * m * n * n)
+                        if mode == "fp64_tc" else None),
+           "cpu_baseline": None,
+           "cpu_baseline_note": "not measured: the oracle's serial Jacobi solves at n = 512 "
+                                "take minutes",
            "accuracy": {"sigma_err_normwise": float((out["S"].double() - st).abs().max() / st[0]),
                         "orth_U": float((U.T @ U - torch.eye(n, dtype=U.dtype, device=dev)).abs().max()),
                         "grad_norm": float(out["G"].double().norm())},

@@ -52,17 +52,20 @@ typedef enum {
     TSSVD_FP64 = 0,
     /* Mixed: the first pass's products (Gram of A and A V~) run on the
      * tcgen05 tensor cores with BF16x3 split operands and FP32 accumulation
-     * drained to FP64; the second orthonormalisation pass, the eigensolves
-     * and all n x n work stay FP64.  Two bf16 terms per value (about 16
-     * significant bits), three term products per product.  n <= 256.
-     * Singular values to about 1e-6 of the largest; U orthonormal to 1e-12
-     * for condition numbers up to about 1e5 (beyond that the first pass
-     * leaves Y too ill-conditioned for the second to repair: 3.7e-12 at
-     * 1e6, 3e-11 at 1e8). */
+     * drained to FP64; the products of the later orthonormalisation
+     * pass(es) and the final U are FP64-accurate (the digit products of
+     * TSSVD_FP64_TC); eigensolves and all n x n work stay FP64.  Two bf16
+     * terms per value (about 16 significant bits), three term products per
+     * product.  n <= 256.  Singular values to about 1e-6 of the largest.
+     * With passes = 2, U is orthonormal to 1e-12 for condition numbers up
+     * to about 1e5 (measured 1.4e-12 at 1e6, 6.8e-12 at 1e8: the first
+     * pass leaves Y too ill-conditioned for one more pass to repair);
+     * passes = 3 adds a pass that brings it back under 1e-12. */
     TSSVD_BF16X3 = 1,
     /* As TSSVD_BF16X3 with three bf16 terms per value (about 24 significant
      * bits, the accuracy of FP32 inputs) and six term products. n <= 256.
-     * U orthonormal to 1e-12 for condition numbers up to about 1e5. */
+     * With passes = 2, U orthonormal to 1e-12 for condition numbers up to
+     * about 1e5 (1.9e-12 at 1e6, 2.7e-9 at 1e8); passes = 3 as above. */
     TSSVD_BF16X6 = 2,
     /* FP64-accurate products on the tensor cores: every tall product of
      * both passes is emulated with seven 7-bit integer digits per value
@@ -77,9 +80,15 @@ typedef enum {
 } tssvd_mode;
 
 typedef struct {
-    /* 1 = single orthonormalisation (Algorithm 3); 2 = double (Algorithm 4). */
+    /* 1 = single orthonormalisation (Algorithm 3); 2 = double (Algorithm 4);
+     * 3 = Algorithm 4 with its second pass (Gram of Y, eigendecomposition,
+     * Q = Y W T^-1, R <- T W^T R) run once more on Q, an opt-in repair for
+     * first passes too rough for one repair (the BF16-split modes at high
+     * condition numbers); it costs one more Gram, eigensolve and tall
+     * product, and an m x n double buffer in TSSVD_FP64 mode.  The TSQR
+     * methods (ts_svd_tsqr, lowrank_svd_tsqr) take 1 or 2. */
     int passes;
-    /* MaxEntry column scaling (2 = passes only): column j of A is divided by
+    /* MaxEntry column scaling (passes >= 2 only): column j of A is divided by
      * the smallest power of two >= max_i |A_ij| before the Gram matrix is
      * formed, and the scaling is folded back into the small SVD. */
     int scale;
@@ -100,7 +109,8 @@ typedef struct {
      * on its pivoted Cholesky factor), [1] eig of Y^T Y, [2] SVD of R;
      * for 256 < n <= 2048 the one-sided solves ([0] and [2]) start with an
      * FP32 phase, and [0], [2] count their FP64 sweeps while [3] holds the
-     * FP32 sweeps of both such solves, summed (0 when none ran) */
+     * FP32 sweeps of both such solves, summed (0 when none ran); with
+     * passes = 3, [1] is the third pass's eigensolve */
     int sweeps[4];
     int ranks[2];     /* ranks kept by the first and second discard steps */
 } tssvd_opts;

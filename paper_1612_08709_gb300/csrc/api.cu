@@ -113,7 +113,8 @@ cudaError_t shard_norms(const tssvd_comm *c, const double *NP, int g, i64 N, dou
 
 // ------------------------------------------------------------ TS-SVD core
 
-// Enqueues Algorithm 3 (passes == 1) or Algorithm 4 (passes == 2) on A
+// Enqueues Algorithm 3 (passes == 1) or Algorithm 4 (passes == 2; passes ==
+// 3 runs its second pass twice) on A
 // (m x n, lda, type T).  Writes U (m x n, ldu, type T), S (n) and V (n x n,
 // row-major, ldv) as doubles or T per the template parameters; all outputs
 // carry zeros past the numerical rank.  In sizing mode only the workspace
@@ -144,8 +145,10 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 {
     if (n <= kPcholMaxN) {
         CK(launch_pchol(B, (int)n, Xw, n, piv, s));
-        CK(launch_jacobi(Xw, n, Jw, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s, 0x1p-51));
-        CK(launch_jacobi_finalize(Xw, n, Jw, n, (int)n, (int)n, norms, perm, B2, n, lam, Xn, n, s));
+        CK(launch_jacobi(Xw, n, nullptr, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
+                         0x1p-51));
+        CK(launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n, lam,
+                                  Xn, n, s));
         return launch_row_scatter(Xn, piv, (int)n, Vt, s);
     }
     if (n <= kPcholGridMaxN) {
@@ -174,7 +177,8 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 // Otherwise the Gram-form solver.
 static cudaError_t second_eig(double *Z, double *Z2, i64 n, double *Xw, double *Jw, double *lam,
                               double *norms, double *W, int max_sweeps, int *ctr, double *prm,
-                              int *perm, DevStatus *st, cudaStream_t s, const JacobiMixedScratch &mw)
+                              int *perm, int *piv, DevStatus *st, cudaStream_t s,
+                              const JacobiMixedScratch &mw)
 {
     if (jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
         CK(launch_pchol_grid(Z, (int)n, Xw, n, (unsigned long long *)prm, st, s));
@@ -208,9 +212,8 @@ static cudaError_t final_svd(double *R, i64 n, const double *d, double *Xw, doub
 template <typename T, typename TO>
 cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                     int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                    cudaStream_t s, int mode = TSSVD_FP64, const tssvd_comm *comm = nullptr)
+                    cudaStream_t s, const tssvd_comm *comm = nullptr)
 {
-    const int terms = (passes == 2) ? mode_terms(mode) : 0;
     const bool sizing = ws.sizing();
     const i64 nn = n * n;
     int *ctr = ws.take<int>((size_t)max_sweeps + 4);
@@ -233,11 +236,9 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     int *perm = ws.take<int>(n), *piv = ws.take<int>(n);
     double *prm = ws.take<double>(jacobi_prm_doubles(n));
     double *B2 = ws.take<double>(nn);
-    double *Yt = (passes == 2) ? ws.take<double>((size_t)m * n) : nullptr;
-    const int tsp = terms ? tc_gram_splits(m) : 0;
-    double *Ptc = terms ? ws.take<double>((size_t)tsp * nn) : nullptr;
-    uint8_t *Bimg = terms ? ws.take<uint8_t>(tc_split_b_bytes((int)n, (int)n, terms)) : nullptr;
-    double *G2 = terms ? ws.take<double>(nn) : nullptr;
+    double *Yt = (passes >= 2) ? ws.take<double>((size_t)m * n) : nullptr;
+    // Q~ of the second pass, the third pass's input
+    double *Q2 = (passes == 3) ? ws.take<double>((size_t)m * n) : nullptr;
     if (sizing) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
 
@@ -277,66 +278,60 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
         CK(launch_pow2_scale(bits, n, d, dinv, s));
         rs1 = dinv;
     }
-    if (terms) {
-        // Mixed form of the first pass: both products on the tensor cores
-        // with BF16-split operands.  B = (A D^-1)^T (A D^-1).
-        CK(launch_tc_gram<T>(A, lda, m, (int)n, terms, tsp, Ptc, st, s));
-        CK(launch_tn_reduce(Ptc, tsp, n, n, rs1, rs1, true, B, n, s));
-    } else {
-        // B = (A D^-1)^T (A D^-1).
-        CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
-        CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
-    }
+    // B = (A D^-1)^T (A D^-1).
+    CK(launch_tn_partial<T, T>(A, lda, A, lda, m, n, n, sp1, true, P, s));
+    CK(launch_tn_reduce(P, sp1, n, n, rs1, rs1, true, B, n, s));
     CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
-    // B = V~ D~ V~^T (B consumed).  The BF16-split first pass leaves errors
-    // in B far above its FP64 rounding, the floor the Cholesky form assumes:
-    // it keeps the Gram-form solver.
-    if (terms)
-        CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
-                             s, true));
-    else
-        CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s,
-                     JacobiMixedScratch{B2, Jw, W, G, R, P, NP}));
+    // B = V~ D~ V~^T (B consumed).
+    CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s,
+                 JacobiMixedScratch{B2, Jw, W, G, R, P, NP}));
     // Y~ = (A D^-1) V~ = A (D^-1 V~); Sigma~ = explicit column norms.
     if (scale) {
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
         M1 = M;
     }
-    if (terms) {
-        CK(launch_tc_split_b(M1, n, (int)n, (int)n, terms, Bimg, s));
-        CK(launch_tc_nn<T>(A, lda, m, (int)n, Bimg, (int)n, terms, Yt, n, st, s));
-        // the explicit column norms of Y~ come from the diagonal of its
-        // FP64 Gram matrix, which the second pass forms anyway
-        CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
-        CK(launch_tn_reduce(P, sp1, n, n, nullptr, nullptr, true, G2, n, s));
-        CK(comm_allreduce(comm, G2, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
-        CK(launch_diag_sqrt(G2, n, n, sig, s));
-        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
-        CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
-    } else {
-        CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
-        CK(shard_norms(comm, NP, gy, n, sig, s));
-        // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
-        // products instead of a separate pass over Y.
-        CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
-        // Z = Y^T Y = Sigma~^-1 (Y~^T Y~) Sigma~^-1.
-        CK(launch_tn_partial<double, double>(Yt, n, Yt, n, m, n, n, sp1, true, P, s));
-        CK(launch_tn_reduce(P, sp1, n, n, sinv, sinv, true, B, n, s));
-        CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
-    }
-    // Z = W D W^T.
-    CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, st, s,
-                  JacobiMixedScratch{B2, Jw, G, R, Pm, P, NP}));
-    // Q~ = Y W = Y~ (Sigma~^-1 W); T = explicit column norms of Q~.
-    CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
-    CK(launch_nn<double, double>(Yt, n, M, n, m, n, n, (double *)nullptr, 0, NP, s));
-    CK(shard_norms(comm, NP, gy, n, Tn, s));
-    CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
-    CK(launch_keepval(Tn, tinv, n, Tk, s));
-    // R = T W^T Sigma~ V~^T D.
+    CK(launch_nn<T, double>(A, lda, M1, n, m, n, n, Yt, n, NP, s));
+    CK(shard_norms(comm, NP, gy, n, sig, s));
+    // Discard; Y = Y~ Sigma~^{-1} is kept implicit: sinv scales the next
+    // products instead of a separate pass over Y.
+    CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+    // R = T W^T Sigma~ V~^T D is built from G = Sigma~ V~^T D.
     CK(launch_build_g(sig, sinv, Vt, n, scale ? d : nullptr, n, G, s));
-    CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
-    CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+
+    // The second orthonormalisation pass on Y = Yin diag(cin); with
+    // passes = 3 once more on the second pass's Q = Q~ T^-1 (Q~ written
+    // out, T its explicit column norms): Yin = Q~, cin = T^-1 (zero for
+    // the columns the second pass dropped), and R <- T3 W3^T R, since
+    // Q = Q3 T3 W3^T.
+    const double *Yin = Yt;
+    const double *cin = sinv;
+    for (int pass = 2; pass <= passes; ++pass) {
+        const bool last = pass == passes;
+        // Z = Y^T Y = diag(cin) (Yin^T Yin) diag(cin).
+        CK(launch_tn_partial<double, double>(Yin, n, Yin, n, m, n, n, sp1, true, P, s));
+        CK(launch_tn_reduce(P, sp1, n, n, cin, cin, true, B, n, s));
+        CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
+        // Z = W D W^T.
+        CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, piv, st, s,
+                      JacobiMixedScratch{B2, Jw, M3, Pm, Vo, P, NP}));
+        // Q~ = Y W = Yin (diag(cin) W); T = explicit column norms of Q~
+        // (Q~ itself is written out only when another pass reads it).
+        CK(launch_scale2(W, n, n, n, cin, nullptr, M, n, s));
+        CK(launch_nn<double, double>(Yin, n, M, n, m, n, n, last ? (double *)nullptr : Q2,
+                                     last ? 0 : n, NP, s));
+        CK(shard_norms(comm, NP, gy, n, Tn, s));
+        CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
+        CK(launch_keepval(Tn, tinv, n, Tk, s));
+        // R = T W^T G (G = Sigma~ V~^T D in the second pass, the previous
+        // R in the third)
+        CK(launch_tn_partial<double, double>(W, n, pass == 2 ? G : R, n, n, n, n, sp2, false, P,
+                                             s));
+        CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+        if (!last) {
+            Yin = Q2;
+            cin = tinv;
+        }
+    }
     // R = P Sigma V^T by one-sided Jacobi (final_svd): on the columns of
     // R^T (R row-major = R^T column-major: R^T P = X, Sigma = column norms,
     // V = X Sigma^-1), or of R when the MaxEntry scaling is strongly graded
@@ -345,10 +340,11 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
                  perm, st, s, JacobiMixedScratch{B, B2, M3, G, W, P, NP}));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
-    // U = Q P = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
+    // U = Q P = Yin (diag(cin) W T^-1 P diag(sgn)) with the last pass's
+    // input, M = diag(cin) W and T.
     CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
     CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
-    CK(launch_nn<double, TO>(Yt, n, M3, n, m, n, n, U, ldu, NP, s));
+    CK(launch_nn<double, TO>(Yin, n, M3, n, m, n, n, U, ldu, NP, s));
     CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
     CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
     return cudaSuccess;
@@ -359,8 +355,13 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
 template <typename T, typename TO>
 cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                        int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                       cudaStream_t s, const tssvd_comm *comm = nullptr)
+                       cudaStream_t s, const tssvd_comm *comm = nullptr, int terms = 0)
 {
+    // terms > 0 (the BF16-split modes, two or three passes, n <= 256): the
+    // first pass's two products (Gram of A, A V~) are BF16-split
+    // tensor-core products with that many bf16 terms a value; the later
+    // passes and the final U stay FP64-accurate (digit products).
+    if (passes < 2) terms = 0;
     const bool sizing = ws.sizing();
     const i64 nn = n * n;
     int *ctr = ws.take<int>((size_t)max_sweeps + 4);
@@ -374,7 +375,8 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     double *P = ws.take<double>((size_t)(osp > sp2 ? osp : sp2) * nn);
     const int gcs = colsumsq_rows(m, n);
     const int gys = nn_grid_rows(n, n);
-    const bool fuse = oz_nn_fuses((int)n);  // column maxima from the product epilogue
+    // column maxima of Y~ from the digit product's epilogue
+    const bool fuse = !terms && oz_nn_fuses((int)n);
     double *NP = ws.take<double>((size_t)(gcs > gys ? gcs : gys) * n);
     uint8_t *img = ws.take<uint8_t>(oz_image_bytes((int)n, (int)n));
     double *B = ws.take<double>(nn), *G2 = ws.take<double>(nn), *Jw = ws.take<double>(nn);
@@ -393,7 +395,10 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
     uint8_t *big = ws.take<uint8_t>(gib > rib ? gib : rib);  // digit images of the tall operand
     const bool u_is_double = sizeof(TO) == sizeof(double);
-    double *Qt = (passes == 2 && !u_is_double) ? ws.take<double>((size_t)m * n) : nullptr;
+    double *Qt = (passes >= 2 && !u_is_double) ? ws.take<double>((size_t)m * n) : nullptr;
+    const int tsp = terms ? tc_gram_splits(m) : 0;
+    double *Ptc = terms ? ws.take<double>((size_t)tsp * nn) : nullptr;
+    uint8_t *Bimg = terms ? ws.take<uint8_t>(tc_split_b_bytes((int)n, (int)n, terms)) : nullptr;
     if (sizing) return cudaSuccess;
     if (ws.overflow) return cudaErrorMemoryAllocation;
 
@@ -402,7 +407,7 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_colmax<T>(A, m, n, lda, bits, s));
     CK(comm_allreduce(comm, bits, n, TSSVD_DT_U64, TSSVD_OP_MAX, s));
     CK(launch_oz_exp_from_bits(bits, (int)n, exA, s));
-    const bool sc = (passes == 2) && scale;
+    const bool sc = (passes >= 2) && scale;
     const double *rs1 = nullptr;
     const int *pkA = nullptr;
     if (sc) {
@@ -412,17 +417,28 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         pkA = pk1;
     }
     // B = (A D^-1)^T (A D^-1)
-    CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
-    // A's row image for Y~ = A (D^-1 V~) (A's columns prescaled by D^-1
-    // for the digit scales; the product is unchanged).  Building the row
-    // images beside the Jacobi kernels on a second stream was tried and
-    // slowed the latency-bound solves 2.5x (L2 and issue contention).
-    CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
-    CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
-    CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
+    if (terms) {
+        CK(launch_tc_gram<T>(A, lda, m, (int)n, terms, tsp, Ptc, st, s));
+        CK(launch_tn_reduce(Ptc, tsp, n, n, rs1, rs1, true, B, n, s));
+    } else {
+        CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
+        // A's row image for Y~ = A (D^-1 V~) (A's columns prescaled by D^-1
+        // for the digit scales; the product is unchanged).  Building the
+        // row images beside the Jacobi kernels on a second stream was tried
+        // and slowed the latency-bound solves 2.5x (L2 and issue contention).
+        CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
+        CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
+        CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
+    }
     CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
-    // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm 3)
-    if (passes == 2)
+    // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm
+    // 3).  A B from split products carries errors far above its FP64
+    // rounding, the floor the Cholesky form assumes: it takes the Gram-form
+    // solver with the normwise floor.
+    if (terms)
+        CK(launch_jacobi_eig(B, B2, n, Jw, n, lam, Vt, n, (int)n, max_sweeps, ctr, prm, perm, st, 0,
+                             s, true));
+    else if (passes >= 2)
         CK(first_eig(B, B2, n, Xw, Jw, Pm, lam, norms, Vt, max_sweeps, ctr, prm, perm, piv, st, s,
                      JacobiMixedScratch{B2, Jw, W, G, R, P, NP}));
     else
@@ -433,12 +449,18 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         CK(launch_scale2(Vt, n, n, n, dinv, nullptr, M, n, s));
         M1 = M;
     }
-    CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
-    // Y~, with its column maxima (the next Gram's digit scales) taken in the
-    // product's epilogue
-    if (fuse) CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
-    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Yt, n, st, s,
-                                fuse ? bits : nullptr, nullptr));
+    if (terms) {
+        // Y~ = A (D^-1 V~) by the split product (A itself, unscaled)
+        CK(launch_tc_split_b(M1, n, (int)n, (int)n, terms, Bimg, s));
+        CK(launch_tc_nn<T>(A, lda, m, (int)n, Bimg, (int)n, terms, Yt, n, st, s));
+    } else {
+        CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, em, img, s));
+        // Y~, with its column maxima (the next Gram's digit scales) taken in
+        // the product's epilogue
+        if (fuse) CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+        CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Yt, n, st, s,
+                                    fuse ? bits : nullptr, nullptr));
+    }
 
     if (passes == 1) {
         // Sigma = explicit column norms; U = U~ Sigma^-1 with the sign convention
@@ -457,52 +479,79 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         return cudaSuccess;
     }
 
-    // Z = Y^T Y with Y = Y~ Sigma~^-1; Sigma~ = explicit column norms of Y~
-    // (the diagonal of its Gram matrix)
-    if (!fuse) {
-        CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
-        CK(launch_colmax<double>(Yt, m, n, n, bits, s));
-    }
-    CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
-    CK(launch_oz_gram<double>(Yt, n, m, (int)n, exY, osp, big, P, st, s));
-    CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
-    CK(comm_allreduce(comm, G2, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
-    CK(launch_diag_sqrt(G2, n, n, sig, s));
-    CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
-    // Y~'s row image for Q~ = Y W = (Y~ 2^pk2) (2^-pk2 Sigma~^-1 W) and for
-    // the final U (both prescaled by pk2 = round(log2 Sigma~^-1))
-    CK(launch_oz_pow2_of(sinv, (int)n, pk2, s));
-    CK(launch_oz_rowexp<double>(Yt, n, m, (int)n, pk2, er, s));
-    CK(launch_oz_row_image<double>(Yt, n, m, (int)n, pk2, er, big, s));
-    CK(launch_scale2(G2, n, n, n, sinv, sinv, B, n, s));
-    // Z = W D W^T
-    CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, st, s,
-                  JacobiMixedScratch{B2, Jw, G, R, Pm, P, NP}));
-    // Q~; T = explicit column norms
-    CK(launch_scale2(W, n, n, n, sinv, nullptr, M, n, s));
-    CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
+    // The second orthonormalisation pass on Y = Yin diag(cin); with
+    // passes = 3 once more on the second pass's Q = Q~ T^-1: Yin = Q~
+    // (written out), cin = T^-1 (zero for the columns the second pass
+    // dropped) and R <- T3 W3^T R, since Q = Q3 T3 W3^T.  In the second
+    // pass cin = Sigma~^-1 from the diagonal of Y~'s Gram matrix.
     double *Qb = u_is_double ? (double *)U : Qt;
     const i64 ldq = u_is_double ? ldu : n;
-    // (the column sums of squares are a separate pass: in the product's
-    // epilogue their FP64 FMAs cost more than the pass they save)
-    CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Qb, ldq, st, s));
-    CK(launch_colsumsq(Qb, ldq, m, n, NP, s));
-    CK(shard_norms(comm, NP, gcs, n, Tn, s));
-    CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
-    CK(launch_keepval(Tn, tinv, n, Tk, s));
-    // R = T W^T Sigma~ V~^T D; R = P Sigma V^T
-    CK(launch_build_g(sig, sinv, Vt, n, sc ? d : nullptr, n, G, s));
-    CK(launch_tn_partial<double, double>(W, n, G, n, n, n, n, sp2, false, P, s));
-    CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+    const double *Yin = Yt;
+    i64 ldy = n;
+    const double *cin = sinv;
+    bool have_bits = fuse;  // column maxima of Yin from the producing product
+    for (int pass = 2; pass <= passes; ++pass) {
+        const bool last = pass == passes;
+        // Gram of Yin on the digit kernels (the local column maxima of Yin
+        // set the digit scales: any bound on the local values serves)
+        if (!have_bits) {
+            CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+            CK(launch_colmax<double>(Yin, m, n, ldy, bits, s));
+        }
+        CK(launch_oz_exp_from_bits(bits, (int)n, exY, s));
+        CK(launch_oz_gram<double>(Yin, ldy, m, (int)n, exY, osp, big, P, st, s));
+        CK(launch_tn_reduce(P, osp, n, n, nullptr, nullptr, true, G2, n, s));
+        CK(comm_allreduce(comm, G2, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
+        if (pass == 2) {
+            CK(launch_diag_sqrt(G2, n, n, sig, s));
+            CK(launch_discard(sig, n, tol, sinv, &st->rank1, s));
+        }
+        // Yin's row image for Q~ = Y W = (Yin 2^pk2) (2^-pk2 diag(cin) W)
+        // and, in the last pass, for the final U (both prescaled by pk2 =
+        // round(log2 cin))
+        CK(launch_oz_pow2_of(cin, (int)n, pk2, s));
+        CK(launch_oz_rowexp<double>(Yin, ldy, m, (int)n, pk2, er, s));
+        CK(launch_oz_row_image<double>(Yin, ldy, m, (int)n, pk2, er, big, s));
+        CK(launch_scale2(G2, n, n, n, cin, cin, B, n, s));
+        // Z = W D W^T
+        CK(second_eig(B, B2, n, Xw, Jw, lam, norms, W, max_sweeps, ctr, prm, perm, piv, st, s,
+                      JacobiMixedScratch{B2, Jw, M3, Pm, Vo, P, NP}));
+        // Q~; T = explicit column norms (the column sums of squares are a
+        // separate pass: in the product's epilogue their FP64 FMAs cost
+        // more than the pass they save).  Q~ goes to U's storage (or Qt);
+        // a third pass reads it, and its own Q~ (norms only) goes to Yt.
+        CK(launch_scale2(W, n, n, n, cin, nullptr, M, n, s));
+        CK(launch_oz_image(M, n, (int)n, (int)n, pk2, em, img, s));
+        double *Qo = (Yin == Yt) ? Qb : Yt;
+        const i64 ldo = (Yin == Yt) ? ldq : n;
+        have_bits = fuse && !last;
+        if (have_bits) CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
+        CK(launch_oz_nn_run<double>(big, m, (int)n, er, img, em, (int)n, Qo, ldo, st, s,
+                                    have_bits ? bits : nullptr, nullptr));
+        CK(launch_colsumsq(Qo, ldo, m, n, NP, s));
+        CK(shard_norms(comm, NP, gcs, n, Tn, s));
+        CK(launch_discard(Tn, n, tol, tinv, &st->rank2, s));
+        CK(launch_keepval(Tn, tinv, n, Tk, s));
+        // R = T W^T Sigma~ V~^T D (second pass), R <- T W^T R (third)
+        if (pass == 2) CK(launch_build_g(sig, sinv, Vt, n, sc ? d : nullptr, n, G, s));
+        CK(launch_tn_partial<double, double>(W, n, pass == 2 ? G : R, n, n, n, n, sp2, false, P,
+                                             s));
+        CK(launch_tn_reduce(P, sp2, n, n, Tk, nullptr, false, R, n, s));
+        if (!last) {
+            Yin = Qo;
+            ldy = ldo;
+            cin = tinv;
+        }
+    }
     CK(final_svd(R, n, sc ? d : nullptr, Xw, Jw, norms, Pm, sigma, Vo, max_sweeps, ctr, prm, perm,
                  st, s, JacobiMixedScratch{B, B2, M3, G, W, P, NP}));
     CK(launch_signs(Vo, n, n, n, sigma, sgn, s));
     CK(launch_count_positive(sigma, n, &st->rank, s));
-    // U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)), prescaled like Q~
+    // U = Yin (diag(cin) W T^-1 P diag(sgn)) with the last pass's input,
+    // prescaled like that pass's Q~ (Yin's row image is still in place)
     CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
     CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
     CK(launch_oz_image(M3, n, (int)n, (int)n, pk2, em, img, s));
-    // (Y~'s row image from the Q~ product is still in place)
     CK(launch_oz_nn_run<TO>(big, m, (int)n, er, img, em, (int)n, U, ldu, st, s));
     CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
     CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
@@ -518,8 +567,13 @@ cudaError_t ts_any(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO 
     if (mode == TSSVD_FP64_TC)
         return ts_core_oz<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps,
                                  ws, st, s, comm);
+    // The BF16-split modes: split products in the first pass, digit
+    // products (FP64-accurate) in the second (and third)
+    if ((mode == TSSVD_BF16X3 || mode == TSSVD_BF16X6) && passes >= 2)
+        return ts_core_oz<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps,
+                                 ws, st, s, comm, mode_terms(mode));
     return ts_core<T, TO>(A, m, n, lda, U, ldu, S, V, ldv, passes, scale, tol, max_sweeps, ws, st,
-                          s, mode, comm);
+                          s, comm);
 }
 
 // Status words are summarised into the ABI's status code.
@@ -572,7 +626,7 @@ int acquire_ws(tssvd_opts *o, size_t need, void **base, std::unique_lock<std::mu
 
 // ------------------------------------------------------------- batched
 
-constexpr int kWorkers = 16;  // worker streams of a batch
+constexpr int kWorkers = 32;  // worker streams of a batch
 
 struct WorkerStreams {
     bool ready = false;
@@ -775,8 +829,6 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaEventRecord(W.fork, s);
         for (int w = 0; w < kWorkers && e == cudaSuccess; w++) e = cudaStreamWaitEvent(W.w[w], W.fork, 0);
-        std::vector<Bump> slices;
-        for (int w = 0; w < kWorkers; w++) slices.emplace_back(slice_base[w], plan.slice[w]);
         for (int i : plan.order) {
             if (e != cudaSuccess) break;
             const int w = plan.worker[i];
@@ -832,7 +884,7 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
         if (h[i].err)
             code = TSSVD_ETIMEOUT;
         else {
-            const int solves = o->passes == 2 ? 3 : 1;
+            const int solves = o->passes >= 2 ? 3 : 1;
             for (int j = 0; j < solves; j++)
                 if (h[i].sweeps[j] < 0) code = TSSVD_ENOCONV;
             if (code == TSSVD_OK && h[i].rank < d[i].n) code = TSSVD_RANKDEF;
@@ -845,10 +897,12 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
     return first;
 }
 
-int check_opts(const tssvd_opts *o)
+// passes: 1 (Algorithm 3), 2 (Algorithm 4) or 3 (Algorithm 4 with its
+// second pass run twice); the TSQR methods take 1 or 2 (max_passes 2).
+int check_opts(const tssvd_opts *o, int max_passes = 3)
 {
     if (!o) return 0;
-    if (o->passes != 1 && o->passes != 2) return 0;
+    if (o->passes < 1 || o->passes > max_passes) return 0;
     if (!(o->drop_tol >= 0.0) || o->drop_tol >= 1.0) return 0;
     if (o->max_sweeps < 1 || o->max_sweeps > 1000) return 0;
     if (o->mode < TSSVD_FP64 || o->mode > TSSVD_FP64_TC) return 0;
@@ -932,11 +986,11 @@ int ts_svd_entry(const T *A, int64_t m, int64_t n, int64_t lda, T *U, T *S, T *V
         return TSSVD_ECUDA;
     }
     std::vector<DevStatus> v(1, h);
-    int code = summarise(v, opts->passes == 2 ? 3 : 1, nullptr);
+    int code = summarise(v, opts->passes >= 2 ? 3 : 1, nullptr);
     opts->out_rank = h.rank;
     for (int i = 0; i < 4; i++) opts->sweeps[i] = h.sweeps[i];
     opts->ranks[0] = h.rank1;
-    opts->ranks[1] = opts->passes == 2 ? h.rank2 : h.rank1;
+    opts->ranks[1] = opts->passes >= 2 ? h.rank2 : h.rank1;
     if (code == TSSVD_OK && h.rank < n) code = TSSVD_RANKDEF;
     return code;
 }
@@ -1406,7 +1460,7 @@ int tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, const double 
     if (!U) return -7;
     if (!S) return -8;
     if (!V) return -9;
-    if (!check_opts(opts)) return -10;
+    if (!check_opts(opts, 2)) return -10;
     if (opts->mode != TSSVD_FP64 && opts->mode != TSSVD_FP64_TC) return -10;
     const bool oz = opts->mode == TSSVD_FP64_TC;
     cudaStream_t s = (cudaStream_t)opts->stream;
@@ -1480,7 +1534,7 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
     if (!U) return -11;
     if (!S) return -12;
     if (!V) return -13;
-    if (!check_opts(opts)) return -14;
+    if (!check_opts(opts, 2)) return -14;
     if (opts->mode != TSSVD_FP64 && opts->mode != TSSVD_FP64_TC) return -14;
     cudaStream_t s = (cudaStream_t)opts->stream;
     const bool oz = opts->mode == TSSVD_FP64_TC;
@@ -1874,7 +1928,7 @@ int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opt
     if (!descs) return -1;
     if (count < 1) return -2;
     if (elem_bytes != 4 && elem_bytes != 8) return -3;
-    if (!opts || opts->passes < 1 || opts->passes > 2 || !(opts->drop_tol >= 0.0) ||
+    if (!opts || opts->passes < 1 || opts->passes > 3 || !(opts->drop_tol >= 0.0) ||
         opts->drop_tol >= 1.0 || opts->max_sweeps < 1 || opts->max_sweeps > 1000 ||
         opts->mode < TSSVD_FP64 || opts->mode > TSSVD_AUTO)
         return -4;

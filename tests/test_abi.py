@@ -73,7 +73,9 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     assert L.ts_svd(p, 10, 0, 3, p, p, p, ctypes.byref(o)) == -3
     assert L.ts_svd(p, 10, 3, 2, p, p, p, ctypes.byref(o)) == -4
     assert L.ts_svd(p, 10, 3, 3, None, p, p, ctypes.byref(o)) == -5
-    o.passes = 3
+    o.passes = 4
+    assert L.ts_svd(p, 10, 3, 3, p, p, p, ctypes.byref(o)) == -8
+    o.passes = 0
     assert L.ts_svd(p, 10, 3, 3, p, p, p, ctypes.byref(o)) == -8
     L.tssvd_default_opts(ctypes.byref(o))
     assert L.lowrank_svd(p, 10, 8, 8, 5, 4, 2, p, p, p, p, ctypes.byref(o)) == -5
@@ -98,7 +100,7 @@ def test_pca_argument_validation_without_gpu():
     assert L.ts_pca(f, 10, 2, 2, f, f, None, f, ctypes.byref(o)) == -7
     assert L.ts_pca(f, 10, 2, 2, f, f, f, None, ctypes.byref(o)) == -8
     assert L.ts_pca(f, 10, 2, 2, f, f, f, f, None) == -9
-    o.passes = 3
+    o.passes = 4
     assert L.ts_pca(f, 10, 2, 2, f, f, f, f, ctypes.byref(o)) == -9
     # the workspace query is host arithmetic: the SVD's plus the centred copy
     L.tssvd_default_opts(ctypes.byref(o))
@@ -125,6 +127,8 @@ def test_tsqr_argument_validation_without_gpu():
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, None, f, ctypes.byref(o)) == -8
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, None, ctypes.byref(o)) == -9
     assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, f, None) == -10
+    o.passes = 3  # Algorithms 1 and 2 only: no third pass
+    assert L.ts_svd_tsqr(f, 10, 2, 2, f, f, f, f, f, ctypes.byref(o)) == -10
 
 
 def test_lowrank_tsqr_argument_validation_without_gpu():

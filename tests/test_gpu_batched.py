@@ -37,6 +37,26 @@ def test_batched_equals_per_member_calls(mode):
 
 
 @gpu
+def test_batched_wide_members_match_oracle(orc):
+    """Members with n from 100 to 256: the batch gives the oracle's SVD,
+    member by member."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    shapes, mats = _members(6, 9, m_range=(2000, 30000), n_range=(100, 256))
+    As = [torch.as_tensor(A, device="cuda") for A in mats]
+    outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=0.0, mode="fp64_tc")
+    for A, (U, S, V), info in zip(mats, outs, infos):
+        Ur, Sr, Vr, rr, st = orc.ts_svd(A, drop_tol=0.0)
+        n = A.shape[1]
+        S, U, V = S.cpu().numpy(), U.cpu().numpy(), V.cpu().numpy()
+        assert info["rank"] == rr == n
+        assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+        assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-12
+        assert np.abs(V.T @ V - np.eye(n)).max() <= 1e-12
+        assert np.abs(A @ V - U * S).max() <= 1e-10 * Sr[0]
+
+
+@gpu
 def test_batched_replay_and_oracle(orc):
     torch = _torch()
     import paper_1612_08709_gb300 as pkg

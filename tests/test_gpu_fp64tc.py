@@ -109,3 +109,40 @@ def test_fp64tc_fp32_storage(orc):
     U = U.double().cpu().numpy()
     assert np.abs(S - ref[1]).max() <= 1e-6 * ref[1][0]
     assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-5
+
+
+@gpu
+@pytest.mark.parametrize("mode", ["fp64_tc", "fp64"])
+@pytest.mark.parametrize("m,n,lo,seed,rank", [(20000, 50, 1e-8, 11, 50), (3001, 130, 1e-6, 12, 130),
+                                              (5000, 60, 1e-4, 13, 40)])
+def test_three_passes_match_oracle(orc, mode, m, n, lo, seed, rank):
+    """passes = 3 (the second pass of Algorithm 4 run once more on Q):
+    the same SVD as the oracle's two passes, to the two-pass tolerances;
+    columns dropped by the second pass stay dropped (rank 40 of 60: the
+    trailing singular values are exact zeros)."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    s = workloads.sigma_geometric(n, lo)
+    s[rank:] = 0.0
+    A, _, _, _ = workloads.known_spectrum(m, n, s, seed)
+    tol = 0.0 if rank == n else 1e-6
+    Ur, Sr, Vr, rr, st = orc.ts_svd(A, passes=2, scale=True, drop_tol=tol)
+    U, S, V, info = pkg.ts_svd(torch.as_tensor(A, device="cuda"), passes=3, scale=True,
+                               drop_tol=tol, mode=mode)
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    assert info["rank"] == rr == rank
+    assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+    r = rr
+    assert np.abs(U[:, :r].T @ U[:, :r] - np.eye(r)).max() <= 1e-12
+    assert np.abs(V[:, :r].T @ V[:, :r] - np.eye(r)).max() <= 1e-12
+    g = np.full(r, np.inf)
+    for j in range(r):
+        if j > 0:
+            g[j] = min(g[j], Sr[j - 1] - Sr[j])
+        if j + 1 < r:
+            g[j] = min(g[j], Sr[j] - Sr[j + 1])
+    tolv = np.clip(1e-10 * Sr[0] / g, 1e-13, 1.0)
+    assert np.all(_col_err(V[:, :r], Vr[:, :r]) <= tolv)
+    assert np.all(_col_err(U[:, :r], Ur[:, :r]) <= tolv)
+    assert np.all(S[r:] == 0) and np.all(U[:, r:] == 0) and np.all(V[:, r:] == 0)
+    assert np.abs(A @ V - U * S).max() <= 1e-10 * Sr[0]
