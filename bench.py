@@ -57,6 +57,8 @@ WORKLOADS = {
     # 512 uneven tall-skinny SVDs in one graph launch (m in [1e3, 2e5], n in
     # [16, 256], sigma log-uniform in [1e-6, 1])
     "batch_512": dict(kind="batch", count=512, m_range=(1000, 200000), n_range=(16, 256), seed=5),
+    # a small batch of the same recipe for profiling captures
+    "batch_32": dict(kind="batch", count=32, m_range=(1000, 40000), n_range=(16, 256), seed=5),
     # randomized low-rank SVD of a 100,000 x 20,000 matrix (rank-200 signal
     # with sigma_j = 1/j plus 1e-4 Gaussian noise), k = 50, l = 60, 2 power steps
     "lowrank_100k_x_20k": dict(kind="lowrank", m=100_000, n=20_000, r=200, k=50, l=60, iters=2,
@@ -951,6 +953,8 @@ def run_batched(args):
            "config": {"workload": args.workload, "members": len(shapes),
                       "m_range": list(w["m_range"]), "n_range": list(w["n_range"]),
                       "mode": mode, "modes_chosen": modes, "passes": 2, "scale": 1,
+                      "executor": "phased" if (mode in ("auto", "fp64_tc") and
+                                               max(n for _, n in shapes) <= 256) else "per member",
                       "l2": "inputs larger than L2 (%.0f GB)" % (sum(m * n for m, n in shapes) * 8 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
            "accuracy": {"sigma_err_normwise_max": err, "orth_U_max": orth},

@@ -392,7 +392,16 @@ typedef struct {
  * element type (elem_bytes 8 = double, 4 = float) and the same options.
  * The members are ordered largest first and spread over worker streams;
  * members on one worker stream run one after another and share one slice
- * of the workspace (ts_svd_batched_workspace_size).  The whole batch is
+ * of the workspace (ts_svd_batched_workspace_size).  When every member has
+ * n <= 256, passes = 2 and the mode is TSSVD_FP64_TC or TSSVD_AUTO, the
+ * batch runs in phases instead: the members' tall products and small steps
+ * on the worker streams, and each of the three Jacobi solves of all members
+ * as one launch with one thread block per member (the eigensolves
+ * one-sided on the pivoted Cholesky factor); every member then runs
+ * TSSVD_FP64_TC, its per-solve state is kept in the workspace between the
+ * phases, and for double members U's storage holds Y~ until U is written.
+ * Results match single calls to rounding (bit for bit on the per-member
+ * path).  The whole batch is
  * captured once into a CUDA graph, which is cached by the batch's
  * descriptors and options and replayed on later calls with the same ones;
  * one graph launch on opts->stream runs the batch.  Returns after the

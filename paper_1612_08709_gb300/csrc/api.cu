@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -716,6 +717,429 @@ int check_member(const tssvd_desc &d, int mode)
     return 0;
 }
 
+// Replays a batch graph on s and turns the members' status blocks into
+// their status codes (the first failure is returned).
+int finish_batch(BatchGraph *g, tssvd_desc *d, int count, const tssvd_opts *o, DevStatus *sts,
+                 const std::vector<int> &modes, cudaStream_t s)
+{
+    std::vector<DevStatus> h(count);
+    if (cudaGraphLaunch(g->exec, s) != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), sts, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TSSVD_ECUDA;
+    }
+    int first = TSSVD_OK;
+    for (int i = 0; i < count; i++) {
+        int code = TSSVD_OK;
+        if (h[i].err)
+            code = TSSVD_ETIMEOUT;
+        else {
+            const int solves = o->passes >= 2 ? 3 : 1;
+            for (int j = 0; j < solves; j++)
+                if (h[i].sweeps[j] < 0) code = TSSVD_ENOCONV;
+            if (code == TSSVD_OK && h[i].rank < d[i].n) code = TSSVD_RANKDEF;
+        }
+        d[i].status = code;
+        d[i].out_rank = h[i].rank;
+        d[i].mode = modes[i];
+        if (first == TSSVD_OK && code != TSSVD_OK) first = code;
+    }
+    return first;
+}
+
+// Pinned host copies of the three task arrays of a cached phased graph
+// (the graph copies them to the device at the start of every replay).
+struct PinnedTasks {
+    JacobiTask *h = nullptr;
+    ~PinnedTasks()
+    {
+        if (h) cudaFreeHost(h);
+    }
+};
+std::vector<std::pair<std::vector<unsigned long long>, std::shared_ptr<PinnedTasks>>> g_phased_tasks;
+
+void evict_tasks(const std::vector<unsigned long long> &key)
+{
+    for (size_t k = 0; k < g_phased_tasks.size(); k++)
+        if (g_phased_tasks[k].first == key) {
+            g_phased_tasks.erase(g_phased_tasks.begin() + (long)k);
+            return;
+        }
+}
+
+// ------------------------------------------------ phased batch (FP64_TC)
+//
+// The batch of members with n <= kJacobiBatchMaxN in the FP64-accurate
+// tensor-core form (Algorithm 4 per member) runs in phases: the members'
+// tall products and small steps go to the worker streams, and each of the
+// three Jacobi solves of every member runs in one launch of the batched
+// solver (one CTA per member, jacobi_batch.cu) between them:
+//   A: column maxima, Gram of A, pivoted Cholesky of B    | solve 1 (eig 1)
+//   B: eigenvectors, Y~ = A (D^-1 V~), Gram of Y~, pivoted Cholesky of Z
+//                                                          | solve 2 (eig 2)
+//   C: W, Q~ and T, R = T W^T Sigma~ V~^T D                | solve 3 (SVD of R)
+//   D: P, Sigma, V, U = Y~ (Sigma~^-1 W T^-1 P)
+// Both eigensolves are one-sided on the pivoted Cholesky factor without
+// accumulation (the factor's orthogonalised columns are the eigenvectors),
+// the SVD of R one-sided with accumulation, as in the single-call path.
+// State that lives across a solve (the n x n factors, V~, W, the scales,
+// Y~) is kept per member; digit images, partial sums and the other n x n
+// temporaries are per worker, sized for the worker's largest member.  For
+// double outputs Y~ lives in U's storage (U's row image is built from it
+// before the final product overwrites it).
+
+struct PhasedMember {
+    double *X, *J, *Vt, *W;                // n x n
+    double *d, *dinv, *sig, *sinv, *tinv;  // n
+    int *pk1, *piv, *pk2;                  // n
+    double *Y;                             // m x n: Y~
+};
+
+struct PhasedScratch {
+    unsigned long long *bits;
+    int *exA, *exY, *em, *er, *perm;
+    double *P, *NP, *Qw;
+    uint8_t *img, *big;
+    double *B, *G2, *G, *R, *M, *M3, *Pm, *Vo, *Pp, *Xn;
+    double *lam, *norms, *Tn, *Tk, *sgn, *sigma, *jn;
+};
+
+void take_member(Bump &b, i64 m, i64 n, bool own_y, PhasedMember &p)
+{
+    const i64 nn = n * n;
+    p.X = b.take<double>(nn);
+    p.J = b.take<double>(nn);
+    p.Vt = b.take<double>(nn);
+    p.W = b.take<double>(nn);
+    p.d = b.take<double>(n);
+    p.dinv = b.take<double>(n);
+    p.sig = b.take<double>(n);
+    p.sinv = b.take<double>(n);
+    p.tinv = b.take<double>(n);
+    p.pk1 = b.take<int>(n);
+    p.piv = b.take<int>(n);
+    p.pk2 = b.take<int>(n);
+    p.Y = own_y ? b.take<double>((size_t)m * n) : nullptr;
+}
+
+void take_scratch(Bump &b, i64 m, i64 n, PhasedScratch &c)
+{
+    const i64 nn = n * n;
+    c.bits = b.take<unsigned long long>(n);
+    c.exA = b.take<int>(n);
+    c.exY = b.take<int>(n);
+    c.em = b.take<int>(n);
+    c.perm = b.take<int>(n);
+    c.er = b.take<int>(m);
+    const int osp = oz_gram_splits(m, (int)n), sp2 = tn_splits(n, n, n, false);
+    c.P = b.take<double>((size_t)(osp > sp2 ? osp : sp2) * nn);
+    const int gcs = colsumsq_rows(m, n), gys = nn_grid_rows(n, n);
+    c.NP = b.take<double>((size_t)(gcs > gys ? gcs : gys) * n);
+    c.Qw = b.take<double>((size_t)m * n);
+    c.img = b.take<uint8_t>(oz_image_bytes((int)n, (int)n));
+    const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
+    c.big = b.take<uint8_t>(gib > rib ? gib : rib);
+    double **nxn[] = {&c.B, &c.G2, &c.G, &c.R, &c.M, &c.M3, &c.Pm, &c.Vo, &c.Pp, &c.Xn};
+    for (double **q : nxn) *q = b.take<double>(nn);
+    double **vec[] = {&c.lam, &c.norms, &c.Tn, &c.Tk, &c.sgn, &c.sigma, &c.jn};
+    for (double **q : vec) *q = b.take<double>(n);
+}
+
+bool phased_applies(const tssvd_desc *d, int count, const tssvd_opts *o)
+{
+    if (o->passes != 2 || (o->mode != TSSVD_FP64_TC && o->mode != TSSVD_AUTO)) return false;
+    for (int i = 0; i < count; i++)
+        if (d[i].n < 1 || d[i].n > kJacobiBatchMaxN) return false;
+    return true;
+}
+
+struct PhasedPlan {
+    std::vector<int> order, worker;  // members by decreasing work; their workers
+    std::vector<size_t> member_off;  // byte offsets of the members' state
+    std::vector<size_t> slice_off, slice;  // workers' scratch
+    size_t status_bytes = 0, tasks_off = 0, total = 0;
+};
+
+template <typename T>
+PhasedPlan make_phased_plan(const tssvd_desc *d, int count)
+{
+    PhasedPlan p;
+    p.order.resize(count);
+    for (int i = 0; i < count; i++) p.order[i] = i;
+    auto work = [&](int i) { return (double)d[i].m * (double)d[i].n * (double)d[i].n; };
+    std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) { return work(a) > work(b); });
+    p.worker.assign(count, 0);
+    std::vector<double> load(kWorkers, 0.0);
+    p.slice.assign(kWorkers, 0);
+    for (int i : p.order) {
+        const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        p.worker[i] = w;
+        load[w] += work(i);
+        Bump sz(nullptr, 0);
+        PhasedScratch c;
+        take_scratch(sz, d[i].m, d[i].n, c);
+        p.slice[w] = std::max(p.slice[w], (sz.off + 255) & ~(size_t)255);
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = up(sizeof(DevStatus) * (size_t)count);
+    p.status_bytes = off;
+    p.tasks_off = off;
+    off += up(sizeof(JacobiTask) * 3 * (size_t)count);
+    p.member_off.resize(count);
+    const bool own_y = sizeof(T) != sizeof(double);
+    for (int i = 0; i < count; i++) {
+        p.member_off[i] = off;
+        Bump sz(nullptr, 0);
+        PhasedMember pm;
+        take_member(sz, d[i].m, d[i].n, own_y, pm);
+        off += up(sz.off);
+    }
+    p.slice_off.resize(kWorkers);
+    for (int w = 0; w < kWorkers; w++) {
+        p.slice_off[w] = off;
+        off += p.slice[w];
+    }
+    p.total = off;
+    return p;
+}
+
+// Segment A of member i: column maxima, Gram of A, pivoted Cholesky of B.
+template <typename T>
+cudaError_t phase_a(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
+                    PhasedScratch &c, DevStatus *st, cudaStream_t s)
+{
+    const T *A = (const T *)dd.A;
+    const i64 m = dd.m, n = dd.n, lda = dd.lda;
+    CK(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+    CK(cudaMemsetAsync(c.bits, 0, sizeof(unsigned long long) * n, s));
+    CK(launch_colmax<T>(A, m, n, lda, c.bits, s));
+    CK(launch_oz_exp_from_bits(c.bits, (int)n, c.exA, s));
+    if (o->scale) {
+        CK(launch_pow2_scale(c.bits, n, p.d, p.dinv, s));
+        CK(launch_neg_int(c.exA, (int)n, p.pk1, s));
+    }
+    const int osp = oz_gram_splits(m, (int)n);
+    CK(launch_oz_gram<T>(A, lda, m, (int)n, c.exA, osp, c.big, c.P, st, s));
+    const double *rs = o->scale ? p.dinv : nullptr;
+    CK(launch_tn_reduce(c.P, osp, n, n, rs, rs, true, c.B, n, s));
+    return launch_pchol(c.B, (int)n, p.X, n, p.piv, s);
+}
+
+// Segment B: V~ from the solved factor, Y~ = A (D^-1 V~), its Gram Z,
+// Sigma~, the discard, and the pivoted Cholesky of Z.
+template <typename T>
+cudaError_t phase_b(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
+                    PhasedScratch &c, DevStatus *st, cudaStream_t s)
+{
+    const T *A = (const T *)dd.A;
+    const i64 m = dd.m, n = dd.n, lda = dd.lda;
+    CK(launch_jacobi_finalize(p.X, n, nullptr, n, (int)n, (int)n, c.norms, c.perm, nullptr, n,
+                              c.lam, c.Xn, n, s));
+    CK(launch_row_scatter(c.Xn, p.piv, (int)n, p.Vt, s));
+    const double *M1 = p.Vt;
+    const int *pkA = o->scale ? p.pk1 : nullptr;
+    if (o->scale) {
+        CK(launch_scale2(p.Vt, n, n, n, p.dinv, nullptr, c.M, n, s));
+        M1 = c.M;
+    }
+    CK(launch_oz_image(M1, n, (int)n, (int)n, pkA, c.em, c.img, s));
+    CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, c.er, s));
+    CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, c.er, c.big, s));
+    const bool fuse = oz_nn_fuses((int)n);
+    CK(cudaMemsetAsync(c.bits, 0, sizeof(unsigned long long) * n, s));
+    CK(launch_oz_nn_run<double>(c.big, m, (int)n, c.er, c.img, c.em, (int)n, p.Y, n, st, s,
+                                fuse ? c.bits : nullptr, nullptr));
+    if (!fuse) CK(launch_colmax<double>(p.Y, m, n, n, c.bits, s));
+    CK(launch_oz_exp_from_bits(c.bits, (int)n, c.exY, s));
+    const int osp = oz_gram_splits(m, (int)n);
+    CK(launch_oz_gram<double>(p.Y, n, m, (int)n, c.exY, osp, c.big, c.P, st, s));
+    CK(launch_tn_reduce(c.P, osp, n, n, nullptr, nullptr, true, c.G2, n, s));
+    CK(launch_diag_sqrt(c.G2, n, n, p.sig, s));
+    CK(launch_discard(p.sig, n, o->drop_tol, p.sinv, &st->rank1, s));
+    CK(launch_scale2(c.G2, n, n, n, p.sinv, p.sinv, c.B, n, s));
+    return launch_pchol(c.B, (int)n, p.X, n, p.piv, s);
+}
+
+// Segment C: W from the solved factor, Q~ = Y W and its explicit norms T,
+// the discard, R = T W^T Sigma~ V~^T D, oriented for the one-sided SVD.
+cudaError_t phase_c(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
+                    PhasedScratch &c, DevStatus *st, cudaStream_t s)
+{
+    const i64 m = dd.m, n = dd.n;
+    CK(launch_jacobi_finalize(p.X, n, nullptr, n, (int)n, (int)n, c.norms, c.perm, nullptr, n,
+                              c.lam, c.Xn, n, s));
+    CK(launch_row_scatter(c.Xn, p.piv, (int)n, p.W, s));
+    CK(launch_oz_pow2_of(p.sinv, (int)n, p.pk2, s));
+    CK(launch_oz_rowexp<double>(p.Y, n, m, (int)n, p.pk2, c.er, s));
+    CK(launch_oz_row_image<double>(p.Y, n, m, (int)n, p.pk2, c.er, c.big, s));
+    CK(launch_scale2(p.W, n, n, n, p.sinv, nullptr, c.M, n, s));
+    CK(launch_oz_image(c.M, n, (int)n, (int)n, p.pk2, c.em, c.img, s));
+    CK(launch_oz_nn_run<double>(c.big, m, (int)n, c.er, c.img, c.em, (int)n, c.Qw, n, st, s));
+    CK(launch_colsumsq(c.Qw, n, m, n, c.NP, s));
+    CK(launch_norms_reduce(c.NP, colsumsq_rows(m, n), n, c.Tn, s));
+    CK(launch_discard(c.Tn, n, o->drop_tol, p.tinv, &st->rank2, s));
+    CK(launch_keepval(c.Tn, p.tinv, n, c.Tk, s));
+    const double *dsc = o->scale ? p.d : nullptr;
+    CK(launch_build_g(p.sig, p.sinv, p.Vt, n, dsc, n, c.G, s));
+    const int sp2 = tn_splits(n, n, n, false);
+    CK(launch_tn_partial<double, double>(p.W, n, c.G, n, n, n, n, sp2, false, c.P, s));
+    CK(launch_tn_reduce(c.P, sp2, n, n, c.Tk, nullptr, false, c.R, n, s));
+    return launch_orient_copy(dsc, &st->rank2, c.R, n, p.X, &st->orient, s);
+}
+
+// Segment D: P, Sigma, V from the solved R, signs, rank, and
+// U = Y~ (Sigma~^-1 W T^-1 P diag(sgn)).
+template <typename T>
+cudaError_t phase_d(const tssvd_desc &dd, PhasedMember &p, PhasedScratch &c, DevStatus *st,
+                    cudaStream_t s)
+{
+    const i64 m = dd.m, n = dd.n;
+    CK(launch_jacobi_finalize(p.X, n, p.J, n, (int)n, (int)n, c.norms, c.perm, c.Pm, n, c.sigma,
+                              c.Vo, n, s, &st->orient, c.jn));
+    CK(launch_signs(c.Vo, n, n, n, c.sigma, c.sgn, s));
+    CK(launch_count_positive(c.sigma, n, &st->rank, s));
+    CK(launch_scale2(c.Pm, n, n, n, p.tinv, c.sgn, c.Pp, n, s));
+    CK(launch_scale2(p.W, n, n, n, p.sinv, nullptr, c.M, n, s));
+    CK(launch_nn<double, double>(c.M, n, c.Pp, n, n, n, n, c.M3, n, c.NP, s));
+    CK(launch_oz_rowexp<double>(p.Y, n, m, (int)n, p.pk2, c.er, s));
+    CK(launch_oz_row_image<double>(p.Y, n, m, (int)n, p.pk2, c.er, c.big, s));
+    CK(launch_oz_image(c.M3, n, (int)n, (int)n, p.pk2, c.em, c.img, s));
+    CK(launch_oz_nn_run<T>(c.big, m, (int)n, c.er, c.img, c.em, (int)n, (T *)dd.U, n, st, s));
+    CK(launch_convert<T>(c.sigma, n, 1, n, (T *)dd.S, n, s));
+    return launch_convert<T>(c.Vo, n, n, n, (T *)dd.V, n, s);
+}
+
+template <typename T>
+int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSSVD_ECUDA;
+    std::lock_guard<std::mutex> glk(g_batch_mu);
+    if (ensure_workers(dev)) return TSSVD_ECUDA;
+    WorkerStreams &W = g_workers[dev];
+    cudaStream_t s = o->stream ? (cudaStream_t)o->stream : W.own;
+    for (int i = 0; i < count; i++)
+        if (check_member(d[i], TSSVD_FP64_TC)) return -(100 + i);
+    PhasedPlan plan = make_phased_plan<T>(d, count);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(o, plan.total + 256, &base, lk);
+    if (rc) return rc;
+    base = (void *)(((size_t)base + 255) & ~(size_t)255);
+    char *cb = (char *)base;
+    DevStatus *sts = (DevStatus *)base;
+    JacobiTask *dtasks = (JacobiTask *)(cb + plan.tasks_off);
+    const bool own_y = sizeof(T) != sizeof(double);
+    std::vector<PhasedMember> pm(count);
+    for (int i = 0; i < count; i++) {
+        Bump b(cb + plan.member_off[i], (size_t)1 << 62);
+        take_member(b, d[i].m, d[i].n, own_y, pm[i]);
+        if (!own_y) pm[i].Y = (double *)d[i].U;
+    }
+
+    std::vector<unsigned long long> key;
+    key.push_back(0x9a5edULL);  // phased graphs apart from the per-member ones
+    key.push_back((unsigned long long)count);
+    key.push_back((unsigned long long)sizeof(T));
+    key.push_back((unsigned long long)(uintptr_t)base);
+    key.push_back((unsigned long long)(uintptr_t)s);
+    unsigned long long tolbits;
+    std::memcpy(&tolbits, &o->drop_tol, 8);
+    key.push_back(tolbits);
+    key.push_back(((unsigned long long)o->scale << 16) | (unsigned long long)o->max_sweeps);
+    for (int i = 0; i < count; i++) {
+        key.push_back((unsigned long long)(uintptr_t)d[i].A);
+        key.push_back((unsigned long long)(uintptr_t)d[i].U);
+        key.push_back((unsigned long long)(uintptr_t)d[i].S);
+        key.push_back((unsigned long long)(uintptr_t)d[i].V);
+        key.push_back((unsigned long long)d[i].m);
+        key.push_back((unsigned long long)d[i].n);
+        key.push_back((unsigned long long)d[i].lda);
+    }
+    BatchGraph *g = nullptr;
+    for (auto &bg : g_graphs)
+        if (bg.key == key) g = &bg;
+    if (!g) {
+        // the solve tasks, members by decreasing n (the long solves first)
+        auto pin = std::make_shared<PinnedTasks>();
+        if (cudaMallocHost(&pin->h, sizeof(JacobiTask) * 3 * (size_t)count) != cudaSuccess) {
+            cudaGetLastError();
+            return TSSVD_ENOMEM;
+        }
+        std::vector<int> by_n(count);
+        for (int i = 0; i < count; i++) by_n[i] = i;
+        std::stable_sort(by_n.begin(), by_n.end(), [&](int a, int b) { return d[a].n > d[b].n; });
+        for (int k = 0; k < count; k++) {
+            const int i = by_n[k];
+            const int n = (int)d[i].n;
+            pin->h[k] = JacobiTask{pm[i].X, nullptr, n, 0, 0x1p-51, &sts[i]};
+            pin->h[count + k] = JacobiTask{pm[i].X, nullptr, n, 1, (double)n * 0x1p-53, &sts[i]};
+            pin->h[2 * count + k] = JacobiTask{pm[i].X, pm[i].J, n, 2, (double)n * 0x1p-53, &sts[i]};
+        }
+        const long long n0 = tssvd_launch_count();
+        const int prof = tssvd_profile_enable(0);  // no event records inside the graph
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dtasks, pin->h, sizeof(JacobiTask) * 3 * (size_t)count,
+                                cudaMemcpyHostToDevice, s);
+        for (int phase = 0; phase < 4 && e == cudaSuccess; phase++) {
+            e = cudaEventRecord(W.fork, s);
+            for (int w = 0; w < kWorkers && e == cudaSuccess; w++)
+                e = cudaStreamWaitEvent(W.w[w], W.fork, 0);
+            for (int i : plan.order) {
+                if (e != cudaSuccess) break;
+                const int w = plan.worker[i];
+                Bump b(cb + plan.slice_off[w], plan.slice[w]);
+                PhasedScratch c;
+                take_scratch(b, d[i].m, d[i].n, c);
+                cudaStream_t ws_ = W.w[w];
+                if (phase == 0) e = phase_a<T>(d[i], o, pm[i], c, &sts[i], ws_);
+                else if (phase == 1) e = phase_b<T>(d[i], o, pm[i], c, &sts[i], ws_);
+                else if (phase == 2) e = phase_c(d[i], o, pm[i], c, &sts[i], ws_);
+                else e = phase_d<T>(d[i], pm[i], c, &sts[i], ws_);
+            }
+            for (int w = 0; w < kWorkers; w++) {
+                cudaError_t e2 = cudaEventRecord(W.join[w], W.w[w]);
+                if (e == cudaSuccess) e = e2;
+                e2 = cudaStreamWaitEvent(s, W.join[w], 0);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (phase < 3 && e == cudaSuccess)
+                e = launch_jacobi_batch(dtasks + (size_t)phase * count, count, o->max_sweeps, s);
+        }
+        cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        tssvd_profile_enable(prof);
+        if (e == cudaSuccess) e = ec;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "tssvd: batch capture failed: %s\n", cudaGetErrorString(e));
+            cudaGetLastError();
+            return TSSVD_ECUDA;
+        }
+        BatchGraph nb;
+        nb.key = key;
+        nb.exec = exec;
+        nb.kernels = tssvd_launch_count() - n0;
+        if (g_graphs.size() >= 8) {
+            evict_tasks(g_graphs.back().key);
+            cudaGraphExecDestroy(g_graphs.back().exec);
+            g_graphs.pop_back();
+        }
+        g_graphs.insert(g_graphs.begin(), nb);
+        g_phased_tasks.emplace_back(key, pin);
+        g = &g_graphs.front();
+    } else {
+        add_launches(g->kernels);
+    }
+    std::vector<int> modes(count, TSSVD_FP64_TC);
+    return finish_batch(g, d, count, o, sts, modes, s);
+}
+
 template <typename T>
 int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
 {
@@ -862,6 +1286,7 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
         nb.exec = exec;
         nb.kernels = tssvd_launch_count() - n0;
         if (g_graphs.size() >= 8) {
+            evict_tasks(g_graphs.back().key);
             cudaGraphExecDestroy(g_graphs.back().exec);
             g_graphs.pop_back();
         }
@@ -870,31 +1295,7 @@ int batched_impl(tssvd_desc *d, int count, tssvd_opts *o)
     } else {
         add_launches(g->kernels);
     }
-    std::vector<DevStatus> h(count);
-    if (cudaGraphLaunch(g->exec, s) != cudaSuccess ||
-        cudaMemcpyAsync(h.data(), sts, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return TSSVD_ECUDA;
-    }
-    int first = TSSVD_OK;
-    for (int i = 0; i < count; i++) {
-        int code = TSSVD_OK;
-        if (h[i].err)
-            code = TSSVD_ETIMEOUT;
-        else {
-            const int solves = o->passes >= 2 ? 3 : 1;
-            for (int j = 0; j < solves; j++)
-                if (h[i].sweeps[j] < 0) code = TSSVD_ENOCONV;
-            if (code == TSSVD_OK && h[i].rank < d[i].n) code = TSSVD_RANKDEF;
-        }
-        d[i].status = code;
-        d[i].out_rank = h[i].rank;
-        d[i].mode = modes[i];
-        if (first == TSSVD_OK && code != TSSVD_OK) first = code;
-    }
-    return first;
+    return finish_batch(g, d, count, o, sts, modes, s);
 }
 
 // passes: 1 (Algorithm 3), 2 (Algorithm 4) or 3 (Algorithm 4 with its
@@ -1912,6 +2313,9 @@ size_t ts_svd_batched_workspace_size(const tssvd_desc *descs, int count, int ele
                                      const tssvd_opts *opts)
 {
     if (!descs || count < 1 || !opts || (elem_bytes != 4 && elem_bytes != 8)) return 0;
+    if (phased_applies(descs, count, opts))
+        return (elem_bytes == 8 ? make_phased_plan<double>(descs, count)
+                                : make_phased_plan<float>(descs, count)).total + 256;
     std::vector<int> modes(count, opts->mode == TSSVD_AUTO ? TSSVD_FP64_TC : opts->mode);
     // TSSVD_AUTO may pick either engine: size for the larger
     Plan p1 = elem_bytes == 8 ? make_plan<double>(descs, count, opts, modes)
@@ -1932,6 +2336,9 @@ int ts_svd_batched(tssvd_desc *descs, int count, int elem_bytes, tssvd_opts *opt
         opts->drop_tol >= 1.0 || opts->max_sweeps < 1 || opts->max_sweeps > 1000 ||
         opts->mode < TSSVD_FP64 || opts->mode > TSSVD_AUTO)
         return -4;
+    if (phased_applies(descs, count, opts))
+        return elem_bytes == 8 ? batched_phased<double>(descs, count, opts)
+                               : batched_phased<float>(descs, count, opts);
     return elem_bytes == 8 ? batched_impl<double>(descs, count, opts)
                            : batched_impl<float>(descs, count, opts);
 }

@@ -234,6 +234,24 @@ constexpr int kJacobiMixedF32Sweeps = 40;
 struct JacobiMixedScratch {
     double *f32, *K, *T, *H, *X0, *P, *NP;
 };
+
+// Batched one-sided Jacobi (jacobi_batch.cu): one CTA per task, each an
+// independent n x n problem (n <= kJacobiBatchMaxN) with X column-major
+// (ldx = n), J (n x n, column-major) set to the identity and receiving the
+// rotations when non-null, threshold tol as launch_jacobi, and its sweep
+// count in st->sweeps[which] (-1 when max_sweeps ran out).  tasks is a
+// device array of ntasks entries, ordered largest first.
+constexpr int kJacobiBatchMaxN = 256;
+struct JacobiTask {
+    double *X;
+    double *J;
+    int n;
+    int which;
+    double tol;
+    DevStatus *st;
+};
+cudaError_t launch_jacobi_batch(const JacobiTask *tasks, int ntasks, int max_sweeps,
+                                cudaStream_t s);
 bool jacobi_mixed_applies(i64 n);
 cudaError_t launch_jacobi_mixed(double *X, i64 n, double *Jout, const JacobiMixedScratch &w,
                                 int max_sweeps, int *ctr, double *prm, DevStatus *st, int which,

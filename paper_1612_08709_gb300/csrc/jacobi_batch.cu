@@ -1,0 +1,175 @@
+// Batched one-sided (Hestenes) Jacobi: many independent small solves in one
+// launch, one CTA per problem.
+//
+// The grid solver (jacobi.cu) spreads one problem over the GPU, one CTA per
+// rotation pair and a grid barrier per round, which minimises one solve's
+// latency.  A batch of hundreds of problems wants throughput instead: on
+// this GPU the FP64 pipe (two lanes per clock per SM) bounds the rotations,
+// so each problem's rounds run inside one CTA (a __syncthreads per round,
+// no grid barrier and no spin-wait), and the problems fill the SMs side by
+// side.  Tasks are given largest first so that the long solves start first.
+//
+// A CTA of 8 warps takes the n/2 pairs of a round, one warp per pair at a
+// time: each lane holds up to 8 entries of the two columns in registers,
+// the inner product is a warp reduction (an xor butterfly, so every lane
+// holds the same bits and takes the same decision), the rotation comes
+// from the same parameter function as the grid solver (jac_rotation), and
+// the squared column norms are tracked in shared memory in closed form
+// (recomputed at every sweep start, and for a column whose update cancels
+// below 2^-16 of its inputs).  Rounds follow the circle schedule, so a
+// sweep visits every pair once, in the grid solver's order.
+#include "jacobi_common.cuh"
+
+namespace tssvd {
+
+namespace {
+
+constexpr int kBatchJacobiThreads = 256;
+constexpr int kBatchJacobiWarps = kBatchJacobiThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kBatchJacobiThreads)
+    jacobi_batch_kernel(const JacobiTask *tasks, int max_sweeps)
+{
+    __shared__ double nrm[kJacobiBatchMaxN];
+    __shared__ int rot_count;
+    const JacobiTask tk = tasks[blockIdx.x];
+    const int n = tk.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (n < 2 || n > kJacobiBatchMaxN) {
+        if (threadIdx.x == 0) tk.st->sweeps[tk.which] = n < 2 ? 0 : -1;
+        return;
+    }
+    double *X = tk.X, *J = tk.J;
+    const int npad = n + (n & 1), rounds = npad - 1;
+    const double tol = tk.tol;
+    const float log2tol = log2f((float)tol);
+    int done = -1;
+    for (int sweep = 1; sweep <= max_sweeps; sweep++) {
+        for (int j = warp; j < n; j += kBatchJacobiWarps) {
+            const double *x = X + (size_t)j * n;
+            double acc = 0.0;
+            for (int i = lane; i < n; i += 32) acc = fma(x[i], x[i], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) nrm[j] = acc;
+        }
+        if (threadIdx.x == 0) rot_count = 0;
+        __syncthreads();
+        int my_rot = 0;
+        for (int t = 0; t < rounds; t++) {
+            for (int k = warp; k < npad / 2; k += kBatchJacobiWarps) {
+                int P, Q;
+                circle_pair(k, t, npad, P, Q);
+                if (Q >= n) continue;
+                double *xp = X + (size_t)P * n, *xq = X + (size_t)Q * n;
+                double u[8], v[8];
+                double g = 0.0;
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    const int i = lane + 32 * c;
+                    u[c] = i < n ? xp[i] : 0.0;
+                    v[c] = i < n ? xq[i] : 0.0;
+                    g = fma(u[c], v[c], g);
+                }
+                g = warp_sum(g);
+                double a = nrm[P], b = nrm[Q];
+                if (a < 0.0 || b < 0.0) {
+                    double sa = 0.0, sb = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                        sa = fma(u[c], u[c], sa);
+                        sb = fma(v[c], v[c], sb);
+                    }
+                    sa = warp_sum(sa);
+                    sb = warp_sum(sb);
+                    if (a < 0.0) a = sa;
+                    if (b < 0.0) b = sb;
+                }
+                const double4 r = jac_rotation(a, b, g, tol, log2tol);
+                if (r.w == 0.0) {
+                    if (lane == 0) {
+                        nrm[P] = a;
+                        nrm[Q] = b;
+                    }
+                    continue;
+                }
+                const double c = r.x, sn = r.y;
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const int i = lane + 32 * e;
+                    if (i < n) {
+                        xp[i] = c * u[e] - sn * v[e];
+                        xq[i] = sn * u[e] + c * v[e];
+                    }
+                }
+                if (J) {
+                    double *jp = J + (size_t)P * n, *jq = J + (size_t)Q * n;
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const int i = lane + 32 * e;
+                        if (i < n) {
+                            const double x = jp[i], y = jq[i];
+                            jp[i] = c * x - sn * y;
+                            jq[i] = sn * x + c * y;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    // ||c x_P - s x_Q||^2 and ||s x_P + c x_Q||^2; an update
+                    // that cancels below 2^-16 of its inputs is recomputed
+                    const double cc = c * c, ss = sn * sn, cs2 = 2.0 * c * sn;
+                    const double a1 = fma(cc, a, fma(-cs2, g, ss * b));
+                    const double b1 = fma(ss, a, fma(cs2, g, cc * b));
+                    const double floor = 0x1p-16 * (a + b);
+                    nrm[P] = (a1 >= floor) ? a1 : -1.0;
+                    nrm[Q] = (b1 >= floor) ? b1 : -1.0;
+                }
+                my_rot++;
+            }
+            __syncthreads();  // this round's columns written before the next reads them
+        }
+        if (lane == 0 && my_rot != 0) atomicAdd(&rot_count, my_rot);
+        __syncthreads();
+        const int total = rot_count;
+        __syncthreads();  // every thread has read the count before it is reset
+        if (total == 0) {
+            done = sweep;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) tk.st->sweeps[tk.which] = done;
+}
+
+__global__ void init_identity_batch_kernel(const JacobiTask *tasks)
+{
+    const JacobiTask tk = tasks[blockIdx.x];
+    if (!tk.J || tk.n < 1 || tk.n > kJacobiBatchMaxN) return;
+    const int n = tk.n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        tk.J[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_jacobi_batch(const JacobiTask *tasks, int ntasks, int max_sweeps,
+                                cudaStream_t s)
+{
+    if (ntasks < 1) return cudaSuccess;
+    {
+        ProfScope ps_("init_identity", s);
+        init_identity_batch_kernel<<<ntasks, 256, 0, s>>>(tasks);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ProfScope ps_("jacobi_batch", s);
+    jacobi_batch_kernel<<<ntasks, kBatchJacobiThreads, 0, s>>>(tasks, max_sweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace tssvd

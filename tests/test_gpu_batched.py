@@ -31,9 +31,19 @@ def test_batched_equals_per_member_calls(mode):
     outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode)
     for A, (U, S, V), info in zip(As, outs, infos):
         U1, S1, V1, i1 = pkg.ts_svd(A, drop_tol=0.0, mode=mode)
-        # same kernels, same launch shapes: identical results
-        assert torch.equal(S, S1) and torch.equal(U, U1) and torch.equal(V, V1)
         assert info["rank"] == i1["rank"] and info["status"] == i1["status"]
+        if mode == "fp64":
+            # same kernels, same launch shapes: identical results
+            assert torch.equal(S, S1) and torch.equal(U, U1) and torch.equal(V, V1)
+        else:
+            # the phased batch (one-CTA Jacobi solves, one-sided second
+            # eigensolve): the same SVD to rounding
+            n = A.shape[1]
+            eye = torch.eye(n, dtype=A.dtype, device=A.device)
+            assert (S - S1).abs().max() <= 1e-12 * S1[0]
+            assert (U.T @ U - eye).abs().max() <= 1e-12
+            assert (V.T @ V - eye).abs().max() <= 1e-12
+            assert (A @ V - U * S).abs().max() <= 1e-11 * S1[0]
 
 
 @gpu
