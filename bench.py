@@ -14,9 +14,11 @@ and the 2,000,000 x 200 workload of the same recipe is timed after it
 Prints one JSON line (rank 0).  `value` is GFLOP/s of the algorithm's
 nominal products, 6 m n^2 for two passes (Gram A^T A counted as m n^2,
 A V~ 2 m n^2, Gram Y^T Y m n^2, Y W 2 m n^2; the final U = Q P is not
-counted), with A resident in HBM; `e2e` is the same metric for the same
-C-ABI call with A copied in from pinned host memory and U, S, V copied
-back, both copies inside the timed region (`phases_ms` splits them out).
+counted), with A resident in HBM; `e2e` is the same metric through the
+host-buffer C-ABI call (ts_svd_host) from pinned host memory, the copies of
+A in and of U, S, V back inside the timed region and overlapped with the
+compute by row chunks (`serial_ms` gives copy, compute and copy run in
+turn for comparison).
 The FP64 roofline peak is the FP64 FMA rate measured on the same GPU in
 the same run (tssvd_fp64_fma_rate).  `--impl reference` times the FP64 CPU
 oracle instead (bounded samples of the same workload on the host cores).
@@ -426,26 +428,19 @@ def run_ours(args):
             restore = numa.pop("restore", None)
             if restore is not None:
                 os.sched_setaffinity(0, restore)
-        Ad = torch.empty_like(A)
-        kw2 = dict(kw)
-        phases = []
+        # the public host-buffer call: A's row chunks go in and U's come out
+        # on the library's copy streams, overlapped with the compute
+        wsh = torch.empty((pkg.ts_svd_host_workspace_size(m, n, drop_tol=0.0, mode=args.mode,
+                                                          passes=args.passes),),
+                          dtype=torch.uint8, device=dev)
+        kwh = dict(passes=args.passes, scale=True, drop_tol=0.0, mode=args.mode, workspace=wsh,
+                   out=(Uh, Sh, Vh))
 
         def e2e_step():
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            ev[0].record(stream)
-            Ad.copy_(Ah, non_blocking=True)
-            ev[1].record(stream)
-            pkg.ts_svd(Ad, **kw2)
-            ev[2].record(stream)
-            Uh.copy_(U, non_blocking=True)
-            Sh.copy_(S, non_blocking=True)
-            Vh.copy_(V, non_blocking=True)
-            ev[3].record(stream)
-            phases.append(ev)
+            pkg.ts_svd_host(Ah, **kwh)
 
         e2e_step()
         torch.cuda.synchronize()
-        phases.clear()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -455,11 +450,29 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_e = f0.elapsed_time(f1) / args.e2e_steps
         ms_e = max_over_ranks(ms_e, dev)
-        ph = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in phases) / len(phases) for i in range(3)]
+        eye = torch.eye(n, dtype=torch.float64, device=dev)
+        Ue = Uh.to(dev)
+        e2e_orth = float((Ue.T @ Ue - eye).abs().max())
+        del Ue, wsh
+        # the same copies and call in turn, for the breakdown
+        Ad = torch.empty_like(A)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        Ad.copy_(Ah, non_blocking=True)
+        ev[1].record(stream)
+        pkg.ts_svd(Ad, **kw)
+        ev[2].record(stream)
+        Uh.copy_(U, non_blocking=True)
+        Sh.copy_(S, non_blocking=True)
+        Vh.copy_(V, non_blocking=True)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        ph = [ev[i].elapsed_time(ev[i + 1]) for i in range(3)]
         e2e = {"value": job_gflops(flops, world, ms_e), "unit": "GFLOP/s",
                "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (m * n + n + n * n) * 8,
-               "ms_per_step": ms_e,
-               "phases_ms": {"h2d": ph[0], "ts_svd": ph[1], "d2h": ph[2]},
+               "ms_per_step": ms_e, "api": "ts_svd_host (pinned host buffers, overlapped copies)",
+               "orth_U": e2e_orth,
+               "serial_ms": {"h2d": ph[0], "ts_svd": ph[1], "d2h": ph[2], "total": sum(ph)},
                "host_numa": numa}
         del Ah, Uh, Sh, Vh, Ad
 

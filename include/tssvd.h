@@ -150,6 +150,28 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
 int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S,
            double *V, tssvd_opts *opts);
 
+/*
+ * ts_svd on host buffers (Algorithm 4 or 3 as opts->passes says): A (m x n,
+ * row-major, lda), U (m x n, leading dimension n), S (n), V (n x n) are in
+ * host memory; the call copies A to the device, runs the TS-SVD there and
+ * copies the results back, then returns (the copies are ordered after the
+ * work already queued on opts->stream).  A is copied in row chunks (about
+ * 256 MB, at most 64) on a copy stream of the library's; with
+ * TSSVD_FP64_TC and passes >= 2 the first pass's column maxima and Gram
+ * partials start on each chunk as it lands (Section 2's per-partition
+ * Gram matrices, summed), and U goes back in the same chunks while the
+ * next chunk's product runs.  Other modes copy, compute and copy in turn.
+ * The overlap needs page-locked host buffers (cudaHostAlloc or
+ * cudaHostRegister); pageable ones work, with the copies serialised.  The
+ * workspace (opts->workspace, or the internal one) also holds device
+ * copies of A and U: ts_svd_host_workspace_size.  Host-buffer calls on one
+ * device share the copy streams and take turns.  Status and errors as
+ * ts_svd.
+ */
+size_t ts_svd_host_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts);
+int ts_svd_host(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S,
+                double *V, tssvd_opts *opts);
+
 /* As ts_svd for FP32 storage: A, U, S, V are float.  The n x n
  * eigensolves and small SVD run in FP64; tall products as opts->mode says
  * (FP64 arithmetic on the FP32 data, or BF16x3 on the tensor cores). */

@@ -16,7 +16,7 @@ from ._binding import (  # noqa: F401
     ts_matmul, ts_svd_batched, ts_svd_batched_workspace_size,
     ts_svd_workspace_size, lowrank_svd_workspace_size, TSSVD, exported_symbols,
     ts_pca, ts_pca_workspace_size, lowrank_svd_backward, LowRankSVD, ts_svd_tsqr,
-    lowrank_svd_tsqr, TSSVD_ECOMM,
+    lowrank_svd_tsqr, TSSVD_ECOMM, ts_svd_host, ts_svd_host_workspace_size,
 )
 from ._rowshard import (  # noqa: F401
     ts_svd_rowshard, DistComm, row_block, reduce_fixed_order,

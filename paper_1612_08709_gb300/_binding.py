@@ -134,6 +134,10 @@ def lib():
     L.tssvd_fp64_fma_rate.restype = ctypes.c_int
     L.ts_svd_rowshard.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, op]
     L.ts_svd_rowshard.restype = ctypes.c_int
+    L.ts_svd_host.argtypes = [vp, i64, i64, i64, vp, vp, vp, op]
+    L.ts_svd_host.restype = ctypes.c_int
+    L.ts_svd_host_workspace_size.argtypes = [i64, i64, op]
+    L.ts_svd_host_workspace_size.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -147,7 +151,8 @@ def exported_symbols():
             "ts_svd_backward_f32", "ts_svd_batched", "ts_svd_batched_workspace_size",
             "ts_pca_workspace_size", "ts_pca", "ts_pca_f32", "lowrank_svd_backward",
             "ts_svd_tsqr_workspace_size", "ts_svd_tsqr", "lowrank_svd_tsqr",
-            "tssvd_fp64_fma_rate", "ts_svd_rowshard"]
+            "tssvd_fp64_fma_rate", "ts_svd_rowshard", "ts_svd_host",
+            "ts_svd_host_workspace_size"]
 
 
 def _opts(passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
@@ -231,6 +236,43 @@ def ts_svd(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sw
         rc = f(_ptr(A), m, n, A.stride(0), _ptr(U), _ptr(S), _ptr(V), ctypes.byref(o))
     _check(rc, "ts_svd")
     return U, S, V, _info(o, rc)
+
+
+def ts_svd_host(A, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64", max_sweeps=50,
+                stream=None, workspace=None, out=None, device=None):
+    """Thin SVD of a float64 CPU tensor A (m x n, row-major rows; pin it with
+    A.pin_memory() for the copies to overlap the compute) computed on the
+    current (or given) CUDA device; returns CPU tensors (U, S, V, info).
+    See include/tssvd.h (ts_svd_host)."""
+    if not (isinstance(A, torch.Tensor) and not A.is_cuda and A.dim() == 2 and
+            A.dtype == torch.float64 and A.stride(1) == 1):
+        raise TsSvdError("ts_svd_host: A must be a float64 CPU matrix with unit column stride")
+    m, n = A.shape
+    if out is None:
+        pin = A.is_pinned()
+        U = torch.empty((m, n), dtype=torch.float64, pin_memory=pin)
+        S = torch.empty((n,), dtype=torch.float64, pin_memory=pin)
+        V = torch.empty((n, n), dtype=torch.float64, pin_memory=pin)
+    else:
+        U, S, V = out
+    for x in (U, S, V):
+        if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise TsSvdError("ts_svd_host: outputs must be contiguous float64 CPU tensors")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    with torch.cuda.device(dev):
+        o = _opts(passes, scale, drop_tol, mode, max_sweeps, stream, workspace)
+        rc = lib().ts_svd_host(_ptr(A), m, n, A.stride(0), _ptr(U), _ptr(S), _ptr(V),
+                               ctypes.byref(o))
+    _check(rc, "ts_svd_host")
+    return U, S, V, _info(o, rc)
+
+
+def ts_svd_host_workspace_size(m, n, **kw):
+    o = _opts(**kw) if torch.cuda.is_available() else None
+    if o is None:
+        o = _Opts()
+        lib().tssvd_default_opts(ctypes.byref(o))
+    return int(lib().ts_svd_host_workspace_size(m, n, ctypes.byref(o)))
 
 
 def ts_pca_workspace_size(m, n, dtype=torch.float64, **kw):

@@ -351,12 +351,32 @@ cudaError_t ts_core(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO
     return cudaSuccess;
 }
 
+// Host-buffer form (ts_svd_host): A's rows arrive in chunks of `rows` rows
+// (a multiple of 128; the last chunk may be shorter) on a copy stream, chunk
+// k signalled by arrived[k]; U leaves in the same chunks on the stream
+// `out` (ready[k] recorded on the compute stream after chunk k's product).
+struct HostIO {
+    int chunks;
+    i64 rows;
+    cudaEvent_t *arrived, *ready;
+    double *U_host;
+    i64 ldu_host;
+    cudaStream_t out;
+};
+
+inline i64 io_rows(const HostIO *io, i64 m, int k)
+{
+    const i64 r0 = (i64)k * io->rows;
+    return std::min(io->rows, m - r0);
+}
+
 // The FP64-accurate tensor-core form: the same steps as ts_core, with every
 // tall product on the digit-sliced tensor-core kernels.
 template <typename T, typename TO>
 cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S, TO *V, i64 ldv,
                        int passes, int scale, double tol, int max_sweeps, Bump &ws, DevStatus *st,
-                       cudaStream_t s, const tssvd_comm *comm = nullptr, int terms = 0)
+                       cudaStream_t s, const tssvd_comm *comm = nullptr, int terms = 0,
+                       const HostIO *io = nullptr)
 {
     // terms > 0 (the BF16-split modes, two or three passes, n <= 256): the
     // first pass's two products (Gram of A, A V~) are BF16-split
@@ -371,9 +391,15 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     int *exA = ws.take<int>(n), *pk1 = ws.take<int>(n), *exY = ws.take<int>(n);
     int *pk2 = ws.take<int>(n), *em = ws.take<int>(n);
     int *er = ws.take<int>(m);
+    // (host-buffer form: two passes, digit products only)
+    if (passes < 2 || terms || comm) io = nullptr;
     const int osp = oz_gram_splits(m, (int)n);
     const int sp2 = tn_splits(n, n, n, false);
-    double *P = ws.take<double>((size_t)(osp > sp2 ? osp : sp2) * nn);
+    int osp_io = 0;  // the chunks' Gram partials, side by side
+    if (io)
+        for (int k = 0; k < io->chunks; k++) osp_io += oz_gram_splits(io_rows(io, m, k), (int)n);
+    double *P = ws.take<double>((size_t)std::max(std::max(osp, sp2), osp_io) * nn);
+    unsigned long long *bitsk = io ? ws.take<unsigned long long>(n) : nullptr;
     const int gcs = colsumsq_rows(m, n);
     const int gys = nn_grid_rows(n, n);
     // column maxima of Y~ from the digit product's epilogue
@@ -405,7 +431,27 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
 
     // MaxEntry of every column: the Gram's digit scales (and D when scaling)
     CK(cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * n, s));
-    CK(launch_colmax<T>(A, m, n, lda, bits, s));
+    int osp_used = osp;
+    if (io) {
+        // A's chunks as they arrive: each chunk's column maxima (the running
+        // maxima for D, the chunk's own for its digit scales: any bound at
+        // or above the chunk's values serves) and its Gram partials
+        osp_used = 0;
+        for (int k = 0; k < io->chunks; k++) {
+            const i64 r0 = (i64)k * io->rows, rk = io_rows(io, m, k);
+            CK(cudaStreamWaitEvent(s, io->arrived[k], 0));
+            CK(cudaMemsetAsync(bitsk, 0, sizeof(unsigned long long) * n, s));
+            CK(launch_colmax<T>(A + r0 * lda, rk, n, lda, bitsk, s));
+            CK(launch_bits_max(bits, bitsk, n, s));
+            CK(launch_oz_exp_from_bits(bitsk, (int)n, exY, s));
+            const int ok = oz_gram_splits(rk, (int)n);
+            CK(launch_oz_gram<T>(A + r0 * lda, lda, rk, (int)n, exY, ok, big,
+                                 P + (size_t)osp_used * nn, st, s));
+            osp_used += ok;
+        }
+    } else {
+        CK(launch_colmax<T>(A, m, n, lda, bits, s));
+    }
     CK(comm_allreduce(comm, bits, n, TSSVD_DT_U64, TSSVD_OP_MAX, s));
     CK(launch_oz_exp_from_bits(bits, (int)n, exA, s));
     const bool sc = (passes >= 2) && scale;
@@ -422,14 +468,14 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
         CK(launch_tc_gram<T>(A, lda, m, (int)n, terms, tsp, Ptc, st, s));
         CK(launch_tn_reduce(Ptc, tsp, n, n, rs1, rs1, true, B, n, s));
     } else {
-        CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
+        if (!io) CK(launch_oz_gram<T>(A, lda, m, (int)n, exA, osp, big, P, st, s));
         // A's row image for Y~ = A (D^-1 V~) (A's columns prescaled by D^-1
         // for the digit scales; the product is unchanged).  Building the
         // row images beside the Jacobi kernels on a second stream was tried
         // and slowed the latency-bound solves 2.5x (L2 and issue contention).
         CK(launch_oz_rowexp<T>(A, lda, m, (int)n, pkA, er, s));
         CK(launch_oz_row_image<T>(A, lda, m, (int)n, pkA, er, big, s));
-        CK(launch_tn_reduce(P, osp, n, n, rs1, rs1, true, B, n, s));
+        CK(launch_tn_reduce(P, osp_used, n, n, rs1, rs1, true, B, n, s));
     }
     CK(comm_allreduce(comm, B, nn, TSSVD_DT_F64, TSSVD_OP_SUM, s));
     // B = V~ D~ V~^T (to B's rounding for Algorithm 4, relative for Algorithm
@@ -553,7 +599,23 @@ cudaError_t ts_core_oz(const T *A, i64 m, i64 n, i64 lda, TO *U, i64 ldu, TO *S,
     CK(launch_scale2(Pm, n, n, n, tinv, sgn, Pp, n, s));
     CK(launch_nn<double, double>(M, n, Pp, n, n, n, n, M3, n, NP, s));
     CK(launch_oz_image(M3, n, (int)n, (int)n, pk2, em, img, s));
-    CK(launch_oz_nn_run<TO>(big, m, (int)n, er, img, em, (int)n, U, ldu, st, s));
+    if (io) {
+        // U by row chunks, each copied out while the next is computed (the
+        // row image is stored by 128-row tiles)
+        const size_t tile_bytes = oz_row_image_bytes(128, (int)n);
+        for (int k = 0; k < io->chunks; k++) {
+            const i64 r0 = (i64)k * io->rows, rk = io_rows(io, m, k);
+            CK(launch_oz_nn_run<TO>(big + (size_t)(r0 / 128) * tile_bytes, rk, (int)n, er + r0,
+                                    img, em, (int)n, U + r0 * ldu, ldu, st, s));
+            CK(cudaEventRecord(io->ready[k], s));
+            CK(cudaStreamWaitEvent(io->out, io->ready[k], 0));
+            CK(cudaMemcpy2DAsync(io->U_host + r0 * io->ldu_host, sizeof(double) * io->ldu_host,
+                                 U + r0 * ldu, sizeof(TO) * ldu, sizeof(double) * n, rk,
+                                 cudaMemcpyDeviceToHost, io->out));
+        }
+    } else {
+        CK(launch_oz_nn_run<TO>(big, m, (int)n, er, img, em, (int)n, U, ldu, st, s));
+    }
     CK(launch_convert<TO>(sigma, n, 1, n, S, n, s));
     CK(launch_convert<TO>(Vo, n, n, n, V, ldv, s));
     return cudaSuccess;
@@ -2145,6 +2207,163 @@ int lowrank_tsqr_entry(const double *A, int64_t m, int64_t n, int64_t lda, int64
     return code;
 }
 
+// ------------------------------------------------------- host-buffer calls
+
+// Copy streams and chunk events of the host-buffer calls, one set per
+// device, created on first use and kept for the process.
+constexpr int kHostMaxChunks = 64;
+struct HostCopies {
+    bool ready = false;
+    cudaStream_t in, out;
+    cudaEvent_t arrived[kHostMaxChunks], done[kHostMaxChunks], start, in_done, out_done;
+};
+HostCopies g_host[64];
+std::mutex g_host_mu;
+
+int ensure_host_copies(int dev)
+{
+    HostCopies &H = g_host[dev];
+    if (H.ready) return 0;
+    if (cudaStreamCreateWithFlags(&H.in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&H.out, cudaStreamNonBlocking) != cudaSuccess)
+        return -1;
+    cudaEvent_t *all[] = {&H.start, &H.in_done, &H.out_done};
+    for (cudaEvent_t *e : all)
+        if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return -1;
+    for (int k = 0; k < kHostMaxChunks; k++)
+        if (cudaEventCreateWithFlags(&H.arrived[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&H.done[k], cudaEventDisableTiming) != cudaSuccess)
+            return -1;
+    H.ready = true;
+    return 0;
+}
+
+// Rows per chunk: about 256 MB of A, a multiple of 128 (U's row image is
+// stored by 128-row tiles), at most kHostMaxChunks chunks.
+i64 host_chunk_rows(i64 m, i64 n)
+{
+    i64 rows = ((i64)(256ll << 20) / (8 * n) + 127) / 128 * 128;
+    const i64 least = ((m + kHostMaxChunks - 1) / kHostMaxChunks + 127) / 128 * 128;
+    if (rows < least) rows = least;
+    if (rows < 128) rows = 128;
+    return rows;
+}
+
+bool host_overlaps(const tssvd_opts *o) { return o->mode == TSSVD_FP64_TC && o->passes >= 2; }
+
+// Workspace of a host-buffer call: status, device copies of A and U, S, V,
+// and the TS-SVD's own (with the chunked Gram partials when overlapping).
+void host_sizes(Bump &b, i64 m, i64 n, const tssvd_opts *o, const HostIO *io)
+{
+    b.take<DevStatus>(1);
+    b.take<double>((size_t)m * n);
+    b.take<double>((size_t)m * n);
+    b.take<double>(n);
+    b.take<double>((size_t)n * n);
+    if (host_overlaps(o))
+        ts_core_oz<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
+                                   (double *)nullptr, n, o->passes, o->scale, o->drop_tol,
+                                   o->max_sweeps, b, nullptr, nullptr, nullptr, 0, io);
+    else
+        ts_any<double, double>(nullptr, m, n, n, (double *)nullptr, n, (double *)nullptr,
+                               (double *)nullptr, n, o->passes, o->scale, o->drop_tol,
+                               o->max_sweeps, b, nullptr, nullptr, o->mode);
+}
+
+int ts_svd_host_entry(const double *A, i64 m, i64 n, i64 lda, double *U, double *S, double *V,
+                      tssvd_opts *opts)
+{
+    if (!A) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1 || n > 16384) return -3;
+    if (lda < n) return -4;
+    if (!U) return -5;
+    if (!S) return -6;
+    if (!V) return -7;
+    if (!check_opts(opts)) return -8;
+    if ((opts->mode == TSSVD_BF16X3 || opts->mode == TSSVD_BF16X6) && n > 256) {
+        fprintf(stderr, "tssvd: the mixed-precision modes take n <= 256 (n = %lld)\n",
+                (long long)n);
+        return -3;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSSVD_ECUDA;
+    std::lock_guard<std::mutex> hlk(g_host_mu);  // the chunk events are shared
+    if (ensure_host_copies(dev)) return TSSVD_ECUDA;
+    HostCopies &H = g_host[dev];
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const i64 rows = host_chunk_rows(m, n);
+    const int chunks = (int)((m + rows - 1) / rows);
+    HostIO io{chunks, rows, H.arrived, H.done, U, n, H.out};
+    const bool ov = host_overlaps(opts);
+
+    Bump sz(nullptr, 0);
+    host_sizes(sz, m, n, opts, &io);
+    void *base = nullptr;
+    std::unique_lock<std::mutex> lk;
+    int rc = acquire_ws(opts, sz.off, &base, lk);
+    if (rc) return rc;
+    Bump ws(base, sz.off + 256);
+    DevStatus *st = ws.take<DevStatus>(1);
+    double *Ad = ws.take<double>((size_t)m * n), *Ud = ws.take<double>((size_t)m * n);
+    double *Sd = ws.take<double>(n), *Vd = ws.take<double>((size_t)n * n);
+    auto fail = [&](cudaError_t e) {
+        // copies may still be in flight on the copy streams: let them end
+        // before the caller's buffers can go away
+        cudaStreamSynchronize(H.in);
+        cudaStreamSynchronize(H.out);
+        cudaStreamSynchronize(s);
+        fprintf(stderr, "tssvd: %s\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TSSVD_ENOMEM : TSSVD_ECUDA;
+    };
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    // A's chunks on the input stream, after the work already queued on s
+    if (e == cudaSuccess) e = cudaEventRecord(H.start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(H.in, H.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(H.out, H.start, 0);
+    for (int k = 0; k < chunks && e == cudaSuccess; k++) {
+        const i64 r0 = (i64)k * rows, rk = io_rows(&io, m, k);
+        e = cudaMemcpy2DAsync(Ad + r0 * n, sizeof(double) * n, A + r0 * lda, sizeof(double) * lda,
+                              sizeof(double) * n, rk, cudaMemcpyHostToDevice, H.in);
+        if (e == cudaSuccess) e = cudaEventRecord(H.arrived[k], H.in);
+    }
+    if (e != cudaSuccess) return fail(e);
+    if (ov) {
+        // the first Gram consumes A's chunks as they land; U leaves in chunks
+        e = ts_core_oz<double, double>(Ad, m, n, n, Ud, n, Sd, Vd, n, opts->passes, opts->scale,
+                                       opts->drop_tol, opts->max_sweeps, ws, st, s, nullptr, 0,
+                                       &io);
+    } else {
+        e = cudaEventRecord(H.in_done, H.in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, H.in_done, 0);
+        if (e == cudaSuccess)
+            e = ts_any<double, double>(Ad, m, n, n, Ud, n, Sd, Vd, n, opts->passes, opts->scale,
+                                       opts->drop_tol, opts->max_sweeps, ws, st, s, opts->mode);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(U, Ud, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S, Sd, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(V, Vd, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(H.out_done, H.out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, H.out_done, 0);
+    if (e != cudaSuccess) return fail(e);
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cudaErrorUnknown);
+    std::vector<DevStatus> v(1, h);
+    int code = summarise(v, opts->passes >= 2 ? 3 : 1, nullptr);
+    opts->out_rank = h.rank;
+    for (int i = 0; i < 4; i++) opts->sweeps[i] = h.sweeps[i];
+    opts->ranks[0] = h.rank1;
+    opts->ranks[1] = opts->passes >= 2 ? h.rank2 : h.rank1;
+    if (code == TSSVD_OK && h.rank < n) code = TSSVD_RANKDEF;
+    return code;
+}
+
 }  // namespace
 }  // namespace tssvd
 
@@ -2197,6 +2416,22 @@ int ts_svd(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double
            tssvd_opts *opts)
 {
     return ts_svd_entry<double>(A, m, n, lda, U, S, V, opts);
+}
+
+size_t ts_svd_host_workspace_size(int64_t m, int64_t n, const tssvd_opts *opts)
+{
+    if (!opts || m < 1 || n < 1 || m < n) return 0;
+    const i64 rows = host_chunk_rows(m, n);
+    HostIO io{(int)((m + rows - 1) / rows), rows, nullptr, nullptr, nullptr, n, nullptr};
+    Bump sz(nullptr, 0);
+    host_sizes(sz, m, n, opts, &io);
+    return sz.off + 256;
+}
+
+int ts_svd_host(const double *A, int64_t m, int64_t n, int64_t lda, double *U, double *S,
+                double *V, tssvd_opts *opts)
+{
+    return ts_svd_host_entry(A, m, n, lda, U, S, V, opts);
 }
 
 int ts_svd_f32(const float *A, int64_t m, int64_t n, int64_t lda, float *U, float *S, float *V,

@@ -186,6 +186,10 @@ cudaError_t launch_oz_exp_from_bits(const unsigned long long *bits, int n, int *
 cudaError_t launch_oz_pow2_of(const double *sc, int n, int *pk, cudaStream_t s);
 // out[j] = -in[j].
 cudaError_t launch_neg_int(const int *in, int n, int *out, cudaStream_t s);
+// dst[j] = max(dst[j], src[j]) for column maxima held as the bit patterns
+// of non-negative doubles (launch_colmax), whose integer order is numeric.
+cudaError_t launch_bits_max(unsigned long long *dst, const unsigned long long *src, i64 n,
+                            cudaStream_t s);
 
 // -------------------------------------------------------------- Jacobi
 // One-sided (Hestenes) Jacobi with a parallel round-robin pair order, as

@@ -311,6 +311,22 @@ cudaError_t launch_diag_sqrt(const double *G, i64 ldg, i64 n, double *out, cudaS
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void bits_max_kernel(unsigned long long *dst, const unsigned long long *src, i64 n)
+{
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (i64)gridDim.x * blockDim.x)
+        if (src[j] > dst[j]) dst[j] = src[j];
+}
+}  // namespace
+
+cudaError_t launch_bits_max(unsigned long long *dst, const unsigned long long *src, i64 n,
+                            cudaStream_t s)
+{
+    ProfScope ps_("bits_max", s);
+    bits_max_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_keepval(const double *val, const double *keep, i64 n, double *out,
                            cudaStream_t s)
 {
