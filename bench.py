@@ -901,6 +901,7 @@ def run_batched(args):
         sig.append(torch.as_tensor(s, device=dev))
     flops = sum(6.0 * m * n * n for m, n in shapes)
     mode = "auto" if args.mode == "fp64_tc" else args.mode
+    set_fp64_peak(pkg.lib())
     outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode)  # tunes + captures
     for _ in range(max(0, args.warmup - 1)):
         pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode, outs=outs)
@@ -908,7 +909,13 @@ def run_batched(args):
     n0 = L.tssvd_launch_count()
     clocks = ClockSampler(0)
     clocks.start()
+    # the batched solves are timed by event nodes of the graph and reported
+    # through the library's profiler
+    L.tssvd_profile_enable(1)
+    L.tssvd_profile_report(ctypes.create_string_buffer(16), 16)  # clear
     ms = _timed(torch, lambda: pkg.ts_svd_batched(As, drop_tol=0.0, mode=mode, outs=outs), args.steps)
+    L.tssvd_profile_enable(0)
+    kernels = read_profile(L)
     clk = clocks.stop()
     launches = L.tssvd_launch_count() - n0
     err = max(float((o[1] - s).abs().max() / s[0]) for o, s in zip(outs, sig))
@@ -931,7 +938,24 @@ def run_batched(args):
     # Gram matrices, A V~, Y W, U), as 28 digit-pair products on the tensor
     # cores when every member ran FP64_TC.
     roof = None
-    if set(modes) == {"fp64_tc"}:
+    if "jacobi_batch" in kernels:
+        # the phased executor's dominant kernel: the batched one-sided
+        # solves, FP64 work as bench.kernel_models counts it (6 n^2 a round
+        # without accumulation, 9 n^2 with), each member's own sweep counts
+        jf = 0.0
+        for (m, n), inf in zip(shapes, infos):
+            sw = inf["sweeps"]
+            rounds = n - 1 + (n & 1)
+            jf += (6.0 * max(sw[0], 0) + 6.0 * max(sw[1], 0) + 9.0 * max(sw[2], 0)) * rounds * n * n
+        c, t = kernels["jacobi_batch"]
+        steps_seen = c / 3.0
+        peak, src = FP64_PEAK_GFLOPS / 1e3, FP64_PEAK_SOURCE
+        ach = jf * steps_seen / (t * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "jacobi_batch (three launches a step)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": src, "traffic": None,
+                "launch_ms_mean": t / c, "share_of_step": t / steps_seen / ms}
+    elif set(modes) == {"fp64_tc"}:
         peak, src = bf16_peak(sustained=True)
         ach = 28.0 * sum(8.0 * m * n * n for m, n in shapes) / (ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "whole step (digit products of all members)",
@@ -970,6 +994,7 @@ def run_batched(args):
                                                max(n for _, n in shapes) <= 256) else "per member",
                       "l2": "inputs larger than L2 (%.0f GB)" % (sum(m * n for m, n in shapes) * 8 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
+           "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()},
            "accuracy": {"sigma_err_normwise_max": err, "orth_U_max": orth},
            "loop_baseline": None if loop_ms is None else
            {"ms_per_step": loop_ms, "value": flops / (loop_ms * 1e-3) / 1e9,

@@ -406,6 +406,7 @@ typedef struct {
     int64_t out_rank; /* [out] */
     int status;      /* [out] status of this member (as ts_svd returns) */
     int mode;        /* [out] arithmetic mode used (TSSVD_AUTO resolved) */
+    int sweeps[3];   /* [out] Jacobi sweeps of its three solves, as tssvd_opts */
 } tssvd_desc;
 
 /*
@@ -418,7 +419,7 @@ typedef struct {
  * n <= 256, passes = 2 and the mode is TSSVD_FP64_TC or TSSVD_AUTO, the
  * batch runs in phases instead: the members' tall products and small steps
  * on the worker streams, and each of the three Jacobi solves of all members
- * as one launch with one thread block per member (the eigensolves
+ * as one launch with a cluster of two thread blocks per member (the eigensolves
  * one-sided on the pivoted Cholesky factor); every member then runs
  * TSSVD_FP64_TC, its per-solve state is kept in the workspace between the
  * phases, and for double members U's storage holds Y~ until U is written.

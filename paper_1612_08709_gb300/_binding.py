@@ -54,7 +54,7 @@ class _Desc(ctypes.Structure):
         ("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
         ("lda", ctypes.c_int64), ("U", ctypes.c_void_p), ("S", ctypes.c_void_p),
         ("V", ctypes.c_void_p), ("out_rank", ctypes.c_int64), ("status", ctypes.c_int),
-        ("mode", ctypes.c_int),
+        ("mode", ctypes.c_int), ("sweeps", ctypes.c_int * 3),
     ]
 
 
@@ -390,7 +390,8 @@ def ts_svd_batched(As, passes=2, scale=True, drop_tol=PAPER_DROP_TOL, mode="fp64
     if rc in (TSSVD_ETIMEOUT, TSSVD_ECUDA, TSSVD_ENOMEM, TSSVD_ECOMM):
         raise TsSvdError("ts_svd_batched: %s" % lib().tssvd_status_string(rc).decode())
     infos = [{"status": descs[i].status, "rank": int(descs[i].out_rank),
-              "mode": _MODE_NAMES.get(descs[i].mode, descs[i].mode)} for i in range(len(As))]
+              "mode": _MODE_NAMES.get(descs[i].mode, descs[i].mode),
+              "sweeps": list(descs[i].sweeps)} for i in range(len(As))]
     return res, infos, rc
 
 

@@ -126,32 +126,25 @@ inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSS
 // The first Gram eigensolve of Algorithm 4, B = V~ D~ V~^T (B consumed),
 // accurate to the FP64 rounding already in B (the second pass repairs the
 // rest), for a B formed with FP64-accurate products.
-// For n <= kPcholMaxN: pivoted Cholesky P^T B P = R^T R with the floor of
-// launch_pchol, one-sided Jacobi on the columns of R^T (rotation threshold
-// 2^-51: the columns come out orthogonal to rounding), whose normalised
-// columns, sorted by norm and un-pivoted, are the eigenvectors: B = P R^T R
-// P^T and R^T = (X Sigma^-1) Sigma K^T give B = P (X Sigma^-1) Sigma^2
-// (X Sigma^-1)^T P^T.  On a graded B this converges in a third of the
-// sweeps of the Gram-form solver.  For kPcholMaxN < n <= kPcholGridMaxN
-// the factorization runs over the whole grid with logical pivoting
-// (launch_pchol_grid; nothing to un-pivot), and the rotations are not
-// accumulated (only the orthogonalised columns are used): 13 sweeps
-// instead of 37 on 1,000,000 x 1,000 with sigma 1 .. 1e-8.  Larger n:
-// Gram-form Jacobi with the normwise floor.  Scratch: Xw, Jw, B2, Xn
-// (n x n), norms, lam (n), perm, piv (n ints).
+// For n <= kPcholGridMaxN: pivoted Cholesky P^T B P = R^T R over the whole
+// grid with logical pivoting (launch_pchol_grid: X = (R P^T)^T, nothing to
+// un-pivot), one-sided Jacobi on the columns of X without accumulating
+// the rotations (threshold 2^-51: the columns come out orthogonal to
+// rounding), whose normalised columns, sorted by norm, are the
+// eigenvectors: B = X X^T = (X K)(X K)^T with X K = W Sigma gives
+// B = W Sigma^2 W^T.  On a graded B this converges in a third of the
+// sweeps of the Gram-form solver (13 sweeps instead of 37 on 1,000,000 x
+// 1,000 with sigma 1 .. 1e-8).  The grid factorization replaced the
+// single-CTA one here (2.9 -> 1.1 ms at n = 200); the single-CTA one
+// serves the batched solves.  For n > kJacobiMixedMinN the Jacobi solve
+// starts with the FP32 phase.  Larger n: Gram-form Jacobi with the
+// normwise floor.  Scratch: Xw, Jw, B2, Xn (n x n), norms, lam (n), perm,
+// piv (n ints).
 static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *Jw, double *Xn,
                              double *lam, double *norms, double *Vt, int max_sweeps, int *ctr,
                              double *prm, int *perm, int *piv, DevStatus *st, cudaStream_t s,
                              const JacobiMixedScratch &mw)
 {
-    if (n <= kPcholMaxN) {
-        CK(launch_pchol(B, (int)n, Xw, n, piv, s));
-        CK(launch_jacobi(Xw, n, nullptr, n, (int)n, (int)n, max_sweeps, ctr, prm, st, 0, s,
-                         0x1p-51));
-        CK(launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n, lam,
-                                  Xn, n, s));
-        return launch_row_scatter(Xn, piv, (int)n, Vt, s);
-    }
     if (n <= kPcholGridMaxN) {
         CK(launch_pchol_grid(B, (int)n, Xw, n, (unsigned long long *)prm, st, s));
         if (jacobi_mixed_applies(n))
@@ -806,18 +799,23 @@ int finish_batch(BatchGraph *g, tssvd_desc *d, int count, const tssvd_opts *o, D
         d[i].status = code;
         d[i].out_rank = h[i].rank;
         d[i].mode = modes[i];
+        for (int j = 0; j < 3; j++) d[i].sweeps[j] = h[i].sweeps[j];
         if (first == TSSVD_OK && code != TSSVD_OK) first = code;
     }
     return first;
 }
 
 // Pinned host copies of the three task arrays of a cached phased graph
-// (the graph copies them to the device at the start of every replay).
+// (the graph copies them to the device at the start of every replay), and
+// the event pairs the graph records around its three batched solves.
 struct PinnedTasks {
     JacobiTask *h = nullptr;
+    cudaEvent_t ev[6] = {};
     ~PinnedTasks()
     {
         if (h) cudaFreeHost(h);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 std::vector<std::pair<std::vector<unsigned long long>, std::shared_ptr<PinnedTasks>>> g_phased_tasks;
@@ -1130,6 +1128,11 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
             cudaGetLastError();
             return TSSVD_ENOMEM;
         }
+        for (cudaEvent_t &ev : pin->ev)
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                cudaGetLastError();
+                return TSSVD_ECUDA;
+            }
         std::vector<int> by_n(count);
         for (int i = 0; i < count; i++) by_n[i] = i;
         std::stable_sort(by_n.begin(), by_n.end(), [&](int a, int b) { return d[a].n > d[b].n; });
@@ -1169,8 +1172,13 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
                 e2 = cudaStreamWaitEvent(s, W.join[w], 0);
                 if (e == cudaSuccess) e = e2;
             }
+            // (external records: event nodes of the graph, readable after a replay)
+            if (phase < 3 && e == cudaSuccess)
+                e = cudaEventRecordWithFlags(pin->ev[2 * phase], s, cudaEventRecordExternal);
             if (phase < 3 && e == cudaSuccess)
                 e = launch_jacobi_batch(dtasks + (size_t)phase * count, count, o->max_sweeps, s);
+            if (phase < 3 && e == cudaSuccess)
+                e = cudaEventRecordWithFlags(pin->ev[2 * phase + 1], s, cudaEventRecordExternal);
         }
         cudaError_t ec = cudaStreamEndCapture(s, &graph);
         tssvd_profile_enable(prof);
@@ -1199,7 +1207,19 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
         add_launches(g->kernels);
     }
     std::vector<int> modes(count, TSSVD_FP64_TC);
-    return finish_batch(g, d, count, o, sts, modes, s);
+    const int code = finish_batch(g, d, count, o, sts, modes, s);
+    if (profiling())
+        for (auto &pt : g_phased_tasks)
+            if (pt.first == key)
+                for (int p = 0; p < 3; p++) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, pt.second->ev[2 * p], pt.second->ev[2 * p + 1]) ==
+                        cudaSuccess)
+                        prof_add_ms("jacobi_batch", ms);
+                    else
+                        cudaGetLastError();
+                }
+    return code;
 }
 
 template <typename T>

@@ -30,6 +30,11 @@ int num_sms();
 
 // Adds kernel launches made by a graph replay to the launch counter.
 void add_launches(long long k);
+// Whether launch profiling is on, and a kernel time measured by the caller
+// (a launch inside a graph replay, timed by event nodes of the graph) added
+// to the profile under `name`.
+bool profiling();
+void prof_add_ms(const char *name, double ms);
 
 // Wraps one kernel launch: counts it, and when profiling is on records a
 // CUDA event pair around it on its stream (see profiler.cu).
@@ -239,7 +244,7 @@ struct JacobiMixedScratch {
     double *f32, *K, *T, *H, *X0, *P, *NP;
 };
 
-// Batched one-sided Jacobi (jacobi_batch.cu): one CTA per task, each an
+// Batched one-sided Jacobi (jacobi_batch.cu): a cluster of two CTAs per task, each an
 // independent n x n problem (n <= kJacobiBatchMaxN) with X column-major
 // (ldx = n), J (n x n, column-major) set to the identity and receiving the
 // rotations when non-null, threshold tol as launch_jacobi, and its sweep

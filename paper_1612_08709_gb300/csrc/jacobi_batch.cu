@@ -1,15 +1,16 @@
 // Batched one-sided (Hestenes) Jacobi: many independent small solves in one
-// launch, one CTA per problem.
+// launch, a cluster of two CTAs per problem.
 //
 // The grid solver (jacobi.cu) spreads one problem over the GPU, one CTA per
 // rotation pair and a grid barrier per round, which minimises one solve's
 // latency.  A batch of hundreds of problems wants throughput instead: on
 // this GPU the FP64 pipe (two lanes per clock per SM) bounds the rotations,
-// so each problem's rounds run inside one CTA (a __syncthreads per round,
-// no grid barrier and no spin-wait), and the problems fill the SMs side by
-// side.  Tasks are given largest first so that the long solves start first.
+// so each problem's rounds run inside a small cluster (a hardware cluster
+// barrier per round, no grid barrier and no spin-wait), and the problems
+// fill the SMs side by side.  Tasks are given largest first so that the
+// long solves start first.
 //
-// A CTA of 8 warps takes the n/2 pairs of a round, one warp per pair at a
+// The cluster's warps take the n/2 pairs of a round, one warp per pair at a
 // time: each lane holds up to 8 entries of the two columns in registers,
 // the inner product is a warp reduction (an xor butterfly, so every lane
 // holds the same bits and takes the same decision), the rotation comes
@@ -18,6 +19,8 @@
 // (recomputed at every sweep start, and for a column whose update cancels
 // below 2^-16 of its inputs).  Rounds follow the circle schedule, so a
 // sweep visits every pair once, in the grid solver's order.
+#include <cooperative_groups.h>
+
 #include "jacobi_common.cuh"
 
 namespace tssvd {
@@ -26,6 +29,10 @@ namespace {
 
 constexpr int kBatchJacobiThreads = 256;
 constexpr int kBatchJacobiWarps = kBatchJacobiThreads / 32;
+// CTAs per task.  Measured on 512 members (n 16..256): one CTA 1,965 ms a
+// step, two 1,550, four 1,631 -- two halve the largest members' solves,
+// which set each launch's length, for one cluster barrier a round.
+constexpr int kBatchCluster = 2;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -34,36 +41,57 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(kBatchJacobiThreads)
-    jacobi_batch_kernel(const JacobiTask *tasks, int max_sweeps)
+// One solve spread over a cluster of C CTAs (C x 8 warps take the pairs of
+// a round).  The round boundary is the cluster barrier (a
+// hardware barrier with release / acquire ordering at cluster scope, so the
+// columns one CTA rotated are seen by the others in the next round); each
+// CTA keeps a copy of the tracked norms in its shared memory and a warp
+// that updates a norm writes it into every copy (distributed shared
+// memory); the sweep's rotation count is summed in rank 0's shared memory.
+// Control flow is uniform over the cluster (the sweep loop ends on the
+// summed count), so every CTA reaches every barrier.
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kBatchJacobiThreads)
+    jacobi_batch_cluster_kernel(const JacobiTask *tasks, int max_sweeps)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
     __shared__ double nrm[kJacobiBatchMaxN];
     __shared__ int rot_count;
-    const JacobiTask tk = tasks[blockIdx.x];
+    const int rank = (int)cl.block_rank();
+    const JacobiTask tk = tasks[blockIdx.x / C];
     const int n = tk.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (n < 2 || n > kJacobiBatchMaxN) {
-        if (threadIdx.x == 0) tk.st->sweeps[tk.which] = n < 2 ? 0 : -1;
+        if (threadIdx.x == 0 && rank == 0) tk.st->sweeps[tk.which] = n < 2 ? 0 : -1;
         return;
     }
+    double *nrm_r[C];
+#pragma unroll
+    for (int r = 0; r < C; r++) nrm_r[r] = cl.map_shared_rank(nrm, r);
+    int *cnt0 = cl.map_shared_rank(&rot_count, 0);
+    cl.sync();  // every CTA of the cluster runs before its shared memory is written
+    const int gw = rank * kBatchJacobiWarps + warp, GW = C * kBatchJacobiWarps;
     double *X = tk.X, *J = tk.J;
     const int npad = n + (n & 1), rounds = npad - 1;
     const double tol = tk.tol;
     const float log2tol = log2f((float)tol);
     int done = -1;
     for (int sweep = 1; sweep <= max_sweeps; sweep++) {
-        for (int j = warp; j < n; j += kBatchJacobiWarps) {
+        for (int j = gw; j < n; j += GW) {
             const double *x = X + (size_t)j * n;
             double acc = 0.0;
             for (int i = lane; i < n; i += 32) acc = fma(x[i], x[i], acc);
             acc = warp_sum(acc);
-            if (lane == 0) nrm[j] = acc;
+            if (lane == 0)
+#pragma unroll
+                for (int r = 0; r < C; r++) nrm_r[r][j] = acc;
         }
-        if (threadIdx.x == 0) rot_count = 0;
-        __syncthreads();
+        if (threadIdx.x == 0 && rank == 0) rot_count = 0;
+        cl.sync();
         int my_rot = 0;
         for (int t = 0; t < rounds; t++) {
-            for (int k = warp; k < npad / 2; k += kBatchJacobiWarps) {
+            for (int k = gw; k < npad / 2; k += GW) {
                 int P, Q;
                 circle_pair(k, t, npad, P, Q);
                 if (Q >= n) continue;
@@ -92,58 +120,56 @@ __global__ void __launch_bounds__(kBatchJacobiThreads)
                     if (b < 0.0) b = sb;
                 }
                 const double4 r = jac_rotation(a, b, g, tol, log2tol);
-                if (r.w == 0.0) {
-                    if (lane == 0) {
-                        nrm[P] = a;
-                        nrm[Q] = b;
-                    }
-                    continue;
-                }
-                const double c = r.x, sn = r.y;
-#pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    const int i = lane + 32 * e;
-                    if (i < n) {
-                        xp[i] = c * u[e] - sn * v[e];
-                        xq[i] = sn * u[e] + c * v[e];
-                    }
-                }
-                if (J) {
-                    double *jp = J + (size_t)P * n, *jq = J + (size_t)Q * n;
+                double a1 = a, b1 = b;
+                if (r.w != 0.0) {
+                    const double c = r.x, sn = r.y;
 #pragma unroll
                     for (int e = 0; e < 8; e++) {
                         const int i = lane + 32 * e;
                         if (i < n) {
-                            const double x = jp[i], y = jq[i];
-                            jp[i] = c * x - sn * y;
-                            jq[i] = sn * x + c * y;
+                            xp[i] = c * u[e] - sn * v[e];
+                            xq[i] = sn * u[e] + c * v[e];
                         }
                     }
-                }
-                if (lane == 0) {
-                    // ||c x_P - s x_Q||^2 and ||s x_P + c x_Q||^2; an update
-                    // that cancels below 2^-16 of its inputs is recomputed
+                    if (J) {
+                        double *jp = J + (size_t)P * n, *jq = J + (size_t)Q * n;
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int i = lane + 32 * e;
+                            if (i < n) {
+                                const double x = jp[i], y = jq[i];
+                                jp[i] = c * x - sn * y;
+                                jq[i] = sn * x + c * y;
+                            }
+                        }
+                    }
                     const double cc = c * c, ss = sn * sn, cs2 = 2.0 * c * sn;
-                    const double a1 = fma(cc, a, fma(-cs2, g, ss * b));
-                    const double b1 = fma(ss, a, fma(cs2, g, cc * b));
+                    a1 = fma(cc, a, fma(-cs2, g, ss * b));
+                    b1 = fma(ss, a, fma(cs2, g, cc * b));
                     const double floor = 0x1p-16 * (a + b);
-                    nrm[P] = (a1 >= floor) ? a1 : -1.0;
-                    nrm[Q] = (b1 >= floor) ? b1 : -1.0;
+                    if (!(a1 >= floor)) a1 = -1.0;
+                    if (!(b1 >= floor)) b1 = -1.0;
+                    my_rot++;
                 }
-                my_rot++;
+                if (lane == 0)
+#pragma unroll
+                    for (int q = 0; q < C; q++) {
+                        nrm_r[q][P] = a1;
+                        nrm_r[q][Q] = b1;
+                    }
             }
-            __syncthreads();  // this round's columns written before the next reads them
+            cl.sync();  // this round's columns and norms seen by the whole cluster
         }
-        if (lane == 0 && my_rot != 0) atomicAdd(&rot_count, my_rot);
-        __syncthreads();
-        const int total = rot_count;
-        __syncthreads();  // every thread has read the count before it is reset
+        if (lane == 0 && my_rot != 0) atomicAdd(cnt0, my_rot);
+        cl.sync();
+        const int total = *cnt0;
+        cl.sync();  // every CTA has read the count before rank 0 resets it
         if (total == 0) {
             done = sweep;
             break;
         }
     }
-    if (threadIdx.x == 0) tk.st->sweeps[tk.which] = done;
+    if (threadIdx.x == 0 && rank == 0) tk.st->sweeps[tk.which] = done;
 }
 
 __global__ void init_identity_batch_kernel(const JacobiTask *tasks)
@@ -168,7 +194,8 @@ cudaError_t launch_jacobi_batch(const JacobiTask *tasks, int ntasks, int max_swe
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ProfScope ps_("jacobi_batch", s);
-    jacobi_batch_kernel<<<ntasks, kBatchJacobiThreads, 0, s>>>(tasks, max_sweeps);
+    jacobi_batch_cluster_kernel<kBatchCluster>
+        <<<kBatchCluster * ntasks, kBatchJacobiThreads, 0, s>>>(tasks, max_sweeps);
     return cudaGetLastError();
 }
 

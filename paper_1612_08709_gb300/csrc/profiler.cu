@@ -30,6 +30,7 @@ std::atomic<int> g_enabled{0};
 std::mutex g_mu;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
+std::vector<std::pair<const char *, double>> g_host_recs;  // times taken elsewhere
 
 cudaEvent_t take_event()
 {
@@ -73,6 +74,15 @@ ProfScope::~ProfScope()
 }
 
 void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+bool profiling() { return g_enabled.load(std::memory_order_relaxed) != 0; }
+
+void prof_add_ms(const char *name, double ms)
+{
+    if (!profiling()) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_host_recs.emplace_back(name, ms);
+}
 
 namespace {
 
@@ -173,6 +183,12 @@ size_t tssvd_profile_report(char *buf, size_t len)
         }
     }
     if (consume) g_recs.clear();
+    for (auto &hr : g_host_recs) {
+        auto &e = agg[hr.first];
+        e.first += 1;
+        e.second += hr.second;
+    }
+    if (consume) g_host_recs.clear();
     std::string out;
     char line[256];
     for (auto &kv : agg) {
