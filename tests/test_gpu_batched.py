@@ -140,3 +140,40 @@ def test_batched_full_ranges_every_member_vs_oracle(orc, mode):
         tolv = np.clip(1e-10 * Sr[0] / gaps(Sr), 1e-13, 1.0)
         assert np.all(col_err_up_to_sign(V, Vr) <= tolv)
         assert np.all(col_err_up_to_sign(U, Ur) <= tolv)
+
+
+@gpu
+def test_phased_batch_fp32_storage_and_rank_deficiency(orc):
+    """The phased executor (mode auto, n <= 256) with FP32 storage, and with
+    FP64 storage on members whose trailing singular values are exactly
+    zero (the discard steps drop those columns: exact zeros in S, U, V)."""
+    torch = _torch()
+    import paper_1612_08709_gb300 as pkg
+    shapes = [(6000, 40), (3000, 120), (9000, 7), (2500, 200)]
+    mats, ranks = [], []
+    for i, (m, n) in enumerate(shapes):
+        s = workloads.sigma_geometric(n, 1e-4)
+        r = max(1, n - 1 - n // 4)
+        s[r:] = 0.0
+        A, _, _, _ = workloads.known_spectrum(m, n, s, 4100 + i)
+        mats.append(A)
+        ranks.append(r)
+    As = [torch.as_tensor(A, device="cuda") for A in mats]
+    outs, infos, rc = pkg.ts_svd_batched(As, drop_tol=1e-6, mode="auto")
+    for A, r, (U, S, V), info in zip(mats, ranks, outs, infos):
+        Ur, Sr, Vr, rr, st = orc.ts_svd(A, drop_tol=1e-6)
+        assert info["mode"] == "fp64_tc" and info["rank"] == rr == r
+        U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+        assert np.abs(S - Sr).max() <= 1e-11 * Sr[0]
+        assert np.all(S[r:] == 0) and np.all(U[:, r:] == 0) and np.all(V[:, r:] == 0)
+        assert np.abs(U[:, :r].T @ U[:, :r] - np.eye(r)).max() <= 1e-12
+        assert np.abs(V[:, :r].T @ V[:, :r] - np.eye(r)).max() <= 1e-12
+    As32 = [torch.as_tensor(A, dtype=torch.float32, device="cuda") for A in mats]
+    outs, infos, rc = pkg.ts_svd_batched(As32, drop_tol=1e-6, mode="auto")
+    for A, (U, S, V), info in zip(mats, outs, infos):
+        Sr = np.linalg.svd(A.astype(np.float32).astype(np.float64), compute_uv=False)
+        r = info["rank"]
+        assert info["mode"] == "fp64_tc"
+        assert np.abs(S.double().cpu().numpy()[:r] - Sr[:r]).max() <= 1e-5 * Sr[0]
+        Ud = U.double().cpu().numpy()[:, :r]
+        assert np.abs(Ud.T @ Ud - np.eye(r)).max() <= 1e-5
