@@ -107,10 +107,10 @@ typedef struct {
     /* Jacobi sweeps: [0] the first eigensolve (of A^T A, D-scaled; with
      * passes = 2, n <= 2048 and an FP64-accurate mode, the one-sided sweeps
      * on its pivoted Cholesky factor), [1] eig of Y^T Y, [2] SVD of R;
-     * for 256 < n <= 2048 the one-sided solves ([0] and [2]) start with an
-     * FP32 phase, and [0], [2] count their FP64 sweeps while [3] holds the
-     * FP32 sweeps of both such solves, summed (0 when none ran); with
-     * passes = 3, [1] is the third pass's eigensolve */
+     * for 128 < n <= 2048 the one-sided solves ([0] and [2]; [1] too for
+     * n > 256) start with an FP32 phase, and [0..2] count their FP64 sweeps
+     * while [3] holds the FP32 sweeps of all such solves, summed (0 when
+     * none ran); with passes = 3, [1] is the third pass's eigensolve */
     int sweeps[4];
     int ranks[2];     /* ranks kept by the first and second discard steps */
 } tssvd_opts;
@@ -136,9 +136,10 @@ size_t ts_svd_workspace_size(int64_t m, int64_t n, int elem_bytes, const tssvd_o
  * Gram matrix (the second pass repairs the rest): for n <= 2048 in the
  * FP64-accurate modes it is a pivoted Cholesky factorization followed by
  * one-sided Jacobi on the factor, otherwise Gram-form Jacobi with a
- * normwise floor.  For 256 < n <= 2048 the one-sided solves (the first
- * eigensolve and the SVD of R) run an FP32 phase first to pick the
- * starting basis, then converge in FP64 (FP64 results either way).
+ * normwise floor.  For 128 < n <= 2048 the one-sided solves (the first
+ * eigensolve and the SVD of R; for n > 256 the second eigensolve too, on
+ * the pivoted Cholesky factor of Y^T Y) run an FP32 phase first to pick
+ * the starting basis, then converge in FP64 (FP64 results either way).
  *   A   [in]  m x n, row-major, leading dimension lda >= n; not modified.
  *   U   [out] m x n, row-major (leading dimension n).
  *   S   [out] n.

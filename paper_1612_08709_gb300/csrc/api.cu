@@ -136,7 +136,7 @@ inline int mode_terms(int mode) { return mode == TSSVD_BF16X6 ? 3 : (mode == TSS
 // sweeps of the Gram-form solver (13 sweeps instead of 37 on 1,000,000 x
 // 1,000 with sigma 1 .. 1e-8).  The grid factorization replaced the
 // single-CTA one here (2.9 -> 1.1 ms at n = 200); the single-CTA one
-// serves the batched solves.  For n > kJacobiMixedMinN the Jacobi solve
+// serves the batched solves.  For n >= kJacobiMixedMinN the Jacobi solve
 // starts with the FP32 phase.  Larger n: Gram-form Jacobi with the
 // normwise floor.  Scratch: Xw, Jw, B2, Xn (n x n), norms, lam (n), perm,
 // piv (n ints).
@@ -161,20 +161,21 @@ static cudaError_t first_eig(double *B, double *B2, i64 n, double *Xw, double *J
 
 // The second eigensolve of Algorithm 4, Z = W D W^T (Z consumed), with
 // the relative rotation test (W must diagonalise Z to working precision:
-// it sets the orthonormality of Q).  For kJacobiMixedMinN <= n <=
+// it sets the orthonormality of Q).  For kPcholMaxN < n <=
 // kPcholGridMaxN: Z = R~^T R~ by the grid pivoted Cholesky (Z is well
 // conditioned: the first pass leaves Y with a condition number near 10),
 // then the two-precision one-sided Jacobi on R~^T without accumulation;
 // the orthogonalised columns, normalised, are the eigenvectors.  Its FP64
 // sweeps cost 3.5 n^2 operations a round against the Gram-form solver's
 // 6 n^2, and the FP32 phase takes the first few orders of magnitude.
-// Otherwise the Gram-form solver.
+// Otherwise the Gram-form solver (at n <= 256 its two rounds a barrier
+// keep it the faster one).
 static cudaError_t second_eig(double *Z, double *Z2, i64 n, double *Xw, double *Jw, double *lam,
                               double *norms, double *W, int max_sweeps, int *ctr, double *prm,
                               int *perm, int *piv, DevStatus *st, cudaStream_t s,
                               const JacobiMixedScratch &mw)
 {
-    if (jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
+    if (n > kPcholMaxN && jacobi_mixed_applies(n) && n <= kPcholGridMaxN) {
         CK(launch_pchol_grid(Z, (int)n, Xw, n, (unsigned long long *)prm, st, s));
         CK(launch_jacobi_mixed(Xw, n, nullptr, mw, max_sweeps, ctr, prm, st, 1, s));
         return launch_jacobi_finalize(Xw, n, nullptr, n, (int)n, (int)n, norms, perm, nullptr, n,

@@ -237,7 +237,9 @@ cudaError_t launch_pchol_grid(double *W, int n, double *X, i64 ldx, unsigned lon
 // K, T, H, X0 (n x n doubles each), P (tn_splits(n, n, n, false) * n * n
 // doubles) and NP (nn_grid_rows(n, n) * n doubles); prm and ctr as for
 // launch_jacobi.
-constexpr int kJacobiMixedMinN = 257;
+// From n = 129 the FP32 phase pays for its conversions and Newton-Schulz
+// products (2,000,000 x 200: 67.9 -> 63.4 ms; at n = 50..100 even).
+constexpr int kJacobiMixedMinN = 129;
 constexpr int kJacobiMixedMaxN = 2048;
 constexpr int kJacobiMixedF32Sweeps = 40;
 struct JacobiMixedScratch {
