@@ -995,7 +995,10 @@ def run_batched(args):
                       "l2": "inputs larger than L2 (%.0f GB)" % (sum(m * n for m, n in shapes) * 8 / 1e9)},
            "gpu_launches": int(launches), "clocks": clk,
            "kernels_ms": {k: {"launches": c, "total_ms": t} for k, (c, t) in kernels.items()},
-           "accuracy": {"sigma_err_normwise_max": err, "orth_U_max": orth},
+           "accuracy": {"sigma_err_normwise_max": err, "orth_U_max": orth,
+                        "sweeps_mean": [round(sum(max(i["sweeps"][j], 0) for i in infos) / len(infos), 2)
+                                        for j in range(3)],
+                        "sweeps_max": [max(i["sweeps"][j] for i in infos) for j in range(3)]},
            "loop_baseline": None if loop_ms is None else
            {"ms_per_step": loop_ms, "value": flops / (loop_ms * 1e-3) / 1e9,
             "speedup_of_batched": loop_ms / ms}}

@@ -856,7 +856,14 @@ struct PhasedMember {
     double *d, *dinv, *sig, *sinv, *tinv;  // n
     int *pk1, *piv, *pk2;                  // n
     double *Y;                             // m x n: Y~
+    float *w32;                            // 2 n^2: FP32 phase (n >= kBatchMixedMinN)
+    double *wk;                            // 2 n^2: Newton-Schulz
 };
+
+// From this n the batched first eigensolve and SVD of R start with an FP32
+// phase (the batch is bound by FP64 work: the phase leaves about 4 FP64
+// sweeps of 10-14, for about two sweeps' worth of Newton-Schulz products).
+constexpr i64 kBatchMixedMinN = 64;
 
 struct PhasedScratch {
     unsigned long long *bits;
@@ -883,6 +890,9 @@ void take_member(Bump &b, i64 m, i64 n, bool own_y, PhasedMember &p)
     p.piv = b.take<int>(n);
     p.pk2 = b.take<int>(n);
     p.Y = own_y ? b.take<double>((size_t)m * n) : nullptr;
+    const bool mixed = n >= kBatchMixedMinN;
+    p.w32 = mixed ? b.take<float>(2 * (size_t)nn) : nullptr;
+    p.wk = mixed ? b.take<double>(2 * (size_t)nn) : nullptr;
 }
 
 void take_scratch(Bump &b, i64 m, i64 n, PhasedScratch &c)
@@ -1140,9 +1150,11 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
         for (int k = 0; k < count; k++) {
             const int i = by_n[k];
             const int n = (int)d[i].n;
-            pin->h[k] = JacobiTask{pm[i].X, nullptr, n, 0, 0x1p-51, &sts[i]};
-            pin->h[count + k] = JacobiTask{pm[i].X, nullptr, n, 1, (double)n * 0x1p-53, &sts[i]};
-            pin->h[2 * count + k] = JacobiTask{pm[i].X, pm[i].J, n, 2, (double)n * 0x1p-53, &sts[i]};
+            pin->h[k] = JacobiTask{pm[i].X, nullptr, n, 0, 0x1p-51, &sts[i], pm[i].w32, pm[i].wk};
+            pin->h[count + k] = JacobiTask{pm[i].X, nullptr, n, 1, (double)n * 0x1p-53, &sts[i],
+                                           nullptr, nullptr};
+            pin->h[2 * count + k] = JacobiTask{pm[i].X, pm[i].J, n, 2, (double)n * 0x1p-53,
+                                               &sts[i], pm[i].w32, pm[i].wk};
         }
         const long long n0 = tssvd_launch_count();
         const int prof = tssvd_profile_enable(0);  // no event records inside the graph

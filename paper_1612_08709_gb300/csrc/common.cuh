@@ -260,6 +260,10 @@ struct JacobiTask {
     int which;
     double tol;
     DevStatus *st;
+    // non-null: the solve starts with an FP32 phase (its sweeps added to
+    // st->sweeps[3]); scratch of 2 n^2 floats and 2 n^2 doubles
+    float *w32;
+    double *wk;
 };
 cudaError_t launch_jacobi_batch(const JacobiTask *tasks, int ntasks, int max_sweeps,
                                 cudaStream_t s);

@@ -33,12 +33,67 @@ constexpr int kBatchJacobiWarps = kBatchJacobiThreads / 32;
 // step, two 1,550, four 1,631 -- two halve the largest members' solves,
 // which set each launch's length, for one cluster barrier a round.
 constexpr int kBatchCluster = 2;
+constexpr int kBatchF32Sweeps = 40;  // cap of the FP32 phase
 
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_maxi(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// C = op(A) B for n x n column-major matrices (op(A) = A^T when trans),
+// the cluster's threads (tid of NTC) sharing 4 x 4 output blocks.  FP64
+// FMAs from L1/L2-resident operands: n^3 FMAs, about two FP64 sweeps'
+// worth of work at n = 256.
+__device__ void cluster_gemm(const double *A, const double *B, double *Cm, int n, bool trans,
+                             int tid, int NTC)
+{
+    const int nb = (n + 3) / 4;
+    for (int blk = tid; blk < nb * nb; blk += NTC) {
+        const int i0 = (blk % nb) * 4, j0 = (blk / nb) * 4;
+        double acc[4][4];
+#pragma unroll
+        for (int ii = 0; ii < 4; ii++)
+#pragma unroll
+            for (int jj = 0; jj < 4; jj++) acc[ii][jj] = 0.0;
+        for (int k = 0; k < n; k++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int ii = 0; ii < 4; ii++) {
+                const int i = i0 + ii;
+                a[ii] = i < n ? (trans ? A[(size_t)i * n + k] : A[(size_t)k * n + i]) : 0.0;
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; jj++) {
+                const int j = j0 + jj;
+                b[jj] = j < n ? B[(size_t)j * n + k] : 0.0;
+            }
+#pragma unroll
+            for (int ii = 0; ii < 4; ii++)
+#pragma unroll
+                for (int jj = 0; jj < 4; jj++) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; jj++)
+#pragma unroll
+            for (int ii = 0; ii < 4; ii++)
+                if (i0 + ii < n && j0 + jj < n) Cm[(size_t)(j0 + jj) * n + i0 + ii] = acc[ii][jj];
+    }
 }
 
 // One solve spread over a cluster of C CTAs (C x 8 warps take the pairs of
@@ -58,6 +113,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kBatchJacobiThreads)
     cg::cluster_group cl = cg::this_cluster();
     __shared__ double nrm[kJacobiBatchMaxN];
     __shared__ int rot_count;
+    __shared__ int emax_s;
     const int rank = (int)cl.block_rank();
     const JacobiTask tk = tasks[blockIdx.x / C];
     const int n = tk.n;
@@ -76,6 +132,116 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kBatchJacobiThreads)
     const int npad = n + (n & 1), rounds = npad - 1;
     const double tol = tk.tol;
     const float log2tol = log2f((float)tol);
+    if (tk.w32) {
+        // Two-precision start: the same one-sided sweeps in FP32 on X
+        // scaled by a power of two (threshold 2^-20, at most
+        // kBatchF32Sweeps sweeps) accumulate J32; K = J32 in FP64 made
+        // orthogonal by two Newton-Schulz steps K <- K (3I - K^T K) / 2;
+        // X <- X K, and J starts as K.  The FP64 sweeps below then decide
+        // the result.
+        const int nn = n * n;
+        const int tid = rank * kBatchJacobiThreads + (int)threadIdx.x;
+        const int NTC = C * kBatchJacobiThreads;
+        float *X32 = tk.w32, *J32 = tk.w32 + (size_t)nn;
+        double *K = tk.wk, *H = tk.wk + (size_t)nn, *Kn = reinterpret_cast<double *>(tk.w32);
+        int *emax0 = cl.map_shared_rank(&emax_s, 0);
+        if (threadIdx.x == 0 && rank == 0) emax_s = -2000;
+        cl.sync();
+        int em = -2000;
+        for (int e = tid; e < nn; e += NTC) {
+            const double v = fabs(X[e]);
+            if (v > 0.0) em = max(em, ilogb(v));
+        }
+        em = warp_maxi(em);
+        if (lane == 0) atomicMax(emax0, em);
+        cl.sync();
+        const int E = *emax0;
+        for (int e = tid; e < nn; e += NTC) {
+            X32[e] = (float)ldexp(X[e], -E);
+            J32[e] = (e / n == e % n) ? 1.0f : 0.0f;
+        }
+        cl.sync();
+        int f32_sweeps = kBatchF32Sweeps;
+        for (int sweep = 1; sweep <= kBatchF32Sweeps; sweep++) {
+            if (threadIdx.x == 0 && rank == 0) rot_count = 0;
+            cl.sync();
+            int my_rot = 0;
+            for (int t = 0; t < rounds; t++) {
+                for (int k = gw; k < npad / 2; k += GW) {
+                    int P, Q;
+                    circle_pair(k, t, npad, P, Q);
+                    if (Q >= n) continue;
+                    float *xp = X32 + (size_t)P * n, *xq = X32 + (size_t)Q * n;
+                    float *jp = J32 + (size_t)P * n, *jq = J32 + (size_t)Q * n;
+                    float u[8], v[8], ju[8], jv[8];
+                    float a = 0.0f, b = 0.0f, g = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                        const int i = lane + 32 * c;
+                        u[c] = i < n ? xp[i] : 0.0f;
+                        v[c] = i < n ? xq[i] : 0.0f;
+                        ju[c] = i < n ? jp[i] : 0.0f;
+                        jv[c] = i < n ? jq[i] : 0.0f;
+                        a = fmaf(u[c], u[c], a);
+                        b = fmaf(v[c], v[c], b);
+                        g = fmaf(u[c], v[c], g);
+                    }
+                    a = warp_sumf(a);
+                    b = warp_sumf(b);
+                    g = warp_sumf(g);
+                    if (!(a > 0.0f && b > 0.0f && fabsf(g) > 0x1p-20f * sqrtf(a) * sqrtf(b)))
+                        continue;
+                    const float zeta = (b - a) / (2.0f * g);
+                    const float tt = fabsf(zeta) > 1e18f
+                                         ? 0.5f / zeta
+                                         : copysignf(1.0f, zeta) /
+                                               (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                    const float c = rsqrtf(fmaf(tt, tt, 1.0f)), sn = c * tt;
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const int i = lane + 32 * e;
+                        if (i < n) {
+                            xp[i] = c * u[e] - sn * v[e];
+                            xq[i] = sn * u[e] + c * v[e];
+                            jp[i] = c * ju[e] - sn * jv[e];
+                            jq[i] = sn * ju[e] + c * jv[e];
+                        }
+                    }
+                    my_rot++;
+                }
+                cl.sync();
+            }
+            if (lane == 0 && my_rot != 0) atomicAdd(cnt0, my_rot);
+            cl.sync();
+            const int total = *cnt0;
+            cl.sync();
+            if (total == 0) {
+                f32_sweeps = sweep;
+                break;
+            }
+        }
+        if (threadIdx.x == 0 && rank == 0) atomicAdd(&tk.st->sweeps[3], f32_sweeps);
+        for (int e = tid; e < nn; e += NTC) K[e] = (double)J32[e];
+        cl.sync();
+        for (int it = 0; it < 2; it++) {
+            cluster_gemm(K, K, H, n, true, tid, NTC);  // H = K^T K
+            cl.sync();
+            for (int e = tid; e < nn; e += NTC)
+                H[e] = ((e / n == e % n) ? 1.5 : 0.0) - 0.5 * H[e];
+            cl.sync();
+            cluster_gemm(K, H, Kn, n, false, tid, NTC);  // Kn = K (3I - K^T K) / 2
+            cl.sync();
+            for (int e = tid; e < nn; e += NTC) K[e] = Kn[e];
+            cl.sync();
+        }
+        cluster_gemm(X, K, H, n, false, tid, NTC);  // H = X K
+        cl.sync();
+        for (int e = tid; e < nn; e += NTC) {
+            X[e] = H[e];
+            if (J) J[e] = K[e];
+        }
+        cl.sync();
+    }
     int done = -1;
     for (int sweep = 1; sweep <= max_sweeps; sweep++) {
         for (int j = gw; j < n; j += GW) {
