@@ -421,7 +421,9 @@ typedef struct {
  * batch runs in phases instead: the members' tall products and small steps
  * on the worker streams, and each of the three Jacobi solves of all members
  * as one launch with a cluster of two thread blocks per member (the eigensolves
- * one-sided on the pivoted Cholesky factor); every member then runs
+ * one-sided on the pivoted Cholesky factor; for n >= 64 the first
+ * eigensolve and the SVD of R start with an FP32 phase, as the single-call
+ * solver does from n = 129); every member then runs
  * TSSVD_FP64_TC, its per-solve state is kept in the workspace between the
  * phases, and for double members U's storage holds Y~ until U is written.
  * Results match single calls to rounding (bit for bit on the per-member

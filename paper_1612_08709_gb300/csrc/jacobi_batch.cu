@@ -1,5 +1,6 @@
 // Batched one-sided (Hestenes) Jacobi: many independent small solves in one
-// launch, a cluster of two CTAs per problem.
+// launch, a cluster of two CTAs per problem, optionally started by an FP32
+// phase (see the kernel).
 //
 // The grid solver (jacobi.cu) spreads one problem over the GPU, one CTA per
 // rotation pair and a grid barrier per round, which minimises one solve's
