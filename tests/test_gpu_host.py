@@ -20,9 +20,9 @@ def _torch():
 
 
 @gpu
-@pytest.mark.parametrize("mode", ["fp64_tc", "fp64"])
+@pytest.mark.parametrize("mode,passes", [("fp64_tc", 2), ("fp64", 2), ("fp64_tc", 3)])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_call_matches_oracle(orc, mode, pinned):
+def test_host_call_matches_oracle(orc, mode, passes, pinned):
     torch = _torch()
     import paper_1612_08709_gb300 as pkg
     m, n = 20011, 48
@@ -30,7 +30,7 @@ def test_host_call_matches_oracle(orc, mode, pinned):
     Ah = torch.as_tensor(A)
     if pinned:
         Ah = Ah.pin_memory()
-    U, S, V, info = pkg.ts_svd_host(Ah, drop_tol=0.0, mode=mode)
+    U, S, V, info = pkg.ts_svd_host(Ah, passes=passes, drop_tol=0.0, mode=mode)
     assert not U.is_cuda and info["rank"] == n
     Ur, Sr, Vr, rr, st = orc.ts_svd(A, drop_tol=0.0)
     U, S, V = U.numpy(), S.numpy(), V.numpy()
