@@ -811,10 +811,12 @@ int finish_batch(BatchGraph *g, tssvd_desc *d, int count, const tssvd_opts *o, D
 // the event pairs the graph records around its three batched solves.
 struct PinnedTasks {
     JacobiTask *h = nullptr;
+    PcholTask *hp = nullptr;
     cudaEvent_t ev[6] = {};
     ~PinnedTasks()
     {
         if (h) cudaFreeHost(h);
+        if (hp) cudaFreeHost(hp);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -852,6 +854,7 @@ void evict_tasks(const std::vector<unsigned long long> &key)
 // before the final product overwrites it).
 
 struct PhasedMember {
+    double *B;                             // n x n: the Gram matrix to factor
     double *X, *J, *Vt, *W;                // n x n
     double *d, *dinv, *sig, *sinv, *tinv;  // n
     int *pk1, *piv, *pk2;                  // n
@@ -870,13 +873,14 @@ struct PhasedScratch {
     int *exA, *exY, *em, *er, *perm;
     double *P, *NP, *Qw;
     uint8_t *img, *big;
-    double *B, *G2, *G, *R, *M, *M3, *Pm, *Vo, *Pp, *Xn;
+    double *G2, *G, *R, *M, *M3, *Pm, *Vo, *Pp, *Xn;
     double *lam, *norms, *Tn, *Tk, *sgn, *sigma, *jn;
 };
 
 void take_member(Bump &b, i64 m, i64 n, bool own_y, PhasedMember &p)
 {
     const i64 nn = n * n;
+    p.B = b.take<double>(nn);
     p.X = b.take<double>(nn);
     p.J = b.take<double>(nn);
     p.Vt = b.take<double>(nn);
@@ -912,7 +916,7 @@ void take_scratch(Bump &b, i64 m, i64 n, PhasedScratch &c)
     c.img = b.take<uint8_t>(oz_image_bytes((int)n, (int)n));
     const size_t gib = oz_gram_image_bytes(m, (int)n), rib = oz_row_image_bytes(m, (int)n);
     c.big = b.take<uint8_t>(gib > rib ? gib : rib);
-    double **nxn[] = {&c.B, &c.G2, &c.G, &c.R, &c.M, &c.M3, &c.Pm, &c.Vo, &c.Pp, &c.Xn};
+    double **nxn[] = {&c.G2, &c.G, &c.R, &c.M, &c.M3, &c.Pm, &c.Vo, &c.Pp, &c.Xn};
     for (double **q : nxn) *q = b.take<double>(nn);
     double **vec[] = {&c.lam, &c.norms, &c.Tn, &c.Tk, &c.sgn, &c.sigma, &c.jn};
     for (double **q : vec) *q = b.take<double>(n);
@@ -930,7 +934,7 @@ struct PhasedPlan {
     std::vector<int> order, worker;  // members by decreasing work; their workers
     std::vector<size_t> member_off;  // byte offsets of the members' state
     std::vector<size_t> slice_off, slice;  // workers' scratch
-    size_t status_bytes = 0, tasks_off = 0, total = 0;
+    size_t status_bytes = 0, tasks_off = 0, ptasks_off = 0, total = 0;
 };
 
 template <typename T>
@@ -958,6 +962,8 @@ PhasedPlan make_phased_plan(const tssvd_desc *d, int count)
     p.status_bytes = off;
     p.tasks_off = off;
     off += up(sizeof(JacobiTask) * 3 * (size_t)count);
+    p.ptasks_off = off;
+    off += up(sizeof(PcholTask) * (size_t)count);
     p.member_off.resize(count);
     const bool own_y = sizeof(T) != sizeof(double);
     for (int i = 0; i < count; i++) {
@@ -976,7 +982,8 @@ PhasedPlan make_phased_plan(const tssvd_desc *d, int count)
     return p;
 }
 
-// Segment A of member i: column maxima, Gram of A, pivoted Cholesky of B.
+// Segment A of member i: column maxima and the Gram matrix B of A (its
+// pivoted Cholesky runs batched after the segment).
 template <typename T>
 cudaError_t phase_a(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
                     PhasedScratch &c, DevStatus *st, cudaStream_t s)
@@ -994,12 +1001,11 @@ cudaError_t phase_a(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
     const int osp = oz_gram_splits(m, (int)n);
     CK(launch_oz_gram<T>(A, lda, m, (int)n, c.exA, osp, c.big, c.P, st, s));
     const double *rs = o->scale ? p.dinv : nullptr;
-    CK(launch_tn_reduce(c.P, osp, n, n, rs, rs, true, c.B, n, s));
-    return launch_pchol(c.B, (int)n, p.X, n, p.piv, s);
+    return launch_tn_reduce(c.P, osp, n, n, rs, rs, true, p.B, n, s);
 }
 
 // Segment B: V~ from the solved factor, Y~ = A (D^-1 V~), its Gram Z,
-// Sigma~, the discard, and the pivoted Cholesky of Z.
+// Sigma~ and the discard (Z's pivoted Cholesky runs batched after it).
 template <typename T>
 cudaError_t phase_b(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
                     PhasedScratch &c, DevStatus *st, cudaStream_t s)
@@ -1029,8 +1035,7 @@ cudaError_t phase_b(const tssvd_desc &dd, const tssvd_opts *o, PhasedMember &p,
     CK(launch_tn_reduce(c.P, osp, n, n, nullptr, nullptr, true, c.G2, n, s));
     CK(launch_diag_sqrt(c.G2, n, n, p.sig, s));
     CK(launch_discard(p.sig, n, o->drop_tol, p.sinv, &st->rank1, s));
-    CK(launch_scale2(c.G2, n, n, n, p.sinv, p.sinv, c.B, n, s));
-    return launch_pchol(c.B, (int)n, p.X, n, p.piv, s);
+    return launch_scale2(c.G2, n, n, n, p.sinv, p.sinv, p.B, n, s);
 }
 
 // Segment C: W from the solved factor, Q~ = Y W and its explicit norms T,
@@ -1102,6 +1107,7 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
     char *cb = (char *)base;
     DevStatus *sts = (DevStatus *)base;
     JacobiTask *dtasks = (JacobiTask *)(cb + plan.tasks_off);
+    PcholTask *dptasks = (PcholTask *)(cb + plan.ptasks_off);
     const bool own_y = sizeof(T) != sizeof(double);
     std::vector<PhasedMember> pm(count);
     for (int i = 0; i < count; i++) {
@@ -1135,7 +1141,8 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
     if (!g) {
         // the solve tasks, members by decreasing n (the long solves first)
         auto pin = std::make_shared<PinnedTasks>();
-        if (cudaMallocHost(&pin->h, sizeof(JacobiTask) * 3 * (size_t)count) != cudaSuccess) {
+        if (cudaMallocHost(&pin->h, sizeof(JacobiTask) * 3 * (size_t)count) != cudaSuccess ||
+            cudaMallocHost(&pin->hp, sizeof(PcholTask) * (size_t)count) != cudaSuccess) {
             cudaGetLastError();
             return TSSVD_ENOMEM;
         }
@@ -1155,13 +1162,18 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
                                            nullptr, nullptr};
             pin->h[2 * count + k] = JacobiTask{pm[i].X, pm[i].J, n, 2, (double)n * 0x1p-53,
                                                &sts[i], pm[i].w32, pm[i].wk};
+            pin->hp[k] = PcholTask{pm[i].B, pm[i].X, pm[i].piv, n};
         }
+        const int nmax = (int)d[by_n[0]].n;
         const long long n0 = tssvd_launch_count();
         const int prof = tssvd_profile_enable(0);  // no event records inside the graph
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(dtasks, pin->h, sizeof(JacobiTask) * 3 * (size_t)count,
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dptasks, pin->hp, sizeof(PcholTask) * (size_t)count,
                                 cudaMemcpyHostToDevice, s);
         for (int phase = 0; phase < 4 && e == cudaSuccess; phase++) {
             e = cudaEventRecord(W.fork, s);
@@ -1185,6 +1197,8 @@ int batched_phased(tssvd_desc *d, int count, tssvd_opts *o)
                 e2 = cudaStreamWaitEvent(s, W.join[w], 0);
                 if (e == cudaSuccess) e = e2;
             }
+            // the pivoted Cholesky factorizations of segments A and B, batched
+            if (phase < 2 && e == cudaSuccess) e = launch_pchol_batch(dptasks, count, nmax, s);
             // (external records: event nodes of the graph, readable after a replay)
             if (phase < 3 && e == cudaSuccess)
                 e = cudaEventRecordWithFlags(pin->ev[2 * phase], s, cudaEventRecordExternal);

@@ -218,6 +218,15 @@ cudaError_t launch_jacobi(double *X, i64 ldx, double *J, i64 ldj, int nr, int nc
 // One CTA; used for n <= kPcholMaxN.
 constexpr int kPcholMaxN = 256;
 cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStream_t s);
+// The same for many independent problems in one launch, one CTA each
+// (X with ldx = n; every n <= nmax <= 256; tasks a device array).
+struct PcholTask {
+    double *W;
+    double *X;
+    int *piv;
+    int n;
+};
+cudaError_t launch_pchol_batch(const PcholTask *tasks, int ntasks, int nmax, cudaStream_t s);
 // The same factorization over the whole grid (cooperative launch, one
 // barrier per pivot step) with logical pivoting: W stays in the original
 // order and X's column k is row k of R~ = R P^T (so W = R~^T R~, and X's

@@ -1184,9 +1184,8 @@ __global__ void permute_out_kernel(const double *X, i64 ldx, const double *J, i6
 // index i is original index piv[i]).
 constexpr int kPcholThreads = 1024;
 
-__global__ void __launch_bounds__(kPcholThreads, 1)
-    pchol_kernel(double *__restrict__ W, int n, double *__restrict__ X, i64 ldx,
-                 int *__restrict__ piv)
+__device__ __forceinline__ void pchol_body(double *__restrict__ W, int n, double *__restrict__ X,
+                                           i64 ldx, int *__restrict__ piv)
 {
     extern __shared__ double pc_s[];
     double *rk = pc_s;                               // row k of R (n)
@@ -1317,6 +1316,20 @@ __global__ void __launch_bounds__(kPcholThreads, 1)
     const double tail = delta > 0.0 ? sqrt(delta) : 1.0;
     for (int i = k + tid; i < n; i += kPcholThreads) X[(i64)i * ldx + i] = tail;
     for (int i = tid; i < n; i += kPcholThreads) piv[i] = pm[i];
+}
+
+__global__ void __launch_bounds__(kPcholThreads, 1)
+    pchol_kernel(double *__restrict__ W, int n, double *__restrict__ X, i64 ldx,
+                 int *__restrict__ piv)
+{
+    pchol_body(W, n, X, ldx, piv);
+}
+
+// Many factorizations in one launch, one CTA each (the batched TS-SVD).
+__global__ void __launch_bounds__(kPcholThreads, 1) pchol_batch_kernel(const PcholTask *tasks)
+{
+    const PcholTask t = tasks[blockIdx.x];
+    pchol_body(t.W, t.n, t.X, t.n, t.piv);
 }
 
 // Pivoted Cholesky over the whole grid, for n above one CTA's reach:
@@ -1509,6 +1522,21 @@ cudaError_t launch_pchol(double *W, int n, double *X, i64 ldx, int *piv, cudaStr
     if (n > 256) return cudaErrorInvalidValue;  // rows held as 8 values per lane
     ProfScope ps_("pchol", s);
     pchol_kernel<<<1, kPcholThreads, smem, s>>>(W, n, X, ldx, piv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pchol_batch(const PcholTask *tasks, int ntasks, int nmax, cudaStream_t s)
+{
+    if (ntasks < 1) return cudaSuccess;
+    if (nmax > 256) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * ((size_t)nmax + 32) + sizeof(int) * ((size_t)nmax + 32);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pchol_batch_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    ProfScope ps_("pchol", s);
+    pchol_batch_kernel<<<ntasks, kPcholThreads, smem, s>>>(tasks);
     return cudaGetLastError();
 }
 
